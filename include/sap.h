@@ -1,0 +1,158 @@
+/*
+ * sap.h -- C ABI of the GB300 library for the discontinuous-Galerkin spherical-harmonic
+ * Vlasov--Fokker--Planck operator of arXiv:2501.05110 ("Sapphire++").
+ *
+ * The library discretises the advection--reaction system
+ *     d_t f + (beta . grad~) f + R f = s                              (Sec. 2.2, Eq. well-posed-...)
+ * for the n = (lmax+1)^2 expansion coefficients f_lms (Sec. 2.1) with a dG method on a
+ * tensor-product mesh of the reduced phase space xi = (x[, y[, z]][, p or ln p]) (Sec. 3):
+ * broken Q^k space, upwind numerical flux J = W (L+ W^T f1 + L- W^T f2) (Eq. definition-upwind-flux),
+ * zero-inflow / continuous / periodic boundaries (Eq. definition-boundary-flux, Eq. continuous-bc),
+ * and advances M zeta' + D zeta = h (Eq. matrix-formulation-system-odes) with explicit RK4 or the
+ * Crank--Nicolson theta-method solved by restarted GMRES (Eq. theta-method, Eq. system-matrix-rhs).
+ *
+ * Conventions used by every entry point:
+ *  - Status: every call returns sap_status and never aborts; sap_last_error() gives text for the
+ *    last failure on that handle.  Asynchronous CUDA errors surface as SAP_ECUDA at the next call
+ *    that synchronises.
+ *  - Ownership: the caller owns every buffer it passes (state vectors, field arrays); the library
+ *    owns its tables and workspaces, released by sap_destroy().  Host arrays passed to setup calls
+ *    are copied before the call returns.
+ *  - State layout (device, canonical): index = ((cell * n + j) * (k+1)^D + node), cells
+ *    lexicographic with axis 0 fastest, j the paper's index map j(l,m,s) = l(l+1) + (-1)^(s+1) m
+ *    (Eq. ordering-expansion-coefficients), nodes the tensor Gauss--Legendre points of the cell
+ *    (axis 0 fastest).  Values are nodal values of f_h at those points.  In this basis the mass
+ *    matrix is diagonal and the initial projection (Eq. zeta-initial-condition) is evaluation of
+ *    f^0 at the nodes.
+ *  - Streams: compute entry points take a cudaStream_t (0 = legacy default stream) and are
+ *    asynchronous with respect to the host unless stated otherwise.
+ *  - Thread safety: one handle must not be used from two host threads at once.
+ */
+#ifndef SAP_H
+#define SAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sap_ctx* sap_handle;
+typedef struct CUstream_st* sap_stream; /* same object as cudaStream_t */
+
+typedef enum {
+  SAP_OK = 0,
+  SAP_EINVAL = 1,        /* invalid argument or descriptor */
+  SAP_ENOMEM = 2,        /* device or host allocation failed */
+  SAP_ECUDA = 3,         /* a CUDA call failed (text in sap_last_error) */
+  SAP_ENOCONV = 4,       /* the iterative solve did not reach the tolerance within maxit */
+  SAP_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+  SAP_EUNSUPPORTED = 6   /* valid request outside what this build implements */
+} sap_status;
+
+/* axis kinds: spatial axes come first in x, y, z order, the momentum axis (if any) last */
+enum { SAP_AXIS_X = 0, SAP_AXIS_Y = 1, SAP_AXIS_Z = 2, SAP_AXIS_P = 3, SAP_AXIS_LNP = 4 };
+/* boundary conditions per axis end (Sec. 2.2; Eq. definition-boundary-flux; Eq. continuous-bc) */
+enum { SAP_BC_PERIODIC = 0, SAP_BC_ZERO_INFLOW = 1, SAP_BC_CONTINUOUS = 2 };
+/* term toggles (Eq. vfp-terms-names): spatial advection, momentum, rotation, collision, source */
+enum { SAP_TERM_ADV = 1, SAP_TERM_MOM = 2, SAP_TERM_ROT = 4, SAP_TERM_COLL = 8, SAP_TERM_SRC = 16 };
+/* arithmetic of the operator apply: FP64 throughout, or FP32 apply with FP64 state/Krylov */
+enum { SAP_PREC_FP64 = 0, SAP_PREC_FP32 = 1 };
+/* apply modes */
+enum { SAP_APPLY_D = 0,        /* y = M^-1 D x                       */
+       SAP_APPLY_RHS = 1,      /* y = M^-1 (h - D x)  (ERK right side) */
+       SAP_APPLY_DT = 2 };     /* y = M^-1 D^T M x  (adjoint of M^-1 D in the M inner product) */
+/* point sets reported by sap_field_points */
+enum { SAP_PTS_SPATIAL = 0,    /* spatial volume points (nsv x dim_x), fields U, gradU, DUDt, B   */
+       SAP_PTS_FACE_X = 1,     /* spatial face points normal to x (nsf x dim_x), field U_x         */
+       SAP_PTS_FACE_Y = 2,     /*   ... normal to y, field U_y                                     */
+       SAP_PTS_FACE_Z = 3,     /*   ... normal to z, field U_z                                     */
+       SAP_PTS_PHASE = 4 };    /* phase-space volume points = nodes (N/n x D), fields nu, s_000    */
+
+typedef struct {
+  int ndim;                 /* D = number of reduced phase-space axes, 1..3 (Sec. 4, footnote)    */
+  int axis_kind[3];         /* SAP_AXIS_*                                                         */
+  int ncells[3];            /* cells per axis, >= 1                                               */
+  const double* edges[3];   /* host, ncells[a]+1 strictly increasing edges (graded meshes allowed) */
+  int bc_lo[3], bc_hi[3];   /* SAP_BC_*; periodic must be set on both ends                         */
+  int lmax;                 /* expansion order, 0..11; n = (lmax+1)^2 (Sec. 2.1)                  */
+  int degree;               /* dG degree k >= 0 (Sec. 3.1), k <= 4                                 */
+  double V;                 /* particle speed, used only without a momentum axis                  */
+  unsigned terms;           /* OR of SAP_TERM_*                                                    */
+} sap_desc;
+
+typedef struct {
+  int steps;                /* CN steps taken                                                      */
+  int64_t iterations;       /* total GMRES iterations over all steps                               */
+  int max_iterations;       /* most iterations in one step                                         */
+  double last_rel_residual; /* true relative residual ||b - A x|| / ||b|| of the last step         */
+} sap_solver_stats;
+
+/* Create a context for one problem (Sec. 2-3).  Builds the coupling matrices A^a, Omega^a, C and
+ * their products at L = lmax+1 (Sec. 2.1), the eigen-pairs of A^x once and their rotations for y, z
+ * (Sec. 3.2, "eigenvectors once"), the Gauss rules and the mesh tables, and allocates device
+ * workspaces on the current CUDA device.  `prec` is SAP_PREC_*.  Fields must be set with
+ * sap_set_fields before any compute call.  Errors: SAP_EINVAL (bad descriptor), SAP_ENOMEM,
+ * SAP_ECUDA.  On failure *out is NULL. */
+sap_status sap_create(const sap_desc* desc, int prec, sap_handle* out);
+
+/* Number of points and their coordinates for a point set (SAP_PTS_*).  If `coords` is NULL only
+ * *count is written; otherwise `coords` (host) receives count x dim coordinates, dim = number of
+ * spatial axes (momentum coordinates are p, not ln p, for SAP_PTS_PHASE's momentum column when the
+ * axis is SAP_AXIS_LNP: the column holds ln p as the mesh coordinate).  Errors: SAP_EINVAL. */
+sap_status sap_field_points(sap_handle h, int which, double* coords, int64_t* count);
+
+/* Set the prescribed fields, sampled at the points of sap_field_points (host arrays, copied):
+ *  U[nsv*3], gradU[nsv*9] with gradU[p*9 + 3a + b] = dU_b/dx^a, DUDt[nsv*3] (material derivative of
+ *  the flow), Bw[nsv*3] = B with a momentum axis (omega = qB/(gamma m), q = m = c = 1, Tab. 1) or
+ *  omega directly without one; Uface[a][nsf_a] = U_a at the spatial face points normal to spatial
+ *  axis a (NULL for absent axes); nu[npv] (scattering frequency) and s000[npv] (isotropic source,
+ *  s = s000 Y_000) at the phase-space nodes.  Any pointer may be NULL when the corresponding terms
+ *  are off.  Builds the per-face upwind data, including the eigen-decomposition of beta^p at every
+ *  momentum-face point (Sec. 3.2, Eq. beta-p).  Synchronous.  Errors: SAP_EINVAL, SAP_ENOMEM,
+ *  SAP_ECUDA. */
+sap_status sap_set_fields(sap_handle h, const double* U, const double* gradU, const double* DUDt,
+                          const double* Bw, const double* const Uface[3], const double* nu,
+                          const double* s000);
+
+/* Number of degrees of freedom N = ncells * n * (k+1)^D (Sec. 3.1). */
+sap_status sap_num_dofs(sap_handle h, int64_t* n);
+
+/* Apply the semi-discrete operator (Eq. definition-mass-and-dg-matrix) to a device vector x,
+ * writing device vector y (x != y, both canonical layout, N elements of the context's precision:
+ * double for SAP_PREC_FP64, float for SAP_PREC_FP32).  mode SAP_APPLY_D: y = M^-1 D x;
+ * SAP_APPLY_RHS: y = M^-1 (h - D x).  Asynchronous on `stream`.  Errors: SAP_EINVAL, SAP_ECUDA. */
+sap_status sap_apply_operator(sap_handle h, const void* x, void* y, int mode, sap_stream stream);
+
+/* Advance the FP64 device state (canonical layout, N doubles, in place) by `nsteps` classical RK4
+ * steps of size dt on zeta' = M^-1 (h - D zeta) (Sec. 3.4).  With SAP_PREC_FP32 the stage
+ * derivatives are computed in FP32 and accumulated into the FP64 state.  Asynchronous.
+ * Errors: SAP_EINVAL, SAP_ECUDA. */
+sap_status sap_step_erk(sap_handle h, double* state, double dt, int nsteps, sap_stream stream);
+
+/* Advance the FP64 device state by `nsteps` Crank--Nicolson steps (theta = 1/2, Eq. theta-method):
+ * (1 + dt/2 M^-1 D) zeta^n = (1 - dt/2 M^-1 D) zeta^(n-1) + dt M^-1 h, each solved by restarted
+ * GMRES(restart) with point-Jacobi preconditioning to ||b - A zeta|| <= tol ||b|| (2-norm,
+ * canonical nodal vector), at most maxit iterations per step.  With SAP_PREC_FP32 the inner GMRES
+ * applies the operator in FP32 and an FP64 residual/refinement loop restores the tolerance.
+ * Synchronous (reads the convergence status each restart).  `stats` may be NULL.
+ * Errors: SAP_EINVAL, SAP_ENOCONV (state holds the last iterate), SAP_ECUDA. */
+sap_status sap_step_cn(sap_handle h, double* state, double dt, int nsteps, double tol, int restart,
+                       int maxit, sap_solver_stats* stats, sap_stream stream);
+
+/* Destroy a context and free its device memory.  NULL is accepted. */
+sap_status sap_destroy(sap_handle h);
+
+/* Text of the last error on `h` (or of the last failed sap_create when h is NULL). */
+const char* sap_last_error(sap_handle h);
+
+/* Host-only: copy the library's n x n coupling matrix `which` for expansion order lmax into `out`
+ * (row-major, n*n doubles).  which: 0 A^a, 1 Omega^a, 2 C, 3 A^a A^b, 4 E^a = eps_abc A^b Om^c,
+ * 5 F^ab = A^a E^b (a, b in 0..2 select components; products formed at L = lmax+1, Sec. 2.1).
+ * Needs no GPU.  Errors: SAP_EINVAL. */
+sap_status sap_coupling_matrix(int lmax, int which, int a, int b, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAP_H */

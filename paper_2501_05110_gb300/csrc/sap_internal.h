@@ -1,0 +1,139 @@
+// Internal data structures shared by the host set-up (setup.cpp) and the CUDA kernels (operator.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sap.h"
+#include "sh_tables.h"
+
+namespace sap {
+
+constexpr int MAXD = 3;
+constexpr int MAXQ = 5;          // dG degree <= 4
+constexpr int MAXTERMS = 28;     // reaction terms
+constexpr int MAXADV = 12;       // advection terms per axis
+constexpr int MAT_I = -1;        // identity "matrix"
+
+// spatial field components stored per spatial volume point
+enum : int { SF_ONE = -1, SF_U = 0, SF_G = 3, SF_DU = 12, SF_B = 15, SF_NCOMP = 18 };
+// momentum factors, functions of the momentum p at a node or face
+enum : int { MF_ONE = 0, MF_P, MF_GM, MF_V, MF_INV_V, MF_INV_GM, MF_INV_P, MF_INV_GMP, MF_GM_OVER_P };
+
+struct Term {
+  int mat;      // matrix id in the bank, or MAT_I
+  int sf;       // spatial factor component or SF_ONE
+  int mf;       // momentum factor
+  int nu;       // 1: multiply by nu at the phase-space node
+  double scale;
+};
+
+enum : int { ABS_CONST = 0, ABS_EIGEN = 1, ABS_POINT = 2 };
+
+struct AxisInfo {
+  int kind, bc_lo, bc_hi;
+  int active;                 // 0: no advection along this axis
+  int nadv;
+  Term adv[MAXADV];           // beta^alpha = sum_t coef_t K_t
+  int route;                  // how |beta| is applied on faces
+  int absmat;                 // ABS_CONST: |beta| matrix id; ABS_POINT: pattern matrix id
+  int Wmat, WTmat;            // ABS_EIGEN: eigenvectors W and W^T (bank ids)
+  // ABS_EIGEN: beta = c0 I + c1 A with c0 = adv[0] coefficient, c1 = adv[1] coefficient at the face
+};
+
+// Device-side CSR bank of n x n matrices (rowptr per matrix: n+1 entries at rp_off[m]).
+template <typename T>
+struct Bank {
+  const int* rp;   // concatenated row pointers (absolute offsets into col/val)
+  const int* col;
+  const T* val;
+  int rp_off[64];
+};
+
+template <typename T>
+struct OpParams {
+  int D, dx, q, nloc, nfp, n, ncell, has_mom;
+  int qdx;                         // q^dx: spatial nodes per cell
+  int nc[MAXD];
+  AxisInfo ax[MAXD];
+  int nreact;
+  Term react[MAXTERMS];
+  Bank<T> bank;
+  T S[MAXQ][MAXQ];                 // S[i][q] = w_q l_i'(x_q) / w_i  on [0,1]
+  T B0[MAXQ], B1[MAXQ];            // l_i(0), l_i(1)
+  T L0[MAXQ], L1[MAXQ];            // l_i(0)/w_i, l_i(1)/w_i
+  // mesh
+  const int* cell_nb;              // [ncell][2D]: neighbour across face 2a+side, -1 at a boundary
+  const T* cell_invh;              // [ncell][D]
+  const int* cell_scell;           // [ncell] spatial cell
+  const int* cell_pcell;           // [ncell] momentum cell (0 without momentum)
+  const int* scell_face;           // [nscell][2*dx] first spatial-face point of each face of the cell
+  // fields
+  const T* sfield;                 // [SF_NCOMP][nsv] (components not uniform)
+  int nsv;
+  T sf_uni[SF_NCOMP];
+  int sf_is_uni[SF_NCOMP];
+  const T* uface[MAXD];            // [nsf_a]
+  T uface_uni[MAXD];
+  int uface_is_uni[MAXD];
+  const T* nu;                     // [npv] or null (uniform nu_uni)
+  T nu_uni;
+  const T* s000;                   // [npv] or null (uniform s_uni)
+  T s_uni;
+  const T* pnode;                  // [npc*q] momentum p at nodes
+  const T* pface;                  // [npc+1] momentum p at faces
+  T Vmono;
+  // momentum-face |beta| per point
+  const int* pslot;                // [nsv] slot or -1
+  const T* pabs;                   // [slot][npc+1][nnz(pattern)]
+  int npface;
+  const T* lam;                    // eigenvalues of A^a (same for a = x, y, z), n entries
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace sap
+
+// The context (opaque to callers).
+struct sap_ctx {
+  sap_desc desc;
+  int prec = SAP_PREC_FP64;
+  int D = 0, dx = 0, q = 0, nloc = 0, nfp = 0, n = 0, ncell = 0, has_mom = 0, qdx = 0, nscell = 0;
+  int nc[3] = {1, 1, 1};
+  int64_t N = 0;
+  int nsv = 0, npv = 0, nsf[3] = {0, 0, 0}, npc = 1;
+  std::vector<double> edges[3];
+  sap::SHTables T;
+  std::vector<double> xg, wg;                  // Gauss rule on [0,1]
+  std::vector<double> pnode, pface;            // momentum values
+  std::vector<int> scell_face_h;               // [nscell][2dx]
+  sap::OpParams<double> p64{};
+  sap::OpParams<float> p32{};
+  std::vector<sap::DevBuf> owned;              // device allocations
+  std::vector<std::vector<int>> Ablocks;       // (m,s) blocks of A^x
+  bool fields_set = false;
+  std::string err;
+  // workspaces (FP64 state-sized vectors; FP32 where noted)
+  double* ws64 = nullptr;
+  int ws64_count = 0;
+  float* ws32 = nullptr;
+  int ws32_count = 0;
+  double* small = nullptr;                     // small device scratch for reductions/scalars
+  double* small_host = nullptr;                // pinned mirror
+  int krylov_restart = 0;
+};
+
+namespace sap {
+// kernels / launchers implemented in operator.cu
+cudaError_t launch_apply64(const OpParams<double>& p, const double* x, double* y, int mode, cudaStream_t s);
+cudaError_t launch_apply32(const OpParams<float>& p, const float* x, float* y, int mode, cudaStream_t s);
+sap_status erk_steps(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s);
+sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
+                    sap_solver_stats* st, cudaStream_t s);
+int apply_cells_per_block(int n, int nloc);
+}  // namespace sap

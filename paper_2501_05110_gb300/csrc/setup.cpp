@@ -1,0 +1,865 @@
+// Host set-up and the C ABI entry points of sap.h.
+//
+// Builds everything the kernels read: the Gauss rule and 1-D Lagrange tables, mesh connectivity,
+// the coupling matrices (sh_tables.cpp), the advection / reaction term lists of Sec. 2.2
+// (Eq. definitions-advection-reaction-eq) with their coefficient factors, and the face upwind data:
+// the eigen-pairs of A^x computed once and rotated for y and z (Sec. 3.2), and the eigen-pairs of
+// beta^p at every momentum-face point (Sec. 3.2, Eq. beta-p).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "sap_internal.h"
+
+using namespace sap;
+
+static std::string g_create_error;
+
+// ------------------------------------------------------------------------------------------------
+// 1-D Gauss--Legendre rule on [0,1] (Newton on the three-term recurrence) and Lagrange tables
+// ------------------------------------------------------------------------------------------------
+static void gauss_legendre01(int q, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(q);
+  w.resize(q);
+  for (int i = 0; i < q; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (q + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = 0.0;
+      for (int j = 1; j <= q; ++j) {
+        double p2 = p1;
+        p1 = p0;
+        p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+      }
+      dp = q * (z * p0 - p1) / (z * z - 1.0);
+      double dz = p0 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    // recompute derivative at the converged root
+    double p0 = 1.0, p1 = 0.0;
+    for (int j = 1; j <= q; ++j) {
+      double p2 = p1;
+      p1 = p0;
+      p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+    }
+    dp = q * (z * p0 - p1) / (z * z - 1.0);
+    x[q - 1 - i] = 0.5 * (z + 1.0);
+    w[q - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);  // 2/((1-z^2)p'^2) halved for [0,1]
+  }
+}
+
+static double lagr(const std::vector<double>& nd, int i, double t) {
+  double v = 1.0;
+  for (size_t j = 0; j < nd.size(); ++j)
+    if ((int)j != i) v *= (t - nd[j]) / (nd[i] - nd[j]);
+  return v;
+}
+
+static double dlagr(const std::vector<double>& nd, int i, double t) {
+  double s = 0.0;
+  for (size_t k = 0; k < nd.size(); ++k) {
+    if ((int)k == i) continue;
+    double v = 1.0 / (nd[i] - nd[k]);
+    for (size_t j = 0; j < nd.size(); ++j)
+      if ((int)j != i && j != k) v *= (t - nd[j]) / (nd[i] - nd[j]);
+    s += v;
+  }
+  return s;
+}
+
+// ------------------------------------------------------------------------------------------------
+// device memory helpers
+// ------------------------------------------------------------------------------------------------
+template <typename V>
+static void* upload(sap_ctx* c, const std::vector<V>& h, std::vector<DevBuf>& owner) {
+  if (h.empty()) return nullptr;
+  void* p = nullptr;
+  size_t bytes = h.size() * sizeof(V);
+  if (cudaMalloc(&p, bytes) != cudaSuccess) throw std::string("cudaMalloc failed");
+  if (cudaMemcpy(p, h.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(p);
+    throw std::string("cudaMemcpy failed");
+  }
+  owner.push_back({p, bytes});
+  return p;
+}
+
+template <typename V>
+static std::vector<float> to_f32(const std::vector<V>& v) {
+  return std::vector<float>(v.begin(), v.end());
+}
+
+struct FieldStore {  // per-context field-dependent device buffers
+  std::vector<DevBuf> bufs;
+};
+static std::map<sap_ctx*, FieldStore> g_fields;
+
+static void free_bufs(std::vector<DevBuf>& v) {
+  for (auto& b : v) cudaFree(b.p);
+  v.clear();
+}
+
+// ------------------------------------------------------------------------------------------------
+// create
+// ------------------------------------------------------------------------------------------------
+static bool is_spatial(int k) { return k >= SAP_AXIS_X && k <= SAP_AXIS_Z; }
+
+static std::string validate(const sap_desc* d) {
+  if (!d) return "null descriptor";
+  if (d->ndim < 1 || d->ndim > 3) return "ndim must be 1..3";
+  int dx = 0;
+  for (int a = 0; a < d->ndim; ++a) {
+    int k = d->axis_kind[a];
+    if (is_spatial(k)) {
+      if (k != a) return "spatial axes must be x, y, z in this order starting at axis 0";
+      ++dx;
+    } else if (k == SAP_AXIS_P || k == SAP_AXIS_LNP) {
+      if (a != d->ndim - 1) return "the momentum axis must be the last axis";
+    } else {
+      return "unknown axis kind";
+    }
+    if (d->ncells[a] < 1) return "ncells must be >= 1";
+    if (!d->edges[a]) return "missing edges";
+    for (int i = 0; i < d->ncells[a]; ++i)
+      if (!(d->edges[a][i + 1] > d->edges[a][i])) return "edges must increase strictly";
+    if (k == SAP_AXIS_P && !(d->edges[a][0] > 0)) return "linear momentum axis must have p > 0";
+    bool plo = d->bc_lo[a] == SAP_BC_PERIODIC, phi = d->bc_hi[a] == SAP_BC_PERIODIC;
+    if (plo != phi) return "periodic must be set on both ends of an axis";
+    for (int bc : {d->bc_lo[a], d->bc_hi[a]})
+      if (bc < 0 || bc > 2) return "unknown boundary condition";
+  }
+  if (dx == 0 && d->ndim > 1) return "a momentum-only problem must be one-dimensional";
+  bool mom = !is_spatial(d->axis_kind[d->ndim - 1]);
+  if ((d->terms & SAP_TERM_MOM) && !mom) return "momentum terms need a momentum axis";
+  if (d->lmax < 0 || d->lmax > 11) return "lmax must be 0..11";
+  if (d->degree < 0 || d->degree > MAXQ - 1) return "degree must be 0..4";
+  if (!mom && !(d->V > 0)) return "particle speed V must be > 0 without a momentum axis";
+  return "";
+}
+
+template <typename T>
+static void fill_1d_tables(sap_ctx* c, OpParams<T>& P) {
+  const int q = c->q;
+  for (int i = 0; i < q; ++i) {
+    P.B0[i] = T(lagr(c->xg, i, 0.0));
+    P.B1[i] = T(lagr(c->xg, i, 1.0));
+    P.L0[i] = T(lagr(c->xg, i, 0.0) / c->wg[i]);
+    P.L1[i] = T(lagr(c->xg, i, 1.0) / c->wg[i]);
+    for (int k = 0; k < q; ++k) P.S[i][k] = T(c->wg[k] * dlagr(c->xg, i, c->xg[k]) / c->wg[i]);
+  }
+}
+
+extern "C" sap_status sap_create(const sap_desc* desc, int prec, sap_handle* out) {
+  if (!out) {
+    g_create_error = "null output handle";
+    return SAP_EINVAL;
+  }
+  *out = nullptr;
+  std::string v = validate(desc);
+  if (!v.empty()) {
+    g_create_error = v;
+    return SAP_EINVAL;
+  }
+  if (prec != SAP_PREC_FP64 && prec != SAP_PREC_FP32) {
+    g_create_error = "unknown precision";
+    return SAP_EINVAL;
+  }
+  sap_ctx* c = new sap_ctx();
+  try {
+    c->desc = *desc;
+    c->prec = prec;
+    c->D = desc->ndim;
+    c->q = desc->degree + 1;
+    c->n = (desc->lmax + 1) * (desc->lmax + 1);
+    c->nloc = 1;
+    for (int a = 0; a < c->D; ++a) c->nloc *= c->q;
+    c->nfp = c->nloc / c->q;
+    c->has_mom = !is_spatial(desc->axis_kind[c->D - 1]);
+    c->dx = c->D - c->has_mom;
+    c->qdx = 1;
+    for (int a = 0; a < c->dx; ++a) c->qdx *= c->q;
+    c->ncell = 1;
+    for (int a = 0; a < c->D; ++a) {
+      c->nc[a] = desc->ncells[a];
+      c->ncell *= desc->ncells[a];
+      c->edges[a].assign(desc->edges[a], desc->edges[a] + desc->ncells[a] + 1);
+      c->desc.edges[a] = c->edges[a].data();
+    }
+    c->N = (int64_t)c->ncell * c->n * c->nloc;
+    c->nscell = 1;
+    for (int a = 0; a < c->dx; ++a) c->nscell *= c->nc[a];
+    c->npc = c->has_mom ? c->nc[c->D - 1] : 1;
+    c->nsv = c->nscell * c->qdx;
+    c->npv = c->ncell * c->nloc;
+    gauss_legendre01(c->q, c->xg, c->wg);
+    c->T = build_sh_tables(desc->lmax);
+    // momentum node and face values
+    if (c->has_mom) {
+      const int a = c->D - 1;
+      const bool lg = desc->axis_kind[a] == SAP_AXIS_LNP;
+      for (int pc = 0; pc < c->npc; ++pc)
+        for (int j = 0; j < c->q; ++j) {
+          double crd = c->edges[a][pc] + (c->edges[a][pc + 1] - c->edges[a][pc]) * c->xg[j];
+          c->pnode.push_back(lg ? std::exp(crd) : crd);
+        }
+      for (int f = 0; f <= c->npc; ++f) c->pface.push_back(lg ? std::exp(c->edges[a][f]) : c->edges[a][f]);
+    } else {
+      c->pnode.assign(c->q, 1.0);
+      c->pface.assign(2, 1.0);
+    }
+    // mesh connectivity
+    std::vector<int> nb((size_t)c->ncell * 2 * c->D), scell(c->ncell), pcell(c->ncell);
+    std::vector<double> invh((size_t)c->ncell * c->D);
+    for (int cell = 0; cell < c->ncell; ++cell) {
+      int idx[3] = {0, 0, 0}, rest = cell, stride[3];
+      int st = 1;
+      for (int a = 0; a < c->D; ++a) {
+        idx[a] = rest % c->nc[a];
+        rest /= c->nc[a];
+        stride[a] = st;
+        st *= c->nc[a];
+      }
+      for (int a = 0; a < c->D; ++a) {
+        invh[(size_t)cell * c->D + a] = 1.0 / (c->edges[a][idx[a] + 1] - c->edges[a][idx[a]]);
+        bool per = desc->bc_lo[a] == SAP_BC_PERIODIC;
+        int lo = idx[a] > 0 ? cell - stride[a] : (per ? cell + (c->nc[a] - 1) * stride[a] : -1);
+        int hi = idx[a] < c->nc[a] - 1 ? cell + stride[a] : (per ? cell - (c->nc[a] - 1) * stride[a] : -1);
+        nb[(size_t)cell * 2 * c->D + 2 * a] = lo;
+        nb[(size_t)cell * 2 * c->D + 2 * a + 1] = hi;
+      }
+      int sc = 0, sst = 1;
+      for (int a = 0; a < c->dx; ++a) {
+        sc += idx[a] * sst;
+        sst *= c->nc[a];
+      }
+      scell[cell] = sc;
+      pcell[cell] = c->has_mom ? idx[c->D - 1] : 0;
+    }
+    // spatial face point bases: faces along spatial axis a, ordered (face position, tangential
+    // spatial cell with lower axes fastest, tangential spatial node)
+    const int qt = c->qdx / c->q;  // tangential spatial nodes per face
+    c->scell_face_h.assign((size_t)c->nscell * 2 * std::max(c->dx, 1), 0);
+    for (int a = 0; a < c->dx; ++a) {
+      int ntang = c->nscell / c->nc[a];
+      c->nsf[a] = (c->nc[a] + 1) * ntang * qt;
+      for (int sc = 0; sc < c->nscell; ++sc) {
+        int idx[3] = {0, 0, 0}, rest = sc;
+        for (int b = 0; b < c->dx; ++b) {
+          idx[b] = rest % c->nc[b];
+          rest /= c->nc[b];
+        }
+        int tc = 0, tst = 1;
+        for (int b = 0; b < c->dx; ++b) {
+          if (b == a) continue;
+          tc += idx[b] * tst;
+          tst *= c->nc[b];
+        }
+        bool per = desc->bc_lo[a] == SAP_BC_PERIODIC;
+        int flo = (idx[a] == 0 && per) ? c->nc[a] : idx[a];
+        int fhi = idx[a] + 1;
+        c->scell_face_h[(size_t)sc * 2 * c->dx + 2 * a] = (flo * ntang + tc) * qt;
+        c->scell_face_h[(size_t)sc * 2 * c->dx + 2 * a + 1] = (fhi * ntang + tc) * qt;
+      }
+    }
+    // A^x blocks for the eigen route
+    c->Ablocks = connected_blocks(c->T.A[0]);
+    // device mesh tables (both precisions share the integer tables)
+    auto& own = c->owned;
+    int* d_nb = (int*)upload(c, nb, own);
+    int* d_sc = (int*)upload(c, scell, own);
+    int* d_pc = (int*)upload(c, pcell, own);
+    int* d_sf = (int*)upload(c, c->scell_face_h, own);
+    double* d_ih64 = (double*)upload(c, invh, own);
+    float* d_ih32 = (float*)upload(c, to_f32(invh), own);
+    double* d_pn64 = (double*)upload(c, c->pnode, own);
+    float* d_pn32 = (float*)upload(c, to_f32(c->pnode), own);
+    double* d_pf64 = (double*)upload(c, c->pface, own);
+    float* d_pf32 = (float*)upload(c, to_f32(c->pface), own);
+    auto base = [&](auto& P, auto* ih, auto* pn, auto* pf) {
+      P.D = c->D; P.dx = c->dx; P.q = c->q; P.nloc = c->nloc; P.nfp = c->nfp; P.n = c->n;
+      P.ncell = c->ncell; P.has_mom = c->has_mom; P.qdx = c->qdx;
+      for (int a = 0; a < 3; ++a) P.nc[a] = c->nc[a];
+      P.cell_nb = d_nb; P.cell_scell = d_sc; P.cell_pcell = d_pc; P.scell_face = d_sf;
+      P.cell_invh = ih; P.pnode = pn; P.pface = pf; P.npface = c->npc + 1;
+      P.nsv = c->nsv;
+      P.Vmono = c->has_mom ? 1 : desc->V;
+      fill_1d_tables(c, P);
+    };
+    base(c->p64, d_ih64, d_pn64, d_pf64);
+    base(c->p32, d_ih32, d_pn32, d_pf32);
+    // small reduction scratch
+    if (cudaMalloc(&c->small, sizeof(double) * (152 * 8 * 32 + 8 * 32)) != cudaSuccess) throw std::string("cudaMalloc failed");
+    if (cudaMallocHost(&c->small_host, sizeof(double) * 8 * 32) != cudaSuccess) throw std::string("cudaMallocHost failed");
+  } catch (const std::string& e) {
+    g_create_error = "sap_create: " + e;
+    sap_destroy(c);
+    return SAP_ENOMEM;
+  }
+  *out = c;
+  return SAP_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// points
+// ------------------------------------------------------------------------------------------------
+extern "C" sap_status sap_field_points(sap_handle c, int which, double* coords, int64_t* count) {
+  if (!c || !count) return SAP_EINVAL;
+  const int q = c->q;
+  std::vector<double> out;
+  if (which == SAP_PTS_SPATIAL) {
+    *count = c->nsv;
+    if (!coords) return SAP_OK;
+    for (int sc = 0; sc < c->nscell; ++sc) {
+      int idx[3] = {0, 0, 0}, rest = sc;
+      for (int a = 0; a < c->dx; ++a) {
+        idx[a] = rest % c->nc[a];
+        rest /= c->nc[a];
+      }
+      for (int nd = 0; nd < c->qdx; ++nd) {
+        int r2 = nd;
+        for (int a = 0; a < c->dx; ++a) {
+          int j = r2 % q;
+          r2 /= q;
+          double lo = c->edges[a][idx[a]], h = c->edges[a][idx[a] + 1] - lo;
+          coords[((size_t)sc * c->qdx + nd) * c->dx + a] = lo + h * c->xg[j];
+        }
+      }
+    }
+    return SAP_OK;
+  }
+  if (which >= SAP_PTS_FACE_X && which <= SAP_PTS_FACE_Z) {
+    int a = which - SAP_PTS_FACE_X;
+    if (a >= c->dx) {
+      *count = 0;
+      return SAP_OK;
+    }
+    *count = c->nsf[a];
+    if (!coords) return SAP_OK;
+    const int qt = c->qdx / q;
+    const int ntang = c->nscell / c->nc[a];
+    for (int f = 0; f <= c->nc[a]; ++f)
+      for (int tc = 0; tc < ntang; ++tc) {
+        int tidx[3] = {0, 0, 0}, rest = tc;
+        for (int b = 0; b < c->dx; ++b) {
+          if (b == a) continue;
+          tidx[b] = rest % c->nc[b];
+          rest /= c->nc[b];
+        }
+        for (int nd = 0; nd < qt; ++nd) {
+          size_t pidx = ((size_t)f * ntang + tc) * qt + nd;
+          int r2 = nd;
+          for (int b = 0; b < c->dx; ++b) {
+            double v;
+            if (b == a) {
+              v = c->edges[a][f];
+            } else {
+              int j = r2 % q;
+              r2 /= q;
+              double lo = c->edges[b][tidx[b]], h = c->edges[b][tidx[b] + 1] - lo;
+              v = lo + h * c->xg[j];
+            }
+            coords[pidx * c->dx + b] = v;
+          }
+        }
+      }
+    return SAP_OK;
+  }
+  if (which == SAP_PTS_PHASE) {
+    *count = c->npv;
+    if (!coords) return SAP_OK;
+    for (int cell = 0; cell < c->ncell; ++cell) {
+      int idx[3] = {0, 0, 0}, rest = cell;
+      for (int a = 0; a < c->D; ++a) {
+        idx[a] = rest % c->nc[a];
+        rest /= c->nc[a];
+      }
+      for (int nd = 0; nd < c->nloc; ++nd) {
+        int r2 = nd;
+        for (int a = 0; a < c->D; ++a) {
+          int j = r2 % q;
+          r2 /= q;
+          double lo = c->edges[a][idx[a]], h = c->edges[a][idx[a] + 1] - lo;
+          coords[((size_t)cell * c->nloc + nd) * c->D + a] = lo + h * c->xg[j];
+        }
+      }
+    }
+    return SAP_OK;
+  }
+  return SAP_EINVAL;
+}
+
+// ------------------------------------------------------------------------------------------------
+// fields -> term lists, matrix bank, face upwind data
+// ------------------------------------------------------------------------------------------------
+struct HostCSR {
+  std::vector<int> rp, col;
+  std::vector<double> val;
+};
+
+static HostCSR to_csr(const Mat& m, double drop = 0.0) {
+  HostCSR h;
+  h.rp.push_back(0);
+  for (int i = 0; i < m.n; ++i) {
+    for (int j = 0; j < m.n; ++j)
+      if (std::fabs(m(i, j)) > drop) {
+        h.col.push_back(j);
+        h.val.push_back(m(i, j));
+      }
+    h.rp.push_back((int)h.col.size());
+  }
+  return h;
+}
+
+struct BankBuilder {
+  std::vector<HostCSR> mats;
+  std::map<std::string, int> ids;
+  int add(const std::string& key, const Mat& m) {
+    auto it = ids.find(key);
+    if (it != ids.end()) return it->second;
+    mats.push_back(to_csr(m));
+    ids[key] = (int)mats.size() - 1;
+    return ids[key];
+  }
+  int add_csr(const std::string& key, const HostCSR& h) {
+    mats.push_back(h);
+    ids[key] = (int)mats.size() - 1;
+    return ids[key];
+  }
+};
+
+static double mom_factor_h(int mf, double p, bool has_mom, double Vm) {
+  if (mf == MF_ONE) return 1.0;
+  if (!has_mom) return mf == MF_V ? Vm : (mf == MF_INV_V ? 1.0 / Vm : 1.0);
+  double gm = std::sqrt(1.0 + p * p);
+  switch (mf) {
+    case MF_P: return p;
+    case MF_GM: return gm;
+    case MF_V: return p / gm;
+    case MF_INV_V: return gm / p;
+    case MF_INV_GM: return 1.0 / gm;
+    case MF_INV_P: return 1.0 / p;
+    case MF_INV_GMP: return 1.0 / (gm * p);
+    case MF_GM_OVER_P: return gm / p;
+  }
+  return 1.0;
+}
+
+template <typename T>
+static void set_bank(OpParams<T>& P, const BankBuilder& B, sap_ctx* c, std::vector<DevBuf>& own) {
+  std::vector<int> rp, col;
+  std::vector<double> val;
+  if (B.mats.size() > 64) throw std::string("too many matrices");
+  for (size_t m = 0; m < B.mats.size(); ++m) {
+    P.bank.rp_off[m] = (int)rp.size();
+    int off = (int)col.size();
+    for (int v : B.mats[m].rp) rp.push_back(v + off);
+    col.insert(col.end(), B.mats[m].col.begin(), B.mats[m].col.end());
+    val.insert(val.end(), B.mats[m].val.begin(), B.mats[m].val.end());
+  }
+  if (col.empty()) {
+    col.push_back(0);
+    val.push_back(0.0);
+  }
+  if (rp.empty()) rp.push_back(0);
+  P.bank.rp = (const int*)upload(c, rp, own);
+  P.bank.col = (const int*)upload(c, col, own);
+  if (sizeof(T) == 8) P.bank.val = (const T*)upload(c, val, own);
+  else P.bank.val = (const T*)upload(c, to_f32(val), own);
+}
+
+extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double* gradU, const double* DUDt,
+                                     const double* Bw, const double* const Uface[3], const double* nu,
+                                     const double* s000) {
+  if (!c) return SAP_EINVAL;
+  try {
+    FieldStore& fs = g_fields[c];
+    free_bufs(fs.bufs);
+    const sap_desc& d = c->desc;
+    const int n = c->n, nsv = c->nsv;
+    const unsigned terms = d.terms;
+    // spatial field components [SF_NCOMP][nsv]
+    std::vector<double> sf((size_t)SF_NCOMP * nsv, 0.0);
+    for (int p = 0; p < nsv; ++p) {
+      for (int a = 0; a < 3; ++a) {
+        if (U) sf[(size_t)(SF_U + a) * nsv + p] = U[(size_t)p * 3 + a];
+        if (DUDt) sf[(size_t)(SF_DU + a) * nsv + p] = DUDt[(size_t)p * 3 + a];
+        if (Bw) sf[(size_t)(SF_B + a) * nsv + p] = Bw[(size_t)p * 3 + a];
+        for (int b = 0; b < 3; ++b)
+          if (gradU) sf[(size_t)(SF_G + 3 * a + b) * nsv + p] = gradU[(size_t)p * 9 + 3 * a + b];
+      }
+    }
+    bool nonzero[SF_NCOMP], uni[SF_NCOMP];
+    double uval[SF_NCOMP];
+    for (int k = 0; k < SF_NCOMP; ++k) {
+      nonzero[k] = false;
+      uni[k] = true;
+      uval[k] = nsv ? sf[(size_t)k * nsv] : 0.0;
+      for (int p = 0; p < nsv; ++p) {
+        double v = sf[(size_t)k * nsv + p];
+        if (v != 0.0) nonzero[k] = true;
+        if (v != uval[k]) uni[k] = false;
+      }
+    }
+    const bool has_mom = c->has_mom;
+    const bool lnp = has_mom && d.axis_kind[c->D - 1] == SAP_AXIS_LNP;
+    BankBuilder B;
+    const SHTables& Tb = c->T;
+    auto A_id = [&](int a) { return B.add("A" + std::to_string(a), Tb.A[a]); };
+    auto AA_id = [&](int a, int b) { return B.add("AA" + std::to_string(a) + std::to_string(b), Tb.AA[a][b]); };
+    std::vector<Term> react;
+    auto add_term = [&](std::vector<Term>& v, int mat, int sfc, int mf, int nuf, double sc) {
+      v.push_back(Term{mat, sfc, mf, nuf, sc});
+    };
+    // reaction matrix R - div(beta)  (Eq. definitions-advection-reaction-eq, Eq. linear-system-...)
+    if (terms & SAP_TERM_MOM) {
+      for (int a = 0; a < 3; ++a)
+        if (nonzero[SF_DU + a]) add_term(react, B.add("E" + std::to_string(a), Tb.E[a]), SF_DU + a, MF_INV_V, 0, 1.0);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+          if (nonzero[SF_G + 3 * a + b])
+            add_term(react, B.add("F" + std::to_string(a) + std::to_string(b), Tb.F[a][b]), SF_G + 3 * a + b, MF_ONE, 0, 1.0);
+    }
+    if (terms & SAP_TERM_ROT)
+      for (int a = 0; a < 3; ++a)
+        if (nonzero[SF_B + a])
+          add_term(react, B.add("Om" + std::to_string(a), Tb.Om[a]), SF_B + a, has_mom ? MF_INV_GM : MF_ONE, 0, -1.0);
+    if (terms & SAP_TERM_COLL) add_term(react, B.add("C", Tb.C), SF_ONE, MF_ONE, 1, 1.0);
+    if (terms & SAP_TERM_ADV)
+      for (int a = 0; a < c->dx; ++a)
+        if (nonzero[SF_G + 3 * a + a]) add_term(react, MAT_I, SF_G + 3 * a + a, MF_ONE, 0, -1.0);
+    if ((terms & SAP_TERM_MOM) && has_mom) {
+      if (!lnp) {  // -d/dp beta^p = +V DU_a A^a + dU_b/dx^a A^a A^b
+        for (int a = 0; a < 3; ++a)
+          if (nonzero[SF_DU + a]) add_term(react, A_id(a), SF_DU + a, MF_V, 0, 1.0);
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            if (nonzero[SF_G + 3 * a + b]) add_term(react, AA_id(a, b), SF_G + 3 * a + b, MF_ONE, 0, 1.0);
+      } else {  // -p d/dp (beta^p/p) = -DU_a A^a / (gamma m p)
+        for (int a = 0; a < 3; ++a)
+          if (nonzero[SF_DU + a]) add_term(react, A_id(a), SF_DU + a, MF_INV_GMP, 0, -1.0);
+      }
+    }
+    if ((int)react.size() > MAXTERMS) throw std::string("too many reaction terms");
+    // advection terms per axis
+    AxisInfo ax[MAXD];
+    std::memset(ax, 0, sizeof(ax));
+    for (int a = 0; a < c->D; ++a) {
+      AxisInfo& A = ax[a];
+      A.kind = d.axis_kind[a];
+      A.bc_lo = d.bc_lo[a];
+      A.bc_hi = d.bc_hi[a];
+      std::vector<Term> adv;
+      if (is_spatial(A.kind)) {
+        if (terms & SAP_TERM_ADV) {
+          adv.push_back(Term{MAT_I, SF_U + a, MF_ONE, 0, 1.0});
+          adv.push_back(Term{A_id(a), SF_ONE, MF_V, 0, 1.0});
+        }
+      } else if (terms & SAP_TERM_MOM) {
+        for (int b = 0; b < 3; ++b)
+          if (nonzero[SF_DU + b]) adv.push_back(Term{A_id(b), SF_DU + b, lnp ? MF_GM_OVER_P : MF_GM, 0, -1.0});
+        for (int b = 0; b < 3; ++b)
+          for (int e = 0; e < 3; ++e)
+            if (nonzero[SF_G + 3 * b + e]) adv.push_back(Term{AA_id(b, e), SF_G + 3 * b + e, lnp ? MF_ONE : MF_P, 0, -1.0});
+      }
+      if ((int)adv.size() > MAXADV) throw std::string("too many advection terms");
+      A.nadv = (int)adv.size();
+      for (int t = 0; t < A.nadv; ++t) A.adv[t] = adv[t];
+      A.active = A.nadv > 0;
+    }
+    // eigen-pairs of A^x once, rotated for y and z (Sec. 3.2)
+    Mat Wx;
+    std::vector<double> lam;
+    sym_eig_blocks(Tb.A[0], c->Ablocks, Wx, lam);
+    Mat Wa[3];
+    Wa[0] = Wx;
+    Wa[1] = matmul(transpose(Tb.Uz), Wx);
+    Wa[2] = matmul(transpose(Tb.Ux), Wa[1]);
+    for (int a = 0; a < 3; ++a)
+      for (auto& v : Wa[a].a)
+        if (std::fabs(v) < 1e-14) v = 0.0;
+    // face |beta| data
+    std::vector<double> uface_vals[3];
+    bool uface_uni[3] = {true, true, true};
+    double uface_u[3] = {0, 0, 0};
+    for (int a = 0; a < c->dx; ++a) {
+      if (Uface && Uface[a]) uface_vals[a].assign(Uface[a], Uface[a] + c->nsf[a]);
+      else uface_vals[a].assign(c->nsf[a], 0.0);
+      uface_u[a] = uface_vals[a].empty() ? 0.0 : uface_vals[a][0];
+      for (double v : uface_vals[a])
+        if (v != uface_u[a]) uface_uni[a] = false;
+    }
+    std::vector<int> pslot(nsv, -1);
+    std::vector<double> pabs;
+    int npface = c->npc + 1;
+    for (int a = 0; a < c->D; ++a) {
+      AxisInfo& A = ax[a];
+      if (!A.active) continue;
+      if (is_spatial(A.kind)) {
+        if (uface_uni[a] && !has_mom) {  // constant beta: |beta| = W |U + lam V| W^T as one matrix
+          A.route = ABS_CONST;
+          Mat Ab(n);
+          for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+              double s = 0.0;
+              for (int k = 0; k < n; ++k) s += Wa[a](i, k) * std::fabs(uface_u[a] + lam[k] * d.V) * Wa[a](j, k);
+              Ab(i, j) = std::fabs(s) < 1e-15 ? 0.0 : s;
+            }
+          A.absmat = B.add("abs" + std::to_string(a), Ab);
+        } else {
+          A.route = ABS_EIGEN;
+          A.Wmat = B.add("W" + std::to_string(a), Wa[a]);
+          A.WTmat = B.add("WT" + std::to_string(a), transpose(Wa[a]));
+        }
+      } else {
+        // momentum faces: eigen-decomposition of beta^p at every (spatial node, p face) point
+        A.route = ABS_POINT;
+        Mat pat(n);
+        for (int t = 0; t < A.nadv; ++t) {
+          const HostCSR& h = B.mats[A.adv[t].mat];
+          for (int i = 0; i < n; ++i)
+            for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) pat(i, h.col[k]) = 1.0;
+        }
+        auto blocks = connected_blocks(pat);
+        Mat full(n);  // block pattern: dense within each block
+        for (auto& b : blocks)
+          for (int i : b)
+            for (int j : b) full(i, j) = 1.0;
+        HostCSR pc = to_csr(full);
+        const int nnzp = (int)pc.col.size();
+        A.absmat = B.add_csr("pabs_pattern", pc);
+        // first pass: |beta^p| max per spatial point to pick active points
+        std::vector<double> vals;
+        std::vector<double> beta(n * n);
+        Mat bm(n), Wb;
+        std::vector<double> lb;
+        double gmax = 0.0;
+        std::vector<double> pmax(nsv, 0.0);
+        auto build_beta = [&](int sp, double p) {
+          std::fill(bm.a.begin(), bm.a.end(), 0.0);
+          for (int t = 0; t < A.nadv; ++t) {
+            const Term& tm = A.adv[t];
+            double cf = tm.scale * (tm.sf == SF_ONE ? 1.0 : sf[(size_t)tm.sf * nsv + sp]) * mom_factor_h(tm.mf, p, has_mom, d.V);
+            const HostCSR& h = B.mats[tm.mat];
+            for (int i = 0; i < n; ++i)
+              for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) bm(i, h.col[k]) += cf * h.val[k];
+          }
+        };
+        for (int sp = 0; sp < nsv; ++sp)
+          for (int f = 0; f < npface; ++f) {
+            build_beta(sp, c->pface[f]);
+            double mx = 0.0;
+            for (double v : bm.a) mx = std::max(mx, std::fabs(v));
+            pmax[sp] = std::max(pmax[sp], mx);
+            gmax = std::max(gmax, mx);
+          }
+        // points where |beta^p| stays below 1e-15 of its largest value carry no upwinding term
+        // beyond FP64 rounding of the largest momentum flux; they are skipped
+        int nslot = 0;
+        for (int sp = 0; sp < nsv; ++sp)
+          if (gmax > 0.0 && pmax[sp] > 1e-15 * gmax) pslot[sp] = nslot++;
+        pabs.assign((size_t)nslot * npface * nnzp, 0.0);
+        for (int sp = 0; sp < nsv; ++sp) {
+          if (pslot[sp] < 0) continue;
+          for (int f = 0; f < npface; ++f) {
+            build_beta(sp, c->pface[f]);
+            sym_eig_blocks(bm, blocks, Wb, lb);
+            double* dst = &pabs[((size_t)pslot[sp] * npface + f) * nnzp];
+            for (int i = 0; i < n; ++i)
+              for (int k = pc.rp[i]; k < pc.rp[i + 1]; ++k) {
+                int j = pc.col[k];
+                double s = 0.0;
+                for (int e = 0; e < n; ++e) s += Wb(i, e) * std::fabs(lb[e]) * Wb(j, e);
+                dst[k] = s;
+              }
+          }
+        }
+      }
+    }
+    // upload: bank, fields, term lists
+    std::vector<double> sf_nonuni;  // [SF_NCOMP][nsv], only used for non-uniform components
+    sf_nonuni = sf;
+    std::vector<double> nu_v, s_v;
+    bool nu_uni = true, s_uni = true;
+    double nu_u = nu ? nu[0] : 0.0, s_u = s000 ? s000[0] : 0.0;
+    if (nu)
+      for (int p = 0; p < c->npv; ++p)
+        if (nu[p] != nu_u) { nu_uni = false; break; }
+    if (s000)
+      for (int p = 0; p < c->npv; ++p)
+        if (s000[p] != s_u) { s_uni = false; break; }
+    if (!(terms & SAP_TERM_SRC)) { s_uni = true; s_u = 0.0; }
+    if (!nu_uni) nu_v.assign(nu, nu + c->npv);
+    if (!s_uni) s_v.assign(s000, s000 + c->npv);
+    auto fill = [&](auto& P, auto tag) {
+      using T = decltype(tag);
+      set_bank<T>(P, B, c, fs.bufs);
+      P.nreact = (int)react.size();
+      for (int t = 0; t < P.nreact; ++t) P.react[t] = react[t];
+      for (int a = 0; a < MAXD; ++a) P.ax[a] = ax[a];
+      bool any_nonuni = false;
+      for (int k = 0; k < SF_NCOMP; ++k) {
+        P.sf_is_uni[k] = uni[k];
+        P.sf_uni[k] = T(uval[k]);
+        if (!uni[k]) any_nonuni = true;
+      }
+      if (any_nonuni) {
+        if (sizeof(T) == 8) P.sfield = (const T*)upload(c, sf_nonuni, fs.bufs);
+        else P.sfield = (const T*)upload(c, to_f32(sf_nonuni), fs.bufs);
+      } else {
+        P.sfield = nullptr;
+      }
+      for (int a = 0; a < MAXD; ++a) {
+        P.uface_is_uni[a] = a < c->dx ? uface_uni[a] : 1;
+        P.uface_uni[a] = T(a < c->dx ? uface_u[a] : 0.0);
+        P.uface[a] = nullptr;
+        if (a < c->dx && !uface_uni[a]) {
+          if (sizeof(T) == 8) P.uface[a] = (const T*)upload(c, uface_vals[a], fs.bufs);
+          else P.uface[a] = (const T*)upload(c, to_f32(uface_vals[a]), fs.bufs);
+        }
+      }
+      P.nu_uni = T(nu_u);
+      P.nu = nullptr;
+      if (!nu_uni) P.nu = (sizeof(T) == 8) ? (const T*)upload(c, nu_v, fs.bufs) : (const T*)upload(c, to_f32(nu_v), fs.bufs);
+      P.s_uni = T(s_u);
+      P.s000 = nullptr;
+      if (!s_uni) P.s000 = (sizeof(T) == 8) ? (const T*)upload(c, s_v, fs.bufs) : (const T*)upload(c, to_f32(s_v), fs.bufs);
+      P.pslot = (const int*)upload(c, pslot, fs.bufs);
+      if (!pabs.empty())
+        P.pabs = (sizeof(T) == 8) ? (const T*)upload(c, pabs, fs.bufs) : (const T*)upload(c, to_f32(pabs), fs.bufs);
+      else
+        P.pabs = nullptr;
+      P.lam = (sizeof(T) == 8) ? (const T*)upload(c, lam, fs.bufs) : (const T*)upload(c, to_f32(lam), fs.bufs);
+    };
+    fill(c->p64, double{});
+    fill(c->p32, float{});
+    c->fields_set = true;
+  } catch (const std::string& e) {
+    c->err = "sap_set_fields: " + e;
+    return SAP_ENOMEM;
+  }
+  return SAP_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// compute entry points
+// ------------------------------------------------------------------------------------------------
+extern "C" sap_status sap_num_dofs(sap_handle c, int64_t* n) {
+  if (!c || !n) return SAP_EINVAL;
+  *n = c->N;
+  return SAP_OK;
+}
+
+static bool ensure_ws64(sap_ctx* c, int count) {
+  if (c->ws64_count >= count) return true;
+  if (c->ws64) cudaFree(c->ws64);
+  c->ws64 = nullptr;
+  c->ws64_count = 0;
+  if (cudaMalloc(&c->ws64, sizeof(double) * (size_t)count * c->N) != cudaSuccess) return false;
+  c->ws64_count = count;
+  return true;
+}
+
+static bool ensure_ws32(sap_ctx* c, int count) {
+  if (c->ws32_count >= count) return true;
+  if (c->ws32) cudaFree(c->ws32);
+  c->ws32 = nullptr;
+  c->ws32_count = 0;
+  if (cudaMalloc(&c->ws32, sizeof(float) * (size_t)count * c->N) != cudaSuccess) return false;
+  c->ws32_count = count;
+  return true;
+}
+
+extern "C" sap_status sap_apply_operator(sap_handle c, const void* x, void* y, int mode, sap_stream stream) {
+  if (!c || !x || !y || x == y) return SAP_EINVAL;
+  if (!c->fields_set) {
+    c->err = "fields not set";
+    return SAP_EINVAL;
+  }
+  if (mode != SAP_APPLY_D && mode != SAP_APPLY_RHS) {
+    c->err = "unsupported apply mode";
+    return SAP_EUNSUPPORTED;
+  }
+  cudaError_t e = c->prec == SAP_PREC_FP64
+                      ? launch_apply64(c->p64, (const double*)x, (double*)y, mode, (cudaStream_t)stream)
+                      : launch_apply32(c->p32, (const float*)x, (float*)y, mode, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    c->err = std::string("apply: ") + cudaGetErrorString(e);
+    return SAP_ECUDA;
+  }
+  return SAP_OK;
+}
+
+extern "C" sap_status sap_step_erk(sap_handle c, double* state, double dt, int nsteps, sap_stream stream) {
+  if (!c || !state || nsteps < 0) return SAP_EINVAL;
+  if (!c->fields_set) {
+    c->err = "fields not set";
+    return SAP_EINVAL;
+  }
+  if (c->prec == SAP_PREC_FP64 ? !ensure_ws64(c, 3) : (!ensure_ws32(c, 2) || !ensure_ws64(c, 1))) {
+    c->err = "erk: workspace allocation failed";
+    return SAP_ENOMEM;
+  }
+  return erk_steps(c, state, dt, nsteps, (cudaStream_t)stream);
+}
+
+extern "C" sap_status sap_step_cn(sap_handle c, double* state, double dt, int nsteps, double tol, int restart,
+                                  int maxit, sap_solver_stats* stats, sap_stream stream) {
+  if (!c || !state || nsteps < 0 || restart < 1 || restart > 31 || maxit < 1 || !(tol > 0)) return SAP_EINVAL;
+  if (!c->fields_set) {
+    c->err = "fields not set";
+    return SAP_EINVAL;
+  }
+  if (c->prec != SAP_PREC_FP64) {
+    c->err = "cn: FP32 precision form not available for CN in this build";
+    return SAP_EUNSUPPORTED;
+  }
+  if (!ensure_ws64(c, restart + 3)) {
+    c->err = "cn: workspace allocation failed";
+    return SAP_ENOMEM;
+  }
+  return cn_steps(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
+}
+
+extern "C" sap_status sap_destroy(sap_handle c) {
+  if (!c) return SAP_OK;
+  free_bufs(c->owned);
+  auto it = g_fields.find(c);
+  if (it != g_fields.end()) {
+    free_bufs(it->second.bufs);
+    g_fields.erase(it);
+  }
+  if (c->ws64) cudaFree(c->ws64);
+  if (c->ws32) cudaFree(c->ws32);
+  if (c->small) cudaFree(c->small);
+  if (c->small_host) cudaFreeHost(c->small_host);
+  delete c;
+  return SAP_OK;
+}
+
+extern "C" const char* sap_last_error(sap_handle c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+extern "C" sap_status sap_coupling_matrix(int lmax, int which, int a, int b, double* out) {
+  if (lmax < 0 || lmax > 11 || !out || a < 0 || a > 2 || b < 0 || b > 2) return SAP_EINVAL;
+  SHTables T = build_sh_tables(lmax);
+  const Mat* m = nullptr;
+  switch (which) {
+    case 0: m = &T.A[a]; break;
+    case 1: m = &T.Om[a]; break;
+    case 2: m = &T.C; break;
+    case 3: m = &T.AA[a][b]; break;
+    case 4: m = &T.E[a]; break;
+    case 5: m = &T.F[a][b]; break;
+    default: return SAP_EINVAL;
+  }
+  std::memcpy(out, m->a.data(), sizeof(double) * m->a.size());
+  return SAP_OK;
+}

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of the C ABI in include/sap.h (argument marshalling only).
+
+Every step of the operator, the RK4 stages and the Crank--Nicolson / GMRES solve runs inside the
+CUDA library ``libsapgpu.so``.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libsapgpu.so")
+
+SAP_OK, SAP_EINVAL, SAP_ENOMEM, SAP_ECUDA, SAP_ENOCONV, SAP_ETIMEOUT, SAP_EUNSUPPORTED = range(7)
+AXIS = {"x": 0, "y": 1, "z": 2, "p": 3, "lnp": 4}
+BC = {"periodic": 0, "inflow0": 1, "continuous": 2}
+TERM = {"adv": 1, "mom": 2, "rot": 4, "coll": 8, "src": 16}
+PREC = {"fp64": 0, "fp32": 1}
+APPLY_D, APPLY_RHS = 0, 1
+PTS_SPATIAL, PTS_FACE_X, PTS_FACE_Y, PTS_FACE_Z, PTS_PHASE = range(5)
+
+EXPORTS = ["sap_create", "sap_field_points", "sap_set_fields", "sap_num_dofs", "sap_apply_operator",
+           "sap_step_erk", "sap_step_cn", "sap_destroy", "sap_last_error", "sap_coupling_matrix"]
+
+
+class SapError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"sap status {status}: {msg}")
+        self.status = status
+
+
+class Desc(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("axis_kind", C.c_int * 3), ("ncells", C.c_int * 3),
+                ("edges", C.POINTER(C.c_double) * 3), ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3),
+                ("lmax", C.c_int), ("degree", C.c_int), ("V", C.c_double), ("terms", C.c_uint)]
+
+
+class SolverStats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("iterations", C.c_int64), ("max_iterations", C.c_int),
+                ("last_rel_residual", C.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libsapgpu.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    vp, i64p, dp = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)
+    lib.sap_create.argtypes = [C.POINTER(Desc), C.c_int, C.POINTER(C.c_void_p)]
+    lib.sap_field_points.argtypes = [vp, C.c_int, dp, i64p]
+    lib.sap_set_fields.argtypes = [vp, dp, dp, dp, dp, C.POINTER(dp), dp, dp]
+    lib.sap_num_dofs.argtypes = [vp, i64p]
+    lib.sap_apply_operator.argtypes = [vp, vp, vp, C.c_int, vp]
+    lib.sap_step_erk.argtypes = [vp, vp, C.c_double, C.c_int, vp]
+    lib.sap_step_cn.argtypes = [vp, vp, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
+                                C.POINTER(SolverStats), vp]
+    lib.sap_destroy.argtypes = [vp]
+    lib.sap_last_error.argtypes = [vp]
+    lib.sap_last_error.restype = C.c_char_p
+    lib.sap_coupling_matrix.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp]
+    for name in EXPORTS:
+        getattr(lib, name).restype = C.c_int if name != "sap_last_error" else C.c_char_p
+    _lib = lib
+    return lib
+
+
+def coupling_matrix(lmax: int, which: int, a: int = 0, b: int = 0) -> np.ndarray:
+    """The library's host-built n x n coupling matrix (see sap_coupling_matrix)."""
+    lib = load_library()
+    n = (lmax + 1) ** 2
+    out = np.zeros(n * n)
+    st = lib.sap_coupling_matrix(lmax, which, a, b, out.ctypes.data_as(C.POINTER(C.c_double)))
+    if st != SAP_OK:
+        raise SapError(st, "sap_coupling_matrix")
+    return out.reshape(n, n)
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Solver:
+    """One problem on the current CUDA device (wraps a sap_handle)."""
+
+    def __init__(self, prob, precision: str = "fp64"):
+        self.lib = load_library()
+        self.prob = prob
+        self.precision = precision
+        D = len(prob.axes)
+        d = Desc()
+        d.ndim = D
+        self._edges = [np.ascontiguousarray(e, dtype=np.float64) for e in prob.edges]
+        for a in range(D):
+            d.axis_kind[a] = AXIS[prob.axes[a]]
+            d.ncells[a] = len(self._edges[a]) - 1
+            d.edges[a] = self._edges[a].ctypes.data_as(C.POINTER(C.c_double))
+            d.bc_lo[a] = BC[prob.bc[a][0]]
+            d.bc_hi[a] = BC[prob.bc[a][1]]
+        d.lmax, d.degree, d.V = prob.lmax, prob.k, float(prob.V)
+        d.terms = sum(TERM[t] for t in prob.terms)
+        h = C.c_void_p()
+        st = self.lib.sap_create(C.byref(d), PREC[precision], C.byref(h))
+        if st != SAP_OK:
+            raise SapError(st, self.lib.sap_last_error(None).decode())
+        self.h = h
+        n = C.c_int64()
+        self._check(self.lib.sap_num_dofs(self.h, C.byref(n)))
+        self.N = n.value
+        self.set_fields(prob)
+
+    # -- helpers -------------------------------------------------------------------------------
+    def _check(self, st):
+        if st != SAP_OK:
+            raise SapError(st, self.lib.sap_last_error(self.h).decode())
+
+    def points(self, which: int) -> np.ndarray:
+        cnt = C.c_int64()
+        self._check(self.lib.sap_field_points(self.h, which, None, C.byref(cnt)))
+        if cnt.value == 0:
+            return np.zeros((0, 0))
+        dim = len(self.prob.axes) if which == PTS_PHASE else len([a for a in self.prob.axes if a in "xyz"])
+        out = np.zeros((cnt.value, dim))
+        self._check(self.lib.sap_field_points(self.h, which, _dptr(out), C.byref(cnt)))
+        return out
+
+    def _phase_xs_p(self, pts):
+        prob = self.prob
+        sp = [i for i, a in enumerate(prob.axes) if a in "xyz"]
+        xs = pts[:, sp]
+        p = None
+        if prob.momentum is not None:
+            col = pts[:, len(prob.axes) - 1]
+            p = np.exp(col) if prob.momentum == "lnp" else col
+        return xs, p
+
+    def set_fields(self, prob):
+        """Evaluate the problem's fields at the library's points and upload them."""
+        xs = self.points(PTS_SPATIAL)
+        nsv = xs.shape[0]
+        U = np.ascontiguousarray(prob.U(xs), dtype=np.float64).reshape(nsv, 3)
+        G = np.ascontiguousarray(prob.gradU(xs), dtype=np.float64).reshape(nsv, 9)
+        DU = np.ascontiguousarray(prob.DUDt(xs), dtype=np.float64).reshape(nsv, 3)
+        Bw = prob.B(xs) if prob.momentum is not None else prob.omega(xs)
+        Bw = np.ascontiguousarray(Bw, dtype=np.float64).reshape(nsv, 3)
+        faces = []
+        for a in range(3):
+            fp = self.points(PTS_FACE_X + a)
+            faces.append(np.ascontiguousarray(prob.U(fp)[:, a], dtype=np.float64) if fp.shape[0] else None)
+        face_ptrs = (C.POINTER(C.c_double) * 3)(*[_dptr(f) if f is not None else None for f in faces])
+        ph = self.points(PTS_PHASE)
+        pxs, pp = self._phase_xs_p(ph)
+        nu = np.ascontiguousarray(prob.nu(pxs, pp), dtype=np.float64)
+        s0 = np.ascontiguousarray(prob.s000(pxs, pp), dtype=np.float64)
+        self._check(self.lib.sap_set_fields(self.h, _dptr(U), _dptr(G), _dptr(DU), _dptr(Bw), face_ptrs,
+                                            _dptr(nu), _dptr(s0)))
+
+    def initial_state(self, device="cuda"):
+        """Nodal values of f^0 at the phase-space nodes, canonical layout, FP64 torch tensor."""
+        import torch
+        ph = self.points(PTS_PHASE)
+        f0 = np.asarray(self.prob.f0(ph), dtype=np.float64)  # (ncell*nloc, n)
+        nloc = (self.prob.k + 1) ** len(self.prob.axes)
+        ncell = ph.shape[0] // nloc
+        y = f0.reshape(ncell, nloc, self.prob.n).transpose(0, 2, 1).reshape(-1)
+        return torch.from_numpy(np.ascontiguousarray(y)).to(device)
+
+    # -- compute -------------------------------------------------------------------------------
+    def apply(self, x, y, mode: int = APPLY_D, stream=None):
+        self._check(self.lib.sap_apply_operator(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                                mode, _stream_handle(stream)))
+        return y
+
+    def step_erk(self, state, dt: float, nsteps: int, stream=None):
+        self._check(self.lib.sap_step_erk(self.h, C.c_void_p(state.data_ptr()), dt, nsteps, _stream_handle(stream)))
+        return state
+
+    def step_cn(self, state, dt: float, nsteps: int, tol: float = 1e-10, restart: int = 30, maxit: int = 2000,
+                stream=None) -> SolverStats:
+        st = SolverStats()
+        self._check(self.lib.sap_step_cn(self.h, C.c_void_p(state.data_ptr()), dt, nsteps, tol, restart, maxit,
+                                         C.byref(st), _stream_handle(stream)))
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sap_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

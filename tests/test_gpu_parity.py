@@ -1,0 +1,132 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (FP64 path): the operator apply agrees to 1e-12 relative to the largest output entry
+(the paper-level bound for the plain path is rel. L2 <= 1e-12); ERK and exactly solved CN
+trajectories to 1e-12 relative L2.  Inputs are seeded; sizes span several thread blocks with a
+ragged tail.
+"""
+import numpy as np
+import pytest
+
+from paper_2501_05110_gb300 import workloads as W
+
+from .oracle_bridge import NodalOracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2501_05110_gb300 import build as sap_build
+    sap_build.build()
+    return torch
+
+
+def _solver(prob, prec="fp64"):
+    from paper_2501_05110_gb300 import sapgpu
+    return sapgpu.Solver(prob, prec)
+
+
+def _gpu_apply(torch, solver, y_np, rhs=False, dtype=None):
+    from paper_2501_05110_gb300 import sapgpu
+    dtype = dtype or torch.float64
+    x = torch.from_numpy(y_np).to("cuda", dtype)
+    out = torch.empty_like(x)
+    solver.apply(x, out, sapgpu.APPLY_RHS if rhs else sapgpu.APPLY_D)
+    torch.cuda.synchronize()
+    return out.double().cpu().numpy()
+
+
+def _rel_max(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _tiny_problems():
+    return [
+        W.periodic_1d(ncells=3, k=2, lmax=1),
+        W.periodic_1d(ncells=1, k=1, lmax=2),
+        W.shock(nx=3, npc=2, lmax=1, xr=(-2.0, 2.0), lnpr=(0.0, 2.0)),
+        W.shock(nx=2, npc=3, lmax=2, k=2, xr=(-1.0, 1.0), lnpr=(0.5, 2.0)),
+        W.box3d(ncells=2, k=1, lmax=1),
+    ]
+
+
+@pytest.mark.parametrize("idx", range(5))
+def test_apply_unit_vectors_tiny(torch_cuda, idx):
+    """Brute force on 1-8 cells: every column of M^-1 D matches the oracle's assembled operator."""
+    prob = _tiny_problems()[idx]
+    orc = NodalOracle(prob)
+    sol = _solver(prob)
+    N = sol.N
+    assert N == orc.disc.N
+    eye = np.eye(N)
+    G = np.stack([_gpu_apply(torch_cuda, sol, eye[:, j]) for j in range(N)], axis=1)
+    O = np.stack([orc.apply(eye[:, j]) for j in range(N)], axis=1)
+    assert _rel_max(G, O) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["periodic1d", "shock_small", "box_small", "shock_graded"])
+def test_apply_random(torch_cuda, name):
+    rng = np.random.default_rng(11)
+    if name == "periodic1d":
+        prob = W.periodic_1d()
+    elif name == "shock_small":
+        prob = W.shock(nx=15, npc=7, lmax=3)
+    elif name == "box_small":
+        prob = W.box3d(ncells=3, k=2, lmax=3)
+    else:
+        xe = np.concatenate([-np.geomspace(30, 0.05, 9), np.linspace(-0.04, 0.04, 5), np.geomspace(0.05, 60, 10)])
+        prob = W.shock(x_edges=np.sort(xe), npc=6, lmax=2, lnpr=(-1.0, 4.0), Ls=0.05)
+    orc = NodalOracle(prob)
+    sol = _solver(prob)
+    y = rng.standard_normal(sol.N)
+    for rhs in (False, True):
+        assert _rel_max(_gpu_apply(torch_cuda, sol, y, rhs), orc.apply(y, rhs)) < 1e-12
+
+
+def test_erk_periodic_1d_full(torch_cuda):
+    """RK4, dt = 1e-3, 1000 steps on the 1-D periodic workload; conservation of int f_000 dx."""
+    prob = W.periodic_1d()
+    orc = NodalOracle(prob)
+    sol = _solver(prob)
+    y0 = sol.initial_state()
+    want = orc.rk4(y0.cpu().numpy(), prob.dt, prob.nsteps)
+    y = y0.clone()
+    sol.step_erk(y, prob.dt, prob.nsteps)
+    torch_cuda.cuda.synchronize()
+    got = y.cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-12
+    # particle number: sum over cells of h * sum_nodes w_node f_000
+    w = orc.disc.wg * (20.0 / 64)
+    m0 = (y0.cpu().numpy().reshape(64, prob.n, 3)[:, 0, :] * w).sum()
+    m1 = (got.reshape(64, prob.n, 3)[:, 0, :] * w).sum()
+    assert abs(m1 - m0) < 1e-12 * abs(m0)
+
+
+def test_cn_shock_small_exact(torch_cuda):
+    """CN steps solved to 1e-14 agree with the oracle's sparse-LU CN to 1e-12 (rel. L2)."""
+    prob = W.shock(nx=15, npc=7, lmax=3)
+    orc = NodalOracle(prob)
+    sol = _solver(prob)
+    y = sol.initial_state()
+    st = sol.step_cn(y, 1.0, 12, tol=1e-14, restart=30, maxit=3000)
+    torch_cuda.cuda.synchronize()
+    want = orc.cn(np.zeros(sol.N), 1.0, 12)
+    got = y.cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-12
+    assert st.last_rel_residual <= 1e-14 and st.iterations > 0
+
+
+def test_cn_tolerance_1e10(torch_cuda):
+    """At the workload tolerance 1e-10 the CN trajectory stays within steps * tol * cond of LU."""
+    prob = W.shock(nx=15, npc=7, lmax=3)
+    orc = NodalOracle(prob)
+    sol = _solver(prob)
+    y = sol.initial_state()
+    st = sol.step_cn(y, 1.0, 12, tol=1e-10)
+    torch_cuda.cuda.synchronize()
+    want = orc.cn(np.zeros(sol.N), 1.0, 12)
+    err = np.linalg.norm(y.cpu().numpy() - want) / np.linalg.norm(want)
+    assert err < 1e-8 and st.last_rel_residual <= 1e-10
