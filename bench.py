@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 dG-VFP library on the parallel-shock Crank--Nicolson workload.
+
+Workload (default, "shock"): reduced phase space (x, ln p), x in [-200, 200] with 256 cells,
+ln p in [0, 10] with 64 cells, dG degree 1, lmax = 3 (n = 16), tanh shock U1 = 0.1, r = 4,
+nu = p, B = e_x, Gaussian source, FP64; one step = one Crank--Nicolson step (dt = 1) solved by
+restarted GMRES(30) to a true relative residual of 1e-10.  N = 1,048,576 DoFs.
+
+Prints ONE JSON line.  `value` is whole-job DoF-updates/s per CN step (N * steps / time, summed
+over ranks; each rank runs an independent replica: the single-shock solve does not shard).
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the stream the
+library runs on, with a 256 MiB L2 flush between timed steps (outside the events).
+`--impl reference` times the FP64 CPU oracle (the only baseline that exists: the paper publishes
+no performance numbers) on the same workload and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "phase-space DoF-updates/s per CN step"
+UNIT = "DoF-updates/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e-3  # SMs x DFMA/clk/SM x 2 flop x max GHz = 1.2586 TFLOP/s (FP64)
+# DRAM bytes (read + write) per apply launch from the ncu capture in profiles/apply_kernel_fp64_shock.md,
+# valid only for the kernel source it was taken on (first 16 hex of sha256 of csrc/operator.cu)
+APPLY_TRAFFIC = {"bf2a474848085cbc": 10730240.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="shock", choices=["shock"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--apply-reps", type=int, default=200)
+    return ap.parse_args()
+
+
+def workload_problem():
+    from paper_2501_05110_gb300 import workloads as W
+    return W.shock()
+
+
+def workload_config(prob, extra=None):
+    cfg = {"workload": "shock_x256_lnp64_k1_l3_cn_dt1_tol1e-10", "dofs": prob.ndofs,
+           "cells": prob.ncells, "degree": prob.k, "lmax": prob.lmax, "gmres_restart": prob.gmres_restart,
+           "gmres_tol": prob.gmres_tol, "dt": prob.dt, "l2": "flushed between timed steps (256 MiB write)",
+           "parallelism": "replicas"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle timing (runs in a fresh single-threaded interpreter)
+# ------------------------------------------------------------------------------------------------
+def cpu_worker(nsteps: int):
+    """Time the oracle's CN step (assembled CSR, GMRES(30) with Jacobi, tol 1e-10) on the full
+    workload; assembly is set-up and untimed."""
+    import numpy as np
+    from oracle import dg, steppers
+    prob = workload_problem()
+    d = dg.Discretisation(prob)
+    A = (d.M + 0.5 * prob.dt * d.D).tocsr()
+    B = (d.M - 0.5 * prob.dt * d.D).tocsr()
+    z = np.zeros(d.N)
+    times, its = [], []
+    for _ in range(nsteps):
+        t0 = time.perf_counter()
+        b = B @ z + prob.dt * d.h
+        z, it = steppers.gmres(A, b, z, tol=prob.gmres_tol, restart=prob.gmres_restart)
+        times.append(time.perf_counter() - t0)
+        its.append(it)
+    print(json.dumps({"times": times, "its": its, "N": d.N}))
+
+
+def run_cpu_oracle(nsteps: int, skip: int = 0) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(nsteps)],
+                       capture_output=True, text=True, env=env, cwd=ROOT, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("cpu worker failed: " + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    times = out["times"][skip:]
+    t = sum(times)
+    return {"value": out["N"] * len(times) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "ms_per_step": 1e3 * t / len(times),
+            "sample": f"{len(times)} timed CN steps of the full workload (N={out['N']}) with the oracle's "
+                      f"assembled CSR + GMRES(30)/Jacobi, tol 1e-10, single thread; assembly untimed; "
+                      f"{statistics.mean(out['its']):.1f} GMRES iterations/step",
+            "seconds": t}
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+def run_mine(args):
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2501_05110_gb300 import build as sap_build
+    from paper_2501_05110_gb300 import sapgpu
+    sap_build.build()
+    prob = workload_problem()
+    sol = sapgpu.Solver(prob, "fp64")
+    N = sol.N
+    stream = torch.cuda.current_stream()
+    state = sol.initial_state()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tol, restart, maxit = prob.gmres_tol, prob.gmres_restart, 5000
+    for _ in range(args.warmup):
+        sol.step_cn(state, prob.dt, 1, tol, restart, maxit)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-timed steps --------------------------------------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t_steps, its, launches = [], [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = sol.step_cn(state, prob.dt, 1, tol, restart, maxit)
+        e1.record(stream)
+        e1.synchronize()
+        t_steps.append(e0.elapsed_time(e1) * 1e-3)
+        its.append(st.iterations)
+        launches += st.kernel_launches
+    barrier()
+    clk = clocks.stop()
+    t_total = sum(t_steps)
+    if world > 1:
+        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = N * args.steps * world / t_total
+
+    # ---- end to end through the public API with host buffers -------------------------------------
+    host = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    host.copy_(state.cpu())
+    dev = torch.empty_like(state)
+    barrier()
+    t_e2e = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dev.copy_(host, non_blocking=True)
+        sol.step_cn(dev, prob.dt, 1, tol, restart, maxit)
+        host.copy_(dev, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        t_e2e += e0.elapsed_time(e1) * 1e-3
+    barrier()
+    if world > 1:
+        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e = {"value": N * args.steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": N * 8,
+           "d2h_bytes_per_step": N * 8}
+
+    # ---- dominant kernel: the operator apply, timed alone on the same stream ----------------------
+    flops, abytes = sol.apply_cost()
+    x = state.clone()
+    y = torch.empty_like(x)
+    for _ in range(10):
+        sol.apply(x, y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.apply_reps):
+        sol.apply(x, y)
+    e1.record(stream)
+    e1.synchronize()
+    t_apply = e0.elapsed_time(e1) * 1e-3 / args.apply_reps
+    achieved = flops / t_apply / 1e12
+    import hashlib
+    src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2501_05110_gb300", "csrc", "operator.cu"), "rb").read()).hexdigest()[:16]
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": APPLY_TRAFFIC.get(src_sha),
+                "kernel": "apply_kernel<double>",
+                "apply_us": t_apply * 1e6, "flops_per_apply": flops, "algorithmic_bytes_per_apply": abytes,
+                "hbm_view": {"achieved_gbs": abytes / t_apply / 1e9, "peak_gbs": 6746.3,
+                             "frac": abytes / t_apply / 1e9 / 6746.3},
+                "peak_note": "FP64 nominal from unit counts x max clock (FP64 ALU bound)"}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(prob, {"gmres_iterations_per_step": statistics.mean(its)}),
+           "roofline": roofline, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = run_cpu_oracle(2)
+        except Exception as exc:  # reported, not hidden
+            out["cpu_baseline"] = {"value": None, "error": str(exc)[:300]}
+    if rank == 0:
+        print(json.dumps(out))
+    sol.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = run_cpu_oracle_steps(args.warmup, args.steps)
+    prob = workload_problem()
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": workload_config(prob),
+            "cpu_baseline": {"value": res["value"], "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": res["sample"]},
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_cpu_oracle_steps(warmup: int, steps: int) -> dict:
+    return run_cpu_oracle(warmup + steps, skip=warmup)
+
+
+def main():
+    args = parse()
+    if args.cpu_worker:
+        cpu_worker(args.cpu_worker)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mine(args)
+
+
+if __name__ == "__main__":
+    main()

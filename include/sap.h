@@ -86,6 +86,7 @@ typedef struct {
   int64_t iterations;       /* total GMRES iterations over all steps                               */
   int max_iterations;       /* most iterations in one step                                         */
   double last_rel_residual; /* true relative residual ||b - A x|| / ||b|| of the last step         */
+  int64_t kernel_launches;  /* CUDA kernels this call launched (operator applies + Krylov kernels)  */
 } sap_solver_stats;
 
 /* Create a context for one problem (Sec. 2-3).  Builds the coupling matrices A^a, Omega^a, C and
@@ -139,6 +140,12 @@ sap_status sap_step_erk(sap_handle h, double* state, double dt, int nsteps, sap_
  * Errors: SAP_EINVAL, SAP_ENOCONV (state holds the last iterate), SAP_ECUDA. */
 sap_status sap_step_cn(sap_handle h, double* state, double dt, int nsteps, double tol, int restart,
                        int maxit, sap_solver_stats* stats, sap_stream stream);
+
+/* Algorithmic cost of one sap_apply_operator call on this context: `flops` = floating-point
+ * operations (an FMA counts 2) summed from the kernel's term tables (coefficient set-up, traces,
+ * upwind fluxes, volume terms, lifts); `bytes` = 2 N w (read x, write y; w = word size of the
+ * context's precision).  Host-only.  Errors: SAP_EINVAL (fields not set). */
+sap_status sap_apply_cost(sap_handle h, double* flops, double* bytes);
 
 /* Destroy a context and free its device memory.  NULL is accepted. */
 sap_status sap_destroy(sap_handle h);

@@ -26,6 +26,10 @@
 
 namespace sap {
 
+// kernels launched by this host thread (for the launch counts reported in sap_solver_stats)
+static thread_local int64_t g_launches = 0;
+int64_t launch_count() { return g_launches; }
+
 // ------------------------------------------------------------------------------------------------
 // epilogue: out = d .* (wb*b + ax*x + bl*(Lx) + gs*s), and/or ERK bookkeeping
 // ------------------------------------------------------------------------------------------------
@@ -64,26 +68,14 @@ __device__ __forceinline__ T csr_diag(const Bank<T>& B, int mat, int r) {
   return T(0);
 }
 
+// momentum factors (p, gamma m, V, 1/V, ...) are tabulated on the host per momentum node and face
 template <typename T>
-__device__ __forceinline__ T mom_factor(const OpParams<T>& P, int mf, T p) {
-  if (mf == MF_ONE) return T(1);
-  if (!P.has_mom) {
-    if (mf == MF_V) return P.Vmono;
-    if (mf == MF_INV_V) return T(1) / P.Vmono;
-    return T(1);
-  }
-  const T gm = sqrt(T(1) + p * p);
-  switch (mf) {
-    case MF_P: return p;
-    case MF_GM: return gm;
-    case MF_V: return p / gm;
-    case MF_INV_V: return gm / p;
-    case MF_INV_GM: return T(1) / gm;
-    case MF_INV_P: return T(1) / p;
-    case MF_INV_GMP: return T(1) / (gm * p);
-    case MF_GM_OVER_P: return gm / p;
-  }
-  return T(1);
+__device__ __forceinline__ T mom_node(const OpParams<T>& P, int mf, int pn) {
+  return mf == MF_ONE ? T(1) : __ldg(P.mfn + (size_t)mf * P.npn + pn);
+}
+template <typename T>
+__device__ __forceinline__ T mom_face(const OpParams<T>& P, int mf, int pf) {
+  return mf == MF_ONE ? T(1) : __ldg(P.mff + (size_t)mf * P.npface + pf);
 }
 
 template <typename T>
@@ -152,9 +144,7 @@ __global__ void __launch_bounds__(1024) apply_kernel(const OpParams<T> P, const 
         tm = &P.ax[a].adv[tt - adv_off[a]];
       }
       const int sp = scell * P.qdx + ii % P.qdx;
-      T c = T(tm->scale) * spatial_factor(P, tm->sf, sp);
-      if (P.has_mom) c *= mom_factor(P, tm->mf, __ldg(P.pnode + pcell * q + ii / P.qdx));
-      else c *= mom_factor(P, tm->mf, T(0));
+      T c = T(tm->scale) * spatial_factor(P, tm->sf, sp) * mom_node(P, tm->mf, pcell * q + ii / P.qdx);
       if (tm->nu) c *= P.nu ? __ldg(P.nu + (size_t)cell * nloc + ii) : P.nu_uni;
       CV[w] = c;
     }
@@ -178,12 +168,11 @@ __global__ void __launch_bounds__(1024) apply_kernel(const OpParams<T> P, const 
         } else {
           c *= spatial_factor(P, tm.sf, scell * P.qdx);  // only SF_ONE occurs here
         }
-        if (P.has_mom) c *= mom_factor(P, tm.mf, __ldg(P.pnode + pcell * q + fp / qsp));
-        else c *= mom_factor(P, tm.mf, T(0));
+        c *= mom_node(P, tm.mf, pcell * q + fp / qsp);
       } else {
         // momentum face: spatial factor at the spatial node (fp), momentum at the face
         c *= spatial_factor(P, tm.sf, scell * P.qdx + fp);
-        c *= mom_factor(P, tm.mf, __ldg(P.pface + pcell + side));
+        c *= mom_face(P, tm.mf, pcell + side);
       }
       CF[w] = c;
     }
@@ -374,6 +363,7 @@ static cudaError_t launch_apply(const OpParams<T>& P, const T* x, const Epi<T>& 
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   const int blocks = (P.ncell + cpb - 1) / cpb;
   apply_kernel<T><<<blocks, cpb * per, smem, s>>>(P, x, e, cpb, stride);
+  ++g_launches;
   return cudaGetLastError();
 }
 
@@ -413,6 +403,7 @@ static cudaError_t erk_impl(sap_ctx* c, const OpParams<T>& P, T* ya, T* yb, doub
       stage_in0 = reinterpret_cast<const T*>(state);
     } else {
       cast_kernel<T><<<1024, 256, 0, s>>>(state, ya, c->N);
+  ++g_launches;
       stage_in0 = ya;
     }
     Epi<T> e{};
@@ -460,76 +451,76 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// partial[b][i] = sum over block b's slice of V_i . w, for i < m  (V_i = V + i*ldv)
+// Dot products of w with V_0..V_{m-1} (V_i = V + i*ldv) and, if `with_ww`, of w with itself.
+// Block b handles the chunk [b*KRY_CHUNK, (b+1)*KRY_CHUNK): it stages w in shared memory once, then
+// warp v sums V_i . w for i = v, v+8, ... ; partial[i][b] = the chunk's value (fixed order).
+constexpr int KRY_CHUNK = 2048;
 __global__ void __launch_bounds__(KRY_THREADS) multidot_kernel(const double* __restrict__ V, int64_t ldv, int m,
-                                                               const double* __restrict__ w, int64_t N,
-                                                               double* __restrict__ partial) {
-  __shared__ double red[KRY_THREADS / 32][KRY_MAXV];
-  double acc[KRY_MAXV];
-#pragma unroll
-  for (int i = 0; i < KRY_MAXV; ++i) acc[i] = 0.0;
-  for (int64_t k = blockIdx.x * (int64_t)KRY_THREADS + threadIdx.x; k < N; k += (int64_t)gridDim.x * KRY_THREADS) {
-    const double wk = __ldg(w + k);
-#pragma unroll
-    for (int i = 0; i < KRY_MAXV; ++i)
-      if (i < m) acc[i] += __ldg(V + i * ldv + k) * wk;
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < KRY_MAXV; ++i) {
-    if (i < m) {
-      double v = warp_sum(acc[i]);
-      if (lane == 0) red[wid][i] = v;
-    }
-  }
+                                                               const double* __restrict__ w, int64_t N, int with_ww,
+                                                               double* __restrict__ partial, int nchunks) {
+  __shared__ double ws[KRY_CHUNK];
+  const int64_t k0 = (int64_t)blockIdx.x * KRY_CHUNK;
+  const int len = (int)((N - k0) < KRY_CHUNK ? (N - k0) : KRY_CHUNK);
+  for (int k = threadIdx.x; k < len; k += KRY_THREADS) ws[k] = w[k0 + k];
   __syncthreads();
-  if (threadIdx.x < m) {
-    double v = 0.0;
-    for (int q = 0; q < KRY_THREADS / 32; ++q) v += red[q][threadIdx.x];
-    partial[(size_t)blockIdx.x * KRY_MAXV + threadIdx.x] = v;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mt = m + (with_ww ? 1 : 0);
+  for (int i = warp; i < mt; i += KRY_THREADS / 32) {
+    const double* a = (i < m) ? V + i * ldv + k0 : nullptr;
+    double acc = 0.0;
+    if (a) {
+      for (int k = lane; k < len; k += 32) acc += __ldg(a + k) * ws[k];
+    } else {
+      for (int k = lane; k < len; k += 32) acc += ws[k] * ws[k];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) partial[(size_t)i * nchunks + blockIdx.x] = acc;
   }
 }
 
-// out[i] = sum_b partial[b][i] (fixed order: deterministic)
-__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nblocks, int m, double* __restrict__ out) {
-  const int i = threadIdx.x;
+// out[i] = sum_c partial[i][c], i < m: warp i strides over the chunks, then a fixed-order shuffle
+// reduction (deterministic for a given N).
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nchunks, int m, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31, i = threadIdx.x >> 5;
   if (i >= m) return;
   double v = 0.0;
-  for (int b = 0; b < nblocks; ++b) v += partial[(size_t)b * KRY_MAXV + i];
-  out[i] = v;
+  for (int c = lane; c < nchunks; c += 32) v += partial[(size_t)i * nchunks + c];
+  v = warp_sum(v);
+  if (lane == 0) out[i] = v;
 }
 
-// w -= sum_i h[i] V_i ; optionally partial norm^2 of the result into partial[b][0]
+// w -= sum_i h[i] V_i ; partial[b] = this block's sum of the updated w^2 (block-strided chunks)
 __global__ void __launch_bounds__(KRY_THREADS) update_kernel(const double* __restrict__ V, int64_t ldv, int m,
                                                              const double* __restrict__ h, double* __restrict__ w,
-                                                             int64_t N, double* __restrict__ partial) {
+                                                             int64_t N, double* __restrict__ partial, int nchunks) {
   __shared__ double hs[KRY_MAXV];
   __shared__ double red[KRY_THREADS / 32];
   if (threadIdx.x < m) hs[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
+  const int64_t k0 = (int64_t)blockIdx.x * KRY_CHUNK;
+  const int64_t k1 = (k0 + KRY_CHUNK < N) ? k0 + KRY_CHUNK : N;
   double nrm = 0.0;
-  for (int64_t k = blockIdx.x * (int64_t)KRY_THREADS + threadIdx.x; k < N; k += (int64_t)gridDim.x * KRY_THREADS) {
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += KRY_THREADS) {
     double v = w[k];
     for (int i = 0; i < m; ++i) v -= hs[i] * __ldg(V + i * ldv + k);
     w[k] = v;
     nrm += v * v;
   }
-  if (partial) {
-    nrm = warp_sum(nrm);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double v = 0.0;
-      for (int q = 0; q < KRY_THREADS / 32; ++q) v += red[q];
-      partial[(size_t)blockIdx.x * KRY_MAXV] = v;
-    }
+  nrm = warp_sum(nrm);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < KRY_THREADS / 32; ++q) t += red[q];
+    partial[blockIdx.x] = t;
   }
+  (void)nchunks;
 }
 
-// y = a*x (+ b*y if accumulate)
+// y = a*x with a = 1/a_dev[0] (invert = 1), 1/sqrt(a_dev[0]) (invert = 2) or a_dev[0]
 __global__ void scale_kernel(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ a_dev,
                              int invert, int64_t N) {
-  const double a = invert ? 1.0 / a_dev[0] : a_dev[0];
+  const double a = invert == 1 ? 1.0 / a_dev[0] : (invert == 2 ? 1.0 / sqrt(a_dev[0]) : a_dev[0]);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) y[k] = a * x[k];
 }
 
@@ -546,21 +537,6 @@ __global__ void combine_kernel(const double* __restrict__ V, int64_t ldv, int m,
   }
 }
 
-// partial[b][0] = sum of v^2 over the block's slice
-__global__ void __launch_bounds__(KRY_THREADS) norm2_kernel(const double* __restrict__ v, int64_t N, double* __restrict__ partial) {
-  __shared__ double red[KRY_THREADS / 32];
-  double s = 0.0;
-  for (int64_t k = blockIdx.x * (int64_t)KRY_THREADS + threadIdx.x; k < N; k += (int64_t)gridDim.x * KRY_THREADS) s += v[k] * v[k];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < KRY_THREADS / 32; ++q) t += red[q];
-    partial[(size_t)blockIdx.x * KRY_MAXV] = t;
-  }
-}
-
 }  // namespace sap
 
 // ------------------------------------------------------------------------------------------------
@@ -571,20 +547,38 @@ namespace sap {
 struct KrylovCtx {
   sap_ctx* c;
   cudaStream_t s;
-  int nblocks;
-  double* partial;   // [nblocks][KRY_MAXV]
-  double* dsc;       // device scalars [KRY_MAXV * 4]
-  double* hsc;       // pinned host mirror
+  int nchunks;
+  double* partial;   // [KRY_MAXV + 1][nchunks]
+  double* dsc;       // device scalars [8 * KRY_MAXV]
+  double* hsc;       // pinned host mirror [8 * KRY_MAXV]
 };
 
-static cudaError_t dev_norm2(KrylovCtx& K, const double* v, double* out_host) {
+// dsc_out[i] = V_i . w for i < m, and dsc_out[m] = w . w if with_ww
+static void dots(KrylovCtx& K, const double* V, int m, const double* w, int with_ww, double* dsc_out) {
   const int64_t N = K.c->N;
-  norm2_kernel<<<K.nblocks, KRY_THREADS, 0, K.s>>>(v, N, K.partial);
-  reduce_partials_kernel<<<1, 32, 0, K.s>>>(K.partial, K.nblocks, 1, K.dsc);
-  cudaMemcpyAsync(K.hsc, K.dsc, sizeof(double), cudaMemcpyDeviceToHost, K.s);
-  cudaError_t e = cudaStreamSynchronize(K.s);
-  *out_host = K.hsc[0];
-  return e;
+  multidot_kernel<<<K.nchunks, KRY_THREADS, 0, K.s>>>(V, N, m, w, N, with_ww, K.partial, K.nchunks);
+  ++g_launches;
+  reduce_partials_kernel<<<1, 32 * (m + with_ww), 0, K.s>>>(K.partial, K.nchunks, m + with_ww, dsc_out);
+  ++g_launches;
+}
+
+// w -= V h (m vectors), then dsc_out[0] = |w|^2
+static void update(KrylovCtx& K, const double* V, int m, const double* h, double* w, double* dsc_out) {
+  const int64_t N = K.c->N;
+  update_kernel<<<K.nchunks, KRY_THREADS, 0, K.s>>>(V, N, m, h, w, N, K.partial, K.nchunks);
+  ++g_launches;
+  reduce_partials_kernel<<<1, 32, 0, K.s>>>(K.partial, K.nchunks, 1, dsc_out);
+  ++g_launches;
+}
+
+static cudaError_t fetch(KrylovCtx& K, int first, int count) {
+  cudaMemcpyAsync(K.hsc + first, K.dsc + first, sizeof(double) * count, cudaMemcpyDeviceToHost, K.s);
+  return cudaStreamSynchronize(K.s);
+}
+
+int64_t krylov_scratch_doubles(int64_t N) {
+  const int64_t nchunks = (N + KRY_CHUNK - 1) / KRY_CHUNK;
+  return (KRY_MAXV + 1) * nchunks + 8 * KRY_MAXV;
 }
 
 sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
@@ -594,16 +588,20 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
   double* V = c->ws64;                       // (m+1) vectors
   double* b = V + (size_t)(m + 1) * N;
   double* tmp = b + N;
-  KrylovCtx K{c, s, (int)std::min<int64_t>((N + KRY_THREADS - 1) / KRY_THREADS, 152 * 8), c->small,
-              c->small + 152 * 8 * KRY_MAXV, c->small_host};
+  const int nchunks = (int)((N + KRY_CHUNK - 1) / KRY_CHUNK);
+  KrylovCtx K{c, s, nchunks, c->small, c->small + (size_t)(KRY_MAXV + 1) * nchunks, c->small_host};
+  double* const d_h1 = K.dsc;                  // [0, 32): first Gram-Schmidt coefficients (+ |w|^2 at j+1)
+  double* const d_nrm = K.dsc + KRY_MAXV;      // [32]: |w|^2 after the update
+  double* const d_h2 = K.dsc + 2 * KRY_MAXV;   // [64, 96): re-orthogonalisation coefficients
+  double* const d_y = K.dsc + 3 * KRY_MAXV;    // [96, 128): least-squares solution
   const OpParams<double>& P = c->p64;
   const double half = 0.5 * dt;
   std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), y(m);
   int64_t total_its = 0;
+  const int64_t launches0 = g_launches;
   int max_its = 0;
   double last_rel = 0.0;
   cudaError_t err = cudaSuccess;
-  sap_status status = SAP_OK;
 #define CK(x)                                           \
   do {                                                  \
     err = (x);                                          \
@@ -616,9 +614,9 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
       e.out = b; e.ax = 1.0; e.bl = -half; e.gs = dt;
       CK(launch_apply<double>(P, state, e, s));
     }
-    double bn2;
-    CK(dev_norm2(K, b, &bn2));
-    const double bnorm = std::sqrt(bn2);
+    dots(K, nullptr, 0, b, 1, d_nrm);
+    CK(fetch(K, KRY_MAXV, 1));
+    const double bnorm = std::sqrt(K.hsc[KRY_MAXV]);
     int its = 0;
     double rel = 0.0;
     if (bnorm == 0.0) {
@@ -633,22 +631,21 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
         e.out = tmp; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half;
         CK(launch_apply<double>(P, state, e, s));
       }
-      double tn2;
-      CK(dev_norm2(K, tmp, &tn2));
-      rel = std::sqrt(tn2) / bnorm;
+      dots(K, nullptr, 0, tmp, 1, d_nrm);
+      CK(fetch(K, KRY_MAXV, 1));
+      rel = std::sqrt(K.hsc[KRY_MAXV]) / bnorm;
       if (rel <= tol || its >= maxit) break;
-      // preconditioned residual v0 = P^-1 r
+      // preconditioned residual v0 = P^-1 r, normalised
       {
         Epi<double> e{};
         e.out = V; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.jacobi = 1; e.cj = half;
         CK(launch_apply<double>(P, state, e, s));
       }
-      double beta2;
-      CK(dev_norm2(K, V, &beta2));
-      const double beta = std::sqrt(beta2);
-      K.hsc[0] = beta;
-      CK(cudaMemcpyAsync(K.dsc, K.hsc, sizeof(double), cudaMemcpyHostToDevice, s));
-      scale_kernel<<<K.nblocks, KRY_THREADS, 0, s>>>(V, V, K.dsc, 1, N);
+      dots(K, nullptr, 0, V, 1, d_nrm);
+      scale_kernel<<<1024, KRY_THREADS, 0, s>>>(V, V, d_nrm, 2, N);
+      ++g_launches;
+      CK(fetch(K, KRY_MAXV, 1));
+      const double beta = std::sqrt(K.hsc[KRY_MAXV]);
       std::fill(g.begin(), g.end(), 0.0);
       g[0] = beta;
       // inner target on the preconditioned residual, scaled to the true-residual goal
@@ -661,23 +658,25 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
           e.out = w; e.ax = 1.0; e.bl = half; e.jacobi = 1; e.cj = half;
           CK(launch_apply<double>(P, V + (size_t)j * N, e, s));
         }
-        // classical Gram--Schmidt, twice
-        for (int pass = 0; pass < 2; ++pass) {
-          multidot_kernel<<<K.nblocks, KRY_THREADS, 0, s>>>(V, N, j + 1, w, N, K.partial);
-          reduce_partials_kernel<<<1, 32, 0, s>>>(K.partial, K.nblocks, j + 1, K.dsc + pass * KRY_MAXV);
-          update_kernel<<<K.nblocks, KRY_THREADS, 0, s>>>(V, N, j + 1, K.dsc + pass * KRY_MAXV, w, N,
-                                                          pass == 1 ? K.partial : nullptr);
+        // classical Gram--Schmidt with selective re-orthogonalisation (|w'| < |w|/sqrt(2))
+        dots(K, V, j + 1, w, 1, d_h1);
+        update(K, V, j + 1, d_h1, w, d_nrm);
+        CK(fetch(K, 0, KRY_MAXV + 1));
+        for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] = K.hsc[i2];
+        const double wn0 = std::sqrt(K.hsc[j + 1]);
+        double wn = std::sqrt(K.hsc[KRY_MAXV]);
+        if (wn < 0.7071067811865476 * wn0) {
+          dots(K, V, j + 1, w, 0, d_h2);
+          update(K, V, j + 1, d_h2, w, d_nrm);
+          CK(fetch(K, 2 * KRY_MAXV, j + 1));
+          CK(fetch(K, KRY_MAXV, 1));
+          for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] += K.hsc[2 * KRY_MAXV + i2];
+          wn = std::sqrt(K.hsc[KRY_MAXV]);
         }
-        reduce_partials_kernel<<<1, 32, 0, s>>>(K.partial, K.nblocks, 1, K.dsc + 2 * KRY_MAXV);
-        CK(cudaMemcpyAsync(K.hsc, K.dsc, sizeof(double) * 3 * KRY_MAXV, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] = K.hsc[i2] + K.hsc[KRY_MAXV + i2];
-        const double hn = std::sqrt(K.hsc[2 * KRY_MAXV]);
-        H[(size_t)(j + 1) * m + j] = hn;
-        if (hn > 0.0) {
-          K.hsc[3 * KRY_MAXV] = hn;
-          CK(cudaMemcpyAsync(K.dsc + 3 * KRY_MAXV, K.hsc + 3 * KRY_MAXV, sizeof(double), cudaMemcpyHostToDevice, s));
-          scale_kernel<<<K.nblocks, KRY_THREADS, 0, s>>>(w, w, K.dsc + 3 * KRY_MAXV, 1, N);
+        H[(size_t)(j + 1) * m + j] = wn;
+        if (wn > 0.0) {
+          scale_kernel<<<1024, KRY_THREADS, 0, s>>>(w, w, d_nrm, 2, N);
+          ++g_launches;
         }
         for (int i2 = 0; i2 < j; ++i2) {
           const double a0 = H[(size_t)i2 * m + j], a1 = H[(size_t)(i2 + 1) * m + j];
@@ -694,7 +693,7 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
         g[j] = cs[j] * g[j];
         ++its;
         jdone = j + 1;
-        if (std::fabs(g[j + 1]) <= target || hn == 0.0) break;
+        if (std::fabs(g[j + 1]) <= target || wn == 0.0) break;
       }
       // y = H^-1 g ; zeta += V y
       for (int i2 = jdone - 1; i2 >= 0; --i2) {
@@ -702,27 +701,29 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
         for (int k2 = i2 + 1; k2 < jdone; ++k2) v -= H[(size_t)i2 * m + k2] * y[k2];
         y[i2] = v / H[(size_t)i2 * m + i2];
       }
-      for (int i2 = 0; i2 < jdone; ++i2) K.hsc[i2] = y[i2];
-      CK(cudaMemcpyAsync(K.dsc, K.hsc, sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
-      combine_kernel<<<K.nblocks, KRY_THREADS, 0, s>>>(V, N, jdone, K.dsc, state, N);
+      for (int i2 = 0; i2 < jdone; ++i2) K.hsc[3 * KRY_MAXV + i2] = y[i2];
+      CK(cudaMemcpyAsync(d_y, K.hsc + 3 * KRY_MAXV, sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
+      combine_kernel<<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, d_y, state, N);
+      ++g_launches;
       CK(cudaGetLastError());
     }
     total_its += its;
     max_its = std::max(max_its, its);
     last_rel = rel;
     if (rel > tol) {
-      status = SAP_ENOCONV;
       c->err = "cn: GMRES did not reach the tolerance within maxit";
       if (st) {
         st->steps = step + 1; st->iterations = total_its; st->max_iterations = max_its; st->last_rel_residual = rel;
+        st->kernel_launches = g_launches - launches0;
       }
-      return status;
+      return SAP_ENOCONV;
     }
   }
   if (st) {
     st->steps = nsteps; st->iterations = total_its; st->max_iterations = max_its; st->last_rel_residual = last_rel;
+    st->kernel_launches = g_launches - launches0;
   }
-  return status;
+  return SAP_OK;
 cuda_fail:
   c->err = std::string("cn: ") + cudaGetErrorString(err);
   return SAP_ECUDA;

@@ -20,7 +20,7 @@ constexpr int MAT_I = -1;        // identity "matrix"
 // spatial field components stored per spatial volume point
 enum : int { SF_ONE = -1, SF_U = 0, SF_G = 3, SF_DU = 12, SF_B = 15, SF_NCOMP = 18 };
 // momentum factors, functions of the momentum p at a node or face
-enum : int { MF_ONE = 0, MF_P, MF_GM, MF_V, MF_INV_V, MF_INV_GM, MF_INV_P, MF_INV_GMP, MF_GM_OVER_P };
+enum : int { MF_ONE = 0, MF_P, MF_GM, MF_V, MF_INV_V, MF_INV_GM, MF_INV_P, MF_INV_GMP, MF_GM_OVER_P, MF_COUNT };
 
 struct Term {
   int mat;      // matrix id in the bank, or MAT_I
@@ -84,6 +84,9 @@ struct OpParams {
   T s_uni;
   const T* pnode;                  // [npc*q] momentum p at nodes
   const T* pface;                  // [npc+1] momentum p at faces
+  const T* mfn;                    // [MF_COUNT][npc*q] momentum factors at nodes
+  const T* mff;                    // [MF_COUNT][npc+1] momentum factors at faces
+  int npn;                         // npc*q
   T Vmono;
   // momentum-face |beta| per point
   const int* pslot;                // [nsv] slot or -1
@@ -126,6 +129,8 @@ struct sap_ctx {
   double* small = nullptr;                     // small device scratch for reductions/scalars
   double* small_host = nullptr;                // pinned mirror
   int krylov_restart = 0;
+  std::vector<double> bank_nnz;                // nnz per bank matrix (cost model)
+  int64_t launches = 0;                        // kernels launched by the current call
 };
 
 namespace sap {
@@ -136,4 +141,6 @@ sap_status erk_steps(sap_ctx* c, double* state, double dt, int nsteps, cudaStrea
 sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
                     sap_solver_stats* st, cudaStream_t s);
 int apply_cells_per_block(int n, int nloc);
+int64_t launch_count();
+int64_t krylov_scratch_doubles(int64_t N);
 }  // namespace sap

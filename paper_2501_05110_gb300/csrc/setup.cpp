@@ -143,6 +143,23 @@ static std::string validate(const sap_desc* d) {
   return "";
 }
 
+static double mom_factor_h(int mf, double p, bool has_mom, double Vm) {
+  if (mf == MF_ONE) return 1.0;
+  if (!has_mom) return mf == MF_V ? Vm : (mf == MF_INV_V ? 1.0 / Vm : 1.0);
+  double gm = std::sqrt(1.0 + p * p);
+  switch (mf) {
+    case MF_P: return p;
+    case MF_GM: return gm;
+    case MF_V: return p / gm;
+    case MF_INV_V: return gm / p;
+    case MF_INV_GM: return 1.0 / gm;
+    case MF_INV_P: return 1.0 / p;
+    case MF_INV_GMP: return 1.0 / (gm * p);
+    case MF_GM_OVER_P: return gm / p;
+  }
+  return 1.0;
+}
+
 template <typename T>
 static void fill_1d_tables(sap_ctx* c, OpParams<T>& P) {
   const int q = c->q;
@@ -281,20 +298,31 @@ extern "C" sap_status sap_create(const sap_desc* desc, int prec, sap_handle* out
     float* d_pn32 = (float*)upload(c, to_f32(c->pnode), own);
     double* d_pf64 = (double*)upload(c, c->pface, own);
     float* d_pf32 = (float*)upload(c, to_f32(c->pface), own);
-    auto base = [&](auto& P, auto* ih, auto* pn, auto* pf) {
+    // momentum factor tables (MF_*) at nodes and faces
+    const int npn = (int)c->pnode.size(), npf = (int)c->pface.size();
+    std::vector<double> mfn((size_t)MF_COUNT * npn), mff((size_t)MF_COUNT * npf);
+    for (int mf = 0; mf < MF_COUNT; ++mf) {
+      for (int i = 0; i < npn; ++i) mfn[(size_t)mf * npn + i] = mom_factor_h(mf, c->pnode[i], c->has_mom, desc->V);
+      for (int i = 0; i < npf; ++i) mff[(size_t)mf * npf + i] = mom_factor_h(mf, c->pface[i], c->has_mom, desc->V);
+    }
+    double* d_mfn64 = (double*)upload(c, mfn, own);
+    float* d_mfn32 = (float*)upload(c, to_f32(mfn), own);
+    double* d_mff64 = (double*)upload(c, mff, own);
+    float* d_mff32 = (float*)upload(c, to_f32(mff), own);
+    auto base = [&](auto& P, auto* ih, auto* pn, auto* pf, auto* mn, auto* mfc) {
       P.D = c->D; P.dx = c->dx; P.q = c->q; P.nloc = c->nloc; P.nfp = c->nfp; P.n = c->n;
       P.ncell = c->ncell; P.has_mom = c->has_mom; P.qdx = c->qdx;
       for (int a = 0; a < 3; ++a) P.nc[a] = c->nc[a];
       P.cell_nb = d_nb; P.cell_scell = d_sc; P.cell_pcell = d_pc; P.scell_face = d_sf;
-      P.cell_invh = ih; P.pnode = pn; P.pface = pf; P.npface = c->npc + 1;
+      P.cell_invh = ih; P.pnode = pn; P.pface = pf; P.npface = npf; P.mfn = mn; P.mff = mfc; P.npn = npn;
       P.nsv = c->nsv;
       P.Vmono = c->has_mom ? 1 : desc->V;
       fill_1d_tables(c, P);
     };
-    base(c->p64, d_ih64, d_pn64, d_pf64);
-    base(c->p32, d_ih32, d_pn32, d_pf32);
+    base(c->p64, d_ih64, d_pn64, d_pf64, d_mfn64, d_mff64);
+    base(c->p32, d_ih32, d_pn32, d_pf32, d_mfn32, d_mff32);
     // small reduction scratch
-    if (cudaMalloc(&c->small, sizeof(double) * (152 * 8 * 32 + 8 * 32)) != cudaSuccess) throw std::string("cudaMalloc failed");
+    if (cudaMalloc(&c->small, sizeof(double) * krylov_scratch_doubles(c->N)) != cudaSuccess) throw std::string("cudaMalloc failed");
     if (cudaMallocHost(&c->small_host, sizeof(double) * 8 * 32) != cudaSuccess) throw std::string("cudaMallocHost failed");
   } catch (const std::string& e) {
     g_create_error = "sap_create: " + e;
@@ -433,23 +461,6 @@ struct BankBuilder {
   }
 };
 
-static double mom_factor_h(int mf, double p, bool has_mom, double Vm) {
-  if (mf == MF_ONE) return 1.0;
-  if (!has_mom) return mf == MF_V ? Vm : (mf == MF_INV_V ? 1.0 / Vm : 1.0);
-  double gm = std::sqrt(1.0 + p * p);
-  switch (mf) {
-    case MF_P: return p;
-    case MF_GM: return gm;
-    case MF_V: return p / gm;
-    case MF_INV_V: return gm / p;
-    case MF_INV_GM: return 1.0 / gm;
-    case MF_INV_P: return 1.0 / p;
-    case MF_INV_GMP: return 1.0 / (gm * p);
-    case MF_GM_OVER_P: return gm / p;
-  }
-  return 1.0;
-}
-
 template <typename T>
 static void set_bank(OpParams<T>& P, const BankBuilder& B, sap_ctx* c, std::vector<DevBuf>& own) {
   std::vector<int> rp, col;
@@ -467,6 +478,8 @@ static void set_bank(OpParams<T>& P, const BankBuilder& B, sap_ctx* c, std::vect
     val.push_back(0.0);
   }
   if (rp.empty()) rp.push_back(0);
+  c->bank_nnz.clear();
+  for (size_t m = 0; m < B.mats.size(); ++m) c->bank_nnz.push_back((double)B.mats[m].col.size());
   P.bank.rp = (const int*)upload(c, rp, own);
   P.bank.col = (const int*)upload(c, col, own);
   if (sizeof(T) == 8) P.bank.val = (const T*)upload(c, val, own);
@@ -824,6 +837,45 @@ extern "C" sap_status sap_step_cn(sap_handle c, double* state, double dt, int ns
     return SAP_ENOMEM;
   }
   return cn_steps(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
+}
+
+extern "C" sap_status sap_apply_cost(sap_handle c, double* flops, double* bytes) {
+  if (!c || !flops || !bytes || !c->fields_set) return SAP_EINVAL;
+  const OpParams<double>& P = c->p64;
+  const int n = c->n, nloc = c->nloc, nfp = c->nfp, q = c->q, D = c->D;
+  auto nnz_row_avg = [&](int mat) -> double {
+    if (mat == MAT_I) return 1.0;
+    const std::vector<int>* rp = nullptr;
+    (void)rp;
+    return c->bank_nnz[mat] / double(n);
+  };
+  double per_cell = 0.0;
+  int nvt = P.nreact;
+  for (int a = 0; a < D; ++a) nvt += P.ax[a].nadv;
+  per_cell += 4.0 * nvt * nloc;                       // coefficient tables
+  const double faces = 2.0 * D * n * nfp;            // face entries per cell
+  per_cell += 2.0 * faces * 2.0 * q;                  // own + neighbour traces
+  per_cell += 2.0 * faces;                            // sum / difference
+  for (int a = 0; a < D; ++a) {
+    const AxisInfo& A = P.ax[a];
+    if (!A.active) continue;
+    const double fe = 2.0 * n * nfp;  // this axis' face entries per cell
+    double f = 1.0;
+    for (int t = 0; t < A.nadv; ++t) f += 2.0 * nnz_row_avg(A.adv[t].mat) + 2.0;
+    if (A.route == ABS_EIGEN) f += 2.0 * nnz_row_avg(A.WTmat) + 3.0 + 2.0 * nnz_row_avg(A.Wmat) + 2.0;
+    else f += 2.0 * nnz_row_avg(A.absmat) + 1.0;
+    per_cell += fe * f;
+    double v = 0.0;  // volume advection per DoF
+    for (int t = 0; t < A.nadv; ++t) v += 2.0 * nnz_row_avg(A.adv[t].mat) + 2.0;
+    v += 2.0 * q + 6.0;  // derivative and lifts
+    per_cell += v * n * nloc;
+  }
+  double rx = 0.0;
+  for (int t = 0; t < P.nreact; ++t) rx += 2.0 * nnz_row_avg(P.react[t].mat) + 2.0;
+  per_cell += (rx + 4.0) * n * nloc;
+  *flops = per_cell * c->ncell;
+  *bytes = 2.0 * (double)c->N * (c->prec == SAP_PREC_FP64 ? 8.0 : 4.0);
+  return SAP_OK;
 }
 
 extern "C" sap_status sap_destroy(sap_handle c) {

@@ -23,7 +23,8 @@ APPLY_D, APPLY_RHS = 0, 1
 PTS_SPATIAL, PTS_FACE_X, PTS_FACE_Y, PTS_FACE_Z, PTS_PHASE = range(5)
 
 EXPORTS = ["sap_create", "sap_field_points", "sap_set_fields", "sap_num_dofs", "sap_apply_operator",
-           "sap_step_erk", "sap_step_cn", "sap_destroy", "sap_last_error", "sap_coupling_matrix"]
+           "sap_step_erk", "sap_step_cn", "sap_apply_cost", "sap_destroy", "sap_last_error",
+           "sap_coupling_matrix"]
 
 
 class SapError(RuntimeError):
@@ -40,7 +41,7 @@ class Desc(C.Structure):
 
 class SolverStats(C.Structure):
     _fields_ = [("steps", C.c_int), ("iterations", C.c_int64), ("max_iterations", C.c_int),
-                ("last_rel_residual", C.c_double)]
+                ("last_rel_residual", C.c_double), ("kernel_launches", C.c_int64)]
 
 
 _lib = None
@@ -63,6 +64,7 @@ def load_library(path: str = LIB_PATH):
     lib.sap_step_erk.argtypes = [vp, vp, C.c_double, C.c_int, vp]
     lib.sap_step_cn.argtypes = [vp, vp, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
                                 C.POINTER(SolverStats), vp]
+    lib.sap_apply_cost.argtypes = [vp, dp, dp]
     lib.sap_destroy.argtypes = [vp]
     lib.sap_last_error.argtypes = [vp]
     lib.sap_last_error.restype = C.c_char_p
@@ -196,6 +198,12 @@ class Solver:
         self._check(self.lib.sap_step_cn(self.h, C.c_void_p(state.data_ptr()), dt, nsteps, tol, restart, maxit,
                                          C.byref(st), _stream_handle(stream)))
         return st
+
+    def apply_cost(self):
+        """(flops, bytes) of one operator apply, from the library's cost model."""
+        f, b = C.c_double(), C.c_double()
+        self._check(self.lib.sap_apply_cost(self.h, C.byref(f), C.byref(b)))
+        return f.value, b.value
 
     def close(self):
         if getattr(self, "h", None):
