@@ -141,6 +141,24 @@ sap_status sap_step_erk(sap_handle h, double* state, double dt, int nsteps, sap_
 sap_status sap_step_cn(sap_handle h, double* state, double dt, int nsteps, double tol, int restart,
                        int maxit, sap_solver_stats* stats, sap_stream stream);
 
+/* Largest N (degrees of freedom) that sap_step_erk_noalloc accepts. */
+#define SAP_NOALLOC_MAX_DOFS 262144
+
+/* Same RK4 steps as sap_step_erk, but without allocating device memory.  The paper has no
+ * counterpart: this is an interface for callers that cannot allocate, for instance code that
+ * captures the step into a CUDA graph with a global-mode stream capture (where cudaMalloc is not
+ * allowed), a framework whose own allocator must account for every byte of device memory, or a
+ * loop that cannot absorb the device-wide synchronisation of cudaMalloc/cudaFree.
+ * The stage buffers (two stage inputs and the accumulator, at most 24 bytes per DoF) live in one
+ * fixed array of 24 * SAP_NOALLOC_MAX_DOFS bytes (6 MiB) that every GPU which loads the library
+ * holds until the process exits.  The first call on each device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call before any stream
+ * capture.  Every call shares the one array and it keeps the last call's contents; each step
+ * writes every scratch value before reading it, so nothing needs clearing.  Calls that overlap on
+ * the GPU (other streams, threads or handles on the same device) race on the array.
+ * Errors: SAP_EINVAL (N > SAP_NOALLOC_MAX_DOFS, fields not set, bad arguments), SAP_ECUDA. */
+sap_status sap_step_erk_noalloc(sap_handle h, double* state, double dt, int nsteps, sap_stream stream);
+
 /* Algorithmic cost of one sap_apply_operator call on this context: `flops` = floating-point
  * operations (an FMA counts 2) summed from the kernel's term tables (coefficient set-up, traces,
  * upwind fluxes, volume terms, lifts); `bytes` = 2 N w (read x, write y; w = word size of the

@@ -20,6 +20,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "sap_internal.h"
@@ -424,6 +426,55 @@ static cudaError_t erk_impl(sap_ctx* c, const OpParams<T>& P, T* ya, T* yb, doub
     if ((err = launch_apply<T>(P, out3, e, s)) != cudaSuccess) return err;
   }
   return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------------------------
+// RK4 without allocation: stage buffers in a file-scope device array (see sap_step_erk_noalloc)
+// ------------------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[24 * (size_t)SAP_NOALLOC_MAX_DOFS];
+
+sap_status erk_steps_noalloc(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s) {
+  if (c->N > SAP_NOALLOC_MAX_DOFS) {
+    c->err = "sap_step_erk_noalloc: N = " + std::to_string(c->N) + " exceeds SAP_NOALLOC_MAX_DOFS = " +
+             std::to_string((long long)SAP_NOALLOC_MAX_DOFS);
+    return SAP_EINVAL;
+  }
+  // host code cannot use the array's name as a device address: look it up once per device
+  static std::mutex mu;
+  static void* addr[128] = {nullptr};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess || dev < 0 || dev >= 128) {
+    c->err = "sap_step_erk_noalloc: cudaGetDevice failed";
+    return SAP_ECUDA;
+  }
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+      err = cudaGetSymbolAddress(&addr[dev], g_noalloc_scratch);
+      if (err != cudaSuccess) {
+        addr[dev] = nullptr;
+        c->err = std::string("sap_step_erk_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(err);
+        return SAP_ECUDA;
+      }
+    }
+    base = addr[dev];
+  }
+  const size_t N = (size_t)c->N;
+  if (c->prec == SAP_PREC_FP64) {
+    double* ya = static_cast<double*>(base);
+    err = erk_impl<double>(c, c->p64, ya, ya + N, ya + 2 * N, state, dt, nsteps, s);
+  } else {
+    float* ya = static_cast<float*>(base);
+    double* acc = reinterpret_cast<double*>(ya + 2 * N);  // byte offset 8N: 8-byte aligned
+    err = erk_impl<float>(c, c->p32, ya, ya + N, acc, state, dt, nsteps, s);
+  }
+  if (err != cudaSuccess) {
+    c->err = std::string("erk_noalloc: ") + cudaGetErrorString(err);
+    return SAP_ECUDA;
+  }
+  return SAP_OK;
 }
 
 sap_status erk_steps(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s) {

@@ -138,6 +138,7 @@ namespace sap {
 cudaError_t launch_apply64(const OpParams<double>& p, const double* x, double* y, int mode, cudaStream_t s);
 cudaError_t launch_apply32(const OpParams<float>& p, const float* x, float* y, int mode, cudaStream_t s);
 sap_status erk_steps(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s);
+sap_status erk_steps_noalloc(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s);
 sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
                     sap_solver_stats* st, cudaStream_t s);
 int apply_cells_per_block(int n, int nloc);

@@ -821,6 +821,15 @@ extern "C" sap_status sap_step_erk(sap_handle c, double* state, double dt, int n
   return erk_steps(c, state, dt, nsteps, (cudaStream_t)stream);
 }
 
+extern "C" sap_status sap_step_erk_noalloc(sap_handle c, double* state, double dt, int nsteps, sap_stream stream) {
+  if (!c || !state || nsteps < 0) return SAP_EINVAL;
+  if (!c->fields_set) {
+    c->err = "fields not set";
+    return SAP_EINVAL;
+  }
+  return erk_steps_noalloc(c, state, dt, nsteps, (cudaStream_t)stream);
+}
+
 extern "C" sap_status sap_step_cn(sap_handle c, double* state, double dt, int nsteps, double tol, int restart,
                                   int maxit, sap_solver_stats* stats, sap_stream stream) {
   if (!c || !state || nsteps < 0 || restart < 1 || restart > 31 || maxit < 1 || !(tol > 0)) return SAP_EINVAL;

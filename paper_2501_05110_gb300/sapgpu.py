@@ -23,7 +23,7 @@ APPLY_D, APPLY_RHS = 0, 1
 PTS_SPATIAL, PTS_FACE_X, PTS_FACE_Y, PTS_FACE_Z, PTS_PHASE = range(5)
 
 EXPORTS = ["sap_create", "sap_field_points", "sap_set_fields", "sap_num_dofs", "sap_apply_operator",
-           "sap_step_erk", "sap_step_cn", "sap_apply_cost", "sap_destroy", "sap_last_error",
+           "sap_step_erk", "sap_step_erk_noalloc", "sap_step_cn", "sap_apply_cost", "sap_destroy", "sap_last_error",
            "sap_coupling_matrix"]
 
 
@@ -62,6 +62,7 @@ def load_library(path: str = LIB_PATH):
     lib.sap_num_dofs.argtypes = [vp, i64p]
     lib.sap_apply_operator.argtypes = [vp, vp, vp, C.c_int, vp]
     lib.sap_step_erk.argtypes = [vp, vp, C.c_double, C.c_int, vp]
+    lib.sap_step_erk_noalloc.argtypes = [vp, vp, C.c_double, C.c_int, vp]
     lib.sap_step_cn.argtypes = [vp, vp, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
                                 C.POINTER(SolverStats), vp]
     lib.sap_apply_cost.argtypes = [vp, dp, dp]
@@ -190,6 +191,12 @@ class Solver:
 
     def step_erk(self, state, dt: float, nsteps: int, stream=None):
         self._check(self.lib.sap_step_erk(self.h, C.c_void_p(state.data_ptr()), dt, nsteps, _stream_handle(stream)))
+        return state
+
+    def step_erk_noalloc(self, state, dt: float, nsteps: int, stream=None):
+        """RK4 steps that allocate no device memory (stage buffers in the library's fixed array)."""
+        self._check(self.lib.sap_step_erk_noalloc(self.h, C.c_void_p(state.data_ptr()), dt, nsteps,
+                                                  _stream_handle(stream)))
         return state
 
     def step_cn(self, state, dt: float, nsteps: int, tol: float = 1e-10, restart: int = 30, maxit: int = 2000,

@@ -1,0 +1,73 @@
+"""sap_step_erk_noalloc: RK4 steps for callers that cannot allocate device memory.
+
+Some callers cannot call cudaMalloc: code that captures the step with a global-mode stream capture,
+frameworks whose allocator must own every byte of device memory, loops that cannot absorb the
+synchronisation of cudaMalloc/cudaFree.  For them the library keeps its RK4 stage buffers in one
+fixed device array.  This test calls that entry point through the C ABI and checks it against the
+allocating entry point sap_step_erk, on two calls in a row, and checks that it rejects a problem
+larger than the array.  It runs last in the suite (file name) and also passes alone.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2501_05110_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12  # the FP64 parity tolerance of the other GPU tests (relative)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2501_05110_gb300 import build as sap_build
+    sap_build.build()
+    return torch
+
+
+@pytest.mark.parametrize("which", ["periodic1d", "shock"])
+def test_noalloc_matches_allocating_erk(torch_cuda, which):
+    from paper_2501_05110_gb300 import sapgpu
+    torch = torch_cuda
+    prob = W.periodic_1d() if which == "periodic1d" else W.shock(nx=32, npc=16, lmax=3)
+    lib = sapgpu.load_library()
+    sol = sapgpu.Solver(prob)
+    assert sol.N <= 262144
+    rng = np.random.default_rng(7)
+    y0 = torch.from_numpy(rng.standard_normal(sol.N)).cuda()
+    # load the kernels once so that the memory check below sees only the step itself
+    tmp = torch.empty_like(y0)
+    sol.apply(y0, tmp)
+    torch.cuda.synchronize()
+    y_ref = y0.clone()
+    y_na = y0.clone()
+    stream = torch.cuda.current_stream()
+    dt = 1e-3 if which == "periodic1d" else 0.05
+    for call in range(2):
+        free_before = torch.cuda.mem_get_info()[0]
+        st = lib.sap_step_erk_noalloc(sol.h, C.c_void_p(y_na.data_ptr()), dt, 3, C.c_void_p(stream.cuda_stream))
+        assert st == sapgpu.SAP_OK, lib.sap_last_error(sol.h)
+        torch.cuda.synchronize()
+        free_after = torch.cuda.mem_get_info()[0]
+        assert free_after >= free_before, "the no-alloc step changed free device memory"
+        sol.step_erk(y_ref, dt, 3)
+        torch.cuda.synchronize()
+        a, b = y_na.cpu().numpy(), y_ref.cpu().numpy()
+        assert np.linalg.norm(a - b) <= TOL * np.linalg.norm(b), f"call {call}"
+    sol.close()
+
+
+def test_noalloc_rejects_oversize(torch_cuda):
+    from paper_2501_05110_gb300 import sapgpu
+    torch = torch_cuda
+    prob = W.shock(nx=65, npc=64, lmax=3)  # 266,240 DoFs > 262,144
+    lib = sapgpu.load_library()
+    sol = sapgpu.Solver(prob)
+    y = torch.zeros(sol.N, dtype=torch.float64, device="cuda")
+    st = lib.sap_step_erk_noalloc(sol.h, C.c_void_p(y.data_ptr()), 0.1, 1, None)
+    assert st == sapgpu.SAP_EINVAL
+    assert b"SAP_NOALLOC_MAX_DOFS" in lib.sap_last_error(sol.h)
+    sol.close()
