@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--workload", default="shock", choices=["shock"])
+    ap.add_argument("--workload", default="shock", choices=["shock", "box3d"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--apply-reps", type=int, default=200)
@@ -293,8 +294,62 @@ def run_cpu_oracle_steps(warmup: int, steps: int) -> dict:
     return run_cpu_oracle(warmup + steps, skip=warmup)
 
 
+def run_box3d(args):
+    """RK4 on the 48^3 periodic box (k = 2, lmax = 5, N = 107,495,424): DoF-updates/s per RK4
+    stage; the state (0.86 GB FP64) is larger than L2, so no flush is needed between steps."""
+    import torch
+    from paper_2501_05110_gb300 import build as sap_build
+    from paper_2501_05110_gb300 import sapgpu
+    from paper_2501_05110_gb300 import workloads as W
+    sap_build.build()
+    prob = W.box3d()
+    sol = sapgpu.Solver(prob, args.precision)
+    N = sol.N
+    stream = torch.cuda.current_stream()
+    y = sol.initial_state()
+    for _ in range(args.warmup):
+        sol.step_erk(y, prob.dt, 1)
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sol.step_erk(y, prob.dt, args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    clk = clocks.stop()
+    t = e0.elapsed_time(e1) * 1e-3
+    flops, abytes = sol.apply_cost()
+    x = (y if args.precision == "fp64" else y.float()).clone()
+    out = torch.empty_like(x)
+    for _ in range(3):
+        sol.apply(x, out)
+    e0.record(stream)
+    for _ in range(args.apply_reps):
+        sol.apply(x, out)
+    e1.record(stream)
+    e1.synchronize()
+    t_apply = e0.elapsed_time(e1) * 1e-3 / args.apply_reps
+    w = 8 if args.precision == "fp64" else 4
+    stage_bytes = N * 5 * 8 if args.precision == "fp64" else N * (2 * 4 + 3 * 8)
+    print(json.dumps({"metric": "phase-space DoF-updates/s per ERK stage", "value": N * 4 * args.steps / t,
+                      "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+                      "dtype": "f64" if args.precision == "fp64" else "f32 apply, f64 state",
+                      "data": "synthetic", "config": {"workload": "box3d_48c_k2_l5_erk4_dt0.01", "dofs": N,
+                                                      "l2": "state larger than L2"},
+                      "apply": {"us": t_apply * 1e6, "flops": flops, "tflops": flops / t_apply / 1e12,
+                                "algorithmic_bytes": abytes, "gbs": abytes / t_apply / 1e9,
+                                "hbm_frac": abytes / t_apply / 1e9 / 6746.3},
+                      "stage_algorithmic_bytes_per_dof": stage_bytes / N,
+                      "stage_gbs": stage_bytes * 4 * args.steps / t / 1e9, "clocks": clk}))
+
+
 def main():
     args = parse()
+    if args.workload == "box3d" and not args.cpu_worker:
+        run_box3d(args)
+        return
     if args.cpu_worker:
         cpu_worker(args.cpu_worker)
         return

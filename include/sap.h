@@ -61,7 +61,7 @@ enum { SAP_PREC_FP64 = 0, SAP_PREC_FP32 = 1 };
 /* apply modes */
 enum { SAP_APPLY_D = 0,        /* y = M^-1 D x                       */
        SAP_APPLY_RHS = 1,      /* y = M^-1 (h - D x)  (ERK right side) */
-       SAP_APPLY_DT = 2 };     /* y = M^-1 D^T M x  (adjoint of M^-1 D in the M inner product) */
+       SAP_APPLY_T = 2 };      /* y = (M^-1 D)^T x: transpose of the nodal operator (discrete adjoint) */
 /* point sets reported by sap_field_points */
 enum { SAP_PTS_SPATIAL = 0,    /* spatial volume points (nsv x dim_x), fields U, gradU, DUDt, B   */
        SAP_PTS_FACE_X = 1,     /* spatial face points normal to x (nsf x dim_x), field U_x         */
@@ -97,6 +97,20 @@ typedef struct {
  * SAP_ECUDA.  On failure *out is NULL. */
 sap_status sap_create(const sap_desc* desc, int prec, sap_handle* out);
 
+/* Create a batch of `ninst` independent problems (one descriptor each; different lmax, degree,
+ * meshes and fields allowed) that run together: every operator apply is one kernel launch over all
+ * instances, and sap_step_cn runs one restarted GMRES per instance in lock-step (own Krylov space,
+ * Hessenberg matrix and convergence test; finished instances are masked out).  The batch state is
+ * the concatenation of the instances' canonical states (offsets from sap_batch_instance).  The
+ * thread-block size is autotuned on the first compute call by timing the batched apply.
+ * sap_apply_operator, sap_step_erk and sap_step_cn accept the batch handle.  Fields are set per
+ * instance through the sub-handles of sap_batch_instance.  Errors as sap_create. */
+sap_status sap_create_batch(int ninst, const sap_desc* descs, int prec, sap_handle* out);
+
+/* Sub-handle of instance `inst` of a batch (for sap_field_points, sap_set_fields, sap_num_dofs; owned
+ * by the batch, not to be destroyed) and the instance's first element in the batch state. */
+sap_status sap_batch_instance(sap_handle batch, int inst, sap_handle* sub, int64_t* offset);
+
 /* Number of points and their coordinates for a point set (SAP_PTS_*).  If `coords` is NULL only
  * *count is written; otherwise `coords` (host) receives count x dim coordinates, dim = number of
  * spatial axes (momentum coordinates are p, not ln p, for SAP_PTS_PHASE's momentum column when the
@@ -122,7 +136,10 @@ sap_status sap_num_dofs(sap_handle h, int64_t* n);
 /* Apply the semi-discrete operator (Eq. definition-mass-and-dg-matrix) to a device vector x,
  * writing device vector y (x != y, both canonical layout, N elements of the context's precision:
  * double for SAP_PREC_FP64, float for SAP_PREC_FP32).  mode SAP_APPLY_D: y = M^-1 D x;
- * SAP_APPLY_RHS: y = M^-1 (h - D x).  Asynchronous on `stream`.  Errors: SAP_EINVAL, SAP_ECUDA. */
+ * SAP_APPLY_RHS: y = M^-1 (h - D x); SAP_APPLY_T: y = (M^-1 D)^T x, the transpose of the nodal
+ * operator, built term by term (transposed couplings, S^T along lines, face lifts and traces
+ * exchanged, upwind splits beta+/beta- per side).  Asynchronous on `stream`.
+ * Errors: SAP_EINVAL, SAP_ECUDA. */
 sap_status sap_apply_operator(sap_handle h, const void* x, void* y, int mode, sap_stream stream);
 
 /* Advance the FP64 device state (canonical layout, N doubles, in place) by `nsteps` classical RK4

@@ -300,6 +300,7 @@ class Discretisation:
             self._add(np.broadcast_to(rows, blk.shape), np.broadcast_to(cols, blk.shape), blk)
         # mass matrix and load vector
         mass = np.einsum("cq,qa,qb->cab", W, Phi, Phi)
+        self.mass_blocks = mass  # per assembled cell (same block for every coefficient)
         self._mr, self._mc, self._mv = [], [], []
         for r in range(n):
             rows = self.dof(cells[:, None, None], r, a_idx[None, :, None])

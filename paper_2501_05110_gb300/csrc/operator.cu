@@ -42,6 +42,7 @@ struct Epi {
   T wb, ax, bl, gs;
   int jacobi;           // multiply out by 1 / (1 + cj * diag(R - div beta))
   T cj;
+  float* out32;         // optional: FP32 copy of out / (1 + cj * diag(R - div beta)), before `jacobi`
   // ERK stage (k = s - Lx):  acc += bdt k ; ynext = y0 + adt k ; final: state = acc + bdt k
   double* acc;
   const double* y0;
@@ -94,18 +95,20 @@ __device__ __forceinline__ int face_node(int fp, int j, int a, const int* qpow) 
   return lo + j * qpow[a] + hi * qpow[a + 1];
 }
 
+// Body of the apply for the cells [cell0, cell0 + cpb) of one problem whose state starts at element
+// `doff` of every state-sized vector (0 for a single problem, the instance offset in a batch).
 template <typename T>
-__global__ void __launch_bounds__(1024) apply_kernel(const OpParams<T> P, const T* __restrict__ x, const Epi<T> E,
-                                                     int cpb, int cell_stride) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __restrict__ x, const Epi<T>& E, int cpb,
+                                           int cell_stride, int cell0, int64_t doff, unsigned char* smem_raw) {
   T* sm = reinterpret_cast<T*>(smem_raw);
+  x += doff;
   const int n = P.n, nloc = P.nloc, nfp = P.nfp, D = P.D, q = P.q;
   const int per_cell = n * nloc;
   const int nf = 2 * D;
   const int lc = threadIdx.x / per_cell;
   const int t = threadIdx.x - lc * per_cell;
   const int r = t / nloc, i = t - r * nloc;
-  const int cell = blockIdx.x * cpb + lc;
+  const int cell = cell0 + lc;
   const bool valid = (lc < cpb) && (cell < P.ncell);
   int qpow[MAXD + 2];
   qpow[0] = 1;
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(1024) apply_kernel(const OpParams<T> P, const 
   for (int tt = 0; tt < P.nreact; ++tt) {
     const T c = CV[tt * nloc + i];
     acc += c * csr_row(P.bank, P.react[tt].mat, r, F + i, nloc);
-    if (E.jacobi) rdiag += c * csr_diag(P.bank, P.react[tt].mat, r);
+    if (E.jacobi || E.out32) rdiag += c * csr_diag(P.bank, P.react[tt].mat, r);
   }
   for (int a = 0; a < D; ++a) {
     if (!P.ax[a].active) continue;
@@ -310,7 +313,7 @@ __global__ void __launch_bounds__(1024) apply_kernel(const OpParams<T> P, const 
     const T jdn = Jf[((2 * a) * n + r) * nfp + fp];
     acc += invh * (P.L1[ia] * jup - P.L0[ia] * jdn - ds);
   }
-  const size_t dof = (size_t)cell * per_cell + t;
+  const size_t dof = (size_t)doff + (size_t)cell * per_cell + t;
   T s = T(0);
   if (r == 0) s = P.s000 ? __ldg(P.s000 + (size_t)cell * nloc + i) : P.s_uni;
   if (E.erk) {
@@ -327,8 +330,266 @@ __global__ void __launch_bounds__(1024) apply_kernel(const OpParams<T> P, const 
   }
   T o = E.ax * F[t] + E.bl * acc + E.gs * s;
   if (E.bvec) o += E.wb * __ldg(E.bvec + dof);
+  if (E.out32) E.out32[dof] = float(o / (T(1) + E.cj * rdiag));
   if (E.jacobi) o /= (T(1) + E.cj * rdiag);
-  E.out[dof] = o;
+  if (E.out) E.out[dof] = o;
+}
+
+// Transposed operator L^T = (M^-1 D)^T in the nodal basis (discrete adjoint).  Term by term:
+//   reaction  (R - div beta)^T per node (transposed couplings);
+//   volume    -(1/h_a) beta^a (S^T y along lines)          (beta^a symmetric);
+//   faces     per face g = E_lo^T y_lo - E_hi^T y_hi  (lift-weighted traces, E = lift of the forward
+//             operator), then the lo side receives T_lo^T beta+ g and the hi side T_hi^T beta- g,
+//             beta+- = (beta +- |beta|)/2; a missing side contributes 0 to g; a continuous
+//             boundary uses beta instead of beta+-.
+template <typename T>
+__device__ __forceinline__ void applyT_body(const OpParams<T>& P, const T* __restrict__ x, const Epi<T>& E, int cpb,
+                                            int cell_stride, int cell0, int64_t doff, unsigned char* smem_raw) {
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  x += doff;
+  const int n = P.n, nloc = P.nloc, nfp = P.nfp, D = P.D, q = P.q;
+  const int per_cell = n * nloc;
+  const int nf = 2 * D;
+  const int lc = threadIdx.x / per_cell;
+  const int t = threadIdx.x - lc * per_cell;
+  const int r = t / nloc, i = t - r * nloc;
+  const int cell = cell0 + lc;
+  const bool valid = (lc < cpb) && (cell < P.ncell);
+  int qpow[MAXD + 2];
+  qpow[0] = 1;
+#pragma unroll
+  for (int a = 1; a < MAXD + 2; ++a) qpow[a] = qpow[a - 1] * q;
+  int nvt = P.nreact;
+  int adv_off[MAXD];
+  for (int a = 0; a < D; ++a) {
+    adv_off[a] = nvt;
+    nvt += P.ax[a].nadv;
+  }
+  const int szT = nf * n * nfp;
+  T* F = sm + (size_t)(lc < cpb ? lc : 0) * cell_stride;
+  T* Jf = F + per_cell;
+  T* Tr = Jf + szT;
+  T* Tn = Tr + szT;
+  T* W1 = Tn + szT;
+  T* G = Tr;
+  const int region = (3 * szT > D * per_cell) ? 3 * szT : D * per_cell;
+  T* CV = Tr + region;
+  T* CF = CV + nvt * nloc;
+  const int scell = valid ? P.cell_scell[cell] : 0;
+  const int pcell = valid ? P.cell_pcell[cell] : 0;
+  if (valid) {
+    F[t] = x[(size_t)cell * per_cell + t];
+    for (int w = t; w < nvt * nloc; w += per_cell) {
+      const int tt = w / nloc, ii = w - tt * nloc;
+      const Term* tm;
+      if (tt < P.nreact) {
+        tm = &P.react[tt];
+      } else {
+        int a = 0;
+        while (a + 1 < D && tt >= adv_off[a + 1]) ++a;
+        tm = &P.ax[a].adv[tt - adv_off[a]];
+      }
+      const int sp = scell * P.qdx + ii % P.qdx;
+      T c = T(tm->scale) * spatial_factor(P, tm->sf, sp) * mom_node(P, tm->mf, pcell * q + ii / P.qdx);
+      if (tm->nu) c *= P.nu ? __ldg(P.nu + (size_t)cell * nloc + ii) : P.nu_uni;
+      CV[w] = c;
+    }
+    for (int w = t; w < nf * MAXADV * nfp; w += per_cell) {
+      const int f = w / (MAXADV * nfp);
+      const int tt = (w / nfp) % MAXADV;
+      const int fp = w % nfp;
+      const int a = f >> 1, side = f & 1;
+      const AxisInfo& A = P.ax[a];
+      if (!A.active || tt >= A.nadv) continue;
+      const Term& tm = A.adv[tt];
+      T c = T(tm.scale);
+      if (A.kind <= SAP_AXIS_Z) {
+        const int qsp = P.qdx / q;
+        const int fsp = fp % qsp;
+        if (tm.sf == SF_U + a) {
+          const int base = P.scell_face[scell * 2 * P.dx + 2 * a + side];
+          c *= P.uface_is_uni[a] ? P.uface_uni[a] : __ldg(P.uface[a] + base + fsp);
+        } else {
+          c *= spatial_factor(P, tm.sf, scell * P.qdx);
+        }
+        c *= mom_node(P, tm.mf, pcell * q + fp / qsp);
+      } else {
+        c *= spatial_factor(P, tm.sf, scell * P.qdx + fp);
+        c *= mom_face(P, tm.mf, pcell + side);
+      }
+      CF[w] = c;
+    }
+    // neighbour lift-weighted traces: lower face -> +E_lo^T y_nb (nb is lo), upper -> -E_hi^T y_nb
+    for (int w = t; w < szT; w += per_cell) {
+      const int f = w / (n * nfp);
+      const int rr = (w / nfp) % n;
+      const int fp = w % nfp;
+      const int a = f >> 1, side = f & 1;
+      const int nb = P.cell_nb[cell * nf + f];
+      T v = T(0);
+      if (nb >= 0 && P.ax[a].active) {
+        const T ihn = P.cell_invh[nb * D + a];
+        const T* xn = x + ((size_t)nb * n + rr) * nloc;
+        for (int j = 0; j < q; ++j) v += (side == 0 ? P.L1[j] : -P.L0[j]) * __ldg(xn + face_node(fp, j, a, qpow));
+        v *= ihn;
+      }
+      Tn[w] = v;
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    // own lift-weighted traces: lower face (I am hi) -> -E_hi^T y, upper face (I am lo) -> +E_lo^T y
+    const T* ihm = P.cell_invh + cell * D;
+    for (int w = t; w < szT; w += per_cell) {
+      const int f = w / (n * nfp);
+      const int rr = (w / nfp) % n;
+      const int fp = w % nfp;
+      const int a = f >> 1, side = f & 1;
+      T v = T(0);
+      const T* Fr = F + rr * nloc;
+      for (int j = 0; j < q; ++j) v += (side == 0 ? -P.L0[j] : P.L1[j]) * Fr[face_node(fp, j, a, qpow)];
+      Tr[w] = v * ihm[a];
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    // g = own + neighbour part (a boundary has no neighbour part)
+    for (int w = t; w < szT; w += per_cell) {
+      const int f = w / (n * nfp);
+      const int a = f >> 1;
+      if (!P.ax[a].active) continue;
+      Tr[w] += Tn[w];
+    }
+  }
+  __syncthreads();
+  // K g with K = beta+ (upper face), beta- (lower face), beta (continuous boundary)
+  if (valid) {
+    for (int w = t; w < szT; w += per_cell) {
+      const int f = w / (n * nfp);
+      const int rr = (w / nfp) % n;
+      const int fp = w % nfp;
+      const int a = f >> 1, side = f & 1;
+      const AxisInfo& A = P.ax[a];
+      if (!A.active) continue;
+      const int nb = P.cell_nb[cell * nf + f];
+      const int bc = side == 0 ? A.bc_lo : A.bc_hi;
+      const bool cont = (nb < 0) && (bc == SAP_BC_CONTINUOUS);
+      const T sgn = side == 1 ? T(1) : T(-1);
+      const T* Gb = Tr + f * n * nfp + fp;
+      T acc = T(0);
+      for (int tt = 0; tt < A.nadv; ++tt) acc += CF[(f * MAXADV + tt) * nfp + fp] * csr_row(P.bank, A.adv[tt].mat, rr, Gb, nfp);
+      if (cont) {
+        Jf[w] = acc;
+        if (A.route == ABS_EIGEN) W1[w] = T(0);
+        continue;
+      }
+      if (A.route == ABS_CONST) {
+        Jf[w] = T(0.5) * (acc + sgn * csr_row(P.bank, A.absmat, rr, Gb, nfp));
+      } else if (A.route == ABS_POINT) {
+        const int sp = scell * P.qdx + fp;
+        const int slot = __ldg(P.pslot + sp);
+        T s2 = T(0);
+        if (slot >= 0) {
+          const int* rp = P.bank.rp + P.bank.rp_off[A.absmat];
+          const int nnzp = __ldg(rp + n) - __ldg(rp);
+          const T* vals = P.pabs + ((size_t)slot * P.npface + pcell + side) * nnzp - __ldg(rp);
+          for (int k = __ldg(rp + rr); k < __ldg(rp + rr + 1); ++k) s2 += __ldg(vals + k) * Gb[__ldg(P.bank.col + k) * nfp];
+        }
+        Jf[w] = T(0.5) * (acc + sgn * s2);
+      } else {
+        Jf[w] = T(0.5) * acc;
+        const T c0 = CF[(f * MAXADV + 0) * nfp + fp];
+        const T c1 = CF[(f * MAXADV + 1) * nfp + fp];
+        W1[w] = sgn * fabs(c0 + P.lam[rr] * c1) * csr_row(P.bank, A.WTmat, rr, Gb, nfp);
+      }
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    for (int w = t; w < szT; w += per_cell) {
+      const int f = w / (n * nfp);
+      const int rr = (w / nfp) % n;
+      const int fp = w % nfp;
+      const AxisInfo& A = P.ax[f >> 1];
+      if (!A.active || A.route != ABS_EIGEN) continue;
+      Jf[w] += T(0.5) * csr_row(P.bank, A.Wmat, rr, W1 + f * n * nfp + fp, nfp);
+    }
+  }
+  __syncthreads();
+  // volume: z_a = S^T y along lines (G aliases the face scratch)
+  if (valid) {
+    for (int a = 0; a < D; ++a) {
+      if (!P.ax[a].active) continue;
+      const int ia = (i / qpow[a]) % q;
+      const int base = i - ia * qpow[a];
+      const T* Fa = F + r * nloc + base;
+      T z = T(0);
+      for (int qq = 0; qq < q; ++qq) z += P.S[qq][ia] * Fa[qq * qpow[a]];
+      G[a * per_cell + t] = z;
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  T acc = T(0);
+  T rdiag = T(0);
+  for (int tt = 0; tt < P.nreact; ++tt) {
+    const T c = CV[tt * nloc + i];
+    acc += c * csr_row(P.bank, P.react[tt].matT, r, F + i, nloc);
+    if (E.jacobi || E.out32) rdiag += c * csr_diag(P.bank, P.react[tt].mat, r);
+  }
+  for (int a = 0; a < D; ++a) {
+    if (!P.ax[a].active) continue;
+    const T invh = P.cell_invh[cell * D + a];
+    T g = T(0);
+    for (int tt = 0; tt < P.ax[a].nadv; ++tt)
+      g += CV[(adv_off[a] + tt) * nloc + i] * csr_row(P.bank, P.ax[a].adv[tt].mat, r, G + a * per_cell + i, nloc);
+    const int ia = (i / qpow[a]) % q;
+    const int fp = (i % qpow[a]) + (i / qpow[a + 1]) * qpow[a];
+    const T jup = Jf[((2 * a + 1) * n + r) * nfp + fp];
+    const T jdn = Jf[((2 * a) * n + r) * nfp + fp];
+    acc += P.B1[ia] * jup + P.B0[ia] * jdn - invh * g;
+  }
+  const size_t dof = (size_t)doff + (size_t)cell * per_cell + t;
+  T o = E.ax * F[t] + E.bl * acc;
+  if (E.bvec) o += E.wb * __ldg(E.bvec + dof);
+  if (E.out32) E.out32[dof] = float(o / (T(1) + E.cj * rdiag));
+  if (E.jacobi) o /= (T(1) + E.cj * rdiag);
+  if (E.out) E.out[dof] = o;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) applyT_kernel(const OpParams<T> P, const T* __restrict__ x, const Epi<T> E,
+                                                      int cpb, int cell_stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  applyT_body<T>(P, x, E, cpb, cell_stride, blockIdx.x * cpb, 0, smem_raw);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) apply_kernel(const OpParams<T> P, const T* __restrict__ x, const Epi<T> E,
+                                                     int cpb, int cell_stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  apply_body<T>(P, x, E, cpb, cell_stride, blockIdx.x * cpb, 0, smem_raw);
+}
+
+// Batched apply: block b works on instance blocks[b].x, cells [blocks[b].y, + cpb[inst]).  The
+// instance's parameter block is staged in shared memory; blocks of inactive instances return.
+template <typename T>
+__global__ void __launch_bounds__(1024) apply_kernel_batched(const OpParams<T>* __restrict__ Pall,
+                                                             const int64_t* __restrict__ doffs,
+                                                             const int* __restrict__ cpbs,
+                                                             const int* __restrict__ strides,
+                                                             const int2* __restrict__ blocks,
+                                                             const int* __restrict__ active,
+                                                             const T* __restrict__ x, const Epi<T> E) {
+  __shared__ __align__(16) unsigned char pbuf[sizeof(OpParams<T>)];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 bb = blocks[blockIdx.x];
+  if (active && !active[bb.x]) return;  // uniform over the block: no barrier is skipped by part of it
+  const int* src = reinterpret_cast<const int*>(Pall + bb.x);
+  int* dst = reinterpret_cast<int*>(pbuf);
+  for (int k = threadIdx.x; k < (int)(sizeof(OpParams<T>) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+  apply_body<T>(*reinterpret_cast<const OpParams<T>*>(pbuf), x, E, cpbs[bb.x], strides[bb.x], bb.y, doffs[bb.x], smem_raw);
 }
 
 int apply_cells_per_block(int n, int nloc) {
@@ -337,6 +598,10 @@ int apply_cells_per_block(int n, int nloc) {
   while (cpb > 1 && cpb * per > 1024) --cpb;
   return cpb;
 }
+
+template <typename T>
+static int cell_stride_elems(const OpParams<T>& P);
+int apply_cell_stride(const OpParams<double>& P) { return cell_stride_elems(P); }
 
 template <typename T>
 static int cell_stride_elems(const OpParams<T>& P) {
@@ -370,6 +635,27 @@ static cudaError_t launch_apply(const OpParams<T>& P, const T* x, const Epi<T>& 
 }
 
 template <typename T>
+static cudaError_t launch_applyT(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s) {
+  const int per = P.n * P.nloc;
+  if (per > 1024) return cudaErrorInvalidConfiguration;
+  const int cpb = apply_cells_per_block(P.n, P.nloc);
+  const int stride = cell_stride_elems(P);
+  const size_t smem = (size_t)cpb * stride * sizeof(T);
+  static bool attr_set[2] = {false, false};
+  const int idx = sizeof(T) == 8 ? 0 : 1;
+  if (!attr_set[idx]) {
+    cudaError_t err = cudaFuncSetAttribute(applyT_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (err != cudaSuccess) return err;
+    attr_set[idx] = true;
+  }
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  const int blocks = (P.ncell + cpb - 1) / cpb;
+  applyT_kernel<T><<<blocks, cpb * per, smem, s>>>(P, x, e, cpb, stride);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+template <typename T>
 static Epi<T> epi_plain(T* out, T ax, T bl, T gs) {
   Epi<T> e{};
   e.out = out;
@@ -380,9 +666,11 @@ static Epi<T> epi_plain(T* out, T ax, T bl, T gs) {
 }
 
 cudaError_t launch_apply64(const OpParams<double>& p, const double* x, double* y, int mode, cudaStream_t s) {
+  if (mode == SAP_APPLY_T) return launch_applyT<double>(p, x, epi_plain<double>(y, 0, 1, 0), s);
   return launch_apply<double>(p, x, mode == SAP_APPLY_RHS ? epi_plain<double>(y, 0, -1, 1) : epi_plain<double>(y, 0, 1, 0), s);
 }
 cudaError_t launch_apply32(const OpParams<float>& p, const float* x, float* y, int mode, cudaStream_t s) {
+  if (mode == SAP_APPLY_T) return launch_applyT<float>(p, x, epi_plain<float>(y, 0, 1, 0), s);
   return launch_apply<float>(p, x, mode == SAP_APPLY_RHS ? epi_plain<float>(y, 0, -1, 1) : epi_plain<float>(y, 0, 1, 0), s);
 }
 
@@ -506,21 +794,22 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Block b handles the chunk [b*KRY_CHUNK, (b+1)*KRY_CHUNK): it stages w in shared memory once, then
 // warp v sums V_i . w for i = v, v+8, ... ; partial[i][b] = the chunk's value (fixed order).
 constexpr int KRY_CHUNK = 2048;
-__global__ void __launch_bounds__(KRY_THREADS) multidot_kernel(const double* __restrict__ V, int64_t ldv, int m,
-                                                               const double* __restrict__ w, int64_t N, int with_ww,
+template <typename TV>
+__global__ void __launch_bounds__(KRY_THREADS) multidot_kernel(const TV* __restrict__ V, int64_t ldv, int m,
+                                                               const TV* __restrict__ w, int64_t N, int with_ww,
                                                                double* __restrict__ partial, int nchunks) {
   __shared__ double ws[KRY_CHUNK];
   const int64_t k0 = (int64_t)blockIdx.x * KRY_CHUNK;
   const int len = (int)((N - k0) < KRY_CHUNK ? (N - k0) : KRY_CHUNK);
-  for (int k = threadIdx.x; k < len; k += KRY_THREADS) ws[k] = w[k0 + k];
+  for (int k = threadIdx.x; k < len; k += KRY_THREADS) ws[k] = double(w[k0 + k]);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mt = m + (with_ww ? 1 : 0);
   for (int i = warp; i < mt; i += KRY_THREADS / 32) {
-    const double* a = (i < m) ? V + i * ldv + k0 : nullptr;
+    const TV* a = (i < m) ? V + i * ldv + k0 : nullptr;
     double acc = 0.0;
     if (a) {
-      for (int k = lane; k < len; k += 32) acc += __ldg(a + k) * ws[k];
+      for (int k = lane; k < len; k += 32) acc += double(__ldg(a + k)) * ws[k];
     } else {
       for (int k = lane; k < len; k += 32) acc += ws[k] * ws[k];
     }
@@ -540,9 +829,10 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
   if (lane == 0) out[i] = v;
 }
 
-// w -= sum_i h[i] V_i ; partial[b] = this block's sum of the updated w^2 (block-strided chunks)
-__global__ void __launch_bounds__(KRY_THREADS) update_kernel(const double* __restrict__ V, int64_t ldv, int m,
-                                                             const double* __restrict__ h, double* __restrict__ w,
+// w -= sum_i h[i] V_i (FP64 arithmetic) ; partial[b] = this block's sum of the updated w^2
+template <typename TV>
+__global__ void __launch_bounds__(KRY_THREADS) update_kernel(const TV* __restrict__ V, int64_t ldv, int m,
+                                                             const double* __restrict__ h, TV* __restrict__ w,
                                                              int64_t N, double* __restrict__ partial, int nchunks) {
   __shared__ double hs[KRY_MAXV];
   __shared__ double red[KRY_THREADS / 32];
@@ -552,10 +842,11 @@ __global__ void __launch_bounds__(KRY_THREADS) update_kernel(const double* __res
   const int64_t k1 = (k0 + KRY_CHUNK < N) ? k0 + KRY_CHUNK : N;
   double nrm = 0.0;
   for (int64_t k = k0 + threadIdx.x; k < k1; k += KRY_THREADS) {
-    double v = w[k];
-    for (int i = 0; i < m; ++i) v -= hs[i] * __ldg(V + i * ldv + k);
-    w[k] = v;
-    nrm += v * v;
+    double v = double(w[k]);
+    for (int i = 0; i < m; ++i) v -= hs[i] * double(__ldg(V + i * ldv + k));
+    const TV vs = TV(v);
+    w[k] = vs;
+    nrm += double(vs) * double(vs);
   }
   nrm = warp_sum(nrm);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
@@ -569,21 +860,24 @@ __global__ void __launch_bounds__(KRY_THREADS) update_kernel(const double* __res
 }
 
 // y = a*x with a = 1/a_dev[0] (invert = 1), 1/sqrt(a_dev[0]) (invert = 2) or a_dev[0]
-__global__ void scale_kernel(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ a_dev,
+template <typename TV>
+__global__ void scale_kernel(const TV* __restrict__ x, TV* __restrict__ y, const double* __restrict__ a_dev,
                              int invert, int64_t N) {
   const double a = invert == 1 ? 1.0 / a_dev[0] : (invert == 2 ? 1.0 / sqrt(a_dev[0]) : a_dev[0]);
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) y[k] = a * x[k];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+    y[k] = TV(a * double(x[k]));
 }
 
-// x += sum_i y[i] V_i
-__global__ void combine_kernel(const double* __restrict__ V, int64_t ldv, int m, const double* __restrict__ y,
+// x (FP64) += sum_i y[i] V_i
+template <typename TV>
+__global__ void combine_kernel(const TV* __restrict__ V, int64_t ldv, int m, const double* __restrict__ y,
                                double* __restrict__ x, int64_t N) {
   __shared__ double ys[KRY_MAXV];
   if (threadIdx.x < m) ys[threadIdx.x] = y[threadIdx.x];
   __syncthreads();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
     double v = x[k];
-    for (int i = 0; i < m; ++i) v += ys[i] * __ldg(V + i * ldv + k);
+    for (int i = 0; i < m; ++i) v += ys[i] * double(__ldg(V + i * ldv + k));
     x[k] = v;
   }
 }
@@ -605,18 +899,20 @@ struct KrylovCtx {
 };
 
 // dsc_out[i] = V_i . w for i < m, and dsc_out[m] = w . w if with_ww
-static void dots(KrylovCtx& K, const double* V, int m, const double* w, int with_ww, double* dsc_out) {
+template <typename TV>
+static void dots(KrylovCtx& K, const TV* V, int m, const TV* w, int with_ww, double* dsc_out) {
   const int64_t N = K.c->N;
-  multidot_kernel<<<K.nchunks, KRY_THREADS, 0, K.s>>>(V, N, m, w, N, with_ww, K.partial, K.nchunks);
+  multidot_kernel<TV><<<K.nchunks, KRY_THREADS, 0, K.s>>>(V, N, m, w, N, with_ww, K.partial, K.nchunks);
   ++g_launches;
   reduce_partials_kernel<<<1, 32 * (m + with_ww), 0, K.s>>>(K.partial, K.nchunks, m + with_ww, dsc_out);
   ++g_launches;
 }
 
 // w -= V h (m vectors), then dsc_out[0] = |w|^2
-static void update(KrylovCtx& K, const double* V, int m, const double* h, double* w, double* dsc_out) {
+template <typename TV>
+static void update(KrylovCtx& K, const TV* V, int m, const double* h, TV* w, double* dsc_out) {
   const int64_t N = K.c->N;
-  update_kernel<<<K.nchunks, KRY_THREADS, 0, K.s>>>(V, N, m, h, w, N, K.partial, K.nchunks);
+  update_kernel<TV><<<K.nchunks, KRY_THREADS, 0, K.s>>>(V, N, m, h, w, N, K.partial, K.nchunks);
   ++g_launches;
   reduce_partials_kernel<<<1, 32, 0, K.s>>>(K.partial, K.nchunks, 1, dsc_out);
   ++g_launches;
@@ -630,6 +926,12 @@ static cudaError_t fetch(KrylovCtx& K, int first, int count) {
 int64_t krylov_scratch_doubles(int64_t N) {
   const int64_t nchunks = (N + KRY_CHUNK - 1) / KRY_CHUNK;
   return (KRY_MAXV + 1) * nchunks + 8 * KRY_MAXV;
+}
+
+int64_t krylov_batch_scratch_doubles(const std::vector<int64_t>& Ns) {
+  int64_t nchunks = 0;
+  for (int64_t n : Ns) nchunks += (n + KRY_CHUNK - 1) / KRY_CHUNK;
+  return (KRY_MAXV + 1) * nchunks + (int64_t)Ns.size() * 4 * KRY_MAXV;
 }
 
 sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
@@ -665,7 +967,7 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
       e.out = b; e.ax = 1.0; e.bl = -half; e.gs = dt;
       CK(launch_apply<double>(P, state, e, s));
     }
-    dots(K, nullptr, 0, b, 1, d_nrm);
+    dots<double>(K, nullptr, 0, b, 1, d_nrm);
     CK(fetch(K, KRY_MAXV, 1));
     const double bnorm = std::sqrt(K.hsc[KRY_MAXV]);
     int its = 0;
@@ -682,7 +984,7 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
         e.out = tmp; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half;
         CK(launch_apply<double>(P, state, e, s));
       }
-      dots(K, nullptr, 0, tmp, 1, d_nrm);
+      dots<double>(K, nullptr, 0, tmp, 1, d_nrm);
       CK(fetch(K, KRY_MAXV, 1));
       rel = std::sqrt(K.hsc[KRY_MAXV]) / bnorm;
       if (rel <= tol || its >= maxit) break;
@@ -692,8 +994,8 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
         e.out = V; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.jacobi = 1; e.cj = half;
         CK(launch_apply<double>(P, state, e, s));
       }
-      dots(K, nullptr, 0, V, 1, d_nrm);
-      scale_kernel<<<1024, KRY_THREADS, 0, s>>>(V, V, d_nrm, 2, N);
+      dots<double>(K, nullptr, 0, V, 1, d_nrm);
+      scale_kernel<double><<<1024, KRY_THREADS, 0, s>>>(V, V, d_nrm, 2, N);
       ++g_launches;
       CK(fetch(K, KRY_MAXV, 1));
       const double beta = std::sqrt(K.hsc[KRY_MAXV]);
@@ -726,7 +1028,7 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
         }
         H[(size_t)(j + 1) * m + j] = wn;
         if (wn > 0.0) {
-          scale_kernel<<<1024, KRY_THREADS, 0, s>>>(w, w, d_nrm, 2, N);
+          scale_kernel<double><<<1024, KRY_THREADS, 0, s>>>(w, w, d_nrm, 2, N);
           ++g_launches;
         }
         for (int i2 = 0; i2 < j; ++i2) {
@@ -754,7 +1056,7 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
       }
       for (int i2 = 0; i2 < jdone; ++i2) K.hsc[3 * KRY_MAXV + i2] = y[i2];
       CK(cudaMemcpyAsync(d_y, K.hsc + 3 * KRY_MAXV, sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
-      combine_kernel<<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, d_y, state, N);
+      combine_kernel<double><<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, d_y, state, N);
       ++g_launches;
       CK(cudaGetLastError());
     }
@@ -779,6 +1081,716 @@ cuda_fail:
   c->err = std::string("cn: ") + cudaGetErrorString(err);
   return SAP_ECUDA;
 #undef CK
+}
+
+
+// ------------------------------------------------------------------------------------------------
+// Crank--Nicolson, precision form: FP64 residual and iterative refinement around an inner GMRES
+// whose operator applies, Krylov vectors and preconditioner run in FP32 (dot products, Hessenberg
+// and the solution update accumulate in FP64).
+// ------------------------------------------------------------------------------------------------
+sap_status cn_steps_mixed(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
+                          sap_solver_stats* st, cudaStream_t s) {
+  const int64_t N = c->N;
+  const int m = restart;
+  float* V = c->ws32;                        // (m+1) FP32 vectors
+  double* b = c->ws64;
+  double* r = b + N;
+  const int nchunks = (int)((N + KRY_CHUNK - 1) / KRY_CHUNK);
+  KrylovCtx K{c, s, nchunks, c->small, c->small + (size_t)(KRY_MAXV + 1) * nchunks, c->small_host};
+  double* const d_h1 = K.dsc;
+  double* const d_nrm = K.dsc + KRY_MAXV;
+  double* const d_h2 = K.dsc + 2 * KRY_MAXV;
+  double* const d_y = K.dsc + 3 * KRY_MAXV;
+  const OpParams<double>& P64 = c->p64;
+  const OpParams<float>& P32 = c->p32;
+  const double half = 0.5 * dt;
+  std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), y(m);
+  int64_t total_its = 0;
+  const int64_t launches0 = g_launches;
+  int max_its = 0;
+  double last_rel = 0.0;
+  cudaError_t err = cudaSuccess;
+#define CK(x)                                           \
+  do {                                                  \
+    err = (x);                                          \
+    if (err != cudaSuccess) goto cuda_fail;             \
+  } while (0)
+  for (int step = 0; step < nsteps; ++step) {
+    {
+      Epi<double> e{};
+      e.out = b; e.ax = 1.0; e.bl = -half; e.gs = dt;
+      CK(launch_apply<double>(P64, state, e, s));
+    }
+    dots<double>(K, nullptr, 0, b, 1, d_nrm);
+    CK(fetch(K, KRY_MAXV, 1));
+    const double bnorm = std::sqrt(K.hsc[KRY_MAXV]);
+    int its = 0;
+    double rel = 0.0;
+    if (bnorm == 0.0) {
+      CK(cudaMemsetAsync(state, 0, sizeof(double) * N, s));
+      continue;
+    }
+    for (;;) {
+      // FP64 residual r = b - A zeta, and its Jacobi-scaled FP32 copy as the inner right side
+      {
+        Epi<double> e{};
+        e.out = r; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.out32 = V; e.cj = half;
+        CK(launch_apply<double>(P64, state, e, s));
+      }
+      dots<double>(K, nullptr, 0, r, 1, d_nrm);
+      CK(fetch(K, KRY_MAXV, 1));
+      rel = std::sqrt(K.hsc[KRY_MAXV]) / bnorm;
+      if (rel <= tol || its >= maxit) break;
+      dots<float>(K, nullptr, 0, V, 1, d_nrm);
+      scale_kernel<float><<<1024, KRY_THREADS, 0, s>>>(V, V, d_nrm, 2, N);
+      ++g_launches;
+      CK(fetch(K, KRY_MAXV, 1));
+      const double beta = std::sqrt(K.hsc[KRY_MAXV]);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      // the FP32 operator limits one correction to ~1e-6; ask for no more than that
+      const double target = beta * std::max(0.5 * tol / rel, 1e-6);
+      int jdone = 0;
+      for (int j = 0; j < m && its < maxit; ++j) {
+        float* w = V + (size_t)(j + 1) * N;
+        {
+          Epi<float> e{};
+          e.out = w; e.ax = 1.0f; e.bl = float(half); e.jacobi = 1; e.cj = float(half);
+          CK(launch_apply<float>(P32, V + (size_t)j * N, e, s));
+        }
+        dots<float>(K, V, j + 1, w, 1, d_h1);
+        update<float>(K, V, j + 1, d_h1, w, d_nrm);
+        CK(fetch(K, 0, KRY_MAXV + 1));
+        for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] = K.hsc[i2];
+        const double wn0 = std::sqrt(K.hsc[j + 1]);
+        double wn = std::sqrt(K.hsc[KRY_MAXV]);
+        if (wn < 0.7071067811865476 * wn0) {
+          dots<float>(K, V, j + 1, w, 0, d_h2);
+          update<float>(K, V, j + 1, d_h2, w, d_nrm);
+          CK(fetch(K, 2 * KRY_MAXV, j + 1));
+          CK(fetch(K, KRY_MAXV, 1));
+          for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] += K.hsc[2 * KRY_MAXV + i2];
+          wn = std::sqrt(K.hsc[KRY_MAXV]);
+        }
+        H[(size_t)(j + 1) * m + j] = wn;
+        if (wn > 0.0) {
+          scale_kernel<float><<<1024, KRY_THREADS, 0, s>>>(w, w, d_nrm, 2, N);
+          ++g_launches;
+        }
+        for (int i2 = 0; i2 < j; ++i2) {
+          const double a0 = H[(size_t)i2 * m + j], a1 = H[(size_t)(i2 + 1) * m + j];
+          H[(size_t)i2 * m + j] = cs[i2] * a0 + sn[i2] * a1;
+          H[(size_t)(i2 + 1) * m + j] = -sn[i2] * a0 + cs[i2] * a1;
+        }
+        const double a0 = H[(size_t)j * m + j], a1 = H[(size_t)(j + 1) * m + j];
+        const double den = std::hypot(a0, a1);
+        cs[j] = den > 0 ? a0 / den : 1.0;
+        sn[j] = den > 0 ? a1 / den : 0.0;
+        H[(size_t)j * m + j] = den;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        ++its;
+        jdone = j + 1;
+        if (std::fabs(g[j + 1]) <= target || wn == 0.0) break;
+      }
+      for (int i2 = jdone - 1; i2 >= 0; --i2) {
+        double v = g[i2];
+        for (int k2 = i2 + 1; k2 < jdone; ++k2) v -= H[(size_t)i2 * m + k2] * y[k2];
+        y[i2] = v / H[(size_t)i2 * m + i2];
+      }
+      for (int i2 = 0; i2 < jdone; ++i2) K.hsc[3 * KRY_MAXV + i2] = y[i2];
+      CK(cudaMemcpyAsync(d_y, K.hsc + 3 * KRY_MAXV, sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
+      combine_kernel<float><<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, d_y, state, N);
+      ++g_launches;
+      CK(cudaGetLastError());
+    }
+    total_its += its;
+    max_its = std::max(max_its, its);
+    last_rel = rel;
+    if (rel > tol) {
+      c->err = "cn: GMRES did not reach the tolerance within maxit";
+      if (st) {
+        st->steps = step + 1; st->iterations = total_its; st->max_iterations = max_its; st->last_rel_residual = rel;
+        st->kernel_launches = g_launches - launches0;
+      }
+      return SAP_ENOCONV;
+    }
+  }
+  if (st) {
+    st->steps = nsteps; st->iterations = total_its; st->max_iterations = max_its; st->last_rel_residual = last_rel;
+    st->kernel_launches = g_launches - launches0;
+  }
+  return SAP_OK;
+cuda_fail:
+  c->err = std::string("cn: ") + cudaGetErrorString(err);
+  return SAP_ECUDA;
+#undef CK
+}
+
+
+// ================================================================================================
+// Batches of independent problems (one launch per operator apply over all instances)
+// ================================================================================================
+template <typename T>
+static cudaError_t launch_apply_batched(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e,
+                                        cudaStream_t s) {
+  static bool attr_set[2] = {false, false};
+  const int idx = sizeof(T) == 8 ? 0 : 1;
+  if (!attr_set[idx]) {
+    cudaError_t err = cudaFuncSetAttribute(apply_kernel_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           200 * 1024);
+    if (err != cudaSuccess) return err;
+    attr_set[idx] = true;
+  }
+  if (B.smem > 200 * 1024 || B.threads > 1024 || B.threads < 1) return cudaErrorInvalidConfiguration;
+  apply_kernel_batched<T><<<B.nblocks, B.threads, B.smem, s>>>(B.P, B.doff, B.cpb, B.stride, B.blocks, active, x, e);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+// per-instance Krylov kernels: block b works on chunk b of instance chunks.inst[b]
+template <typename TV>
+__global__ void __launch_bounds__(KRY_THREADS) multidot_b_kernel(const TV* __restrict__ V, int64_t ldv, int m,
+                                                                 const TV* __restrict__ w, int with_ww,
+                                                                 BatchChunks C, const int* __restrict__ active,
+                                                                 double* __restrict__ partial) {
+  __shared__ double ws[KRY_CHUNK];
+  const int inst = C.inst[blockIdx.x];
+  if (!active[inst]) return;
+  const int64_t k0 = C.k0[blockIdx.x];
+  const int len = C.len[blockIdx.x];
+  for (int k = threadIdx.x; k < len; k += KRY_THREADS) ws[k] = double(w[k0 + k]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mt = m + (with_ww ? 1 : 0);
+  for (int i = warp; i < mt; i += KRY_THREADS / 32) {
+    double acc = 0.0;
+    if (i < m) {
+      const TV* a = V + i * ldv + k0;
+      for (int k = lane; k < len; k += 32) acc += double(__ldg(a + k)) * ws[k];
+    } else {
+      for (int k = lane; k < len; k += 32) acc += ws[k] * ws[k];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) partial[(size_t)i * C.nchunks + blockIdx.x] = acc;
+  }
+}
+
+// out[inst*stride + i] = sum over the instance's chunks of partial[i][chunk]; block = instance
+__global__ void reduce_b_kernel(const double* __restrict__ partial, BatchChunks C, const int* __restrict__ active,
+                                int m, double* __restrict__ out, int stride) {
+  const int inst = blockIdx.x;
+  if (!active[inst]) return;
+  const int lane = threadIdx.x & 31, i = threadIdx.x >> 5;
+  if (i >= m) return;
+  const int c0 = C.first[inst], cn = C.count[inst];
+  double v = 0.0;
+  for (int c = lane; c < cn; c += 32) v += partial[(size_t)i * C.nchunks + c0 + c];
+  v = warp_sum(v);
+  if (lane == 0) out[(size_t)inst * stride + i] = v;
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(KRY_THREADS) update_b_kernel(const TV* __restrict__ V, int64_t ldv, int m,
+                                                               const double* __restrict__ h, int hstride,
+                                                               TV* __restrict__ w, BatchChunks C,
+                                                               const int* __restrict__ active,
+                                                               double* __restrict__ partial) {
+  __shared__ double hs[KRY_MAXV];
+  __shared__ double red[KRY_THREADS / 32];
+  const int inst = C.inst[blockIdx.x];
+  if (!active[inst]) return;
+  if (threadIdx.x < m) hs[threadIdx.x] = h[(size_t)inst * hstride + threadIdx.x];
+  __syncthreads();
+  const int64_t k0 = C.k0[blockIdx.x];
+  const int len = C.len[blockIdx.x];
+  double nrm = 0.0;
+  for (int k = threadIdx.x; k < len; k += KRY_THREADS) {
+    double v = double(w[k0 + k]);
+    for (int i = 0; i < m; ++i) v -= hs[i] * double(__ldg(V + i * ldv + k0 + k));
+    const TV vs = TV(v);
+    w[k0 + k] = vs;
+    nrm += double(vs) * double(vs);
+  }
+  nrm = warp_sum(nrm);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < KRY_THREADS / 32; ++q) t += red[q];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// y = x / sqrt(a[inst*stride]) on the active instances
+template <typename TV>
+__global__ void scale_b_kernel(const TV* __restrict__ x, TV* __restrict__ y, const double* __restrict__ a, int stride,
+                               BatchChunks C, const int* __restrict__ active) {
+  const int inst = C.inst[blockIdx.x];
+  if (!active[inst]) return;
+  const double av = a[(size_t)inst * stride];
+  if (!(av > 0.0)) return;
+  const double f = 1.0 / sqrt(av);
+  const int64_t k0 = C.k0[blockIdx.x];
+  for (int k = threadIdx.x; k < C.len[blockIdx.x]; k += blockDim.x) y[k0 + k] = TV(f * double(x[k0 + k]));
+}
+
+// x (FP64) += sum_{i < mi[inst]} y[inst*stride + i] V_i
+template <typename TV>
+__global__ void combine_b_kernel(const TV* __restrict__ V, int64_t ldv, const int* __restrict__ mi,
+                                 const double* __restrict__ y, int stride, double* __restrict__ x, BatchChunks C) {
+  const int inst = C.inst[blockIdx.x];
+  const int m = mi[inst];
+  if (m <= 0) return;
+  __shared__ double ys[KRY_MAXV];
+  if (threadIdx.x < m) ys[threadIdx.x] = y[(size_t)inst * stride + threadIdx.x];
+  __syncthreads();
+  const int64_t k0 = C.k0[blockIdx.x];
+  for (int k = threadIdx.x; k < C.len[blockIdx.x]; k += blockDim.x) {
+    double v = x[k0 + k];
+    for (int i = 0; i < m; ++i) v += ys[i] * double(__ldg(V + i * ldv + k0 + k));
+    x[k0 + k] = v;
+  }
+}
+
+// zero the states of masked instances
+__global__ void zero_b_kernel(double* __restrict__ x, BatchChunks C, const int* __restrict__ mask) {
+  const int inst = C.inst[blockIdx.x];
+  if (!mask[inst]) return;
+  const int64_t k0 = C.k0[blockIdx.x];
+  for (int k = threadIdx.x; k < C.len[blockIdx.x]; k += blockDim.x) x[k0 + k] = 0.0;
+}
+
+template <typename V>
+static void* dev_upload(sap_ctx* c, const std::vector<V>& h) {
+  void* p = nullptr;
+  const size_t bytes = std::max<size_t>(1, h.size()) * sizeof(V);
+  if (cudaMalloc(&p, bytes) != cudaSuccess) throw std::string("cudaMalloc failed");
+  if (!h.empty() && cudaMemcpy(p, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice) != cudaSuccess)
+    throw std::string("cudaMemcpy failed");
+  c->batch_bufs.push_back({p, bytes});
+  return p;
+}
+
+static void batch_tables(sap_ctx* c, int target) {
+  for (auto& b : c->batch_bufs) cudaFree(b.p);
+  c->batch_bufs.clear();
+  const int ni = (int)c->sub.size();
+  std::vector<OpParams<double>> P64(ni);
+  std::vector<OpParams<float>> P32(ni);
+  std::vector<int64_t> doff(ni);
+  std::vector<int> cpb(ni), stride(ni);
+  std::vector<int2> blocks;
+  int threads = 1;
+  size_t smem64 = 0, smem32 = 0;
+  for (int i = 0; i < ni; ++i) {
+    sap_ctx* sc = c->sub[i];
+    P64[i] = sc->p64;
+    P32[i] = sc->p32;
+    doff[i] = c->inst_off[i];
+    const int per = sc->n * sc->nloc;
+    if (per > 1024) throw std::string("an instance has n (k+1)^D > 1024");
+    cpb[i] = std::max(1, std::min(target, 1024) / per);
+    stride[i] = cell_stride_elems(sc->p64);
+    threads = std::max(threads, cpb[i] * per);
+    smem64 = std::max(smem64, (size_t)cpb[i] * stride[i] * sizeof(double));
+    smem32 = std::max(smem32, (size_t)cpb[i] * stride[i] * sizeof(float));
+    for (int c0 = 0; c0 < sc->ncell; c0 += cpb[i]) blocks.push_back(make_int2(i, c0));
+  }
+  std::vector<int> cinst, clen, cfirst(ni), ccount(ni);
+  std::vector<int64_t> ck0;
+  for (int i = 0; i < ni; ++i) {
+    cfirst[i] = (int)cinst.size();
+    const int64_t Ni = c->sub[i]->N;
+    for (int64_t k = 0; k < Ni; k += KRY_CHUNK) {
+      cinst.push_back(i);
+      ck0.push_back(c->inst_off[i] + k);
+      clen.push_back((int)std::min<int64_t>(KRY_CHUNK, Ni - k));
+    }
+    ccount[i] = (int)cinst.size() - cfirst[i];
+  }
+  const int64_t* d_doff = (const int64_t*)dev_upload(c, doff);
+  const int* d_cpb = (const int*)dev_upload(c, cpb);
+  const int* d_stride = (const int*)dev_upload(c, stride);
+  const int2* d_blocks = (const int2*)dev_upload(c, blocks);
+  c->b64 = BatchDev<double>{(const OpParams<double>*)dev_upload(c, P64), d_doff, d_cpb, d_stride, d_blocks,
+                            (int)blocks.size(), threads, smem64};
+  c->b32 = BatchDev<float>{(const OpParams<float>*)dev_upload(c, P32), d_doff, d_cpb, d_stride, d_blocks,
+                           (int)blocks.size(), threads, smem32};
+  c->chunks = BatchChunks{(const int*)dev_upload(c, cinst), (const int64_t*)dev_upload(c, ck0),
+                          (const int*)dev_upload(c, clen), (const int*)dev_upload(c, cfirst),
+                          (const int*)dev_upload(c, ccount), (int)cinst.size()};
+  c->h_active.assign(3 * ni, 1);  // activity mask, combine lengths, zero mask
+  c->d_active = (int*)dev_upload(c, c->h_active);
+}
+
+// Builds the batch tables; on the first call the thread-block size is autotuned by timing the
+// batched apply for several targets (cells per block are picked per instance from the target).
+sap_status batch_prepare(sap_ctx* c, cudaStream_t s) {
+  int version = 0;
+  for (auto* sc : c->sub) {
+    if (!sc->fields_set) {
+      c->err = "batch: fields not set on every instance";
+      return SAP_EINVAL;
+    }
+    version += sc->fields_version;
+  }
+  if (version == c->batch_built_version) return SAP_OK;
+  try {
+    if (!c->batch_tuned) {
+      // autotune on scratch vectors of the context's precision
+      const size_t w = c->prec == SAP_PREC_FP64 ? 8 : 4;
+      void *x = nullptr, *y = nullptr;
+      if (cudaMalloc(&x, w * c->N) != cudaSuccess || cudaMalloc(&y, w * c->N) != cudaSuccess) {
+        if (x) cudaFree(x);
+        c->err = "batch: autotune allocation failed";
+        return SAP_ENOMEM;
+      }
+      cudaMemsetAsync(x, 0, w * c->N, s);
+      float best = 1e30f;
+      int best_t = 256;
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      for (int target : {64, 128, 256, 512, 1024}) {
+        batch_tables(c, target);
+        const int64_t l0 = g_launches;
+        for (int rep = 0; rep < 4; ++rep) {
+          if (rep == 1) cudaEventRecord(e0, s);
+          cudaError_t err = c->prec == SAP_PREC_FP64
+                                ? launch_apply_batched<double>(c->b64, c->d_active, (const double*)x,
+                                                               Epi<double>{(double*)y, nullptr, 0, 0, 1, 0}, s)
+                                : launch_apply_batched<float>(c->b32, c->d_active, (const float*)x,
+                                                              Epi<float>{(float*)y, nullptr, 0, 0, 1, 0}, s);
+          if (err != cudaSuccess) break;
+        }
+        g_launches = l0;
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 1e30f;
+        if (cudaGetLastError() == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          best_t = target;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      cudaFree(x);
+      cudaFree(y);
+      c->batch_target_threads = best_t;
+      c->batch_tuned = true;
+    }
+    batch_tables(c, c->batch_target_threads);
+  } catch (const std::string& e) {
+    c->err = "batch: " + e;
+    return SAP_ENOMEM;
+  }
+  c->batch_built_version = version;
+  return SAP_OK;
+}
+
+sap_status batch_apply(sap_ctx* c, const void* x, void* y, int mode, cudaStream_t s) {
+  sap_status st = batch_prepare(c, s);
+  if (st != SAP_OK) return st;
+  cudaError_t err;
+  if (c->prec == SAP_PREC_FP64) {
+    Epi<double> e = mode == SAP_APPLY_RHS ? epi_plain<double>((double*)y, 0, -1, 1) : epi_plain<double>((double*)y, 0, 1, 0);
+    err = launch_apply_batched<double>(c->b64, c->d_active, (const double*)x, e, s);
+  } else {
+    Epi<float> e = mode == SAP_APPLY_RHS ? epi_plain<float>((float*)y, 0, -1, 1) : epi_plain<float>((float*)y, 0, 1, 0);
+    err = launch_apply_batched<float>(c->b32, c->d_active, (const float*)x, e, s);
+  }
+  if (err != cudaSuccess) {
+    c->err = std::string("batch apply: ") + cudaGetErrorString(err);
+    return SAP_ECUDA;
+  }
+  return SAP_OK;
+}
+
+sap_status batch_erk(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s) {
+  sap_status st = batch_prepare(c, s);
+  if (st != SAP_OK) return st;
+  cudaError_t err = cudaSuccess;
+  const int64_t N = c->N;
+  auto run = [&](auto tag, const auto& B, auto* ya, auto* yb, double* acc) -> cudaError_t {
+    using T = decltype(tag);
+    for (int it = 0; it < nsteps; ++it) {
+      const T* in0;
+      if (sizeof(T) == 8) {
+        in0 = reinterpret_cast<const T*>(state);
+      } else {
+        cast_kernel<T><<<1024, 256, 0, s>>>(state, ya, N);
+        ++g_launches;
+        in0 = ya;
+      }
+      Epi<T> e{};
+      e.acc = acc;
+      e.y0 = state;
+      e.erk = 1; e.bdt = dt / 6.0; e.adt = 0.5 * dt; e.ynext = (sizeof(T) == 8) ? ya : yb;
+      cudaError_t r = launch_apply_batched<T>(B, c->d_active, in0, e, s);
+      if (r != cudaSuccess) return r;
+      const T* in2 = e.ynext;
+      T* out2 = (in2 == ya) ? yb : ya;
+      e.erk = 2; e.bdt = dt / 3.0; e.adt = 0.5 * dt; e.ynext = out2;
+      if ((r = launch_apply_batched<T>(B, c->d_active, in2, e, s)) != cudaSuccess) return r;
+      const T* in3 = out2;
+      T* out3 = (in3 == ya) ? yb : ya;
+      e.erk = 2; e.bdt = dt / 3.0; e.adt = dt; e.ynext = out3;
+      if ((r = launch_apply_batched<T>(B, c->d_active, in3, e, s)) != cudaSuccess) return r;
+      e.erk = 3; e.bdt = dt / 6.0; e.ynext = nullptr; e.state = state;
+      if ((r = launch_apply_batched<T>(B, c->d_active, out3, e, s)) != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  };
+  if (c->prec == SAP_PREC_FP64) err = run(double{}, c->b64, c->ws64, c->ws64 + N, c->ws64 + 2 * N);
+  else err = run(float{}, c->b32, c->ws32, c->ws32 + N, c->ws64);
+  if (err != cudaSuccess) {
+    c->err = std::string("batch erk: ") + cudaGetErrorString(err);
+    return SAP_ECUDA;
+  }
+  return SAP_OK;
+}
+
+// Crank--Nicolson on a batch: every instance runs its own restarted GMRES (own Krylov space,
+// Hessenberg matrix and convergence test); the instances advance in lock-step and finished ones are
+// masked out of every kernel.  TV = double: FP64 operator and vectors; TV = float: FP32 inner
+// GMRES inside the FP64 residual/refinement loop.
+template <typename TV>
+static sap_status batch_cn_impl(sap_ctx* c, double* state, double dt, int nsteps, double tol, int m, int maxit,
+                                sap_solver_stats* st, cudaStream_t s) {
+  const int64_t N = c->N;
+  const int ni = (int)c->sub.size();
+  double* b = c->ws64;
+  double* r = b + N;
+  TV* V = (sizeof(TV) == 8) ? reinterpret_cast<TV*>(c->ws64 + 2 * N) : reinterpret_cast<TV*>(c->ws32);
+  const BatchChunks& C = c->chunks;
+  double* partial = c->small;
+  const int SS = 4 * KRY_MAXV;                     // per-instance scalar stride
+  double* dsc = c->small + (size_t)(KRY_MAXV + 1) * C.nchunks;
+  double* hsc = c->small_host;
+  int* d_act = c->d_active;
+  int* d_mi = d_act + ni;                           // [ni] combine lengths
+  int* d_zero = d_mi + ni;                          // [ni] zero masks
+  const double half = 0.5 * dt;
+  std::vector<double> H((size_t)ni * (m + 1) * m), g((size_t)ni * (m + 1)), cs((size_t)ni * m), sn((size_t)ni * m);
+  std::vector<double> bnorm(ni), rel(ni), target(ni), beta(ni);
+  std::vector<int> act(ni), inner(ni), jdone(ni), its(ni), zero(ni);
+  int64_t total_its = 0;
+  int max_its = 0;
+  double worst_rel = 0.0;
+  const int64_t launches0 = g_launches;
+  cudaError_t err = cudaSuccess;
+  auto put_mask = [&](const std::vector<int>& v, int* d) {
+    cudaMemcpyAsync(d, v.data(), sizeof(int) * ni, cudaMemcpyHostToDevice, s);
+    return cudaStreamSynchronize(s);  // v is pageable host memory reused right after
+  };
+  auto dots = [&](const TV* Vb, int mm, const TV* w, int ww, int region) {
+    multidot_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(Vb, N, mm, w, ww, C, d_act, partial);
+    reduce_b_kernel<<<ni, 32 * (mm + ww), 0, s>>>(partial, C, d_act, mm + ww, dsc + region * KRY_MAXV, SS);
+    g_launches += 2;
+  };
+  auto dots64 = [&](const double* w, int region) {
+    multidot_b_kernel<double><<<C.nchunks, KRY_THREADS, 0, s>>>(nullptr, N, 0, w, 1, C, d_act, partial);
+    reduce_b_kernel<<<ni, 32, 0, s>>>(partial, C, d_act, 1, dsc + region * KRY_MAXV, SS);
+    g_launches += 2;
+  };
+  auto update = [&](const TV* Vb, int mm, int hregion, TV* w) {
+    update_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(Vb, N, mm, dsc + hregion * KRY_MAXV, SS, w, C, d_act, partial);
+    reduce_b_kernel<<<ni, 32, 0, s>>>(partial, C, d_act, 1, dsc + 1 * KRY_MAXV, SS);  // |w|^2 -> region 1 [0]
+    g_launches += 2;
+  };
+  auto fetch_all = [&]() {
+    cudaMemcpyAsync(hsc, dsc, sizeof(double) * ni * SS, cudaMemcpyDeviceToHost, s);
+    return cudaStreamSynchronize(s);
+  };
+  auto apply64 = [&](const double* x, const Epi<double>& e) { return launch_apply_batched<double>(c->b64, d_act, x, e, s); };
+#define CK(x)                               \
+  do {                                      \
+    err = (x);                              \
+    if (err != cudaSuccess) goto cuda_fail; \
+  } while (0)
+  for (int step = 0; step < nsteps; ++step) {
+    std::fill(act.begin(), act.end(), 1);
+    CK(put_mask(act, d_act));
+    {
+      Epi<double> e{};
+      e.out = b; e.ax = 1.0; e.bl = -half; e.gs = dt;
+      CK(apply64(state, e));
+    }
+    dots64(b, 1);
+    CK(fetch_all());
+    for (int i = 0; i < ni; ++i) {
+      bnorm[i] = std::sqrt(hsc[(size_t)i * SS + KRY_MAXV]);
+      zero[i] = bnorm[i] == 0.0;
+      act[i] = !zero[i];
+      its[i] = 0;
+    }
+    CK(put_mask(zero, d_zero));
+    zero_b_kernel<<<C.nchunks, KRY_THREADS, 0, s>>>(state, C, d_zero);
+    ++g_launches;
+    for (;;) {
+      CK(put_mask(act, d_act));
+      // FP64 residual; inner right side v0 = P^-1 r
+      {
+        Epi<double> e{};
+        e.out = r; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half;
+        if (sizeof(TV) == 4) { e.out32 = reinterpret_cast<float*>(V); e.cj = half; }
+        CK(apply64(state, e));
+      }
+      if (sizeof(TV) == 8) {
+        Epi<double> e{};
+        e.out = reinterpret_cast<double*>(V); e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.jacobi = 1;
+        e.cj = half;
+        CK(apply64(state, e));
+      }
+      dots64(r, 1);
+      CK(fetch_all());
+      bool any = false;
+      for (int i = 0; i < ni; ++i) {
+        if (!act[i]) continue;
+        rel[i] = std::sqrt(hsc[(size_t)i * SS + KRY_MAXV]) / bnorm[i];
+        if (rel[i] <= tol || its[i] >= maxit) act[i] = 0;
+        any = any || act[i];
+      }
+      if (!any) break;
+      CK(put_mask(act, d_act));
+      dots(nullptr, 0, V, 1, 1);
+      scale_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(V, V, dsc + KRY_MAXV, SS, C, d_act);
+      ++g_launches;
+      CK(fetch_all());
+      for (int i = 0; i < ni; ++i) {
+        inner[i] = act[i];
+        jdone[i] = 0;
+        if (!act[i]) continue;
+        beta[i] = std::sqrt(hsc[(size_t)i * SS + KRY_MAXV]);
+        std::fill(g.begin() + (size_t)i * (m + 1), g.begin() + (size_t)(i + 1) * (m + 1), 0.0);
+        g[(size_t)i * (m + 1)] = beta[i];
+        target[i] = beta[i] * (sizeof(TV) == 8 ? 0.5 * tol / rel[i] : std::max(0.5 * tol / rel[i], 1e-6));
+      }
+      for (int j = 0; j < m; ++j) {
+        bool anyin = false;
+        for (int i = 0; i < ni; ++i) anyin = anyin || inner[i];
+        if (!anyin) break;
+        CK(put_mask(inner, d_act));
+        TV* w = V + (size_t)(j + 1) * N;
+        {
+          Epi<TV> e{};
+          e.out = w; e.ax = TV(1); e.bl = TV(half); e.jacobi = 1; e.cj = TV(half);
+          if constexpr (sizeof(TV) == 8) CK(launch_apply_batched<double>(c->b64, d_act, V + (size_t)j * N, e, s));
+          else CK(launch_apply_batched<float>(c->b32, d_act, V + (size_t)j * N, e, s));
+        }
+        dots(V, j + 1, w, 1, 0);
+        update(V, j + 1, 0, w);
+        CK(fetch_all());
+        std::vector<int> reo(ni, 0);
+        bool anyre = false;
+        for (int i = 0; i < ni; ++i) {
+          if (!inner[i]) continue;
+          const double* hs = hsc + (size_t)i * SS;
+          double* Hi = &H[(size_t)i * (m + 1) * m];
+          for (int i2 = 0; i2 <= j; ++i2) Hi[(size_t)i2 * m + j] = hs[i2];
+          if (std::sqrt(hs[KRY_MAXV]) < 0.7071067811865476 * std::sqrt(hs[j + 1])) {
+            reo[i] = 1;
+            anyre = true;
+          }
+        }
+        if (anyre) {
+          CK(put_mask(reo, d_act));
+          dots(V, j + 1, w, 0, 2);
+          update(V, j + 1, 2, w);
+          CK(fetch_all());
+          for (int i = 0; i < ni; ++i) {
+            if (!reo[i]) continue;
+            double* Hi = &H[(size_t)i * (m + 1) * m];
+            for (int i2 = 0; i2 <= j; ++i2) Hi[(size_t)i2 * m + j] += hsc[(size_t)i * SS + 2 * KRY_MAXV + i2];
+          }
+          CK(put_mask(inner, d_act));
+        }
+        scale_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(w, w, dsc + KRY_MAXV, SS, C, d_act);
+        ++g_launches;
+        for (int i = 0; i < ni; ++i) {
+          if (!inner[i]) continue;
+          double* Hi = &H[(size_t)i * (m + 1) * m];
+          double* gi = &g[(size_t)i * (m + 1)];
+          double* csi = &cs[(size_t)i * m];
+          double* sni = &sn[(size_t)i * m];
+          const double wn = std::sqrt(hsc[(size_t)i * SS + KRY_MAXV]);
+          Hi[(size_t)(j + 1) * m + j] = wn;
+          for (int i2 = 0; i2 < j; ++i2) {
+            const double a0 = Hi[(size_t)i2 * m + j], a1 = Hi[(size_t)(i2 + 1) * m + j];
+            Hi[(size_t)i2 * m + j] = csi[i2] * a0 + sni[i2] * a1;
+            Hi[(size_t)(i2 + 1) * m + j] = -sni[i2] * a0 + csi[i2] * a1;
+          }
+          const double a0 = Hi[(size_t)j * m + j], a1 = Hi[(size_t)(j + 1) * m + j];
+          const double den = std::hypot(a0, a1);
+          csi[j] = den > 0 ? a0 / den : 1.0;
+          sni[j] = den > 0 ? a1 / den : 0.0;
+          Hi[(size_t)j * m + j] = den;
+          Hi[(size_t)(j + 1) * m + j] = 0.0;
+          gi[j + 1] = -sni[j] * gi[j];
+          gi[j] = csi[j] * gi[j];
+          ++its[i];
+          jdone[i] = j + 1;
+          if (std::fabs(gi[j + 1]) <= target[i] || wn == 0.0 || its[i] >= maxit) inner[i] = 0;
+        }
+      }
+      // y = H^-1 g per instance ; zeta += V y
+      for (int i = 0; i < ni; ++i) {
+        const int jd = act[i] ? jdone[i] : 0;
+        const double* Hi = &H[(size_t)i * (m + 1) * m];
+        const double* gi = &g[(size_t)i * (m + 1)];
+        double* yi = hsc + (size_t)i * SS + 3 * KRY_MAXV;
+        for (int i2 = jd - 1; i2 >= 0; --i2) {
+          double v = gi[i2];
+          for (int k2 = i2 + 1; k2 < jd; ++k2) v -= Hi[(size_t)i2 * m + k2] * yi[k2];
+          yi[i2] = v / Hi[(size_t)i2 * m + i2];
+        }
+        jdone[i] = jd;
+      }
+      CK(cudaMemcpyAsync(dsc, hsc, sizeof(double) * ni * SS, cudaMemcpyHostToDevice, s));
+      CK(put_mask(jdone, d_mi));
+      combine_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(V, N, d_mi, dsc + 3 * KRY_MAXV, SS, state, C);
+      ++g_launches;
+      CK(cudaGetLastError());
+    }
+    for (int i = 0; i < ni; ++i) {
+      total_its += its[i];
+      max_its = std::max(max_its, its[i]);
+      if (!zero[i]) worst_rel = std::max(worst_rel, rel[i]);
+      if (!zero[i] && rel[i] > tol) {
+        c->err = "batch cn: GMRES did not reach the tolerance within maxit on instance " + std::to_string(i);
+        if (st) {
+          st->steps = step + 1; st->iterations = total_its; st->max_iterations = max_its;
+          st->last_rel_residual = worst_rel; st->kernel_launches = g_launches - launches0;
+        }
+        std::fill(act.begin(), act.end(), 1);
+        put_mask(act, d_act);
+        return SAP_ENOCONV;
+      }
+    }
+  }
+  std::fill(act.begin(), act.end(), 1);
+  CK(put_mask(act, d_act));
+  if (st) {
+    st->steps = nsteps; st->iterations = total_its; st->max_iterations = max_its;
+    st->last_rel_residual = worst_rel; st->kernel_launches = g_launches - launches0;
+  }
+  return SAP_OK;
+cuda_fail:
+  c->err = std::string("batch cn: ") + cudaGetErrorString(err);
+  return SAP_ECUDA;
+#undef CK
+}
+
+sap_status batch_cn(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
+                    sap_solver_stats* st, cudaStream_t s) {
+  sap_status ps = batch_prepare(c, s);
+  if (ps != SAP_OK) return ps;
+  return c->prec == SAP_PREC_FP64 ? batch_cn_impl<double>(c, state, dt, nsteps, tol, restart, maxit, st, s)
+                                  : batch_cn_impl<float>(c, state, dt, nsteps, tol, restart, maxit, st, s);
 }
 
 }  // namespace sap

@@ -24,6 +24,7 @@ enum : int { MF_ONE = 0, MF_P, MF_GM, MF_V, MF_INV_V, MF_INV_GM, MF_INV_P, MF_IN
 
 struct Term {
   int mat;      // matrix id in the bank, or MAT_I
+  int matT;     // id of the transposed matrix (for the transposed operator), or MAT_I
   int sf;       // spatial factor component or SF_ONE
   int mf;       // momentum factor
   int nu;       // 1: multiply by nu at the phase-space node
@@ -49,7 +50,7 @@ struct Bank {
   const int* rp;   // concatenated row pointers (absolute offsets into col/val)
   const int* col;
   const T* val;
-  int rp_off[64];
+  int rp_off[96];
 };
 
 template <typename T>
@@ -100,6 +101,29 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// Device tables for a batch of independent problems run by one launch per operator apply.
+template <typename T>
+struct BatchDev {
+  const OpParams<T>* P = nullptr;     // [ninst] parameter blocks (device)
+  const int64_t* doff = nullptr;      // [ninst] first DoF of each instance in the state vectors
+  const int* cpb = nullptr;           // [ninst] cells per thread block
+  const int* stride = nullptr;        // [ninst] shared-memory elements per cell
+  const int2* blocks = nullptr;       // [nblocks] (instance, first cell)
+  int nblocks = 0, threads = 0;
+  size_t smem = 0;
+};
+
+// Chunking of the concatenated state for the per-instance Krylov reductions: chunks never cross an
+// instance boundary.
+struct BatchChunks {
+  const int* inst = nullptr;          // [nchunks] instance of the chunk
+  const int64_t* k0 = nullptr;        // [nchunks] first element
+  const int* len = nullptr;           // [nchunks] length (<= KRY_CHUNK)
+  const int* first = nullptr;         // [ninst] first chunk of the instance
+  const int* count = nullptr;         // [ninst] number of chunks of the instance
+  int nchunks = 0;
+};
+
 }  // namespace sap
 
 // The context (opaque to callers).
@@ -131,6 +155,20 @@ struct sap_ctx {
   int krylov_restart = 0;
   std::vector<double> bank_nnz;                // nnz per bank matrix (cost model)
   int64_t launches = 0;                        // kernels launched by the current call
+  // batches: a batch handle owns one sub-context per instance and runs them with batched launches
+  std::vector<sap_ctx*> sub;
+  std::vector<int64_t> inst_off;
+  int fields_version = 0;                      // bumped by sap_set_fields
+  int batch_built_version = -1;                // sum of the sub versions the batch tables were built for
+  int batch_target_threads = 256;              // autotuned thread-block size target
+  bool batch_tuned = false;
+  std::vector<sap::DevBuf> batch_bufs;
+  sap::BatchDev<double> b64;
+  sap::BatchDev<float> b32;
+  sap::BatchChunks chunks;
+  int* d_active = nullptr;                     // [ninst] device activity mask
+  std::vector<int> h_active;
+  sap_ctx* parent = nullptr;                   // set on the sub-contexts of a batch
 };
 
 namespace sap {
@@ -141,7 +179,16 @@ sap_status erk_steps(sap_ctx* c, double* state, double dt, int nsteps, cudaStrea
 sap_status erk_steps_noalloc(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s);
 sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
                     sap_solver_stats* st, cudaStream_t s);
+sap_status cn_steps_mixed(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
+                          sap_solver_stats* st, cudaStream_t s);
 int apply_cells_per_block(int n, int nloc);
+int apply_cell_stride(const OpParams<double>& P);
+sap_status batch_prepare(sap_ctx* c, cudaStream_t s);
+sap_status batch_apply(sap_ctx* c, const void* x, void* y, int mode, cudaStream_t s);
+sap_status batch_cn(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
+                    sap_solver_stats* st, cudaStream_t s);
+sap_status batch_erk(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s);
 int64_t launch_count();
 int64_t krylov_scratch_doubles(int64_t N);
+int64_t krylov_batch_scratch_doubles(const std::vector<int64_t>& Ns);
 }  // namespace sap

@@ -333,6 +333,50 @@ extern "C" sap_status sap_create(const sap_desc* desc, int prec, sap_handle* out
   return SAP_OK;
 }
 
+extern "C" sap_status sap_create_batch(int ninst, const sap_desc* descs, int prec, sap_handle* out) {
+  if (!out || !descs || ninst < 1) {
+    g_create_error = "sap_create_batch: bad arguments";
+    return SAP_EINVAL;
+  }
+  *out = nullptr;
+  sap_ctx* c = new sap_ctx();
+  c->prec = prec;
+  std::vector<int64_t> Ns;
+  for (int i = 0; i < ninst; ++i) {
+    sap_handle sub = nullptr;
+    sap_status st = sap_create(&descs[i], prec, &sub);
+    if (st != SAP_OK) {
+      g_create_error = "sap_create_batch: instance " + std::to_string(i) + ": " + g_create_error;
+      for (auto* s2 : c->sub) {
+        s2->parent = nullptr;
+        sap_destroy(s2);
+      }
+      delete c;
+      return st;
+    }
+    sub->parent = c;
+    c->inst_off.push_back(c->N);
+    c->N += sub->N;
+    Ns.push_back(sub->N);
+    c->sub.push_back(sub);
+  }
+  if (cudaMalloc(&c->small, sizeof(double) * krylov_batch_scratch_doubles(Ns)) != cudaSuccess ||
+      cudaMallocHost(&c->small_host, sizeof(double) * 4 * 32 * (size_t)ninst) != cudaSuccess) {
+    g_create_error = "sap_create_batch: allocation failed";
+    sap_destroy(c);
+    return SAP_ENOMEM;
+  }
+  *out = c;
+  return SAP_OK;
+}
+
+extern "C" sap_status sap_batch_instance(sap_handle c, int inst, sap_handle* sub, int64_t* offset) {
+  if (!c || c->sub.empty() || inst < 0 || inst >= (int)c->sub.size()) return SAP_EINVAL;
+  if (sub) *sub = c->sub[inst];
+  if (offset) *offset = c->inst_off[inst];
+  return SAP_OK;
+}
+
 // ------------------------------------------------------------------------------------------------
 // points
 // ------------------------------------------------------------------------------------------------
@@ -465,7 +509,7 @@ template <typename T>
 static void set_bank(OpParams<T>& P, const BankBuilder& B, sap_ctx* c, std::vector<DevBuf>& own) {
   std::vector<int> rp, col;
   std::vector<double> val;
-  if (B.mats.size() > 64) throw std::string("too many matrices");
+  if (B.mats.size() > 96) throw std::string("too many matrices");
   for (size_t m = 0; m < B.mats.size(); ++m) {
     P.bank.rp_off[m] = (int)rp.size();
     int off = (int)col.size();
@@ -527,7 +571,18 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
     auto AA_id = [&](int a, int b) { return B.add("AA" + std::to_string(a) + std::to_string(b), Tb.AA[a][b]); };
     std::vector<Term> react;
     auto add_term = [&](std::vector<Term>& v, int mat, int sfc, int mf, int nuf, double sc) {
-      v.push_back(Term{mat, sfc, mf, nuf, sc});
+      int matT = MAT_I;
+      if (mat != MAT_I) {
+        std::string key;
+        for (auto& kv : B.ids)
+          if (kv.second == mat) key = kv.first;
+        Mat m(n);
+        const HostCSR& h = B.mats[mat];
+        for (int i = 0; i < n; ++i)
+          for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) m(h.col[k], i) = h.val[k];
+        matT = B.add(key + "^T", m);
+      }
+      v.push_back(Term{mat, matT, sfc, mf, nuf, sc});
     };
     // reaction matrix R - div(beta)  (Eq. definitions-advection-reaction-eq, Eq. linear-system-...)
     if (terms & SAP_TERM_MOM) {
@@ -570,15 +625,15 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
       std::vector<Term> adv;
       if (is_spatial(A.kind)) {
         if (terms & SAP_TERM_ADV) {
-          adv.push_back(Term{MAT_I, SF_U + a, MF_ONE, 0, 1.0});
-          adv.push_back(Term{A_id(a), SF_ONE, MF_V, 0, 1.0});
+          adv.push_back(Term{MAT_I, MAT_I, SF_U + a, MF_ONE, 0, 1.0});
+          adv.push_back(Term{A_id(a), A_id(a), SF_ONE, MF_V, 0, 1.0});
         }
       } else if (terms & SAP_TERM_MOM) {
         for (int b = 0; b < 3; ++b)
-          if (nonzero[SF_DU + b]) adv.push_back(Term{A_id(b), SF_DU + b, lnp ? MF_GM_OVER_P : MF_GM, 0, -1.0});
+          if (nonzero[SF_DU + b]) adv.push_back(Term{A_id(b), A_id(b), SF_DU + b, lnp ? MF_GM_OVER_P : MF_GM, 0, -1.0});
         for (int b = 0; b < 3; ++b)
           for (int e = 0; e < 3; ++e)
-            if (nonzero[SF_G + 3 * b + e]) adv.push_back(Term{AA_id(b, e), SF_G + 3 * b + e, lnp ? MF_ONE : MF_P, 0, -1.0});
+            if (nonzero[SF_G + 3 * b + e]) adv.push_back(Term{AA_id(b, e), AA_id(b, e), SF_G + 3 * b + e, lnp ? MF_ONE : MF_P, 0, -1.0});
       }
       if ((int)adv.size() > MAXADV) throw std::string("too many advection terms");
       A.nadv = (int)adv.size();
@@ -752,6 +807,7 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
     fill(c->p64, double{});
     fill(c->p32, float{});
     c->fields_set = true;
+    c->fields_version += 1;
   } catch (const std::string& e) {
     c->err = "sap_set_fields: " + e;
     return SAP_ENOMEM;
@@ -790,11 +846,15 @@ static bool ensure_ws32(sap_ctx* c, int count) {
 
 extern "C" sap_status sap_apply_operator(sap_handle c, const void* x, void* y, int mode, sap_stream stream) {
   if (!c || !x || !y || x == y) return SAP_EINVAL;
+  if (!c->sub.empty()) {
+    if (mode != SAP_APPLY_D && mode != SAP_APPLY_RHS) return SAP_EUNSUPPORTED;
+    return batch_apply(c, x, y, mode, (cudaStream_t)stream);
+  }
   if (!c->fields_set) {
     c->err = "fields not set";
     return SAP_EINVAL;
   }
-  if (mode != SAP_APPLY_D && mode != SAP_APPLY_RHS) {
+  if (mode != SAP_APPLY_D && mode != SAP_APPLY_RHS && mode != SAP_APPLY_T) {
     c->err = "unsupported apply mode";
     return SAP_EUNSUPPORTED;
   }
@@ -810,6 +870,13 @@ extern "C" sap_status sap_apply_operator(sap_handle c, const void* x, void* y, i
 
 extern "C" sap_status sap_step_erk(sap_handle c, double* state, double dt, int nsteps, sap_stream stream) {
   if (!c || !state || nsteps < 0) return SAP_EINVAL;
+  if (!c->sub.empty()) {
+    if (c->prec == SAP_PREC_FP64 ? !ensure_ws64(c, 3) : (!ensure_ws32(c, 2) || !ensure_ws64(c, 1))) {
+      c->err = "erk: workspace allocation failed";
+      return SAP_ENOMEM;
+    }
+    return batch_erk(c, state, dt, nsteps, (cudaStream_t)stream);
+  }
   if (!c->fields_set) {
     c->err = "fields not set";
     return SAP_EINVAL;
@@ -833,13 +900,24 @@ extern "C" sap_status sap_step_erk_noalloc(sap_handle c, double* state, double d
 extern "C" sap_status sap_step_cn(sap_handle c, double* state, double dt, int nsteps, double tol, int restart,
                                   int maxit, sap_solver_stats* stats, sap_stream stream) {
   if (!c || !state || nsteps < 0 || restart < 1 || restart > 31 || maxit < 1 || !(tol > 0)) return SAP_EINVAL;
+  if (!c->sub.empty()) {
+    const bool ok = c->prec == SAP_PREC_FP64 ? ensure_ws64(c, restart + 3) : (ensure_ws32(c, restart + 1) && ensure_ws64(c, 2));
+    if (!ok) {
+      c->err = "cn: workspace allocation failed";
+      return SAP_ENOMEM;
+    }
+    return batch_cn(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
+  }
   if (!c->fields_set) {
     c->err = "fields not set";
     return SAP_EINVAL;
   }
-  if (c->prec != SAP_PREC_FP64) {
-    c->err = "cn: FP32 precision form not available for CN in this build";
-    return SAP_EUNSUPPORTED;
+  if (c->prec == SAP_PREC_FP32) {
+    if (!ensure_ws32(c, restart + 1) || !ensure_ws64(c, 2)) {
+      c->err = "cn: workspace allocation failed";
+      return SAP_ENOMEM;
+    }
+    return cn_steps_mixed(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
   }
   if (!ensure_ws64(c, restart + 3)) {
     c->err = "cn: workspace allocation failed";
@@ -849,7 +927,21 @@ extern "C" sap_status sap_step_cn(sap_handle c, double* state, double dt, int ns
 }
 
 extern "C" sap_status sap_apply_cost(sap_handle c, double* flops, double* bytes) {
-  if (!c || !flops || !bytes || !c->fields_set) return SAP_EINVAL;
+  if (!c || !flops || !bytes) return SAP_EINVAL;
+  if (!c->sub.empty()) {
+    double f = 0, b = 0;
+    for (auto* s2 : c->sub) {
+      double f1, b1;
+      sap_status st = sap_apply_cost(s2, &f1, &b1);
+      if (st != SAP_OK) return st;
+      f += f1;
+      b += b1;
+    }
+    *flops = f;
+    *bytes = b;
+    return SAP_OK;
+  }
+  if (!c->fields_set) return SAP_EINVAL;
   const OpParams<double>& P = c->p64;
   const int n = c->n, nloc = c->nloc, nfp = c->nfp, q = c->q, D = c->D;
   auto nnz_row_avg = [&](int mat) -> double {
@@ -889,6 +981,14 @@ extern "C" sap_status sap_apply_cost(sap_handle c, double* flops, double* bytes)
 
 extern "C" sap_status sap_destroy(sap_handle c) {
   if (!c) return SAP_OK;
+  if (c->parent) return SAP_EINVAL;  // sub-handles belong to their batch
+  for (auto* s2 : c->sub) {
+    s2->parent = nullptr;
+    sap_destroy(s2);
+  }
+  c->sub.clear();
+  for (auto& b : c->batch_bufs) cudaFree(b.p);
+  c->batch_bufs.clear();
   free_bufs(c->owned);
   auto it = g_fields.find(c);
   if (it != g_fields.end()) {

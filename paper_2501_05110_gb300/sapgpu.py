@@ -19,10 +19,10 @@ AXIS = {"x": 0, "y": 1, "z": 2, "p": 3, "lnp": 4}
 BC = {"periodic": 0, "inflow0": 1, "continuous": 2}
 TERM = {"adv": 1, "mom": 2, "rot": 4, "coll": 8, "src": 16}
 PREC = {"fp64": 0, "fp32": 1}
-APPLY_D, APPLY_RHS = 0, 1
+APPLY_D, APPLY_RHS, APPLY_T = 0, 1, 2
 PTS_SPATIAL, PTS_FACE_X, PTS_FACE_Y, PTS_FACE_Z, PTS_PHASE = range(5)
 
-EXPORTS = ["sap_create", "sap_field_points", "sap_set_fields", "sap_num_dofs", "sap_apply_operator",
+EXPORTS = ["sap_create", "sap_create_batch", "sap_batch_instance", "sap_field_points", "sap_set_fields", "sap_num_dofs", "sap_apply_operator",
            "sap_step_erk", "sap_step_erk_noalloc", "sap_step_cn", "sap_apply_cost", "sap_destroy", "sap_last_error",
            "sap_coupling_matrix"]
 
@@ -57,6 +57,8 @@ def load_library(path: str = LIB_PATH):
     lib = C.CDLL(path)
     vp, i64p, dp = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)
     lib.sap_create.argtypes = [C.POINTER(Desc), C.c_int, C.POINTER(C.c_void_p)]
+    lib.sap_create_batch.argtypes = [C.c_int, C.POINTER(Desc), C.c_int, C.POINTER(C.c_void_p)]
+    lib.sap_batch_instance.argtypes = [vp, C.c_int, C.POINTER(C.c_void_p), i64p]
     lib.sap_field_points.argtypes = [vp, C.c_int, dp, i64p]
     lib.sap_set_fields.argtypes = [vp, dp, dp, dp, dp, C.POINTER(dp), dp, dp]
     lib.sap_num_dofs.argtypes = [vp, i64p]
@@ -98,30 +100,40 @@ def _stream_handle(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
+def make_desc(prob):
+    """sap_desc for a workloads.Problem; returns (desc, keep-alive edge arrays)."""
+    D = len(prob.axes)
+    d = Desc()
+    d.ndim = D
+    edges = [np.ascontiguousarray(e, dtype=np.float64) for e in prob.edges]
+    for a in range(D):
+        d.axis_kind[a] = AXIS[prob.axes[a]]
+        d.ncells[a] = len(edges[a]) - 1
+        d.edges[a] = edges[a].ctypes.data_as(C.POINTER(C.c_double))
+        d.bc_lo[a] = BC[prob.bc[a][0]]
+        d.bc_hi[a] = BC[prob.bc[a][1]]
+    d.lmax, d.degree, d.V = prob.lmax, prob.k, float(prob.V)
+    d.terms = sum(TERM[t] for t in prob.terms)
+    return d, edges
+
+
 class Solver:
     """One problem on the current CUDA device (wraps a sap_handle)."""
 
-    def __init__(self, prob, precision: str = "fp64"):
+    def __init__(self, prob, precision: str = "fp64", handle=None):
         self.lib = load_library()
         self.prob = prob
         self.precision = precision
-        D = len(prob.axes)
-        d = Desc()
-        d.ndim = D
-        self._edges = [np.ascontiguousarray(e, dtype=np.float64) for e in prob.edges]
-        for a in range(D):
-            d.axis_kind[a] = AXIS[prob.axes[a]]
-            d.ncells[a] = len(self._edges[a]) - 1
-            d.edges[a] = self._edges[a].ctypes.data_as(C.POINTER(C.c_double))
-            d.bc_lo[a] = BC[prob.bc[a][0]]
-            d.bc_hi[a] = BC[prob.bc[a][1]]
-        d.lmax, d.degree, d.V = prob.lmax, prob.k, float(prob.V)
-        d.terms = sum(TERM[t] for t in prob.terms)
-        h = C.c_void_p()
-        st = self.lib.sap_create(C.byref(d), PREC[precision], C.byref(h))
-        if st != SAP_OK:
-            raise SapError(st, self.lib.sap_last_error(None).decode())
-        self.h = h
+        self.owned = handle is None
+        if handle is None:
+            d, self._edges = make_desc(prob)
+            h = C.c_void_p()
+            st = self.lib.sap_create(C.byref(d), PREC[precision], C.byref(h))
+            if st != SAP_OK:
+                raise SapError(st, self.lib.sap_last_error(None).decode())
+            self.h = h
+        else:
+            self.h = handle
         n = C.c_int64()
         self._check(self.lib.sap_num_dofs(self.h, C.byref(n)))
         self.N = n.value
@@ -213,12 +225,52 @@ class Solver:
         return f.value, b.value
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and self.owned:
             self.lib.sap_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
             self.close()
         except Exception:
             pass
+
+
+class Batch(Solver):
+    """Independent problems run together (sap_create_batch): one launch per operator apply over all
+    instances, lock-step per-instance GMRES.  The state is the concatenation of the instances'
+    canonical states (``offsets``)."""
+
+    def __init__(self, probs, precision: str = "fp32"):
+        self.lib = load_library()
+        self.probs = list(probs)
+        self.precision = precision
+        self.owned = True
+        descs = (Desc * len(self.probs))()
+        self._edges = []
+        for i, p in enumerate(self.probs):
+            d, e = make_desc(p)
+            descs[i] = d
+            self._edges.append(e)
+        h = C.c_void_p()
+        st = self.lib.sap_create_batch(len(self.probs), descs, PREC[precision], C.byref(h))
+        if st != SAP_OK:
+            raise SapError(st, self.lib.sap_last_error(None).decode())
+        self.h = h
+        self.instances, self.offsets = [], []
+        for i, p in enumerate(self.probs):
+            sub, off = C.c_void_p(), C.c_int64()
+            self._check(self.lib.sap_batch_instance(self.h, i, C.byref(sub), C.byref(off)))
+            self.instances.append(Solver(p, precision, handle=sub))
+            self.offsets.append(off.value)
+        n = C.c_int64()
+        self._check(self.lib.sap_num_dofs(self.h, C.byref(n)))
+        self.N = n.value
+
+    def initial_state(self, device="cuda"):
+        import torch
+        return torch.cat([s.initial_state(device) for s in self.instances])
+
+    def split(self, v):
+        """Views of a batch vector per instance."""
+        return [v[o:o + s.N] for o, s in zip(self.offsets, self.instances)]

@@ -28,10 +28,10 @@ class NodalOracle:
         d = self.disc
         out = np.zeros_like(v)
         nl = d.mesh.nloc
-        for c in self.cells:
-            for r in range(d.n):
-                idx = d.dof(c, r, 0) + np.arange(nl)
-                out[idx] = np.linalg.solve(d.M[idx][:, idx].toarray(), v[idx])
+        for ci, c in enumerate(self.cells):
+            blk = d.mass_blocks[ci]
+            idx = d.dof(c, 0, 0) + np.arange(d.n * nl)
+            out[idx] = np.linalg.solve(blk, v[idx].reshape(d.n, nl).T).T.ravel()
         return out
 
     def apply(self, y_nodal, rhs=False):
