@@ -158,6 +158,20 @@ sap_status sap_step_erk(sap_handle h, double* state, double dt, int nsteps, sap_
 sap_status sap_step_cn(sap_handle h, double* state, double dt, int nsteps, double tol, int restart,
                        int maxit, sap_solver_stats* stats, sap_stream stream);
 
+/* One step of the discrete adjoint of the Crank--Nicolson step (Eq. theta-method, theta = 1/2).
+ * The forward step maps zeta_prev to zeta_next through A zeta_next = B zeta_prev + dt M^-1 h with
+ * A = 1 + dt/2 M^-1 D, B = 1 - dt/2 M^-1 D.  On entry `lambda` (device, N doubles) holds dJ/dzeta_next;
+ * the call solves A^T mu = lambda by restarted GMRES on the transposed operator (Jacobi, tolerance
+ * `tol` on the true relative residual), overwrites lambda with B^T mu = dJ/dzeta_prev, writes mu to
+ * `mu_out` when it is not NULL (for derivatives the caller forms itself), and, when `grad_nu` is not
+ * NULL, adds dJ/dnu at every phase-space node: -dt/2 sum_j mu_j l_j(l_j+1)/2 (zeta_prev+zeta_next)_j
+ * (the collision term nu C of Eq. definitions-advection-reaction-eq is pointwise in the nodal basis).
+ * zeta_prev / zeta_next are the forward states (device).  Synchronous.  `stats` may be NULL.
+ * Errors: SAP_EINVAL, SAP_ENOCONV, SAP_ECUDA, SAP_EUNSUPPORTED (batch handles, FP32 contexts). */
+sap_status sap_adjoint_step_cn(sap_handle h, const double* zeta_prev, const double* zeta_next, double* lambda,
+                               double dt, double tol, int restart, int maxit, double* mu_out, double* grad_nu,
+                               sap_solver_stats* stats, sap_stream stream);
+
 /* Largest N (degrees of freedom) that sap_step_erk_noalloc accepts. */
 #define SAP_NOALLOC_MAX_DOFS 262144
 

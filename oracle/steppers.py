@@ -93,3 +93,19 @@ def gmres(A, b, x0, tol=1e-10, restart=30, maxit=10000):
         y = np.linalg.solve(np.triu(H[:j_done, :j_done]), g[:j_done])
         x = x + dinv * (V[:j_done].T @ y)
     return x, its
+
+
+def cn_tangent(M, D, h, dD, zeta0, dt, nsteps):
+    """Tangent of the Crank--Nicolson trajectory along a parameter direction with dD = dD/dtheta:
+    differentiating (M + dt/2 D) z^n = (M - dt/2 D) z^(n-1) + dt h (Eq. theta-method, theta = 1/2)
+    gives (M + dt/2 D) d^n = (M - dt/2 D) d^(n-1) - dt/2 dD (z^n + z^(n-1)), d^0 = 0.
+    Returns (z^N, d^N)."""
+    lhs = spla.splu(sp.csc_matrix(M + 0.5 * dt * D))
+    rhs_op = M - 0.5 * dt * D
+    z = np.array(zeta0, dtype=float)
+    d = np.zeros_like(z)
+    for _ in range(nsteps):
+        zn = lhs.solve(rhs_op @ z + dt * h)
+        d = lhs.solve(rhs_op @ d - 0.5 * dt * (dD @ (zn + z)))
+        z = zn
+    return z, d

@@ -1793,4 +1793,171 @@ sap_status batch_cn(sap_ctx* c, double* state, double dt, int nsteps, double tol
                                   : batch_cn_impl<float>(c, state, dt, nsteps, tol, restart, maxit, st, s);
 }
 
+
+// ================================================================================================
+// Discrete adjoint of the Crank--Nicolson step
+// ================================================================================================
+// grad[node] += coef * sum_r mu[r,node] * l_r(l_r+1)/2 * (zp + zn)[r,node]   (l_r = floor(sqrt(r)))
+__global__ void grad_nu_kernel(const double* __restrict__ mu, const double* __restrict__ zp,
+                               const double* __restrict__ zn, int n, int nloc, int64_t npv, double coef,
+                               double* __restrict__ grad) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npv; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = p / nloc;
+    const int i = (int)(p - cell * nloc);
+    double acc = 0.0;
+    for (int r = 1; r < n; ++r) {
+      int l = (int)sqrt((double)r);
+      while ((l + 1) * (l + 1) <= r) ++l;
+      while (l * l > r) --l;
+      const size_t k = ((size_t)cell * n + r) * nloc + i;
+      acc += 0.5 * l * (l + 1) * mu[k] * (zp[k] + zn[k]);
+    }
+    grad[p] += coef * acc;
+  }
+}
+
+sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, double* lambda, double dt, double tol,
+                           int m, int maxit, double* mu_out, double* grad_nu, sap_solver_stats* st, cudaStream_t s) {
+  const int64_t N = c->N;
+  double* V = c->ws64;                       // (m+1) vectors
+  double* b = V + (size_t)(m + 1) * N;       // right side (copy of lambda)
+  double* tmp = b + N;
+  double* mu = tmp + N;                      // solution
+  const int nchunks = (int)((N + KRY_CHUNK - 1) / KRY_CHUNK);
+  KrylovCtx K{c, s, nchunks, c->small, c->small + (size_t)(KRY_MAXV + 1) * nchunks, c->small_host};
+  double* const d_h1 = K.dsc;
+  double* const d_nrm = K.dsc + KRY_MAXV;
+  double* const d_h2 = K.dsc + 2 * KRY_MAXV;
+  double* const d_y = K.dsc + 3 * KRY_MAXV;
+  const OpParams<double>& P = c->p64;
+  const double half = 0.5 * dt;
+  std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), y(m);
+  const int64_t launches0 = g_launches;
+  int its = 0;
+  double rel = 0.0;
+  cudaError_t err = cudaSuccess;
+#define CK(x)                               \
+  do {                                      \
+    err = (x);                              \
+    if (err != cudaSuccess) goto cuda_fail; \
+  } while (0)
+  CK(cudaMemcpyAsync(b, lambda, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(mu, lambda, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));  // initial guess
+  {
+    dots<double>(K, nullptr, 0, b, 1, d_nrm);
+    CK(fetch(K, KRY_MAXV, 1));
+    const double bnorm = std::sqrt(K.hsc[KRY_MAXV]);
+    if (bnorm == 0.0) {
+      CK(cudaMemsetAsync(mu, 0, sizeof(double) * N, s));
+    } else {
+      for (;;) {
+        {  // r = b - A^T mu
+          Epi<double> e{};
+          e.out = tmp; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half;
+          CK(launch_applyT<double>(P, mu, e, s));
+        }
+        dots<double>(K, nullptr, 0, tmp, 1, d_nrm);
+        CK(fetch(K, KRY_MAXV, 1));
+        rel = std::sqrt(K.hsc[KRY_MAXV]) / bnorm;
+        if (rel <= tol || its >= maxit) break;
+        {
+          Epi<double> e{};
+          e.out = V; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.jacobi = 1; e.cj = half;
+          CK(launch_applyT<double>(P, mu, e, s));
+        }
+        dots<double>(K, nullptr, 0, V, 1, d_nrm);
+        scale_kernel<double><<<1024, KRY_THREADS, 0, s>>>(V, V, d_nrm, 2, N);
+        ++g_launches;
+        CK(fetch(K, KRY_MAXV, 1));
+        const double beta = std::sqrt(K.hsc[KRY_MAXV]);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        const double target = 0.5 * beta * (tol / rel);
+        int jdone = 0;
+        for (int j = 0; j < m && its < maxit; ++j) {
+          double* w = V + (size_t)(j + 1) * N;
+          {
+            Epi<double> e{};
+            e.out = w; e.ax = 1.0; e.bl = half; e.jacobi = 1; e.cj = half;
+            CK(launch_applyT<double>(P, V + (size_t)j * N, e, s));
+          }
+          dots<double>(K, V, j + 1, w, 1, d_h1);
+          update<double>(K, V, j + 1, d_h1, w, d_nrm);
+          CK(fetch(K, 0, KRY_MAXV + 1));
+          for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] = K.hsc[i2];
+          const double wn0 = std::sqrt(K.hsc[j + 1]);
+          double wn = std::sqrt(K.hsc[KRY_MAXV]);
+          if (wn < 0.7071067811865476 * wn0) {
+            dots<double>(K, V, j + 1, w, 0, d_h2);
+            update<double>(K, V, j + 1, d_h2, w, d_nrm);
+            CK(fetch(K, 2 * KRY_MAXV, j + 1));
+            CK(fetch(K, KRY_MAXV, 1));
+            for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] += K.hsc[2 * KRY_MAXV + i2];
+            wn = std::sqrt(K.hsc[KRY_MAXV]);
+          }
+          H[(size_t)(j + 1) * m + j] = wn;
+          if (wn > 0.0) {
+            scale_kernel<double><<<1024, KRY_THREADS, 0, s>>>(w, w, d_nrm, 2, N);
+            ++g_launches;
+          }
+          for (int i2 = 0; i2 < j; ++i2) {
+            const double a0 = H[(size_t)i2 * m + j], a1 = H[(size_t)(i2 + 1) * m + j];
+            H[(size_t)i2 * m + j] = cs[i2] * a0 + sn[i2] * a1;
+            H[(size_t)(i2 + 1) * m + j] = -sn[i2] * a0 + cs[i2] * a1;
+          }
+          const double a0 = H[(size_t)j * m + j], a1 = H[(size_t)(j + 1) * m + j];
+          const double den = std::hypot(a0, a1);
+          cs[j] = den > 0 ? a0 / den : 1.0;
+          sn[j] = den > 0 ? a1 / den : 0.0;
+          H[(size_t)j * m + j] = den;
+          H[(size_t)(j + 1) * m + j] = 0.0;
+          g[j + 1] = -sn[j] * g[j];
+          g[j] = cs[j] * g[j];
+          ++its;
+          jdone = j + 1;
+          if (std::fabs(g[j + 1]) <= target || wn == 0.0) break;
+        }
+        for (int i2 = jdone - 1; i2 >= 0; --i2) {
+          double v = g[i2];
+          for (int k2 = i2 + 1; k2 < jdone; ++k2) v -= H[(size_t)i2 * m + k2] * y[k2];
+          y[i2] = v / H[(size_t)i2 * m + i2];
+        }
+        for (int i2 = 0; i2 < jdone; ++i2) K.hsc[3 * KRY_MAXV + i2] = y[i2];
+        CK(cudaMemcpyAsync(d_y, K.hsc + 3 * KRY_MAXV, sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
+        combine_kernel<double><<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, d_y, mu, N);
+        ++g_launches;
+        CK(cudaGetLastError());
+      }
+    }
+  }
+  if (rel > tol) {
+    c->err = "adjoint cn: GMRES did not reach the tolerance within maxit";
+    if (st) {
+      st->steps = 1; st->iterations = its; st->max_iterations = its; st->last_rel_residual = rel;
+      st->kernel_launches = g_launches - launches0;
+    }
+    return SAP_ENOCONV;
+  }
+  {  // lambda <- B^T mu = mu - dt/2 L^T mu
+    Epi<double> e{};
+    e.out = lambda; e.ax = 1.0; e.bl = -half;
+    CK(launch_applyT<double>(P, mu, e, s));
+  }
+  if (grad_nu && (c->desc.terms & SAP_TERM_COLL)) {
+    grad_nu_kernel<<<1024, 256, 0, s>>>(mu, zp, zn, c->n, c->nloc, (int64_t)c->npv, -half, grad_nu);
+    ++g_launches;
+  }
+  if (mu_out) CK(cudaMemcpyAsync(mu_out, mu, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  if (st) {
+    st->steps = 1; st->iterations = its; st->max_iterations = its; st->last_rel_residual = rel;
+    st->kernel_launches = g_launches - launches0;
+  }
+  return SAP_OK;
+cuda_fail:
+  c->err = std::string("adjoint cn: ") + cudaGetErrorString(err);
+  return SAP_ECUDA;
+#undef CK
+}
+
 }  // namespace sap

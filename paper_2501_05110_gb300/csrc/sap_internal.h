@@ -181,6 +181,8 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
                     sap_solver_stats* st, cudaStream_t s);
 sap_status cn_steps_mixed(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
                           sap_solver_stats* st, cudaStream_t s);
+sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, double* lambda, double dt, double tol,
+                           int m, int maxit, double* mu_out, double* grad_nu, sap_solver_stats* st, cudaStream_t s);
 int apply_cells_per_block(int n, int nloc);
 int apply_cell_stride(const OpParams<double>& P);
 sap_status batch_prepare(sap_ctx* c, cudaStream_t s);

@@ -979,6 +979,28 @@ extern "C" sap_status sap_apply_cost(sap_handle c, double* flops, double* bytes)
   return SAP_OK;
 }
 
+extern "C" sap_status sap_adjoint_step_cn(sap_handle c, const double* zeta_prev, const double* zeta_next,
+                                          double* lambda, double dt, double tol, int restart, int maxit,
+                                          double* mu_out, double* grad_nu, sap_solver_stats* stats,
+                                          sap_stream stream) {
+  if (!c || !zeta_prev || !zeta_next || !lambda || restart < 1 || restart > 31 || maxit < 1 || !(tol > 0))
+    return SAP_EINVAL;
+  if (!c->sub.empty() || c->prec != SAP_PREC_FP64) {
+    c->err = "adjoint: FP64 single-problem contexts only";
+    return SAP_EUNSUPPORTED;
+  }
+  if (!c->fields_set) {
+    c->err = "fields not set";
+    return SAP_EINVAL;
+  }
+  if (!ensure_ws64(c, restart + 4)) {
+    c->err = "adjoint: workspace allocation failed";
+    return SAP_ENOMEM;
+  }
+  return adjoint_cn_step(c, zeta_prev, zeta_next, lambda, dt, tol, restart, maxit, mu_out, grad_nu, stats,
+                         (cudaStream_t)stream);
+}
+
 extern "C" sap_status sap_destroy(sap_handle c) {
   if (!c) return SAP_OK;
   if (c->parent) return SAP_EINVAL;  // sub-handles belong to their batch

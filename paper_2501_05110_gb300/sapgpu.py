@@ -23,7 +23,7 @@ APPLY_D, APPLY_RHS, APPLY_T = 0, 1, 2
 PTS_SPATIAL, PTS_FACE_X, PTS_FACE_Y, PTS_FACE_Z, PTS_PHASE = range(5)
 
 EXPORTS = ["sap_create", "sap_create_batch", "sap_batch_instance", "sap_field_points", "sap_set_fields", "sap_num_dofs", "sap_apply_operator",
-           "sap_step_erk", "sap_step_erk_noalloc", "sap_step_cn", "sap_apply_cost", "sap_destroy", "sap_last_error",
+           "sap_step_erk", "sap_step_erk_noalloc", "sap_step_cn", "sap_adjoint_step_cn", "sap_apply_cost", "sap_destroy", "sap_last_error",
            "sap_coupling_matrix"]
 
 
@@ -68,6 +68,8 @@ def load_library(path: str = LIB_PATH):
     lib.sap_step_cn.argtypes = [vp, vp, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
                                 C.POINTER(SolverStats), vp]
     lib.sap_apply_cost.argtypes = [vp, dp, dp]
+    lib.sap_adjoint_step_cn.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int, C.c_int, vp, vp,
+                                        C.POINTER(SolverStats), vp]
     lib.sap_destroy.argtypes = [vp]
     lib.sap_last_error.argtypes = [vp]
     lib.sap_last_error.restype = C.c_char_p
@@ -216,6 +218,16 @@ class Solver:
         st = SolverStats()
         self._check(self.lib.sap_step_cn(self.h, C.c_void_p(state.data_ptr()), dt, nsteps, tol, restart, maxit,
                                          C.byref(st), _stream_handle(stream)))
+        return st
+
+    def adjoint_step_cn(self, zeta_prev, zeta_next, lam, dt: float, tol: float = 1e-12, restart: int = 30,
+                        maxit: int = 4000, mu_out=None, grad_nu=None, stream=None) -> SolverStats:
+        """lam <- dJ/dzeta_prev given dJ/dzeta_next (in place); optional mu and nodal nu-gradient."""
+        st = SolverStats()
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        self._check(self.lib.sap_adjoint_step_cn(self.h, ptr(zeta_prev), ptr(zeta_next), ptr(lam), dt, tol, restart,
+                                                 maxit, ptr(mu_out), ptr(grad_nu), C.byref(st),
+                                                 _stream_handle(stream)))
         return st
 
     def apply_cost(self):

@@ -1,0 +1,128 @@
+"""Discrete adjoint of CN trajectories (library adjoint step + torch.autograd.Function with
+checkpoints): gradients with respect to a per-cell scattering field nu(x, p) and the shock speed U1,
+checked against central finite differences of GPU trajectories and against the FP64 oracle tangent."""
+import numpy as np
+import pytest
+
+from paper_2501_05110_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+XR, LNPR, NX, NPC, LMAX, NSTEPS = (-20.0, 20.0), (0.0, 4.0), 10, 6, 3, 5
+
+
+def _base(U1, nu_field=None):
+    return W.shock(nx=NX, npc=NPC, lmax=LMAX, xr=XR, lnpr=LNPR, U1=U1, nu_field=nu_field)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2501_05110_gb300 import build as sap_build
+    sap_build.build()
+    from paper_2501_05110_gb300 import adjoint, sapgpu
+    prob0 = _base(0.1)
+    xe, pe = prob0.edges
+    nu_cell_fun, z = W.lognormal_cell_nu(xe, pe, seed=6)
+    probe = sapgpu.Solver(_base(0.1, nu_cell_fun))
+    pts = probe.points(sapgpu.PTS_PHASE)
+    xs, p = pts[:, :1], np.exp(pts[:, 1])
+    nu_nodes = nu_cell_fun(xs, p)
+    nloc = 4
+    cell_of_node = np.arange(len(nu_nodes)) // nloc
+    probe.close()
+
+    def make(nu_np, U1):
+        vals = np.ascontiguousarray(nu_np if nu_np is not None else nu_nodes, dtype=np.float64)
+        return _base(U1, lambda xs_, p_, _v=vals: _v)
+
+    rng = np.random.default_rng(17)
+    N = prob0.ndofs
+    w = torch.from_numpy(rng.standard_normal(N)).cuda()
+    return dict(torch=torch, adjoint=adjoint, sapgpu=sapgpu, nu_nodes=nu_nodes, cell_of_node=cell_of_node,
+                make=make, w=w, nu_cell_fun=nu_cell_fun, edges=(xe, pe))
+
+
+def _J_forward(S, nu_np, U1):
+    sol = S["sapgpu"].Solver(S["make"](nu_np, U1))
+    y = sol.initial_state()
+    sol.step_cn(y, 1.0, NSTEPS, tol=1e-13, restart=30, maxit=20000)
+    S["torch"].cuda.synchronize()
+    val = float(S["w"] @ y)
+    sol.close()
+    return val
+
+
+def _adjoint_grads(S, checkpoint):
+    torch = S["torch"]
+    fam = S["adjoint"].CNProblemFamily(make_problem=S["make"], nsteps=NSTEPS, dt=1.0, tol=1e-13,
+                                       checkpoint=checkpoint)
+    nu_t = torch.tensor(S["nu_nodes"], dtype=torch.float64, device="cuda", requires_grad=True)
+    u1_t = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+    zN = S["adjoint"].CNTrajectory.apply(nu_t, u1_t, fam)
+    J = (S["w"] * zN).sum()
+    J.backward()
+    g_node = nu_t.grad.cpu().numpy()
+    g_cell = np.bincount(S["cell_of_node"], weights=g_node)
+    return g_cell, float(u1_t.grad), float(J.detach())
+
+
+def test_adjoint_nu_gradient_vs_finite_differences(setup):
+    S = setup
+    g_cell, _, J = _adjoint_grads(S, checkpoint=2)
+    assert abs(J - _J_forward(S, None, 0.1)) < 1e-12 * abs(J)
+    nu = S["nu_nodes"]
+    for c in (3, 27, 58):
+        eps = 1e-4 * nu[S["cell_of_node"] == c][0]
+        vals = []
+        for sgn in (1, -1):
+            v = nu.copy()
+            v[S["cell_of_node"] == c] += sgn * eps
+            vals.append(_J_forward(S, v, 0.1))
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        assert abs(fd - g_cell[c]) < 1e-6 * max(abs(fd), 1e-3 * np.abs(g_cell).max()), (c, fd, g_cell[c])
+
+
+def test_adjoint_U1_gradient_vs_finite_differences(setup):
+    S = setup
+    _, g_u1, _ = _adjoint_grads(S, checkpoint=3)
+    e = 1e-5 * 0.1
+    fd = (_J_forward(S, None, 0.1 + e) - _J_forward(S, None, 0.1 - e)) / (2 * e)
+    assert abs(fd - g_u1) < 1e-5 * abs(fd), (fd, g_u1)
+
+
+def test_adjoint_checkpoint_interval_invariant(setup):
+    S = setup
+    a = _adjoint_grads(S, checkpoint=1)
+    b = _adjoint_grads(S, checkpoint=50)
+    assert np.allclose(a[0], b[0], rtol=1e-10, atol=1e-14 * np.abs(a[0]).max())
+    assert abs(a[1] - b[1]) < 1e-10 * abs(a[1])
+
+
+def test_adjoint_nu_gradient_vs_oracle_tangent(setup):
+    """Directional derivative along a random per-cell direction: adjoint gradient . v equals the FP64
+    oracle's tangent-linear CN trajectory, contracted with the same weights (nodal basis)."""
+    from oracle import dg, steppers
+    from .oracle_bridge import NodalOracle
+    S = setup
+    xe, pe = S["edges"]
+    g_cell, _, _ = _adjoint_grads(S, checkpoint=2)
+    rng = np.random.default_rng(23)
+    v = rng.standard_normal((len(pe) - 1, len(xe) - 1))
+
+    def cellfun(vals):
+        def f(xs, p):
+            ix = np.clip(np.searchsorted(xe, xs[:, 0], side="right") - 1, 0, len(xe) - 2)
+            ip = np.clip(np.searchsorted(pe, np.log(p), side="right") - 1, 0, len(pe) - 2)
+            return vals[ip, ix]
+        return f
+
+    d0 = dg.Discretisation(_base(0.1, S["nu_cell_fun"]))
+    pv = _base(0.1, cellfun(v))
+    pv.terms = frozenset({"coll"})
+    dD = dg.Discretisation(pv).D
+    _, dz = steppers.cn_tangent(d0.M, d0.D, d0.h, dD, np.zeros(d0.N), 1.0, NSTEPS)
+    dJ_oracle = float(S["w"].cpu().numpy() @ d0.to_gauss_nodal(dz))
+    dJ_adj = float(np.sum(g_cell * v.reshape(-1)))  # cells: x fastest, as v.reshape
+    assert abs(dJ_adj - dJ_oracle) < 1e-8 * abs(dJ_oracle), (dJ_adj, dJ_oracle)

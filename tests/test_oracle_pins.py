@@ -421,3 +421,38 @@ def test_rows_of_cells_subset_matches_full_assembly():
     rows = np.concatenate([full.dof(c, 0, 0) + np.arange(full.n * full.mesh.nloc) for c in cells])
     np.testing.assert_allclose(part.D[rows].toarray(), full.D[rows].toarray(), atol=1e-15)
     np.testing.assert_allclose(part.h[rows], full.h[rows])
+
+
+def test_cn_tangent_matches_trajectory_differences():
+    """The oracle's CN tangent (d zeta^N / d nu along a per-cell direction) equals a central
+    difference of its own CN trajectories; D is linear in nu, so the difference is exact up to
+    rounding."""
+    rng = np.random.default_rng(3)
+    base = W.shock(nx=6, npc=4, lmax=2, xr=(-12.0, 12.0), lnpr=(0.0, 3.0))
+    xe, pe = base.edges
+    v = rng.standard_normal((len(pe) - 1, len(xe) - 1))
+    nu0, _ = W.lognormal_cell_nu(xe, pe, seed=6)
+
+    def cellfun(vals):
+        def f(xs, p):
+            ix = np.clip(np.searchsorted(xe, xs[:, 0], side="right") - 1, 0, len(xe) - 2)
+            ip = np.clip(np.searchsorted(pe, np.log(p), side="right") - 1, 0, len(pe) - 2)
+            return vals[ip, ix]
+        return f
+
+    def disc_with(nu_fun, terms=None):
+        p = W.shock(nx=6, npc=4, lmax=2, xr=(-12.0, 12.0), lnpr=(0.0, 3.0), nu_field=nu_fun)
+        if terms is not None:
+            p.terms = frozenset(terms)
+        return dg.Discretisation(p)
+
+    d0 = disc_with(nu0)
+    dD = disc_with(cellfun(v), terms={"coll"}).D
+    z, dz = steppers.cn_tangent(d0.M, d0.D, d0.h, dD, np.zeros(d0.N), 1.0, 5)
+    eps = 1e-4
+    zs = []
+    for sgn in (1, -1):
+        d = disc_with(lambda xs, p, s=sgn: nu0(xs, p) + s * eps * cellfun(v)(xs, p))
+        zs.append(steppers.theta_method(d.M, d.D, d.h, np.zeros(d.N), 1.0, 5))
+    fd = (zs[0] - zs[1]) / (2 * eps)
+    assert np.abs(fd - dz).max() < 1e-7 * np.abs(dz).max()
