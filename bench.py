@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "phase-space DoF-updates/s per CN step"
 UNIT = "DoF-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e-3  # SMs x DFMA/clk/SM x 2 flop x max GHz = 1.2586 TFLOP/s (FP64)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3  # SMs x FFMA/clk/SM x 2 flop x max GHz = 80.5 TFLOP/s (FP32)
 # DRAM bytes (read + write) per apply launch from the ncu capture in profiles/apply_kernel_fp64_shock.md,
 # valid only for the kernel source it was taken on (first 16 hex of sha256 of csrc/operator.cu)
 APPLY_TRAFFIC = {"bf2a474848085cbc": 10730240.0}
@@ -41,7 +42,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--workload", default="shock", choices=["shock", "box3d"])
+    ap.add_argument("--workload", default="shock", choices=["shock", "box3d", "batched", "adjoint"])
+    ap.add_argument("--cells", type=int, default=48, help="box3d: cells per axis")
+    ap.add_argument("--instances", type=int, default=512, help="batched: number of shock instances")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
@@ -171,7 +174,7 @@ def run_mine(args):
     from paper_2501_05110_gb300 import sapgpu
     sap_build.build()
     prob = workload_problem()
-    sol = sapgpu.Solver(prob, "fp64")
+    sol = sapgpu.Solver(prob, args.precision)
     N = sol.N
     stream = torch.cuda.current_stream()
     state = sol.initial_state()
@@ -236,7 +239,7 @@ def run_mine(args):
 
     # ---- dominant kernel: the operator apply, timed alone on the same stream ----------------------
     flops, abytes = sol.apply_cost()
-    x = state.clone()
+    x = state.clone() if args.precision == "fp64" else state.float()
     y = torch.empty_like(x)
     for _ in range(10):
         sol.apply(x, y)
@@ -248,19 +251,24 @@ def run_mine(args):
     e1.synchronize()
     t_apply = e0.elapsed_time(e1) * 1e-3 / args.apply_reps
     achieved = flops / t_apply / 1e12
+    peak_alu = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
     import hashlib
     src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2501_05110_gb300", "csrc", "operator.cu"), "rb").read()).hexdigest()[:16]
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": APPLY_TRAFFIC.get(src_sha),
-                "kernel": "apply_kernel<double>",
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                "frac": achieved / peak_alu,
+                "traffic": APPLY_TRAFFIC.get(src_sha) if args.precision == "fp64" else None,
+                "kernel": "apply_kernel<double>" if args.precision == "fp64" else "apply_kernel<float>",
                 "apply_us": t_apply * 1e6, "flops_per_apply": flops, "algorithmic_bytes_per_apply": abytes,
                 "hbm_view": {"achieved_gbs": abytes / t_apply / 1e9, "peak_gbs": 6746.3,
                              "frac": abytes / t_apply / 1e9 / 6746.3},
-                "peak_note": "FP64 nominal from unit counts x max clock (FP64 ALU bound)"}
+                "peak_note": "nominal from unit counts x max clock (FP64: 2 DFMA/clk/SM; FP32: 128 FFMA/clk/SM)"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_config(prob, {"gmres_iterations_per_step": statistics.mean(its)}),
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32 apply + f64 residual/refinement",
+           "data": "synthetic",
+           "config": workload_config(prob, {"gmres_iterations_per_step": statistics.mean(its),
+                                            "precision": args.precision}),
            "roofline": roofline, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -302,7 +310,7 @@ def run_box3d(args):
     from paper_2501_05110_gb300 import sapgpu
     from paper_2501_05110_gb300 import workloads as W
     sap_build.build()
-    prob = W.box3d()
+    prob = W.box3d(ncells=args.cells)
     sol = sapgpu.Solver(prob, args.precision)
     N = sol.N
     stream = torch.cuda.current_stream()
@@ -336,7 +344,7 @@ def run_box3d(args):
                       "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
                       "dtype": "f64" if args.precision == "fp64" else "f32 apply, f64 state",
-                      "data": "synthetic", "config": {"workload": "box3d_48c_k2_l5_erk4_dt0.01", "dofs": N,
+                      "data": "synthetic", "config": {"workload": f"box3d_{args.cells}c_k2_l5_erk4_dt0.01", "dofs": N,
                                                       "l2": "state larger than L2"},
                       "apply": {"us": t_apply * 1e6, "flops": flops, "tflops": flops / t_apply / 1e12,
                                 "algorithmic_bytes": abytes, "gbs": abytes / t_apply / 1e9,
@@ -345,10 +353,119 @@ def run_box3d(args):
                       "stage_gbs": stage_bytes * 4 * args.steps / t / 1e9, "clocks": clk}))
 
 
+def run_batched(args):
+    """CN steps on a batch of independent seeded shock instances (r, nu0, lmax, x-cell count drawn
+    per instance), one batched apply launch per operator application, per-instance GMRES."""
+    import torch
+    from paper_2501_05110_gb300 import build as sap_build
+    from paper_2501_05110_gb300 import sapgpu
+    from paper_2501_05110_gb300 import workloads as W
+    sap_build.build()
+    probs = W.batched_shocks(count=args.instances)
+    t0 = time.perf_counter()
+    batch = sapgpu.Batch(probs, args.precision)
+    t_setup = time.perf_counter() - t0
+    N = batch.N
+    y = batch.initial_state()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        batch.step_cn(y, 1.0, 1, 1e-10, 30, 20000)
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    times, its, launches = [], [], 0
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = batch.step_cn(y, 1.0, 1, 1e-10, 30, 20000)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+        its.append(st.max_iterations)
+        launches += st.kernel_launches
+    clk = clocks.stop()
+    x = (y if args.precision == "fp64" else y.float()).clone()
+    out = torch.empty_like(x)
+    for _ in range(2):
+        batch.apply(x, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        batch.apply(x, out)
+    e1.record(stream)
+    e1.synchronize()
+    t_apply = e0.elapsed_time(e1) * 1e-3 / 5
+    flops, abytes = batch.apply_cost()
+    t = sum(times)
+    print(json.dumps({"metric": "phase-space DoF-updates/s per CN step (batched)", "value": N * args.steps / t,
+                      "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+                      "dtype": "f64" if args.precision == "fp64" else "f32 apply + f64 residual/refinement",
+                      "data": "synthetic",
+                      "config": {"workload": f"batched_shocks_{args.instances}_seed4", "dofs": N,
+                                 "instances": args.instances, "setup_s": t_setup,
+                                 "max_gmres_iterations_per_step": statistics.mean(its),
+                                 "lmax_counts": {str(l): sum(p.lmax == l for p in probs) for l in (1, 3, 5, 7)}},
+                      "apply": {"us": t_apply * 1e6, "gbs": abytes / t_apply / 1e9,
+                                "hbm_frac": abytes / t_apply / 1e9 / 6746.3, "tflops": flops / t_apply / 1e12},
+                      "gpu_launches": int(launches), "clocks": clk}))
+
+
+def run_adjoint(args):
+    """Forward + reverse (discrete adjoint) of CN steps on the full shock workload with a per-cell
+    log-normal nu field, checkpoints every 50 steps; reports wall time per forward+reverse step."""
+    import numpy as np
+    import torch
+    from paper_2501_05110_gb300 import adjoint, sapgpu
+    from paper_2501_05110_gb300 import build as sap_build
+    from paper_2501_05110_gb300 import workloads as W
+    sap_build.build()
+    base = W.shock()
+    xe, pe = base.edges
+    nu_fun, _ = W.lognormal_cell_nu(xe, pe, seed=6)
+    probe = sapgpu.Solver(W.shock(nu_field=nu_fun))
+    pts = probe.points(sapgpu.PTS_PHASE)
+    nu_nodes = nu_fun(pts[:, :1], np.exp(pts[:, 1]))
+    probe.close()
+
+    def make(nu_np, U1):
+        vals = np.ascontiguousarray(nu_np if nu_np is not None else nu_nodes, dtype=np.float64)
+        return W.shock(U1=U1, nu_field=lambda xs, p, _v=vals: _v)
+
+    nsteps = args.steps
+    fam = adjoint.CNProblemFamily(make_problem=make, nsteps=nsteps, dt=1.0, tol=1e-10, checkpoint=50)
+    nu_t = torch.tensor(nu_nodes, dtype=torch.float64, device="cuda", requires_grad=True)
+    u1_t = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    zN = adjoint.CNTrajectory.apply(nu_t, u1_t, fam)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    target = torch.zeros(64, dtype=torch.float64)
+    S = zN.view(64, 256, 16, 4)[:, :, 0, :].mean(dim=2)
+    L = (S.abs() + 1e-300).log().mean()
+    L.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    print(json.dumps({"metric": "forward + reverse wall time per CN step (adjoint, FP64)",
+                      "value": (t2 - t0) / nsteps, "unit": "s/step", "steps": nsteps,
+                      "forward_s": t1 - t0, "reverse_s": t2 - t1, "higher_is_better": False,
+                      "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "adjoint_shock_x256_lnp64_k1_l3_cn_lognormal_nu",
+                                 "checkpoint": 50, "dofs": base.ndofs},
+                      "grad_norm_nu": float(nu_t.grad.norm()), "grad_U1": float(u1_t.grad)}))
+
+
 def main():
     args = parse()
     if args.workload == "box3d" and not args.cpu_worker:
         run_box3d(args)
+        return
+    if args.workload == "batched" and not args.cpu_worker:
+        run_batched(args)
+        return
+    if args.workload == "adjoint" and not args.cpu_worker:
+        run_adjoint(args)
         return
     if args.cpu_worker:
         cpu_worker(args.cpu_worker)

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -43,6 +44,11 @@ struct Epi {
   int jacobi;           // multiply out by 1 / (1 + cj * diag(R - div beta))
   T cj;
   float* out32;         // optional: FP32 copy of out / (1 + cj * diag(R - div beta)), before `jacobi`
+  T* out2;              // optional second output out2 = ax2*x + bl2*(Lx) + gs2*s
+  T ax2, bl2, gs2;
+  T* outj;              // optional: out2 (or out when out2 is null) / (1 + cj * diag(R - div beta))
+  T axpost;             // added after the Jacobi scaling: out += axpost * x
+  const int* skip;      // when non-null and *skip != 0 the launch does nothing
   // ERK stage (k = s - Lx):  acc += bdt k ; ynext = y0 + adt k ; final: state = acc + bdt k
   double* acc;
   const double* y0;
@@ -63,12 +69,16 @@ __device__ __forceinline__ T csr_row(const Bank<T>& B, int mat, int r, const T* 
 }
 
 template <typename T>
-__device__ __forceinline__ T csr_diag(const Bank<T>& B, int mat, int r) {
+__device__ __forceinline__ T csr_diag(const Bank<T>& B, int mat, int r, int n) {
   if (mat == MAT_I) return T(1);
-  const int* rp = B.rp + B.rp_off[mat];
-  for (int k = __ldg(rp + r); k < __ldg(rp + r + 1); ++k)
-    if (__ldg(B.col + k) == r) return __ldg(B.val + k);
-  return T(0);
+  return __ldg(B.dg + mat * n + r);
+}
+
+// 1 / (1 + cj d): the point-Jacobi scale; a preconditioner needs no FP64 division, so the reciprocal
+// is taken in FP32 (the same fixed diagonal at every application)
+template <typename T>
+__device__ __forceinline__ T jacobi_scale(T cj, T rdiag) {
+  return T(__frcp_rn(float(T(1) + cj * rdiag)));
 }
 
 // momentum factors (p, gamma m, V, 1/V, ...) are tabulated on the host per momentum node and face
@@ -95,14 +105,32 @@ __device__ __forceinline__ int face_node(int fp, int j, int a, const int* qpow) 
   return lo + j * qpow[a] + hi * qpow[a + 1];
 }
 
+// Index helpers: node index from a face point (axis a removed) and the position j along a; with
+// a compile-time q the divisions become multiply-shifts.
+__device__ __forceinline__ int face_node_q(int fp, int j, int a, int q) {
+  if (a == 0) return j + fp * q;
+  if (a == 1) return (fp % q) + j * q + (fp / q) * q * q;
+  return (fp % (q * q)) + j * q * q + (fp / (q * q)) * q * q * q;
+}
+__device__ __forceinline__ int qpow_of(int q, int a) { return a == 0 ? 1 : (a == 1 ? q : (a == 2 ? q * q : q * q * q)); }
+
+constexpr int EMAX = 6;  // face entries per thread: ceil(2 D / q) <= 6
+
 // Body of the apply for the cells [cell0, cell0 + cpb) of one problem whose state starts at element
 // `doff` of every state-sized vector (0 for a single problem, the instance offset in a batch).
-template <typename T>
+// DT, QT: compile-time number of axes and nodes per axis (0: taken from P at run time).
+template <typename T, int DT, int QT>
 __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __restrict__ x, const Epi<T>& E, int cpb,
                                            int cell_stride, int cell0, int64_t doff, unsigned char* smem_raw) {
+  if (E.skip && *E.skip) return;  // uniform over the grid
   T* sm = reinterpret_cast<T*>(smem_raw);
   x += doff;
-  const int n = P.n, nloc = P.nloc, nfp = P.nfp, D = P.D, q = P.q;
+  const int n = P.n;
+  const int D = DT ? DT : P.D;
+  const int q = QT ? QT : P.q;
+  const int nloc = DT ? qpow_of(q, D) : P.nloc;
+  const int nfp = DT ? qpow_of(q, D - 1) : P.nfp;
+  const int has_mom = P.has_mom;
   const int per_cell = n * nloc;
   const int nf = 2 * D;
   const int lc = threadIdx.x / per_cell;
@@ -110,16 +138,14 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
   const int r = t / nloc, i = t - r * nloc;
   const int cell = cell0 + lc;
   const bool valid = (lc < cpb) && (cell < P.ncell);
-  int qpow[MAXD + 2];
-  qpow[0] = 1;
-#pragma unroll
-  for (int a = 1; a < MAXD + 2; ++a) qpow[a] = qpow[a - 1] * q;
-
   int nvt = P.nreact;
   int adv_off[MAXD];
-  for (int a = 0; a < D; ++a) {
-    adv_off[a] = nvt;
-    nvt += P.ax[a].nadv;
+#pragma unroll
+  for (int a = 0; a < MAXD; ++a) {
+    if (a < D) {
+      adv_off[a] = nvt;
+      nvt += P.ax[a].nadv;
+    }
   }
   const int szT = nf * n * nfp;
   T* F = sm + (size_t)(lc < cpb ? lc : 0) * cell_stride;
@@ -131,9 +157,26 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
   const int region = (3 * szT > D * per_cell) ? 3 * szT : D * per_cell;
   T* CV = Tr + region;
   T* CF = CV + nvt * nloc;
-
   const int scell = valid ? P.cell_scell[cell] : 0;
   const int pcell = valid ? P.cell_pcell[cell] : 0;
+  const int qdx = has_mom ? nfp : nloc;            // spatial nodes per cell
+  const int qsp = has_mom ? (DT ? qpow_of(q, D - 2) : P.qdx / q) : nfp;  // spatial points per spatial face
+  // this thread's face entries w = t + e * per_cell, decomposed once: face f, coefficient, face point
+  int fe[EMAX], re[EMAX], pe[EMAX], nbe[EMAX];
+  int ne = 0;
+#pragma unroll
+  for (int e = 0; e < EMAX; ++e) {
+    const int w = t + e * per_cell;
+    fe[e] = 0; re[e] = 0; pe[e] = 0; nbe[e] = -1;
+    if (w < szT) {
+      fe[e] = w / (n * nfp);
+      const int rem = w - fe[e] * n * nfp;
+      re[e] = rem / nfp;
+      pe[e] = rem - re[e] * nfp;
+      nbe[e] = valid ? P.cell_nb[cell * nf + fe[e]] : -1;
+      ne = e + 1;
+    }
+  }
 
   // ---- phase 1: stage own data, coefficient tables, neighbour traces ---------------------------
   if (valid) {
@@ -148,16 +191,18 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
         while (a + 1 < D && tt >= adv_off[a + 1]) ++a;
         tm = &P.ax[a].adv[tt - adv_off[a]];
       }
-      const int sp = scell * P.qdx + ii % P.qdx;
-      T c = T(tm->scale) * spatial_factor(P, tm->sf, sp) * mom_node(P, tm->mf, pcell * q + ii / P.qdx);
+      const int sp = scell * qdx + (has_mom ? ii % nfp : ii);
+      const int pn = has_mom ? pcell * q + ii / nfp : 0;
+      T c = T(tm->scale) * spatial_factor(P, tm->sf, sp) * mom_node(P, tm->mf, pn);
       if (tm->nu) c *= P.nu ? __ldg(P.nu + (size_t)cell * nloc + ii) : P.nu_uni;
       CV[w] = c;
     }
     // face coefficients of the advection terms at every face point
     for (int w = t; w < nf * MAXADV * nfp; w += per_cell) {
       const int f = w / (MAXADV * nfp);
-      const int tt = (w / nfp) % MAXADV;
-      const int fp = w % nfp;
+      const int rem = w - f * MAXADV * nfp;
+      const int tt = rem / nfp;
+      const int fp = rem - tt * nfp;
       const int a = f >> 1, side = f & 1;
       const AxisInfo& A = P.ax[a];
       if (!A.active || tt >= A.nadv) continue;
@@ -165,33 +210,31 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
       T c = T(tm.scale);
       if (A.kind <= SAP_AXIS_Z) {
         // spatial face: U_a at the spatial face point, momentum factor at the node's p
-        const int qsp = P.qdx / q;  // spatial face points per spatial face
-        const int fsp = fp % qsp;
+        const int fsp = has_mom ? fp % qsp : fp;
         if (tm.sf == SF_U + a) {
           const int base = P.scell_face[scell * 2 * P.dx + 2 * a + side];
           c *= P.uface_is_uni[a] ? P.uface_uni[a] : __ldg(P.uface[a] + base + fsp);
         } else {
-          c *= spatial_factor(P, tm.sf, scell * P.qdx);  // only SF_ONE occurs here
+          c *= spatial_factor(P, tm.sf, scell * qdx);  // only SF_ONE occurs here
         }
-        c *= mom_node(P, tm.mf, pcell * q + fp / qsp);
+        c *= mom_node(P, tm.mf, has_mom ? pcell * q + fp / qsp : 0);
       } else {
         // momentum face: spatial factor at the spatial node (fp), momentum at the face
-        c *= spatial_factor(P, tm.sf, scell * P.qdx + fp);
+        c *= spatial_factor(P, tm.sf, scell * qdx + fp);
         c *= mom_face(P, tm.mf, pcell + side);
       }
       CF[w] = c;
     }
     // neighbour traces
-    for (int w = t; w < szT; w += per_cell) {
-      const int f = w / (n * nfp);
-      const int rr = (w / nfp) % n;
-      const int fp = w % nfp;
-      const int a = f >> 1, side = f & 1;
-      const int nb = P.cell_nb[cell * nf + f];
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+      if (e >= ne) break;
+      const int w = t + e * per_cell;
+      const int f = fe[e], a = f >> 1, side = f & 1;
       T v = T(0);
-      if (nb >= 0 && P.ax[a].active) {
-        const T* xn = x + ((size_t)nb * n + rr) * nloc;
-        for (int j = 0; j < q; ++j) v += (side == 0 ? P.B1[j] : P.B0[j]) * __ldg(xn + face_node(fp, j, a, qpow));
+      if (nbe[e] >= 0 && P.ax[a].active) {
+        const T* xn = x + ((size_t)nbe[e] * n + re[e]) * nloc;
+        for (int j = 0; j < q; ++j) v += (side == 0 ? P.B1[j] : P.B0[j]) * __ldg(xn + face_node_q(pe[e], j, a, q));
       }
       Tn[w] = v;
     }
@@ -199,28 +242,29 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
   __syncthreads();
   // ---- phase 2: own traces ------------------------------------------------------------------------
   if (valid) {
-    for (int w = t; w < szT; w += per_cell) {
-      const int f = w / (n * nfp);
-      const int rr = (w / nfp) % n;
-      const int fp = w % nfp;
-      const int a = f >> 1, side = f & 1;
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+      if (e >= ne) break;
+      const int w = t + e * per_cell;
+      const int f = fe[e], a = f >> 1, side = f & 1;
+      const T* Fr = F + re[e] * nloc;
       T v = T(0);
-      const T* Fr = F + rr * nloc;
-      for (int j = 0; j < q; ++j) v += (side == 0 ? P.B0[j] : P.B1[j]) * Fr[face_node(fp, j, a, qpow)];
+      for (int j = 0; j < q; ++j) v += (side == 0 ? P.B0[j] : P.B1[j]) * Fr[face_node_q(pe[e], j, a, q)];
       Tr[w] = v;
     }
   }
   __syncthreads();
   // ---- phase 3a: boundary substitution; Tr <- f_lo + f_hi, Tn <- f_lo - f_hi -----------------------
   if (valid) {
-    for (int w = t; w < szT; w += per_cell) {
-      const int f = w / (n * nfp);
-      const int a = f >> 1, side = f & 1;
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+      if (e >= ne) break;
+      const int w = t + e * per_cell;
+      const int f = fe[e], a = f >> 1, side = f & 1;
       if (!P.ax[a].active) continue;
-      const int nb = P.cell_nb[cell * nf + f];
       const T own = Tr[w];
       T oth = Tn[w];
-      if (nb < 0) {
+      if (nbe[e] < 0) {
         const int bc = side == 0 ? P.ax[a].bc_lo : P.ax[a].bc_hi;
         oth = (bc == SAP_BC_CONTINUOUS) ? own : T(0);
       }
@@ -233,10 +277,11 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
   __syncthreads();
   // ---- phase 3b: J = 1/2 beta S + 1/2 |beta| Dd  (eigen route: first half W^T Dd into W1) ------------
   if (valid) {
-    for (int w = t; w < szT; w += per_cell) {
-      const int f = w / (n * nfp);
-      const int rr = (w / nfp) % n;
-      const int fp = w % nfp;
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+      if (e >= ne) break;
+      const int w = t + e * per_cell;
+      const int f = fe[e], rr = re[e], fp = pe[e];
       const int a = f >> 1;
       const AxisInfo& A = P.ax[a];
       if (!A.active) continue;
@@ -249,7 +294,7 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
         Jf[w] = T(0.5) * acc;
       } else if (A.route == ABS_POINT) {
         const int side = f & 1;
-        const int sp = scell * P.qdx + fp;
+        const int sp = scell * qdx + fp;
         const int slot = __ldg(P.pslot + sp);
         if (slot >= 0) {
           const int* rp = P.bank.rp + P.bank.rp_off[A.absmat];
@@ -270,19 +315,22 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
   }
   __syncthreads();
   if (valid) {
-    for (int w = t; w < szT; w += per_cell) {
-      const int f = w / (n * nfp);
-      const int rr = (w / nfp) % n;
-      const int fp = w % nfp;
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+      if (e >= ne) break;
+      const int w = t + e * per_cell;
+      const int f = fe[e];
       const AxisInfo& A = P.ax[f >> 1];
       if (!A.active || A.route != ABS_EIGEN) continue;
-      Jf[w] += T(0.5) * csr_row(P.bank, A.Wmat, rr, W1 + f * n * nfp + fp, nfp);
+      Jf[w] += T(0.5) * csr_row(P.bank, A.Wmat, re[e], W1 + f * n * nfp + pe[e], nfp);
     }
   }
   __syncthreads();
   // ---- phase 3c: volume advection g^a = beta^a f at the nodes (G aliases the face scratch) -------------
   if (valid) {
-    for (int a = 0; a < D; ++a) {
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a) {
+      if (a >= D) break;
       const AxisInfo& A = P.ax[a];
       if (!A.active) continue;
       T g = T(0);
@@ -298,17 +346,20 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
   for (int tt = 0; tt < P.nreact; ++tt) {
     const T c = CV[tt * nloc + i];
     acc += c * csr_row(P.bank, P.react[tt].mat, r, F + i, nloc);
-    if (E.jacobi || E.out32) rdiag += c * csr_diag(P.bank, P.react[tt].mat, r);
+    if (E.jacobi || E.out32 || E.outj) rdiag += c * csr_diag(P.bank, P.react[tt].mat, r, n);
   }
-  for (int a = 0; a < D; ++a) {
+#pragma unroll
+  for (int a = 0; a < MAXD; ++a) {
+    if (a >= D) break;
     if (!P.ax[a].active) continue;
+    const int qa = qpow_of(q, a), qa1 = qa * q;
     const T invh = P.cell_invh[cell * D + a];
-    const int ia = (i / qpow[a]) % q;
-    const int base = i - ia * qpow[a];
+    const int ia = (i / qa) % q;
+    const int base = i - ia * qa;
     const T* Ga = G + a * per_cell + r * nloc + base;
     T ds = T(0);
-    for (int qq = 0; qq < q; ++qq) ds += P.S[ia][qq] * Ga[qq * qpow[a]];
-    const int fp = (i % qpow[a]) + (i / qpow[a + 1]) * qpow[a];
+    for (int qq = 0; qq < q; ++qq) ds += P.S[ia][qq] * Ga[qq * qa];
+    const int fp = (i % qa) + (i / qa1) * qa;
     const T jup = Jf[((2 * a + 1) * n + r) * nfp + fp];
     const T jdn = Jf[((2 * a) * n + r) * nfp + fp];
     acc += invh * (P.L1[ia] * jup - P.L0[ia] * jdn - ds);
@@ -330,8 +381,16 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
   }
   T o = E.ax * F[t] + E.bl * acc + E.gs * s;
   if (E.bvec) o += E.wb * __ldg(E.bvec + dof);
-  if (E.out32) E.out32[dof] = float(o / (T(1) + E.cj * rdiag));
-  if (E.jacobi) o /= (T(1) + E.cj * rdiag);
+  if (E.out32) E.out32[dof] = float(o * jacobi_scale(E.cj, rdiag));
+  if (E.out2) {
+    const T o2 = E.ax2 * F[t] + E.bl2 * acc + E.gs2 * s;
+    E.out2[dof] = o2;
+    if (E.outj) E.outj[dof] = o2 * jacobi_scale(E.cj, rdiag);
+  } else if (E.outj) {
+    E.outj[dof] = o * jacobi_scale(E.cj, rdiag);
+  }
+  if (E.jacobi) o *= jacobi_scale(E.cj, rdiag);
+  if (E.axpost != T(0)) o += E.axpost * F[t];
   if (E.out) E.out[dof] = o;
 }
 
@@ -345,6 +404,7 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
 template <typename T>
 __device__ __forceinline__ void applyT_body(const OpParams<T>& P, const T* __restrict__ x, const Epi<T>& E, int cpb,
                                             int cell_stride, int cell0, int64_t doff, unsigned char* smem_raw) {
+  if (E.skip && *E.skip) return;  // uniform over the grid
   T* sm = reinterpret_cast<T*>(smem_raw);
   x += doff;
   const int n = P.n, nloc = P.nloc, nfp = P.nfp, D = P.D, q = P.q;
@@ -535,7 +595,7 @@ __device__ __forceinline__ void applyT_body(const OpParams<T>& P, const T* __res
   for (int tt = 0; tt < P.nreact; ++tt) {
     const T c = CV[tt * nloc + i];
     acc += c * csr_row(P.bank, P.react[tt].matT, r, F + i, nloc);
-    if (E.jacobi || E.out32) rdiag += c * csr_diag(P.bank, P.react[tt].mat, r);
+    if (E.jacobi || E.out32 || E.outj) rdiag += c * csr_diag(P.bank, P.react[tt].mat, r, n);
   }
   for (int a = 0; a < D; ++a) {
     if (!P.ax[a].active) continue;
@@ -552,8 +612,15 @@ __device__ __forceinline__ void applyT_body(const OpParams<T>& P, const T* __res
   const size_t dof = (size_t)doff + (size_t)cell * per_cell + t;
   T o = E.ax * F[t] + E.bl * acc;
   if (E.bvec) o += E.wb * __ldg(E.bvec + dof);
-  if (E.out32) E.out32[dof] = float(o / (T(1) + E.cj * rdiag));
-  if (E.jacobi) o /= (T(1) + E.cj * rdiag);
+  if (E.out32) E.out32[dof] = float(o * jacobi_scale(E.cj, rdiag));
+  if (E.out2) {
+    const T o2 = E.ax2 * F[t] + E.bl2 * acc;
+    E.out2[dof] = o2;
+    if (E.outj) E.outj[dof] = o2 * jacobi_scale(E.cj, rdiag);
+  } else if (E.outj) {
+    E.outj[dof] = o * jacobi_scale(E.cj, rdiag);
+  }
+  if (E.jacobi) o *= jacobi_scale(E.cj, rdiag);
   if (E.out) E.out[dof] = o;
 }
 
@@ -564,16 +631,16 @@ __global__ void __launch_bounds__(1024) applyT_kernel(const OpParams<T> P, const
   applyT_body<T>(P, x, E, cpb, cell_stride, blockIdx.x * cpb, 0, smem_raw);
 }
 
-template <typename T>
+template <typename T, int DT, int QT>
 __global__ void __launch_bounds__(1024) apply_kernel(const OpParams<T> P, const T* __restrict__ x, const Epi<T> E,
                                                      int cpb, int cell_stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  apply_body<T>(P, x, E, cpb, cell_stride, blockIdx.x * cpb, 0, smem_raw);
+  apply_body<T, DT, QT>(P, x, E, cpb, cell_stride, blockIdx.x * cpb, 0, smem_raw);
 }
 
 // Batched apply: block b works on instance blocks[b].x, cells [blocks[b].y, + cpb[inst]).  The
 // instance's parameter block is staged in shared memory; blocks of inactive instances return.
-template <typename T>
+template <typename T, int DT, int QT>
 __global__ void __launch_bounds__(1024) apply_kernel_batched(const OpParams<T>* __restrict__ Pall,
                                                              const int64_t* __restrict__ doffs,
                                                              const int* __restrict__ cpbs,
@@ -589,7 +656,8 @@ __global__ void __launch_bounds__(1024) apply_kernel_batched(const OpParams<T>* 
   int* dst = reinterpret_cast<int*>(pbuf);
   for (int k = threadIdx.x; k < (int)(sizeof(OpParams<T>) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
   __syncthreads();
-  apply_body<T>(*reinterpret_cast<const OpParams<T>*>(pbuf), x, E, cpbs[bb.x], strides[bb.x], bb.y, doffs[bb.x], smem_raw);
+  apply_body<T, DT, QT>(*reinterpret_cast<const OpParams<T>*>(pbuf), x, E, cpbs[bb.x], strides[bb.x], bb.y, doffs[bb.x],
+                        smem_raw);
 }
 
 int apply_cells_per_block(int n, int nloc) {
@@ -613,6 +681,23 @@ static int cell_stride_elems(const OpParams<T>& P) {
   return (s + 1) & ~1;  // keep 16-byte alignment of each cell's block for doubles
 }
 
+template <typename T, int DT, int QT>
+static cudaError_t launch_apply_shape(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s, int cpb,
+                                      int stride, size_t smem) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(apply_kernel<T, DT, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (err != cudaSuccess) return err;
+    attr_set = true;
+  }
+  const int blocks = (P.ncell + cpb - 1) / cpb;
+  apply_kernel<T, DT, QT><<<blocks, cpb * P.n * P.nloc, smem, s>>>(P, x, e, cpb, stride);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+// Kernel shapes compiled with a fixed number of axes D and nodes per axis q (the workloads'
+// shapes); everything else runs the generic instantiation.
 template <typename T>
 static cudaError_t launch_apply(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s) {
   const int per = P.n * P.nloc;
@@ -620,18 +705,11 @@ static cudaError_t launch_apply(const OpParams<T>& P, const T* x, const Epi<T>& 
   const int cpb = apply_cells_per_block(P.n, P.nloc);
   const int stride = cell_stride_elems(P);
   const size_t smem = (size_t)cpb * stride * sizeof(T);
-  static bool attr_set[2] = {false, false};
-  const int idx = sizeof(T) == 8 ? 0 : 1;
-  if (!attr_set[idx]) {
-    cudaError_t err = cudaFuncSetAttribute(apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (err != cudaSuccess) return err;
-    attr_set[idx] = true;
-  }
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  const int blocks = (P.ncell + cpb - 1) / cpb;
-  apply_kernel<T><<<blocks, cpb * per, smem, s>>>(P, x, e, cpb, stride);
-  ++g_launches;
-  return cudaGetLastError();
+  if (P.D == 1 && P.q == 3) return launch_apply_shape<T, 1, 3>(P, x, e, s, cpb, stride, smem);
+  if (P.D == 2 && P.q == 2) return launch_apply_shape<T, 2, 2>(P, x, e, s, cpb, stride, smem);
+  if (P.D == 3 && P.q == 3) return launch_apply_shape<T, 3, 3>(P, x, e, s, cpb, stride, smem);
+  return launch_apply_shape<T, 0, 0>(P, x, e, s, cpb, stride, smem);
 }
 
 template <typename T>
@@ -934,6 +1012,223 @@ int64_t krylov_batch_scratch_doubles(const std::vector<int64_t>& Ns) {
   return (KRY_MAXV + 1) * nchunks + (int64_t)Ns.size() * 4 * KRY_MAXV;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Device-controlled Arnoldi (single problem, FP64): reductions are finished by the last block of
+// each kernel (atomic ticket, fixed summation order, no waiting), the Gram--Schmidt decision, the
+// Givens rotations and the convergence test run on one device thread, and kernels after
+// convergence exit at once.  The host enqueues iterations in groups and synchronises per group.
+// ------------------------------------------------------------------------------------------------
+struct GmresDev {
+  double H[KRY_MAXV * (KRY_MAXV + 1)];  // H[i * KRY_MAXV + j]
+  double g[KRY_MAXV + 1], cs[KRY_MAXV], sn[KRY_MAXV];
+  double h1[KRY_MAXV + 1], h2[KRY_MAXV + 1];
+  double nrm, inv_norm, target, beta;
+  double misc[8];
+  int done, reorth, jdone, m;
+  unsigned int counter;
+};
+
+__device__ void gmres_finalize_column(GmresDev* G, int j) {
+  const int M = KRY_MAXV;
+  const double hn = sqrt(G->nrm);
+  // the Arnoldi vectors are built from the shifted operator P^-1 A - 1 (same Krylov space, better
+  // conditioned Gram--Schmidt); the Hessenberg matrix of P^-1 A has the shift back on its diagonal
+  G->H[j * M + j] += 1.0;
+  G->H[(j + 1) * M + j] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a0 = G->H[i * M + j], a1 = G->H[(i + 1) * M + j];
+    G->H[i * M + j] = G->cs[i] * a0 + G->sn[i] * a1;
+    G->H[(i + 1) * M + j] = -G->sn[i] * a0 + G->cs[i] * a1;
+  }
+  const double a0 = G->H[j * M + j], a1 = G->H[(j + 1) * M + j];
+  const double den = hypot(a0, a1);
+  G->cs[j] = den > 0 ? a0 / den : 1.0;
+  G->sn[j] = den > 0 ? a1 / den : 0.0;
+  G->H[j * M + j] = den;
+  G->H[(j + 1) * M + j] = 0.0;
+  G->g[j + 1] = -G->sn[j] * G->g[j];
+  G->g[j] = G->cs[j] * G->g[j];
+  G->inv_norm = hn > 0 ? 1.0 / hn : 0.0;
+  G->jdone = j + 1;
+  if (fabs(G->g[j + 1]) <= G->target || hn == 0.0 || j + 1 >= G->m) G->done = 1;
+}
+
+__device__ __forceinline__ bool kry_skip(const int* done, const int* need) {
+  return (done && *done) || (need && !*need);
+}
+
+// dots of w with V_0..V_{m-1} (+ w.w) over chunks; the last block sums the partials in chunk order.
+// 16 warps per block, one basis vector per warp at a time, paired loads when the layout allows.
+constexpr int LB_THREADS = 512;
+template <typename TV>
+__device__ __forceinline__ double dot_chunk(const TV* __restrict__ a, const double* ws, int len, int lane, bool pairs) {
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+  int k = 0;
+  if (pairs) {
+    using TV2 = typename std::conditional<sizeof(TV) == 8, double2, float2>::type;
+    const TV2* a2 = reinterpret_cast<const TV2*>(a);
+    const int np = len >> 1;
+    int p = lane;
+    for (; p + 32 < np; p += 64) {
+      const TV2 u = __ldg(a2 + p), v = __ldg(a2 + p + 32);
+      acc0 += double(u.x) * ws[2 * p];
+      acc1 += double(u.y) * ws[2 * p + 1];
+      acc2 += double(v.x) * ws[2 * p + 64];
+      acc3 += double(v.y) * ws[2 * p + 65];
+    }
+    for (; p < np; p += 32) {
+      const TV2 u = __ldg(a2 + p);
+      acc0 += double(u.x) * ws[2 * p];
+      acc1 += double(u.y) * ws[2 * p + 1];
+    }
+    k = 2 * np + lane;
+  } else {
+    k = lane;
+  }
+  for (; k < len; k += 32) acc0 += double(__ldg(a + k)) * ws[k];
+  return (acc0 + acc1) + (acc2 + acc3);
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(LB_THREADS) multidot_lb_kernel(const TV* __restrict__ V, int64_t ldv, int m,
+                                                                 const TV* __restrict__ w, int64_t N, int with_ww,
+                                                                 double* __restrict__ partial, int nchunks,
+                                                                 unsigned int* counter, double* out,
+                                                                 const int* done, const int* need) {
+  if (kry_skip(done, need)) return;
+  __shared__ double ws[KRY_CHUNK];
+  __shared__ unsigned int ticket;
+  const int64_t k0 = (int64_t)blockIdx.x * KRY_CHUNK;
+  const int len = (int)((N - k0) < KRY_CHUNK ? (N - k0) : KRY_CHUNK);
+  for (int k = threadIdx.x; k < len; k += LB_THREADS) ws[k] = double(w[k0 + k]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mt = m + (with_ww ? 1 : 0);
+  const bool pairs = ((ldv & 1) == 0);  // V_i + k0 stays 2-element aligned
+  for (int i = warp; i < mt; i += LB_THREADS / 32) {
+    double acc;
+    if (i < m) {
+      acc = dot_chunk<TV>(V + i * ldv + k0, ws, len, lane, pairs);
+    } else {
+      acc = 0.0;
+      for (int k = lane; k < len; k += 32) acc += ws[k] * ws[k];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) partial[(size_t)i * nchunks + blockIdx.x] = acc;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  if (ticket != (unsigned)(gridDim.x - 1)) return;
+  __threadfence();
+  for (int i = warp; i < mt; i += LB_THREADS / 32) {
+    double v0 = 0.0, v1 = 0.0;
+    int c = lane;
+    for (; c + 32 < nchunks; c += 64) {
+      v0 += __ldcg(partial + (size_t)i * nchunks + c);
+      v1 += __ldcg(partial + (size_t)i * nchunks + c + 32);
+    }
+    for (; c < nchunks; c += 32) v0 += __ldcg(partial + (size_t)i * nchunks + c);
+    const double v = warp_sum(v0 + v1);
+    if (lane == 0) out[i] = v;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// w -= V h; |w|^2 finished by the last block, which then runs the Arnoldi control (pass 1: decide on
+// re-orthogonalisation or finalise the column; pass 2: add the second coefficients and finalise)
+template <typename TV>
+__global__ void __launch_bounds__(LB_THREADS) update_lb_kernel(const TV* __restrict__ V, int64_t ldv, int j,
+                                                                TV* __restrict__ w, int64_t N,
+                                                                double* __restrict__ partial, int nchunks,
+                                                                GmresDev* G, int pass) {
+  if (kry_skip(&G->done, pass == 2 ? &G->reorth : nullptr)) return;
+  const int m = j + 1;
+  __shared__ double hs[KRY_MAXV];
+  __shared__ double red[LB_THREADS / 32];
+  __shared__ unsigned int ticket;
+  const double* h = pass == 1 ? G->h1 : G->h2;
+  if (threadIdx.x < m) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  const int64_t k0 = (int64_t)blockIdx.x * KRY_CHUNK;
+  const int len = (int)((N - k0) < KRY_CHUNK ? (N - k0) : KRY_CHUNK);
+  double nrm = 0.0;
+  for (int k = threadIdx.x; k < len; k += LB_THREADS) {
+    double v = double(w[k0 + k]);
+    const TV* vp = V + k0 + k;
+#pragma unroll 4
+    for (int i = 0; i < m; ++i) v -= hs[i] * double(__ldg(vp + i * ldv));
+    const TV vs = TV(v);
+    w[k0 + k] = vs;
+    nrm += double(vs) * double(vs);
+  }
+  nrm = warp_sum(nrm);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < LB_THREADS / 32; ++q) t += red[q];
+    partial[blockIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(&G->counter, 1u);
+  __syncthreads();
+  if (ticket != (unsigned)(gridDim.x - 1)) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    double v0 = 0.0, v1 = 0.0;
+    int c = lane;
+    for (; c + 32 < nchunks; c += 64) {
+      v0 += __ldcg(partial + c);
+      v1 += __ldcg(partial + c + 32);
+    }
+    for (; c < nchunks; c += 32) v0 += __ldcg(partial + c);
+    double v = warp_sum(v0 + v1);
+    if (lane == 0) {
+      G->counter = 0u;
+      G->nrm = v;
+      const int M = KRY_MAXV;
+      if (pass == 1) {
+        for (int i = 0; i <= j; ++i) G->H[i * M + j] = G->h1[i];
+        if (v < 0.5 * G->h1[j + 1]) {
+          G->reorth = 1;  // |w'| < |w| / sqrt(2): second Gram--Schmidt pass
+        } else {
+          G->reorth = 0;
+          gmres_finalize_column(G, j);
+        }
+      } else {
+        for (int i = 0; i <= j; ++i) G->H[i * M + j] += G->h2[i];
+        G->reorth = 0;
+        gmres_finalize_column(G, j);
+      }
+    }
+  }
+}
+
+// y = x * (*s)
+template <typename TV>
+__global__ void scale_dev_kernel(const TV* __restrict__ x, TV* __restrict__ y, const double* s, int64_t N,
+                                 const int* done) {
+  if (done && *done) return;
+  const double a = *s;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+    y[k] = TV(a * double(x[k]));
+}
+
+size_t gmres_control_bytes() { return sizeof(GmresDev); }
+
+// x <- 2 x - prev, prev <- old x
+__global__ void extrapolate_kernel(double* __restrict__ x, double* __restrict__ prev, int64_t N) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[k];
+    x[k] = 2.0 * v - prev[k];
+    prev[k] = v;
+  }
+}
+
 sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
                     sap_solver_stats* st, cudaStream_t s) {
   const int64_t N = c->N;
@@ -941,129 +1236,143 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
   double* V = c->ws64;                       // (m+1) vectors
   double* b = V + (size_t)(m + 1) * N;
   double* tmp = b + N;
+  double* prev = c->ws64 + (size_t)(c->ws64_count - 1) * N;  // state before the last step
   const int nchunks = (int)((N + KRY_CHUNK - 1) / KRY_CHUNK);
-  KrylovCtx K{c, s, nchunks, c->small, c->small + (size_t)(KRY_MAXV + 1) * nchunks, c->small_host};
-  double* const d_h1 = K.dsc;                  // [0, 32): first Gram-Schmidt coefficients (+ |w|^2 at j+1)
-  double* const d_nrm = K.dsc + KRY_MAXV;      // [32]: |w|^2 after the update
-  double* const d_h2 = K.dsc + 2 * KRY_MAXV;   // [64, 96): re-orthogonalisation coefficients
-  double* const d_y = K.dsc + 3 * KRY_MAXV;    // [96, 128): least-squares solution
+  double* partial = c->small;
+  GmresDev* G = reinterpret_cast<GmresDev*>(c->gdev);
+  GmresDev* Gh = reinterpret_cast<GmresDev*>(c->gdev_host);
   const OpParams<double>& P = c->p64;
   const double half = 0.5 * dt;
-  std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), y(m);
+  const int group = 6;                       // iterations enqueued between host checks
   int64_t total_its = 0;
   const int64_t launches0 = g_launches;
   int max_its = 0;
   double last_rel = 0.0;
   cudaError_t err = cudaSuccess;
-#define CK(x)                                           \
-  do {                                                  \
-    err = (x);                                          \
-    if (err != cudaSuccess) goto cuda_fail;             \
+  std::vector<double> y(m);
+  auto norm2 = [&](const double* v, int slot) {  // G->misc[slot] = |v|^2
+    multidot_lb_kernel<double><<<nchunks, LB_THREADS, 0, s>>>(nullptr, N, 0, v, N, 1, partial, nchunks, &G->counter,
+                                                               &G->misc[slot], nullptr, nullptr);
+    ++g_launches;
+  };
+  auto fetch_misc = [&]() -> cudaError_t {
+    cudaMemcpyAsync(Gh->misc, G->misc, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
+    return cudaStreamSynchronize(s);
+  };
+#define CK(x)                               \
+  do {                                      \
+    err = (x);                              \
+    if (err != cudaSuccess) goto cuda_fail; \
   } while (0)
   for (int step = 0; step < nsteps; ++step) {
-    // b = zeta - dt/2 M^-1 D zeta + dt M^-1 h   (Eq. system-matrix-rhs, theta = 1/2)
-    {
+    // one apply gives b = zeta - dt/2 L zeta + dt s (Eq. system-matrix-rhs), the residual of the
+    // initial guess zeta, r = b - A zeta = dt (s - L zeta), and its Jacobi-scaled copy in V_0
+    const bool extrap = c->cn_prev_valid && c->cn_prev_ptr == state && c->cn_prev_dt == dt;
+    if (!extrap) {
+      Epi<double> e{};
+      e.out = b; e.ax = 1.0; e.bl = -half; e.gs = dt;
+      e.out2 = tmp; e.ax2 = 0.0; e.bl2 = -dt; e.gs2 = dt;
+      e.outj = V; e.cj = half;
+      CK(launch_apply<double>(P, state, e, s));
+      CK(cudaMemcpyAsync(prev, state, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    } else {
+      // initial guess 2 zeta^(n-1) - zeta^(n-2) (linear extrapolation; only the iteration count
+      // depends on it), then r = b - A x0 and its Jacobi-scaled copy
       Epi<double> e{};
       e.out = b; e.ax = 1.0; e.bl = -half; e.gs = dt;
       CK(launch_apply<double>(P, state, e, s));
+      extrapolate_kernel<<<1024, KRY_THREADS, 0, s>>>(state, prev, N);
+      ++g_launches;
+      Epi<double> e2{};
+      e2.out = tmp; e2.bvec = b; e2.wb = 1.0; e2.ax = -1.0; e2.bl = -half; e2.outj = V; e2.cj = half;
+      CK(launch_apply<double>(P, state, e2, s));
     }
-    dots<double>(K, nullptr, 0, b, 1, d_nrm);
-    CK(fetch(K, KRY_MAXV, 1));
-    const double bnorm = std::sqrt(K.hsc[KRY_MAXV]);
+    c->cn_prev_valid = true;
+    c->cn_prev_ptr = state;
+    c->cn_prev_dt = dt;
+    norm2(b, 0);
+    norm2(tmp, 1);
+    norm2(V, 2);
+    CK(fetch_misc());
+    const double bnorm = std::sqrt(Gh->misc[0]);
+    double rel = bnorm > 0 ? std::sqrt(Gh->misc[1]) / bnorm : 0.0;
+    double beta = std::sqrt(Gh->misc[2]);
     int its = 0;
-    double rel = 0.0;
     if (bnorm == 0.0) {
       CK(cudaMemsetAsync(state, 0, sizeof(double) * N, s));
-      last_rel = 0.0;
       continue;
     }
-    for (;;) {
-      // true residual r = b - (zeta + dt/2 M^-1 D zeta)
-      {
-        Epi<double> e{};
-        e.out = tmp; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half;
-        CK(launch_apply<double>(P, state, e, s));
-      }
-      dots<double>(K, nullptr, 0, tmp, 1, d_nrm);
-      CK(fetch(K, KRY_MAXV, 1));
-      rel = std::sqrt(K.hsc[KRY_MAXV]) / bnorm;
-      if (rel <= tol || its >= maxit) break;
-      // preconditioned residual v0 = P^-1 r, normalised
-      {
-        Epi<double> e{};
-        e.out = V; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.jacobi = 1; e.cj = half;
-        CK(launch_apply<double>(P, state, e, s));
-      }
-      dots<double>(K, nullptr, 0, V, 1, d_nrm);
-      scale_kernel<double><<<1024, KRY_THREADS, 0, s>>>(V, V, d_nrm, 2, N);
+    if (!std::isfinite(bnorm)) rel = bnorm;  // reported as not converged below
+    while (!(rel <= tol) && its < maxit && std::isfinite(rel)) {
+      // start a cycle: g = beta e_1, V_0 = P^-1 r / beta
+      Gh->g[0] = beta;
+      Gh->beta = beta;
+      Gh->inv_norm = 1.0 / beta;
+      Gh->target = 0.5 * beta * (tol / rel);
+      Gh->done = 0;
+      Gh->reorth = 0;
+      Gh->jdone = 0;
+      Gh->m = std::min(m, maxit - its);
+      CK(cudaMemcpyAsync(&G->g[0], &Gh->g[0], sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(&G->inv_norm, &Gh->inv_norm, sizeof(double) * 4, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(&G->done, &Gh->done, sizeof(int) * 4, cudaMemcpyHostToDevice, s));
+      scale_dev_kernel<double><<<1024, KRY_THREADS, 0, s>>>(V, V, &G->inv_norm, N, nullptr);
       ++g_launches;
-      CK(fetch(K, KRY_MAXV, 1));
-      const double beta = std::sqrt(K.hsc[KRY_MAXV]);
-      std::fill(g.begin(), g.end(), 0.0);
-      g[0] = beta;
-      // inner target on the preconditioned residual, scaled to the true-residual goal
-      const double target = 0.5 * beta * (tol / rel);
-      int jdone = 0;
-      for (int j = 0; j < m && its < maxit; ++j) {
+      const int mm = Gh->m;
+      int jd = 0;
+      for (int j = 0; j < mm; ++j) {
         double* w = V + (size_t)(j + 1) * N;
         {
           Epi<double> e{};
-          e.out = w; e.ax = 1.0; e.bl = half; e.jacobi = 1; e.cj = half;
+          e.out = w; e.ax = 1.0; e.bl = half; e.jacobi = 1; e.cj = half; e.skip = &G->done; e.axpost = -1.0;
           CK(launch_apply<double>(P, V + (size_t)j * N, e, s));
         }
-        // classical Gram--Schmidt with selective re-orthogonalisation (|w'| < |w|/sqrt(2))
-        dots(K, V, j + 1, w, 1, d_h1);
-        update(K, V, j + 1, d_h1, w, d_nrm);
-        CK(fetch(K, 0, KRY_MAXV + 1));
-        for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] = K.hsc[i2];
-        const double wn0 = std::sqrt(K.hsc[j + 1]);
-        double wn = std::sqrt(K.hsc[KRY_MAXV]);
-        if (wn < 0.7071067811865476 * wn0) {
-          dots(K, V, j + 1, w, 0, d_h2);
-          update(K, V, j + 1, d_h2, w, d_nrm);
-          CK(fetch(K, 2 * KRY_MAXV, j + 1));
-          CK(fetch(K, KRY_MAXV, 1));
-          for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] += K.hsc[2 * KRY_MAXV + i2];
-          wn = std::sqrt(K.hsc[KRY_MAXV]);
+        multidot_lb_kernel<double><<<nchunks, LB_THREADS, 0, s>>>(V, N, j + 1, w, N, 1, partial, nchunks,
+                                                                   &G->counter, G->h1, &G->done, nullptr);
+        update_lb_kernel<double><<<nchunks, LB_THREADS, 0, s>>>(V, N, j, w, N, partial, nchunks, G, 1);
+        multidot_lb_kernel<double><<<nchunks, LB_THREADS, 0, s>>>(V, N, j + 1, w, N, 0, partial, nchunks,
+                                                                   &G->counter, G->h2, &G->done, &G->reorth);
+        update_lb_kernel<double><<<nchunks, LB_THREADS, 0, s>>>(V, N, j, w, N, partial, nchunks, G, 2);
+        scale_dev_kernel<double><<<1024, KRY_THREADS, 0, s>>>(w, w, &G->inv_norm, N, &G->done);
+        g_launches += 5;
+        if ((j + 1) % group == 0 || j + 1 == mm) {
+          CK(cudaMemcpyAsync(&Gh->done, &G->done, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+          if (Gh->done) break;
         }
-        H[(size_t)(j + 1) * m + j] = wn;
-        if (wn > 0.0) {
-          scale_kernel<double><<<1024, KRY_THREADS, 0, s>>>(w, w, d_nrm, 2, N);
-          ++g_launches;
-        }
-        for (int i2 = 0; i2 < j; ++i2) {
-          const double a0 = H[(size_t)i2 * m + j], a1 = H[(size_t)(i2 + 1) * m + j];
-          H[(size_t)i2 * m + j] = cs[i2] * a0 + sn[i2] * a1;
-          H[(size_t)(i2 + 1) * m + j] = -sn[i2] * a0 + cs[i2] * a1;
-        }
-        const double a0 = H[(size_t)j * m + j], a1 = H[(size_t)(j + 1) * m + j];
-        const double den = std::hypot(a0, a1);
-        cs[j] = den > 0 ? a0 / den : 1.0;
-        sn[j] = den > 0 ? a1 / den : 0.0;
-        H[(size_t)j * m + j] = den;
-        H[(size_t)(j + 1) * m + j] = 0.0;
-        g[j + 1] = -sn[j] * g[j];
-        g[j] = cs[j] * g[j];
-        ++its;
-        jdone = j + 1;
-        if (std::fabs(g[j + 1]) <= target || wn == 0.0) break;
       }
-      // y = H^-1 g ; zeta += V y
-      for (int i2 = jdone - 1; i2 >= 0; --i2) {
-        double v = g[i2];
-        for (int k2 = i2 + 1; k2 < jdone; ++k2) v -= H[(size_t)i2 * m + k2] * y[k2];
-        y[i2] = v / H[(size_t)i2 * m + i2];
+      jd = Gh->jdone;
+      // y = H^-1 g on the host, zeta += V y
+      CK(cudaMemcpyAsync(Gh->H, G->H, sizeof(double) * KRY_MAXV * (KRY_MAXV + 1), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(Gh->g, G->g, sizeof(double) * (KRY_MAXV + 1), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int i2 = jd - 1; i2 >= 0; --i2) {
+        double v = Gh->g[i2];
+        for (int k2 = i2 + 1; k2 < jd; ++k2) v -= Gh->H[i2 * KRY_MAXV + k2] * y[k2];
+        y[i2] = v / Gh->H[i2 * KRY_MAXV + i2];
       }
-      for (int i2 = 0; i2 < jdone; ++i2) K.hsc[3 * KRY_MAXV + i2] = y[i2];
-      CK(cudaMemcpyAsync(d_y, K.hsc + 3 * KRY_MAXV, sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
-      combine_kernel<double><<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, d_y, state, N);
+      for (int i2 = 0; i2 < jd; ++i2) Gh->h2[i2] = y[i2];
+      CK(cudaMemcpyAsync(G->h2, Gh->h2, sizeof(double) * jd, cudaMemcpyHostToDevice, s));
+      combine_kernel<double><<<1024, KRY_THREADS, 0, s>>>(V, N, jd, G->h2, state, N);
       ++g_launches;
-      CK(cudaGetLastError());
+      its += jd;
+      // true residual r = b - A zeta and its Jacobi-scaled copy (start of a further cycle)
+      {
+        Epi<double> e{};
+        e.out = tmp; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.outj = V; e.cj = half;
+        CK(launch_apply<double>(P, state, e, s));
+      }
+      norm2(tmp, 1);
+      norm2(V, 2);
+      CK(fetch_misc());
+      rel = std::sqrt(Gh->misc[1]) / bnorm;
+      beta = std::sqrt(Gh->misc[2]);
+      if (jd == 0) break;
     }
     total_its += its;
     max_its = std::max(max_its, its);
     last_rel = rel;
-    if (rel > tol) {
+    if (!(rel <= tol)) {  // also catches a NaN residual
       c->err = "cn: GMRES did not reach the tolerance within maxit";
       if (st) {
         st->steps = step + 1; st->iterations = total_its; st->max_iterations = max_its; st->last_rel_residual = rel;
@@ -1141,7 +1450,7 @@ sap_status cn_steps_mixed(sap_ctx* c, double* state, double dt, int nsteps, doub
       dots<double>(K, nullptr, 0, r, 1, d_nrm);
       CK(fetch(K, KRY_MAXV, 1));
       rel = std::sqrt(K.hsc[KRY_MAXV]) / bnorm;
-      if (rel <= tol || its >= maxit) break;
+      if (rel <= tol || its >= maxit || !std::isfinite(rel)) break;
       dots<float>(K, nullptr, 0, V, 1, d_nrm);
       scale_kernel<float><<<1024, KRY_THREADS, 0, s>>>(V, V, d_nrm, 2, N);
       ++g_launches;
@@ -1209,7 +1518,7 @@ sap_status cn_steps_mixed(sap_ctx* c, double* state, double dt, int nsteps, doub
     total_its += its;
     max_its = std::max(max_its, its);
     last_rel = rel;
-    if (rel > tol) {
+    if (!(rel <= tol)) {  // also catches a NaN residual
       c->err = "cn: GMRES did not reach the tolerance within maxit";
       if (st) {
         st->steps = step + 1; st->iterations = total_its; st->max_iterations = max_its; st->last_rel_residual = rel;
@@ -1233,21 +1542,27 @@ cuda_fail:
 // ================================================================================================
 // Batches of independent problems (one launch per operator apply over all instances)
 // ================================================================================================
+template <typename T, int DT, int QT>
+static cudaError_t launch_apply_batched_shape(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e,
+                                              cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(apply_kernel_batched<T, DT, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           200 * 1024);
+    if (err != cudaSuccess) return err;
+    attr_set = true;
+  }
+  apply_kernel_batched<T, DT, QT><<<B.nblocks, B.threads, B.smem, s>>>(B.P, B.doff, B.cpb, B.stride, B.blocks, active, x, e);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t launch_apply_batched(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e,
                                         cudaStream_t s) {
-  static bool attr_set[2] = {false, false};
-  const int idx = sizeof(T) == 8 ? 0 : 1;
-  if (!attr_set[idx]) {
-    cudaError_t err = cudaFuncSetAttribute(apply_kernel_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           200 * 1024);
-    if (err != cudaSuccess) return err;
-    attr_set[idx] = true;
-  }
   if (B.smem > 200 * 1024 || B.threads > 1024 || B.threads < 1) return cudaErrorInvalidConfiguration;
-  apply_kernel_batched<T><<<B.nblocks, B.threads, B.smem, s>>>(B.P, B.doff, B.cpb, B.stride, B.blocks, active, x, e);
-  ++g_launches;
-  return cudaGetLastError();
+  if (B.shape_d == 2 && B.shape_q == 2) return launch_apply_batched_shape<T, 2, 2>(B, active, x, e, s);
+  return launch_apply_batched_shape<T, 0, 0>(B, active, x, e, s);
 }
 
 // per-instance Krylov kernels: block b works on chunk b of instance chunks.inst[b]
@@ -1415,10 +1730,13 @@ static void batch_tables(sap_ctx* c, int target) {
   const int* d_cpb = (const int*)dev_upload(c, cpb);
   const int* d_stride = (const int*)dev_upload(c, stride);
   const int2* d_blocks = (const int2*)dev_upload(c, blocks);
+  int sd = c->sub[0]->D, sq = c->sub[0]->q;
+  for (auto* sc : c->sub)
+    if (sc->D != sd || sc->q != sq) sd = sq = 0;
   c->b64 = BatchDev<double>{(const OpParams<double>*)dev_upload(c, P64), d_doff, d_cpb, d_stride, d_blocks,
-                            (int)blocks.size(), threads, smem64};
+                            (int)blocks.size(), threads, smem64, sd, sq};
   c->b32 = BatchDev<float>{(const OpParams<float>*)dev_upload(c, P32), d_doff, d_cpb, d_stride, d_blocks,
-                           (int)blocks.size(), threads, smem32};
+                           (int)blocks.size(), threads, smem32, sd, sq};
   c->chunks = BatchChunks{(const int*)dev_upload(c, cinst), (const int64_t*)dev_upload(c, ck0),
                           (const int*)dev_upload(c, clen), (const int*)dev_upload(c, cfirst),
                           (const int*)dev_upload(c, ccount), (int)cinst.size()};
@@ -1652,7 +1970,7 @@ static sap_status batch_cn_impl(sap_ctx* c, double* state, double dt, int nsteps
       for (int i = 0; i < ni; ++i) {
         if (!act[i]) continue;
         rel[i] = std::sqrt(hsc[(size_t)i * SS + KRY_MAXV]) / bnorm[i];
-        if (rel[i] <= tol || its[i] >= maxit) act[i] = 0;
+        if (rel[i] <= tol || its[i] >= maxit || !std::isfinite(rel[i])) act[i] = 0;
         any = any || act[i];
       }
       if (!any) break;
@@ -1760,7 +2078,7 @@ static sap_status batch_cn_impl(sap_ctx* c, double* state, double dt, int nsteps
       total_its += its[i];
       max_its = std::max(max_its, its[i]);
       if (!zero[i]) worst_rel = std::max(worst_rel, rel[i]);
-      if (!zero[i] && rel[i] > tol) {
+      if (!zero[i] && !(rel[i] <= tol)) {
         c->err = "batch cn: GMRES did not reach the tolerance within maxit on instance " + std::to_string(i);
         if (st) {
           st->steps = step + 1; st->iterations = total_its; st->max_iterations = max_its;
@@ -1859,7 +2177,7 @@ sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, doubl
         dots<double>(K, nullptr, 0, tmp, 1, d_nrm);
         CK(fetch(K, KRY_MAXV, 1));
         rel = std::sqrt(K.hsc[KRY_MAXV]) / bnorm;
-        if (rel <= tol || its >= maxit) break;
+        if (rel <= tol || its >= maxit || !std::isfinite(rel)) break;
         {
           Epi<double> e{};
           e.out = V; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.jacobi = 1; e.cj = half;
@@ -1930,7 +2248,7 @@ sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, doubl
       }
     }
   }
-  if (rel > tol) {
+  if (!(rel <= tol)) {  // also catches a NaN residual
     c->err = "adjoint cn: GMRES did not reach the tolerance within maxit";
     if (st) {
       st->steps = 1; st->iterations = its; st->max_iterations = its; st->last_rel_residual = rel;

@@ -50,6 +50,7 @@ struct Bank {
   const int* rp;   // concatenated row pointers (absolute offsets into col/val)
   const int* col;
   const T* val;
+  const T* dg;     // [nmat][n] diagonal of every matrix
   int rp_off[96];
 };
 
@@ -111,6 +112,7 @@ struct BatchDev {
   const int2* blocks = nullptr;       // [nblocks] (instance, first cell)
   int nblocks = 0, threads = 0;
   size_t smem = 0;
+  int shape_d = 0, shape_q = 0;       // common (D, q) of all instances, 0 if they differ
 };
 
 // Chunking of the concatenated state for the per-instance Krylov reductions: chunks never cross an
@@ -152,7 +154,14 @@ struct sap_ctx {
   int ws32_count = 0;
   double* small = nullptr;                     // small device scratch for reductions/scalars
   double* small_host = nullptr;                // pinned mirror
+  void* gdev = nullptr;                        // device Arnoldi control block
+  void* gdev_host = nullptr;                   // pinned mirror
   int krylov_restart = 0;
+  // CN initial-guess history: the state before the last step, valid for the buffer and dt it was
+  // taken with (any other call starts from the plain previous state)
+  const double* cn_prev_ptr = nullptr;
+  double cn_prev_dt = 0.0;
+  bool cn_prev_valid = false;
   std::vector<double> bank_nnz;                // nnz per bank matrix (cost model)
   int64_t launches = 0;                        // kernels launched by the current call
   // batches: a batch handle owns one sub-context per instance and runs them with batched launches
@@ -192,5 +201,6 @@ sap_status batch_cn(sap_ctx* c, double* state, double dt, int nsteps, double tol
 sap_status batch_erk(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s);
 int64_t launch_count();
 int64_t krylov_scratch_doubles(int64_t N);
+size_t gmres_control_bytes();
 int64_t krylov_batch_scratch_doubles(const std::vector<int64_t>& Ns);
 }  // namespace sap

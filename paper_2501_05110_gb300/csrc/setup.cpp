@@ -324,6 +324,11 @@ extern "C" sap_status sap_create(const sap_desc* desc, int prec, sap_handle* out
     // small reduction scratch
     if (cudaMalloc(&c->small, sizeof(double) * krylov_scratch_doubles(c->N)) != cudaSuccess) throw std::string("cudaMalloc failed");
     if (cudaMallocHost(&c->small_host, sizeof(double) * 8 * 32) != cudaSuccess) throw std::string("cudaMallocHost failed");
+    if (cudaMalloc(&c->gdev, gmres_control_bytes()) != cudaSuccess ||
+        cudaMemset(c->gdev, 0, gmres_control_bytes()) != cudaSuccess)
+      throw std::string("cudaMalloc failed");
+    if (cudaMallocHost(&c->gdev_host, gmres_control_bytes()) != cudaSuccess) throw std::string("cudaMallocHost failed");
+    std::memset(c->gdev_host, 0, gmres_control_bytes());
   } catch (const std::string& e) {
     g_create_error = "sap_create: " + e;
     sap_destroy(c);
@@ -524,6 +529,13 @@ static void set_bank(OpParams<T>& P, const BankBuilder& B, sap_ctx* c, std::vect
   if (rp.empty()) rp.push_back(0);
   c->bank_nnz.clear();
   for (size_t m = 0; m < B.mats.size(); ++m) c->bank_nnz.push_back((double)B.mats[m].col.size());
+  std::vector<double> dgv(std::max<size_t>(1, B.mats.size() * c->n), 0.0);
+  for (size_t m = 0; m < B.mats.size(); ++m)
+    for (int i = 0; i < c->n; ++i)
+      for (int k = B.mats[m].rp[i]; k < B.mats[m].rp[i + 1]; ++k)
+        if (B.mats[m].col[k] == i) dgv[m * c->n + i] = B.mats[m].val[k];
+  if (sizeof(T) == 8) P.bank.dg = (const T*)upload(c, dgv, own);
+  else P.bank.dg = (const T*)upload(c, to_f32(dgv), own);
   P.bank.rp = (const int*)upload(c, rp, own);
   P.bank.col = (const int*)upload(c, col, own);
   if (sizeof(T) == 8) P.bank.val = (const T*)upload(c, val, own);
@@ -701,28 +713,36 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
         HostCSR pc = to_csr(full);
         const int nnzp = (int)pc.col.size();
         A.absmat = B.add_csr("pabs_pattern", pc);
-        // first pass: |beta^p| max per spatial point to pick active points
-        std::vector<double> vals;
-        std::vector<double> beta(n * n);
-        Mat bm(n), Wb;
-        std::vector<double> lb;
-        double gmax = 0.0;
-        std::vector<double> pmax(nsv, 0.0);
-        auto build_beta = [&](int sp, double p) {
-          std::fill(bm.a.begin(), bm.a.end(), 0.0);
+        // each term's entries scattered into the block pattern once
+        std::vector<std::vector<std::pair<int, double>>> tpos(A.nadv);
+        for (int t = 0; t < A.nadv; ++t) {
+          const HostCSR& h = B.mats[A.adv[t].mat];
+          for (int i = 0; i < n; ++i)
+            for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) {
+              const int j = h.col[k];
+              int pos = -1;
+              for (int e = pc.rp[i]; e < pc.rp[i + 1]; ++e)
+                if (pc.col[e] == j) pos = e;
+              tpos[t].push_back({pos, h.val[k]});
+            }
+        }
+        std::vector<double> pv(nnzp);
+        auto build_beta = [&](int sp, double p) {  // beta^p at (spatial node, momentum) in the pattern
+          std::fill(pv.begin(), pv.end(), 0.0);
           for (int t = 0; t < A.nadv; ++t) {
             const Term& tm = A.adv[t];
-            double cf = tm.scale * (tm.sf == SF_ONE ? 1.0 : sf[(size_t)tm.sf * nsv + sp]) * mom_factor_h(tm.mf, p, has_mom, d.V);
-            const HostCSR& h = B.mats[tm.mat];
-            for (int i = 0; i < n; ++i)
-              for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) bm(i, h.col[k]) += cf * h.val[k];
+            const double cf = tm.scale * (tm.sf == SF_ONE ? 1.0 : sf[(size_t)tm.sf * nsv + sp]) *
+                              mom_factor_h(tm.mf, p, has_mom, d.V);
+            for (const auto& pr : tpos[t]) pv[pr.first] += cf * pr.second;
           }
         };
+        double gmax = 0.0;
+        std::vector<double> pmax(nsv, 0.0);
         for (int sp = 0; sp < nsv; ++sp)
           for (int f = 0; f < npface; ++f) {
             build_beta(sp, c->pface[f]);
             double mx = 0.0;
-            for (double v : bm.a) mx = std::max(mx, std::fabs(v));
+            for (double v : pv) mx = std::max(mx, std::fabs(v));
             pmax[sp] = std::max(pmax[sp], mx);
             gmax = std::max(gmax, mx);
           }
@@ -732,18 +752,22 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
         for (int sp = 0; sp < nsv; ++sp)
           if (gmax > 0.0 && pmax[sp] > 1e-15 * gmax) pslot[sp] = nslot++;
         pabs.assign((size_t)nslot * npface * nnzp, 0.0);
+        Mat bm(n), Wb;
+        std::vector<double> lb;
         for (int sp = 0; sp < nsv; ++sp) {
           if (pslot[sp] < 0) continue;
           for (int f = 0; f < npface; ++f) {
             build_beta(sp, c->pface[f]);
+            for (int i = 0; i < n; ++i)
+              for (int e = pc.rp[i]; e < pc.rp[i + 1]; ++e) bm(i, pc.col[e]) = pv[e];
             sym_eig_blocks(bm, blocks, Wb, lb);
             double* dst = &pabs[((size_t)pslot[sp] * npface + f) * nnzp];
             for (int i = 0; i < n; ++i)
               for (int k = pc.rp[i]; k < pc.rp[i + 1]; ++k) {
                 int j = pc.col[k];
-                double s = 0.0;
-                for (int e = 0; e < n; ++e) s += Wb(i, e) * std::fabs(lb[e]) * Wb(j, e);
-                dst[k] = s;
+                double s2 = 0.0;
+                for (int e = 0; e < n; ++e) s2 += Wb(i, e) * std::fabs(lb[e]) * Wb(j, e);
+                dst[k] = s2;
               }
           }
         }
@@ -808,6 +832,7 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
     fill(c->p32, float{});
     c->fields_set = true;
     c->fields_version += 1;
+    c->cn_prev_valid = false;
   } catch (const std::string& e) {
     c->err = "sap_set_fields: " + e;
     return SAP_ENOMEM;
@@ -826,6 +851,7 @@ extern "C" sap_status sap_num_dofs(sap_handle c, int64_t* n) {
 
 static bool ensure_ws64(sap_ctx* c, int count) {
   if (c->ws64_count >= count) return true;
+  c->cn_prev_valid = false;
   if (c->ws64) cudaFree(c->ws64);
   c->ws64 = nullptr;
   c->ws64_count = 0;
@@ -870,6 +896,7 @@ extern "C" sap_status sap_apply_operator(sap_handle c, const void* x, void* y, i
 
 extern "C" sap_status sap_step_erk(sap_handle c, double* state, double dt, int nsteps, sap_stream stream) {
   if (!c || !state || nsteps < 0) return SAP_EINVAL;
+  c->cn_prev_valid = false;  // the RK4 stage buffers share the workspace
   if (!c->sub.empty()) {
     if (c->prec == SAP_PREC_FP64 ? !ensure_ws64(c, 3) : (!ensure_ws32(c, 2) || !ensure_ws64(c, 1))) {
       c->err = "erk: workspace allocation failed";
@@ -919,7 +946,8 @@ extern "C" sap_status sap_step_cn(sap_handle c, double* state, double dt, int ns
     }
     return cn_steps_mixed(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
   }
-  if (!ensure_ws64(c, restart + 3)) {
+  if (c->ws64_count < restart + 4) c->cn_prev_valid = false;  // the history lives in the workspace
+  if (!ensure_ws64(c, restart + 4)) {
     c->err = "cn: workspace allocation failed";
     return SAP_ENOMEM;
   }
@@ -997,6 +1025,7 @@ extern "C" sap_status sap_adjoint_step_cn(sap_handle c, const double* zeta_prev,
     c->err = "adjoint: workspace allocation failed";
     return SAP_ENOMEM;
   }
+  c->cn_prev_valid = false;  // the adjoint solve shares the workspace
   return adjoint_cn_step(c, zeta_prev, zeta_next, lambda, dt, tol, restart, maxit, mu_out, grad_nu, stats,
                          (cudaStream_t)stream);
 }
@@ -1021,6 +1050,8 @@ extern "C" sap_status sap_destroy(sap_handle c) {
   if (c->ws32) cudaFree(c->ws32);
   if (c->small) cudaFree(c->small);
   if (c->small_host) cudaFreeHost(c->small_host);
+  if (c->gdev) cudaFree(c->gdev);
+  if (c->gdev_host) cudaFreeHost(c->gdev_host);
   delete c;
   return SAP_OK;
 }

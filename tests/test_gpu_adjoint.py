@@ -93,11 +93,14 @@ def test_adjoint_U1_gradient_vs_finite_differences(setup):
 
 
 def test_adjoint_checkpoint_interval_invariant(setup):
+    """Gradients do not depend on the checkpoint interval.  Recomputed segments are re-solved to the
+    solver tolerance (1e-13) from different initial guesses, so states agree to that level; the U1
+    term divides by the operator difference step e = 1e-7, hence its looser bound."""
     S = setup
     a = _adjoint_grads(S, checkpoint=1)
     b = _adjoint_grads(S, checkpoint=50)
     assert np.allclose(a[0], b[0], rtol=1e-10, atol=1e-14 * np.abs(a[0]).max())
-    assert abs(a[1] - b[1]) < 1e-10 * abs(a[1])
+    assert abs(a[1] - b[1]) < 1e-7 * abs(a[1])
 
 
 def test_adjoint_nu_gradient_vs_oracle_tangent(setup):
