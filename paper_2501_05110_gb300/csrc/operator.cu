@@ -381,13 +381,14 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
   }
   T o = E.ax * F[t] + E.bl * acc + E.gs * s;
   if (E.bvec) o += E.wb * __ldg(E.bvec + dof);
-  if (E.out32) E.out32[dof] = float(o * jacobi_scale(E.cj, rdiag));
   if (E.out2) {
     const T o2 = E.ax2 * F[t] + E.bl2 * acc + E.gs2 * s;
     E.out2[dof] = o2;
     if (E.outj) E.outj[dof] = o2 * jacobi_scale(E.cj, rdiag);
-  } else if (E.outj) {
-    E.outj[dof] = o * jacobi_scale(E.cj, rdiag);
+    if (E.out32) E.out32[dof] = float(o2 * jacobi_scale(E.cj, rdiag));
+  } else {
+    if (E.outj) E.outj[dof] = o * jacobi_scale(E.cj, rdiag);
+    if (E.out32) E.out32[dof] = float(o * jacobi_scale(E.cj, rdiag));
   }
   if (E.jacobi) o *= jacobi_scale(E.cj, rdiag);
   if (E.axpost != T(0)) o += E.axpost * F[t];
@@ -1229,14 +1230,21 @@ __global__ void extrapolate_kernel(double* __restrict__ x, double* __restrict__ 
   }
 }
 
-sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
-                    sap_solver_stats* st, cudaStream_t s) {
+// TV = double: FP64 operator and Krylov vectors (the plain path).  TV = float: precision form: the
+// Arnoldi process applies the FP32 operator to FP32 vectors (FP64 accumulation in dots and updates)
+// inside the FP64 residual / refinement loop, each cycle asking for no more than the FP32 operator
+// can deliver (1e-6).
+template <typename TV>
+static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
+                             sap_solver_stats* st, cudaStream_t s) {
   const int64_t N = c->N;
   const int m = restart;
-  double* V = c->ws64;                       // (m+1) vectors
-  double* b = V + (size_t)(m + 1) * N;
+  constexpr bool f64 = sizeof(TV) == 8;
+  TV* V = f64 ? reinterpret_cast<TV*>(c->ws64) : reinterpret_cast<TV*>(c->ws32);  // (m+1) vectors
+  double* b = f64 ? c->ws64 + (size_t)(m + 1) * N : c->ws64;
   double* tmp = b + N;
   double* prev = c->ws64 + (size_t)(c->ws64_count - 1) * N;  // state before the last step
+  const OpParams<TV>& PV = *reinterpret_cast<const OpParams<TV>*>(f64 ? (const void*)&c->p64 : (const void*)&c->p32);
   const int nchunks = (int)((N + KRY_CHUNK - 1) / KRY_CHUNK);
   double* partial = c->small;
   GmresDev* G = reinterpret_cast<GmresDev*>(c->gdev);
@@ -1255,6 +1263,16 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
                                                                &G->misc[slot], nullptr, nullptr);
     ++g_launches;
   };
+  auto norm2v = [&](const TV* v, int slot) {
+    multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, s>>>(nullptr, N, 0, v, N, 1, partial, nchunks, &G->counter,
+                                                           &G->misc[slot], nullptr, nullptr);
+    ++g_launches;
+  };
+  auto jcopy = [&](Epi<double>& e) {  // Jacobi-scaled copy of the residual into V_0
+    if constexpr (f64) e.outj = reinterpret_cast<double*>(V);
+    else e.out32 = reinterpret_cast<float*>(V);
+    e.cj = half;
+  };
   auto fetch_misc = [&]() -> cudaError_t {
     cudaMemcpyAsync(Gh->misc, G->misc, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
     return cudaStreamSynchronize(s);
@@ -1272,7 +1290,7 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
       Epi<double> e{};
       e.out = b; e.ax = 1.0; e.bl = -half; e.gs = dt;
       e.out2 = tmp; e.ax2 = 0.0; e.bl2 = -dt; e.gs2 = dt;
-      e.outj = V; e.cj = half;
+      jcopy(e);
       CK(launch_apply<double>(P, state, e, s));
       CK(cudaMemcpyAsync(prev, state, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
     } else {
@@ -1284,7 +1302,8 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
       extrapolate_kernel<<<1024, KRY_THREADS, 0, s>>>(state, prev, N);
       ++g_launches;
       Epi<double> e2{};
-      e2.out = tmp; e2.bvec = b; e2.wb = 1.0; e2.ax = -1.0; e2.bl = -half; e2.outj = V; e2.cj = half;
+      e2.out = tmp; e2.bvec = b; e2.wb = 1.0; e2.ax = -1.0; e2.bl = -half;
+      jcopy(e2);
       CK(launch_apply<double>(P, state, e2, s));
     }
     c->cn_prev_valid = true;
@@ -1292,7 +1311,7 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
     c->cn_prev_dt = dt;
     norm2(b, 0);
     norm2(tmp, 1);
-    norm2(V, 2);
+    norm2v(V, 2);
     CK(fetch_misc());
     const double bnorm = std::sqrt(Gh->misc[0]);
     double rel = bnorm > 0 ? std::sqrt(Gh->misc[1]) / bnorm : 0.0;
@@ -1308,7 +1327,7 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
       Gh->g[0] = beta;
       Gh->beta = beta;
       Gh->inv_norm = 1.0 / beta;
-      Gh->target = 0.5 * beta * (tol / rel);
+      Gh->target = f64 ? 0.5 * beta * (tol / rel) : beta * std::max(0.5 * tol / rel, 1e-6);
       Gh->done = 0;
       Gh->reorth = 0;
       Gh->jdone = 0;
@@ -1316,24 +1335,25 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
       CK(cudaMemcpyAsync(&G->g[0], &Gh->g[0], sizeof(double), cudaMemcpyHostToDevice, s));
       CK(cudaMemcpyAsync(&G->inv_norm, &Gh->inv_norm, sizeof(double) * 4, cudaMemcpyHostToDevice, s));
       CK(cudaMemcpyAsync(&G->done, &Gh->done, sizeof(int) * 4, cudaMemcpyHostToDevice, s));
-      scale_dev_kernel<double><<<1024, KRY_THREADS, 0, s>>>(V, V, &G->inv_norm, N, nullptr);
+      scale_dev_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(V, V, &G->inv_norm, N, nullptr);
       ++g_launches;
       const int mm = Gh->m;
       int jd = 0;
       for (int j = 0; j < mm; ++j) {
-        double* w = V + (size_t)(j + 1) * N;
+        TV* w = V + (size_t)(j + 1) * N;
         {
-          Epi<double> e{};
-          e.out = w; e.ax = 1.0; e.bl = half; e.jacobi = 1; e.cj = half; e.skip = &G->done; e.axpost = -1.0;
-          CK(launch_apply<double>(P, V + (size_t)j * N, e, s));
+          Epi<TV> e{};
+          e.out = w; e.ax = TV(1); e.bl = TV(half); e.jacobi = 1; e.cj = TV(half); e.skip = &G->done;
+          e.axpost = TV(-1);
+          CK(launch_apply<TV>(PV, V + (size_t)j * N, e, s));
         }
-        multidot_lb_kernel<double><<<nchunks, LB_THREADS, 0, s>>>(V, N, j + 1, w, N, 1, partial, nchunks,
-                                                                   &G->counter, G->h1, &G->done, nullptr);
-        update_lb_kernel<double><<<nchunks, LB_THREADS, 0, s>>>(V, N, j, w, N, partial, nchunks, G, 1);
-        multidot_lb_kernel<double><<<nchunks, LB_THREADS, 0, s>>>(V, N, j + 1, w, N, 0, partial, nchunks,
-                                                                   &G->counter, G->h2, &G->done, &G->reorth);
-        update_lb_kernel<double><<<nchunks, LB_THREADS, 0, s>>>(V, N, j, w, N, partial, nchunks, G, 2);
-        scale_dev_kernel<double><<<1024, KRY_THREADS, 0, s>>>(w, w, &G->inv_norm, N, &G->done);
+        multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, s>>>(V, N, j + 1, w, N, 1, partial, nchunks,
+                                                               &G->counter, G->h1, &G->done, nullptr);
+        update_lb_kernel<TV><<<nchunks, LB_THREADS, 0, s>>>(V, N, j, w, N, partial, nchunks, G, 1);
+        multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, s>>>(V, N, j + 1, w, N, 0, partial, nchunks,
+                                                               &G->counter, G->h2, &G->done, &G->reorth);
+        update_lb_kernel<TV><<<nchunks, LB_THREADS, 0, s>>>(V, N, j, w, N, partial, nchunks, G, 2);
+        scale_dev_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(w, w, &G->inv_norm, N, &G->done);
         g_launches += 5;
         if ((j + 1) % group == 0 || j + 1 == mm) {
           CK(cudaMemcpyAsync(&Gh->done, &G->done, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
@@ -1353,17 +1373,18 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
       }
       for (int i2 = 0; i2 < jd; ++i2) Gh->h2[i2] = y[i2];
       CK(cudaMemcpyAsync(G->h2, Gh->h2, sizeof(double) * jd, cudaMemcpyHostToDevice, s));
-      combine_kernel<double><<<1024, KRY_THREADS, 0, s>>>(V, N, jd, G->h2, state, N);
+      combine_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(V, N, jd, G->h2, state, N);
       ++g_launches;
       its += jd;
       // true residual r = b - A zeta and its Jacobi-scaled copy (start of a further cycle)
       {
         Epi<double> e{};
-        e.out = tmp; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.outj = V; e.cj = half;
+        e.out = tmp; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half;
+        jcopy(e);
         CK(launch_apply<double>(P, state, e, s));
       }
       norm2(tmp, 1);
-      norm2(V, 2);
+      norm2v(V, 2);
       CK(fetch_misc());
       rel = std::sqrt(Gh->misc[1]) / bnorm;
       beta = std::sqrt(Gh->misc[2]);
@@ -1392,151 +1413,13 @@ cuda_fail:
 #undef CK
 }
 
-
-// ------------------------------------------------------------------------------------------------
-// Crank--Nicolson, precision form: FP64 residual and iterative refinement around an inner GMRES
-// whose operator applies, Krylov vectors and preconditioner run in FP32 (dot products, Hessenberg
-// and the solution update accumulate in FP64).
-// ------------------------------------------------------------------------------------------------
-sap_status cn_steps_mixed(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
-                          sap_solver_stats* st, cudaStream_t s) {
-  const int64_t N = c->N;
-  const int m = restart;
-  float* V = c->ws32;                        // (m+1) FP32 vectors
-  double* b = c->ws64;
-  double* r = b + N;
-  const int nchunks = (int)((N + KRY_CHUNK - 1) / KRY_CHUNK);
-  KrylovCtx K{c, s, nchunks, c->small, c->small + (size_t)(KRY_MAXV + 1) * nchunks, c->small_host};
-  double* const d_h1 = K.dsc;
-  double* const d_nrm = K.dsc + KRY_MAXV;
-  double* const d_h2 = K.dsc + 2 * KRY_MAXV;
-  double* const d_y = K.dsc + 3 * KRY_MAXV;
-  const OpParams<double>& P64 = c->p64;
-  const OpParams<float>& P32 = c->p32;
-  const double half = 0.5 * dt;
-  std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), y(m);
-  int64_t total_its = 0;
-  const int64_t launches0 = g_launches;
-  int max_its = 0;
-  double last_rel = 0.0;
-  cudaError_t err = cudaSuccess;
-#define CK(x)                                           \
-  do {                                                  \
-    err = (x);                                          \
-    if (err != cudaSuccess) goto cuda_fail;             \
-  } while (0)
-  for (int step = 0; step < nsteps; ++step) {
-    {
-      Epi<double> e{};
-      e.out = b; e.ax = 1.0; e.bl = -half; e.gs = dt;
-      CK(launch_apply<double>(P64, state, e, s));
-    }
-    dots<double>(K, nullptr, 0, b, 1, d_nrm);
-    CK(fetch(K, KRY_MAXV, 1));
-    const double bnorm = std::sqrt(K.hsc[KRY_MAXV]);
-    int its = 0;
-    double rel = 0.0;
-    if (bnorm == 0.0) {
-      CK(cudaMemsetAsync(state, 0, sizeof(double) * N, s));
-      continue;
-    }
-    for (;;) {
-      // FP64 residual r = b - A zeta, and its Jacobi-scaled FP32 copy as the inner right side
-      {
-        Epi<double> e{};
-        e.out = r; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.out32 = V; e.cj = half;
-        CK(launch_apply<double>(P64, state, e, s));
-      }
-      dots<double>(K, nullptr, 0, r, 1, d_nrm);
-      CK(fetch(K, KRY_MAXV, 1));
-      rel = std::sqrt(K.hsc[KRY_MAXV]) / bnorm;
-      if (rel <= tol || its >= maxit || !std::isfinite(rel)) break;
-      dots<float>(K, nullptr, 0, V, 1, d_nrm);
-      scale_kernel<float><<<1024, KRY_THREADS, 0, s>>>(V, V, d_nrm, 2, N);
-      ++g_launches;
-      CK(fetch(K, KRY_MAXV, 1));
-      const double beta = std::sqrt(K.hsc[KRY_MAXV]);
-      std::fill(g.begin(), g.end(), 0.0);
-      g[0] = beta;
-      // the FP32 operator limits one correction to ~1e-6; ask for no more than that
-      const double target = beta * std::max(0.5 * tol / rel, 1e-6);
-      int jdone = 0;
-      for (int j = 0; j < m && its < maxit; ++j) {
-        float* w = V + (size_t)(j + 1) * N;
-        {
-          Epi<float> e{};
-          e.out = w; e.ax = 1.0f; e.bl = float(half); e.jacobi = 1; e.cj = float(half);
-          CK(launch_apply<float>(P32, V + (size_t)j * N, e, s));
-        }
-        dots<float>(K, V, j + 1, w, 1, d_h1);
-        update<float>(K, V, j + 1, d_h1, w, d_nrm);
-        CK(fetch(K, 0, KRY_MAXV + 1));
-        for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] = K.hsc[i2];
-        const double wn0 = std::sqrt(K.hsc[j + 1]);
-        double wn = std::sqrt(K.hsc[KRY_MAXV]);
-        if (wn < 0.7071067811865476 * wn0) {
-          dots<float>(K, V, j + 1, w, 0, d_h2);
-          update<float>(K, V, j + 1, d_h2, w, d_nrm);
-          CK(fetch(K, 2 * KRY_MAXV, j + 1));
-          CK(fetch(K, KRY_MAXV, 1));
-          for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] += K.hsc[2 * KRY_MAXV + i2];
-          wn = std::sqrt(K.hsc[KRY_MAXV]);
-        }
-        H[(size_t)(j + 1) * m + j] = wn;
-        if (wn > 0.0) {
-          scale_kernel<float><<<1024, KRY_THREADS, 0, s>>>(w, w, d_nrm, 2, N);
-          ++g_launches;
-        }
-        for (int i2 = 0; i2 < j; ++i2) {
-          const double a0 = H[(size_t)i2 * m + j], a1 = H[(size_t)(i2 + 1) * m + j];
-          H[(size_t)i2 * m + j] = cs[i2] * a0 + sn[i2] * a1;
-          H[(size_t)(i2 + 1) * m + j] = -sn[i2] * a0 + cs[i2] * a1;
-        }
-        const double a0 = H[(size_t)j * m + j], a1 = H[(size_t)(j + 1) * m + j];
-        const double den = std::hypot(a0, a1);
-        cs[j] = den > 0 ? a0 / den : 1.0;
-        sn[j] = den > 0 ? a1 / den : 0.0;
-        H[(size_t)j * m + j] = den;
-        H[(size_t)(j + 1) * m + j] = 0.0;
-        g[j + 1] = -sn[j] * g[j];
-        g[j] = cs[j] * g[j];
-        ++its;
-        jdone = j + 1;
-        if (std::fabs(g[j + 1]) <= target || wn == 0.0) break;
-      }
-      for (int i2 = jdone - 1; i2 >= 0; --i2) {
-        double v = g[i2];
-        for (int k2 = i2 + 1; k2 < jdone; ++k2) v -= H[(size_t)i2 * m + k2] * y[k2];
-        y[i2] = v / H[(size_t)i2 * m + i2];
-      }
-      for (int i2 = 0; i2 < jdone; ++i2) K.hsc[3 * KRY_MAXV + i2] = y[i2];
-      CK(cudaMemcpyAsync(d_y, K.hsc + 3 * KRY_MAXV, sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
-      combine_kernel<float><<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, d_y, state, N);
-      ++g_launches;
-      CK(cudaGetLastError());
-    }
-    total_its += its;
-    max_its = std::max(max_its, its);
-    last_rel = rel;
-    if (!(rel <= tol)) {  // also catches a NaN residual
-      c->err = "cn: GMRES did not reach the tolerance within maxit";
-      if (st) {
-        st->steps = step + 1; st->iterations = total_its; st->max_iterations = max_its; st->last_rel_residual = rel;
-        st->kernel_launches = g_launches - launches0;
-      }
-      return SAP_ENOCONV;
-    }
-  }
-  if (st) {
-    st->steps = nsteps; st->iterations = total_its; st->max_iterations = max_its; st->last_rel_residual = last_rel;
-    st->kernel_launches = g_launches - launches0;
-  }
-  return SAP_OK;
-cuda_fail:
-  c->err = std::string("cn: ") + cudaGetErrorString(err);
-  return SAP_ECUDA;
-#undef CK
+sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
+                    sap_solver_stats* st, cudaStream_t s) {
+  return c->prec == SAP_PREC_FP64 ? cn_steps_t<double>(c, state, dt, nsteps, tol, restart, maxit, st, s)
+                                  : cn_steps_t<float>(c, state, dt, nsteps, tol, restart, maxit, st, s);
 }
+
+
 
 
 // ================================================================================================

@@ -188,8 +188,6 @@ sap_status erk_steps(sap_ctx* c, double* state, double dt, int nsteps, cudaStrea
 sap_status erk_steps_noalloc(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s);
 sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
                     sap_solver_stats* st, cudaStream_t s);
-sap_status cn_steps_mixed(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
-                          sap_solver_stats* st, cudaStream_t s);
 sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, double* lambda, double dt, double tol,
                            int m, int maxit, double* mu_out, double* grad_nu, sap_solver_stats* st, cudaStream_t s);
 int apply_cells_per_block(int n, int nloc);

@@ -940,11 +940,12 @@ extern "C" sap_status sap_step_cn(sap_handle c, double* state, double dt, int ns
     return SAP_EINVAL;
   }
   if (c->prec == SAP_PREC_FP32) {
-    if (!ensure_ws32(c, restart + 1) || !ensure_ws64(c, 2)) {
+    if (c->ws64_count < 3) c->cn_prev_valid = false;
+    if (!ensure_ws32(c, restart + 1) || !ensure_ws64(c, 3)) {
       c->err = "cn: workspace allocation failed";
       return SAP_ENOMEM;
     }
-    return cn_steps_mixed(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
+    return cn_steps(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
   }
   if (c->ws64_count < restart + 4) c->cn_prev_valid = false;  // the history lives in the workspace
   if (!ensure_ws64(c, restart + 4)) {
