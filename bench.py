@@ -33,7 +33,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e-3  # SMs x DFMA/clk/SM x 2 flop x max GH
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3  # SMs x FFMA/clk/SM x 2 flop x max GHz = 80.5 TFLOP/s (FP32)
 # DRAM bytes (read + write) per apply launch from the ncu capture in profiles/apply_kernel_fp64_shock.md,
 # valid only for the kernel source it was taken on (first 16 hex of sha256 of csrc/operator.cu)
-APPLY_TRAFFIC = {"bf2a474848085cbc": 10730240.0}
+APPLY_TRAFFIC = {"658a8cdd1877a401": 10749696.0}
 
 
 def parse():
@@ -441,9 +441,13 @@ def run_adjoint(args):
     zN = adjoint.CNTrajectory.apply(nu_t, u1_t, fam)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    target = torch.zeros(64, dtype=torch.float64)
-    S = zN.view(64, 256, 16, 4)[:, :, 0, :].mean(dim=2)
-    L = (S.abs() + 1e-300).log().mean()
+    # spectrum misfit near the shock: S_j = mean over the x-cells within 20 of the shock of the
+    # cell-averaged f_000 at momentum cell j; L = sum_j (S_j - T_j)^2 with a seeded target
+    xc = 0.5 * (xe[1:] + xe[:-1])
+    sel = torch.from_numpy(np.abs(xc) < 20.0).cuda()
+    S = zN.view(64, 256, 16, 4)[:, :, 0, :].mean(dim=2)[:, sel].mean(dim=1)
+    target = torch.from_numpy(np.random.default_rng(5).normal(0.0, 1e-3, 64)).cuda()
+    L = ((S - target) ** 2).sum()
     L.backward()
     torch.cuda.synchronize()
     t2 = time.perf_counter()

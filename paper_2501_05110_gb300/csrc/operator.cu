@@ -62,10 +62,17 @@ template <typename T>
 __device__ __forceinline__ T csr_row(const Bank<T>& B, int mat, int r, const T* x, int stride) {
   if (mat == MAT_I) return x[r * stride];
   const int* rp = B.rp + B.rp_off[mat];
-  T acc = T(0);
+  T acc0 = T(0), acc1 = T(0);
+  int k = __ldg(rp + r);
   const int e = __ldg(rp + r + 1);
-  for (int k = __ldg(rp + r); k < e; ++k) acc += __ldg(B.val + k) * x[__ldg(B.col + k) * stride];
-  return acc;
+  for (; k + 1 < e; k += 2) {  // two independent chains hide the load latency
+    const int c0 = __ldg(B.col + k), c1 = __ldg(B.col + k + 1);
+    const T v0 = __ldg(B.val + k), v1 = __ldg(B.val + k + 1);
+    acc0 += v0 * x[c0 * stride];
+    acc1 += v1 * x[c1 * stride];
+  }
+  if (k < e) acc0 += __ldg(B.val + k) * x[__ldg(B.col + k) * stride];
+  return acc0 + acc1;
 }
 
 template <typename T>

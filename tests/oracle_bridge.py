@@ -34,13 +34,41 @@ class NodalOracle:
             out[idx] = np.linalg.solve(blk, v[idx].reshape(d.n, nl).T).T.ravel()
         return out
 
+    def _needed_cells(self):
+        """Sampled cells and their face neighbours (the columns their rows touch)."""
+        m = self.disc.mesh
+        need = set(int(c) for c in self.cells)
+        for c in self.cells:
+            multi = [int(v) for v in m.cell_multi(int(c))]
+            for a in range(m.D):
+                for dlt in (-1, 1):
+                    mm = list(multi)
+                    mm[a] = (mm[a] + dlt) % m.nc[a]
+                    need.add(int(m.cell_flat(mm)))
+        return np.array(sorted(need))
+
     def apply(self, y_nodal, rhs=False):
         """M^-1 D x (or M^-1 (h - D x)) in nodal form, for the assembled rows' cells."""
         d = self.disc
-        z = d.from_gauss_nodal(y_nodal)
+        if self.full:
+            z = d.from_gauss_nodal(y_nodal)
+        else:  # only the cells the assembled rows couple to are converted
+            per = d.n * d.mesh.nloc
+            z = np.zeros_like(y_nodal)
+            for c in self._needed_cells():
+                sl = slice(c * per, (c + 1) * per)
+                z[sl] = d.from_gauss_nodal(y_nodal[sl])
         Dz = d.D @ z
         v = (d.h - Dz) if rhs else Dz
-        return d.to_gauss_nodal(self._Minv(v))
+        if self.full:
+            return d.to_gauss_nodal(self._Minv(v))
+        out = np.zeros_like(y_nodal)
+        per = d.n * d.mesh.nloc
+        mv = self._Minv(v)
+        for c in self.cells:
+            sl = slice(c * per, (c + 1) * per)
+            out[sl] = d.to_gauss_nodal(mv[sl])
+        return out
 
     def row_mask(self):
         d = self.disc
