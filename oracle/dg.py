@@ -17,7 +17,7 @@ Follows the paper (arXiv:2501.05110) step by step:
   J = W (L+ + L-) W^T f (Eq. continuous-bc), periodic (Sec. 2.2);
 * M, D, h of Eq. definition-mass-and-dg-matrix.
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
 
 * quadrature: Gauss--Legendre with k+1 points per axis on cells and faces; the coefficient fields
   are sampled at the quadrature points;

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libsapgpu.so")
-SOURCES = ["operator.cu", "setup.cpp", "sh_tables.cpp"]
+SOURCES = ["operator.cu", "apply_rows.cu", "setup.cpp", "sh_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
     """Compile and link; returns the path of the shared library."""
     os.makedirs(OUT, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")] + \
+    deps = srcs + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))] + \
         [os.path.join(HERE, "..", "include", "sap.h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)

@@ -25,38 +25,14 @@
 #include <string>
 #include <vector>
 
-#include "sap_internal.h"
+#include "kernels_common.cuh"
 
 namespace sap {
 
 // kernels launched by this host thread (for the launch counts reported in sap_solver_stats)
 static thread_local int64_t g_launches = 0;
 int64_t launch_count() { return g_launches; }
-
-// ------------------------------------------------------------------------------------------------
-// epilogue: out = d .* (wb*b + ax*x + bl*(Lx) + gs*s), and/or ERK bookkeeping
-// ------------------------------------------------------------------------------------------------
-template <typename T>
-struct Epi {
-  T* out;               // may be null
-  const T* bvec;        // optional
-  T wb, ax, bl, gs;
-  int jacobi;           // multiply out by 1 / (1 + cj * diag(R - div beta))
-  T cj;
-  float* out32;         // optional: FP32 copy of out / (1 + cj * diag(R - div beta)), before `jacobi`
-  T* out2;              // optional second output out2 = ax2*x + bl2*(Lx) + gs2*s
-  T ax2, bl2, gs2;
-  T* outj;              // optional: out2 (or out when out2 is null) / (1 + cj * diag(R - div beta))
-  T axpost;             // added after the Jacobi scaling: out += axpost * x
-  const int* skip;      // when non-null and *skip != 0 the launch does nothing
-  // ERK stage (k = s - Lx):  acc += bdt k ; ynext = y0 + adt k ; final: state = acc + bdt k
-  double* acc;
-  const double* y0;
-  T* ynext;
-  double adt, bdt;
-  int erk;              // 0 none, 1 first stage (acc = y0 + bdt k), 2 middle, 3 last (y0 <- acc + bdt k)
-  double* state;        // for erk == 3
-};
+void note_launch() { ++g_launches; }
 
 template <typename T>
 __device__ __forceinline__ T csr_row(const Bank<T>& B, int mat, int r, const T* x, int stride) {
@@ -75,51 +51,12 @@ __device__ __forceinline__ T csr_row(const Bank<T>& B, int mat, int r, const T* 
   return acc0 + acc1;
 }
 
-template <typename T>
-__device__ __forceinline__ T csr_diag(const Bank<T>& B, int mat, int r, int n) {
-  if (mat == MAT_I) return T(1);
-  return __ldg(B.dg + mat * n + r);
-}
-
-// 1 / (1 + cj d): the point-Jacobi scale; a preconditioner needs no FP64 division, so the reciprocal
-// is taken in FP32 (the same fixed diagonal at every application)
-template <typename T>
-__device__ __forceinline__ T jacobi_scale(T cj, T rdiag) {
-  return T(__frcp_rn(float(T(1) + cj * rdiag)));
-}
-
-// momentum factors (p, gamma m, V, 1/V, ...) are tabulated on the host per momentum node and face
-template <typename T>
-__device__ __forceinline__ T mom_node(const OpParams<T>& P, int mf, int pn) {
-  return mf == MF_ONE ? T(1) : __ldg(P.mfn + (size_t)mf * P.npn + pn);
-}
-template <typename T>
-__device__ __forceinline__ T mom_face(const OpParams<T>& P, int mf, int pf) {
-  return mf == MF_ONE ? T(1) : __ldg(P.mff + (size_t)mf * P.npface + pf);
-}
-
-template <typename T>
-__device__ __forceinline__ T spatial_factor(const OpParams<T>& P, int sf, int sp) {
-  if (sf == SF_ONE) return T(1);
-  if (P.sf_is_uni[sf]) return P.sf_uni[sf];
-  return __ldg(P.sfield + (size_t)sf * P.nsv + sp);
-}
-
 // node index from a face point (axis a removed) and the position j along a
 __device__ __forceinline__ int face_node(int fp, int j, int a, const int* qpow) {
   const int lo = fp % qpow[a];
   const int hi = fp / qpow[a];
   return lo + j * qpow[a] + hi * qpow[a + 1];
 }
-
-// Index helpers: node index from a face point (axis a removed) and the position j along a; with
-// a compile-time q the divisions become multiply-shifts.
-__device__ __forceinline__ int face_node_q(int fp, int j, int a, int q) {
-  if (a == 0) return j + fp * q;
-  if (a == 1) return (fp % q) + j * q + (fp / q) * q * q;
-  return (fp % (q * q)) + j * q * q + (fp / (q * q)) * q * q * q;
-}
-__device__ __forceinline__ int qpow_of(int q, int a) { return a == 0 ? 1 : (a == 1 ? q : (a == 2 ? q * q : q * q * q)); }
 
 constexpr int EMAX = 6;  // face entries per thread: ceil(2 D / q) <= 6
 
@@ -201,7 +138,7 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
       const int sp = scell * qdx + (has_mom ? ii % nfp : ii);
       const int pn = has_mom ? pcell * q + ii / nfp : 0;
       T c = T(tm->scale) * spatial_factor(P, tm->sf, sp) * mom_node(P, tm->mf, pn);
-      if (tm->nu) c *= P.nu ? __ldg(P.nu + (size_t)cell * nloc + ii) : P.nu_uni;
+      if (tm->nu) c *= P.nu ? P.nu[(size_t)cell * nloc + ii] : P.nu_uni;
       CV[w] = c;
     }
     // face coefficients of the advection terms at every face point
@@ -220,7 +157,7 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
         const int fsp = has_mom ? fp % qsp : fp;
         if (tm.sf == SF_U + a) {
           const int base = P.scell_face[scell * 2 * P.dx + 2 * a + side];
-          c *= P.uface_is_uni[a] ? P.uface_uni[a] : __ldg(P.uface[a] + base + fsp);
+          c *= P.uface_is_uni[a] ? P.uface_uni[a] : P.uface[a][base + fsp];
         } else {
           c *= spatial_factor(P, tm.sf, scell * qdx);  // only SF_ONE occurs here
         }
@@ -371,35 +308,9 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
     const T jdn = Jf[((2 * a) * n + r) * nfp + fp];
     acc += invh * (P.L1[ia] * jup - P.L0[ia] * jdn - ds);
   }
-  const size_t dof = (size_t)doff + (size_t)cell * per_cell + t;
   T s = T(0);
-  if (r == 0) s = P.s000 ? __ldg(P.s000 + (size_t)cell * nloc + i) : P.s_uni;
-  if (E.erk) {
-    const double k = double(s) - double(acc);
-    if (E.erk == 1) {
-      E.acc[dof] = E.y0[dof] + E.bdt * k;
-    } else if (E.erk == 2) {
-      E.acc[dof] += E.bdt * k;
-    } else {
-      E.state[dof] = E.acc[dof] + E.bdt * k;
-    }
-    if (E.ynext) E.ynext[dof] = T(E.y0[dof] + E.adt * k);
-    return;
-  }
-  T o = E.ax * F[t] + E.bl * acc + E.gs * s;
-  if (E.bvec) o += E.wb * __ldg(E.bvec + dof);
-  if (E.out2) {
-    const T o2 = E.ax2 * F[t] + E.bl2 * acc + E.gs2 * s;
-    E.out2[dof] = o2;
-    if (E.outj) E.outj[dof] = o2 * jacobi_scale(E.cj, rdiag);
-    if (E.out32) E.out32[dof] = float(o2 * jacobi_scale(E.cj, rdiag));
-  } else {
-    if (E.outj) E.outj[dof] = o * jacobi_scale(E.cj, rdiag);
-    if (E.out32) E.out32[dof] = float(o * jacobi_scale(E.cj, rdiag));
-  }
-  if (E.jacobi) o *= jacobi_scale(E.cj, rdiag);
-  if (E.axpost != T(0)) o += E.axpost * F[t];
-  if (E.out) E.out[dof] = o;
+  if (r == 0) s = P.s000 ? P.s000[(size_t)cell * nloc + i] : P.s_uni;
+  epi_write(E, (size_t)doff + (size_t)cell * per_cell + t, F[t], acc, s, rdiag);
 }
 
 // Transposed operator L^T = (M^-1 D)^T in the nodal basis (discrete adjoint).  Term by term:
@@ -459,7 +370,7 @@ __device__ __forceinline__ void applyT_body(const OpParams<T>& P, const T* __res
       }
       const int sp = scell * P.qdx + ii % P.qdx;
       T c = T(tm->scale) * spatial_factor(P, tm->sf, sp) * mom_node(P, tm->mf, pcell * q + ii / P.qdx);
-      if (tm->nu) c *= P.nu ? __ldg(P.nu + (size_t)cell * nloc + ii) : P.nu_uni;
+      if (tm->nu) c *= P.nu ? P.nu[(size_t)cell * nloc + ii] : P.nu_uni;
       CV[w] = c;
     }
     for (int w = t; w < nf * MAXADV * nfp; w += per_cell) {
@@ -476,7 +387,7 @@ __device__ __forceinline__ void applyT_body(const OpParams<T>& P, const T* __res
         const int fsp = fp % qsp;
         if (tm.sf == SF_U + a) {
           const int base = P.scell_face[scell * 2 * P.dx + 2 * a + side];
-          c *= P.uface_is_uni[a] ? P.uface_uni[a] : __ldg(P.uface[a] + base + fsp);
+          c *= P.uface_is_uni[a] ? P.uface_uni[a] : P.uface[a][base + fsp];
         } else {
           c *= spatial_factor(P, tm.sf, scell * P.qdx);
         }
@@ -633,14 +544,14 @@ __device__ __forceinline__ void applyT_body(const OpParams<T>& P, const T* __res
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) applyT_kernel(const OpParams<T> P, const T* __restrict__ x, const Epi<T> E,
+__global__ void __launch_bounds__(1024) applyT_kernel(const __grid_constant__ OpParams<T> P, const T* __restrict__ x, const Epi<T> E,
                                                       int cpb, int cell_stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   applyT_body<T>(P, x, E, cpb, cell_stride, blockIdx.x * cpb, 0, smem_raw);
 }
 
 template <typename T, int DT, int QT>
-__global__ void __launch_bounds__(1024) apply_kernel(const OpParams<T> P, const T* __restrict__ x, const Epi<T> E,
+__global__ void __launch_bounds__(1024) apply_kernel(const __grid_constant__ OpParams<T> P, const T* __restrict__ x, const Epi<T> E,
                                                      int cpb, int cell_stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   apply_body<T, DT, QT>(P, x, E, cpb, cell_stride, blockIdx.x * cpb, 0, smem_raw);
@@ -704,19 +615,17 @@ static cudaError_t launch_apply_shape(const OpParams<T>& P, const T* x, const Ep
   return cudaGetLastError();
 }
 
-// Kernel shapes compiled with a fixed number of axes D and nodes per axis q (the workloads'
-// shapes); everything else runs the generic instantiation.
+// The shapes (D, q) compiled for the row-per-thread kernel (apply_rows.cu) run there; every other
+// shape runs the generic cell-node kernel.
 template <typename T>
 static cudaError_t launch_apply(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s) {
+  if (rows_supported(P.D, P.q)) return launch_rows<T>(P, x, e, s);
   const int per = P.n * P.nloc;
   if (per > 1024) return cudaErrorInvalidConfiguration;  // n (k+1)^D must fit one thread block
   const int cpb = apply_cells_per_block(P.n, P.nloc);
   const int stride = cell_stride_elems(P);
   const size_t smem = (size_t)cpb * stride * sizeof(T);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  if (P.D == 1 && P.q == 3) return launch_apply_shape<T, 1, 3>(P, x, e, s, cpb, stride, smem);
-  if (P.D == 2 && P.q == 2) return launch_apply_shape<T, 2, 2>(P, x, e, s, cpb, stride, smem);
-  if (P.D == 3 && P.q == 3) return launch_apply_shape<T, 3, 3>(P, x, e, s, cpb, stride, smem);
   return launch_apply_shape<T, 0, 0>(P, x, e, s, cpb, stride, smem);
 }
 
@@ -1451,7 +1360,7 @@ template <typename T>
 static cudaError_t launch_apply_batched(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e,
                                         cudaStream_t s) {
   if (B.smem > 200 * 1024 || B.threads > 1024 || B.threads < 1) return cudaErrorInvalidConfiguration;
-  if (B.shape_d == 2 && B.shape_q == 2) return launch_apply_batched_shape<T, 2, 2>(B, active, x, e, s);
+  if (B.rows) return launch_rows_batched<T>(B, active, x, e, s);
   return launch_apply_batched_shape<T, 0, 0>(B, active, x, e, s);
 }
 
@@ -1586,24 +1495,48 @@ static void batch_tables(sap_ctx* c, int target) {
   std::vector<OpParams<double>> P64(ni);
   std::vector<OpParams<float>> P32(ni);
   std::vector<int64_t> doff(ni);
-  std::vector<int> cpb(ni), stride(ni);
-  std::vector<int2> blocks;
-  int threads = 1;
-  size_t smem64 = 0, smem32 = 0;
+  int sd = c->sub[0]->D, sq = c->sub[0]->q;
+  for (auto* sc : c->sub)
+    if (sc->D != sd || sc->q != sq) sd = sq = 0;
+  const bool rows = sd > 0 && rows_supported(sd, sq);
   for (int i = 0; i < ni; ++i) {
-    sap_ctx* sc = c->sub[i];
-    P64[i] = sc->p64;
-    P32[i] = sc->p32;
+    P64[i] = c->sub[i]->p64;
+    P32[i] = c->sub[i]->p32;
     doff[i] = c->inst_off[i];
-    const int per = sc->n * sc->nloc;
-    if (per > 1024) throw std::string("an instance has n (k+1)^D > 1024");
-    cpb[i] = std::max(1, std::min(target, 1024) / per);
-    stride[i] = cell_stride_elems(sc->p64);
-    threads = std::max(threads, cpb[i] * per);
-    smem64 = std::max(smem64, (size_t)cpb[i] * stride[i] * sizeof(double));
-    smem32 = std::max(smem32, (size_t)cpb[i] * stride[i] * sizeof(float));
-    for (int c0 = 0; c0 < sc->ncell; c0 += cpb[i]) blocks.push_back(make_int2(i, c0));
   }
+  // cells per block, block list, block size and shared memory for one precision
+  auto plan = [&](auto tag, const auto& Pv, std::vector<int>& cpb, std::vector<int>& stride,
+                  std::vector<int2>& blocks, int& threads, size_t& smem) {
+    using T = decltype(tag);
+    cpb.assign(ni, 1);
+    stride.assign(ni, 0);
+    blocks.clear();
+    threads = 1;
+    smem = 0;
+    for (int i = 0; i < ni; ++i) {
+      sap_ctx* sc = c->sub[i];
+      size_t sm = 0;
+      if (rows) {
+        rows_config<T>(Pv[i], target, &cpb[i], &sm);
+        threads = std::max(threads, cpb[i] * sc->n);
+      } else {
+        const int per = sc->n * sc->nloc;
+        if (per > 1024) throw std::string("an instance has n (k+1)^D > 1024");
+        cpb[i] = std::max(1, std::min(target, 1024) / per);
+        stride[i] = cell_stride_elems(sc->p64);
+        threads = std::max(threads, cpb[i] * per);
+        sm = (size_t)cpb[i] * stride[i] * sizeof(T);
+      }
+      smem = std::max(smem, sm);
+      for (int c0 = 0; c0 < sc->ncell; c0 += cpb[i]) blocks.push_back(make_int2(i, c0));
+    }
+  };
+  std::vector<int> cpb64, cpb32, st64, st32;
+  std::vector<int2> bl64, bl32;
+  int th64, th32;
+  size_t sm64, sm32;
+  plan(double{}, P64, cpb64, st64, bl64, th64, sm64);
+  plan(float{}, P32, cpb32, st32, bl32, th32, sm32);
   std::vector<int> cinst, clen, cfirst(ni), ccount(ni);
   std::vector<int64_t> ck0;
   for (int i = 0; i < ni; ++i) {
@@ -1617,16 +1550,12 @@ static void batch_tables(sap_ctx* c, int target) {
     ccount[i] = (int)cinst.size() - cfirst[i];
   }
   const int64_t* d_doff = (const int64_t*)dev_upload(c, doff);
-  const int* d_cpb = (const int*)dev_upload(c, cpb);
-  const int* d_stride = (const int*)dev_upload(c, stride);
-  const int2* d_blocks = (const int2*)dev_upload(c, blocks);
-  int sd = c->sub[0]->D, sq = c->sub[0]->q;
-  for (auto* sc : c->sub)
-    if (sc->D != sd || sc->q != sq) sd = sq = 0;
-  c->b64 = BatchDev<double>{(const OpParams<double>*)dev_upload(c, P64), d_doff, d_cpb, d_stride, d_blocks,
-                            (int)blocks.size(), threads, smem64, sd, sq};
-  c->b32 = BatchDev<float>{(const OpParams<float>*)dev_upload(c, P32), d_doff, d_cpb, d_stride, d_blocks,
-                           (int)blocks.size(), threads, smem32, sd, sq};
+  c->b64 = BatchDev<double>{(const OpParams<double>*)dev_upload(c, P64), d_doff, (const int*)dev_upload(c, cpb64),
+                            (const int*)dev_upload(c, st64), (const int2*)dev_upload(c, bl64), (int)bl64.size(),
+                            th64, sm64, sd, sq, rows ? 1 : 0};
+  c->b32 = BatchDev<float>{(const OpParams<float>*)dev_upload(c, P32), d_doff, (const int*)dev_upload(c, cpb32),
+                           (const int*)dev_upload(c, st32), (const int2*)dev_upload(c, bl32), (int)bl32.size(),
+                           th32, sm32, sd, sq, rows ? 1 : 0};
   c->chunks = BatchChunks{(const int*)dev_upload(c, cinst), (const int64_t*)dev_upload(c, ck0),
                           (const int*)dev_upload(c, clen), (const int*)dev_upload(c, cfirst),
                           (const int*)dev_upload(c, ccount), (int)cinst.size()};
@@ -1662,7 +1591,7 @@ sap_status batch_prepare(sap_ctx* c, cudaStream_t s) {
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
-      for (int target : {64, 128, 256, 512, 1024}) {
+      for (int target : {64, 128, 256, 512}) {
         batch_tables(c, target);
         const int64_t l0 = g_launches;
         for (int rep = 0; rep < 4; ++rep) {

@@ -50,8 +50,21 @@ struct Bank {
   const int* rp;   // concatenated row pointers (absolute offsets into col/val)
   const int* col;
   const T* val;
-  const T* dg;     // [nmat][n] diagonal of every matrix
+  const T* dg;     // [nmat][n] diagonal of every matrix (at least n entries)
   int rp_off[96];
+  // the same matrices in ELL form for the row-per-thread kernels: matrix m, row r, slot k < ell_w[m]
+  // is entry ell_off[m] + k n + r, a (column, value) pair (EllEntry<T>); short rows are padded with
+  // (r, 0), and n spare entries follow the last matrix
+  const void* ell;
+  int ell_off[96];
+  int ell_w[96];
+};
+
+// One ELL entry: the column and the value, loaded together (8 bytes in FP32, 16 in FP64).
+template <typename T>
+struct alignas(2 * sizeof(T)) EllEntry {
+  int col;
+  T val;
 };
 
 template <typename T>
@@ -93,8 +106,13 @@ struct OpParams {
   // momentum-face |beta| per point
   const int* pslot;                // [nsv] slot or -1
   const T* pabs;                   // [slot][npc+1][nnz(pattern)]
+  const T* pabs_ell;               // [slot][npc+1][ell_w(pattern)][n]: the same values in ELL order
   int npface;
   const T* lam;                    // eigenvalues of A^a (same for a = x, y, z), n entries
+  // bit t set: the coefficient of reaction term t (of advection term t of axis a) is the same at
+  // every node of every cell
+  unsigned react_uni;
+  unsigned adv_uni[MAXD];
 };
 
 struct DevBuf {
@@ -113,6 +131,7 @@ struct BatchDev {
   int nblocks = 0, threads = 0;
   size_t smem = 0;
   int shape_d = 0, shape_q = 0;       // common (D, q) of all instances, 0 if they differ
+  int rows = 0;                       // 1: the row-per-thread kernel runs the batch
 };
 
 // Chunking of the concatenated state for the per-instance Krylov reductions: chunks never cross an
@@ -191,6 +210,17 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
 sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, double* lambda, double dt, double tol,
                            int m, int maxit, double* mu_out, double* grad_nu, sap_solver_stats* st, cudaStream_t s);
 int apply_cells_per_block(int n, int nloc);
+// row-per-thread apply (apply_rows.cu) for the compiled shapes (D, q) = (1, 3), (2, 2), (3, 3)
+bool rows_supported(int D, int q);
+template <typename T>
+struct Epi;
+template <typename T>
+cudaError_t launch_rows(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s);
+// cells per block and dynamic shared memory (bytes) of the row kernel for a problem
+template <typename T>
+void rows_config(const OpParams<T>& P, int target_threads, int* cells, size_t* smem);
+template <typename T>
+cudaError_t launch_rows_batched(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e, cudaStream_t s);
 int apply_cell_stride(const OpParams<double>& P);
 sap_status batch_prepare(sap_ctx* c, cudaStream_t s);
 sap_status batch_apply(sap_ctx* c, const void* x, void* y, int mode, cudaStream_t s);

@@ -529,13 +529,33 @@ static void set_bank(OpParams<T>& P, const BankBuilder& B, sap_ctx* c, std::vect
   if (rp.empty()) rp.push_back(0);
   c->bank_nnz.clear();
   for (size_t m = 0; m < B.mats.size(); ++m) c->bank_nnz.push_back((double)B.mats[m].col.size());
-  std::vector<double> dgv(std::max<size_t>(1, B.mats.size() * c->n), 0.0);
+  std::vector<double> dgv(std::max<size_t>(c->n, B.mats.size() * c->n), 0.0);  // >= n: see csr_diag
   for (size_t m = 0; m < B.mats.size(); ++m)
     for (int i = 0; i < c->n; ++i)
       for (int k = B.mats[m].rp[i]; k < B.mats[m].rp[i + 1]; ++k)
         if (B.mats[m].col[k] == i) dgv[m * c->n + i] = B.mats[m].val[k];
   if (sizeof(T) == 8) P.bank.dg = (const T*)upload(c, dgv, own);
   else P.bank.dg = (const T*)upload(c, to_f32(dgv), own);
+  // ELL copy: slot k of row r at ell_off[m] + k n + r; rows shorter than the widest are padded (r, 0)
+  std::vector<EllEntry<T>> ell;
+  for (size_t m = 0; m < B.mats.size(); ++m) {
+    const HostCSR& h = B.mats[m];
+    int w = 0;
+    for (int i = 0; i < c->n; ++i) w = std::max(w, h.rp[i + 1] - h.rp[i]);
+    P.bank.ell_off[m] = (int)ell.size();
+    P.bank.ell_w[m] = w;
+    for (int k = 0; k < w; ++k)
+      for (int i = 0; i < c->n; ++i) {
+        EllEntry<T> e{};
+        const bool in = h.rp[i] + k < h.rp[i + 1];
+        e.col = in ? h.col[h.rp[i] + k] : i;
+        e.val = in ? T(h.val[h.rp[i] + k]) : T(0);
+        ell.push_back(e);
+      }
+  }
+  // n spare entries at the end: a load of slot 0 of an empty last matrix stays inside the table
+  for (int i = 0; i < c->n; ++i) ell.push_back(EllEntry<T>{i, T(0)});
+  P.bank.ell = upload(c, ell, own);
   P.bank.rp = (const int*)upload(c, rp, own);
   P.bank.col = (const int*)upload(c, col, own);
   if (sizeof(T) == 8) P.bank.val = (const T*)upload(c, val, own);
@@ -827,6 +847,33 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
       else
         P.pabs = nullptr;
       P.lam = (sizeof(T) == 8) ? (const T*)upload(c, lam, fs.bufs) : (const T*)upload(c, to_f32(lam), fs.bufs);
+      // the momentum-face |beta| values again in the ELL order of their pattern matrix
+      P.pabs_ell = nullptr;
+      for (int a = 0; a < c->D; ++a) {
+        const AxisInfo& A = ax[a];
+        if (!A.active || A.route != ABS_POINT || pabs.empty()) continue;
+        const HostCSR& pc = B.mats[A.absmat];
+        const int w = P.bank.ell_w[A.absmat];
+        const int nnzp = (int)pc.col.size();
+        const size_t npts = pabs.size() / nnzp;  // slots x momentum faces
+        std::vector<double> pe(npts * w * n, 0.0);
+        for (size_t sp = 0; sp < npts; ++sp)
+          for (int i = 0; i < n; ++i)
+            for (int k = 0; pc.rp[i] + k < pc.rp[i + 1]; ++k) pe[(sp * w + k) * n + i] = pabs[sp * nnzp + pc.rp[i] + k];
+        P.pabs_ell = (sizeof(T) == 8) ? (const T*)upload(c, pe, fs.bufs) : (const T*)upload(c, to_f32(pe), fs.bufs);
+      }
+      // terms whose coefficient is one number for the whole problem
+      auto term_uni = [&](const Term& tm) {
+        return (tm.sf == SF_ONE || uni[tm.sf]) && (tm.mf == MF_ONE || !has_mom) && (!tm.nu || nu_uni);
+      };
+      P.react_uni = 0u;
+      for (int t = 0; t < P.nreact; ++t)
+        if (term_uni(P.react[t])) P.react_uni |= 1u << t;
+      for (int a = 0; a < MAXD; ++a) {
+        P.adv_uni[a] = 0u;
+        for (int t = 0; t < P.ax[a].nadv; ++t)
+          if (term_uni(P.ax[a].adv[t])) P.adv_uni[a] |= 1u << t;
+      }
     };
     fill(c->p64, double{});
     fill(c->p32, float{});

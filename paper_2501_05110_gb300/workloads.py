@@ -138,7 +138,7 @@ def shock_profile(U1, r, Ls):
 def shock(nx=256, npc=64, k=1, lmax=3, U1=0.1, r=4.0, Ls=0.5, xr=(-200.0, 200.0), lnpr=(0.0, 10.0),
           nu0=1.0, nu_field=None, Q=0.1, x0=0.0, lnp0=1.0, sig_x=None, sig_lnp=None, B0=1.0,
           dt=1.0, nsteps=2000, tol=1e-10, restart=30, x_edges=None, name=None):
-    """Parallel shock (Sec. 4.4 set-up with the readings listed in the design doc): x upstream
+    """Parallel shock (Sec. 4.4 set-up, with this library's readings of its open points): x upstream
     zero inflow, x downstream continuous, ln p zero inflow at both ends; nu = nu0 p (or a given
     field); B = B0 e_x; Gaussian isotropic source at (x0, ln p0) with rate Q; zero initial state;
     Crank--Nicolson with GMRES."""

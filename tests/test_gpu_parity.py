@@ -150,7 +150,7 @@ def test_apply_fp32(torch_cuda, name):
 
 def test_erk_fp32_periodic_1d(torch_cuda):
     """RK4 with FP32 stage derivatives and FP64 accumulation (1000 steps): rel. L2 error vs the
-    FP64 oracle below 1e-5 (SURVEY reading: ~1e-6 expected)."""
+    FP64 oracle below 1e-5 (~1e-6 expected from the FP32 stage derivatives)."""
     prob = W.periodic_1d()
     orc = NodalOracle(prob)
     sol = _solver(prob, "fp32")

@@ -114,7 +114,7 @@ def _u(lp, mp, l, m):
 def test_rotation_relations(lmax):
     """Eq. real-direction-op-matrices-and-rotations and the printed rotation elements
     (Eq. representation-matrix-Uz with Eq. complex-rotation).  The printed element formula of
-    Eq. representation-matrix-Ux equals exp(-pi/2 Omega^x) (reading listed in the design doc)."""
+    Eq. representation-matrix-Ux equals exp(-pi/2 Omega^x) (the reading taken for that element)."""
     T = sh.tables(lmax)
     A, Om = T["A"], T["Om"]
     Uz, Ux = expm(0.5 * math.pi * Om[2]), expm(0.5 * math.pi * Om[0])
