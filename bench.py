@@ -31,9 +31,9 @@ METRIC = "phase-space DoF-updates/s per CN step"
 UNIT = "DoF-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e-3  # SMs x DFMA/clk/SM x 2 flop x max GHz = 1.2586 TFLOP/s (FP64)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3  # SMs x FFMA/clk/SM x 2 flop x max GHz = 80.5 TFLOP/s (FP32)
-# DRAM bytes (read + write) per apply launch from the ncu capture in profiles/apply_kernel_fp64_shock.md,
-# valid only for the kernel source it was taken on (first 16 hex of sha256 of csrc/operator.cu)
-APPLY_TRAFFIC = {"658a8cdd1877a401": 10749696.0}
+# DRAM bytes (read + write) per apply launch from the ncu capture in profiles/rows_kernel_fp64_shock.md,
+# valid only for the kernel source it was taken on (first 16 hex of sha256 of csrc/apply_rows.cu)
+APPLY_TRAFFIC = {}
 
 
 def parse():
@@ -253,11 +253,11 @@ def run_mine(args):
     achieved = flops / t_apply / 1e12
     peak_alu = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
     import hashlib
-    src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2501_05110_gb300", "csrc", "operator.cu"), "rb").read()).hexdigest()[:16]
+    src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2501_05110_gb300", "csrc", "apply_rows.cu"), "rb").read()).hexdigest()[:16]
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
                 "frac": achieved / peak_alu,
                 "traffic": APPLY_TRAFFIC.get(src_sha) if args.precision == "fp64" else None,
-                "kernel": "apply_kernel<double>" if args.precision == "fp64" else "apply_kernel<float>",
+                "kernel": "rows_kernel<double,2,2>" if args.precision == "fp64" else "rows_kernel<float,2,2>",
                 "apply_us": t_apply * 1e6, "flops_per_apply": flops, "algorithmic_bytes_per_apply": abytes,
                 "hbm_view": {"achieved_gbs": abytes / t_apply / 1e9, "peak_gbs": 6746.3,
                              "frac": abytes / t_apply / 1e9 / 6746.3},
