@@ -15,6 +15,7 @@ solve and gradient accumulation runs in libsapgpu.so.
 from __future__ import annotations
 
 import dataclasses
+import time
 from typing import Callable
 
 import numpy as np
@@ -33,6 +34,8 @@ class CNProblemFamily:
     restart: int = 30
     checkpoint: int = 50
     u1_rel_eps: float = 1e-6
+    # filled by the backward pass: wall time of its parts (s) and the adjoint GMRES iterations per step
+    last_backward: dict = dataclasses.field(default_factory=dict)
 
     def solver(self, nu_nodes, U1):
         return sapgpu.Solver(self.make_problem(nu_nodes, U1), "fp64")
@@ -69,6 +72,7 @@ class CNTrajectory(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gL):
         fam, ckpts, nu_np, u1 = ctx.fam, ctx.ckpts, ctx.nu_np, ctx.u1
+        t_enter = time.perf_counter()
         sol = fam.solver(nu_np, u1)
         eps = fam.u1_rel_eps * abs(u1)
         sol_p = fam.solver(nu_np, u1 + eps)
@@ -81,23 +85,37 @@ class CNTrajectory(torch.autograd.Function):
         g_u1 = 0.0
         starts = sorted(ckpts)
         end = fam.nsteps
+        t_rec = t_adj = 0.0
+        iters = []
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t_enter
         for s0 in reversed(starts):
             # recompute the states of [s0, end] from the checkpoint
+            t0 = time.perf_counter()
             states = [ckpts[s0].clone()]
             x = ckpts[s0].clone()
             for _ in range(s0, end):
                 sol.step_cn(x, fam.dt, 1, fam.tol, fam.restart, 20000)
                 states.append(x.clone())
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
             for k in range(end - s0, 0, -1):
                 zp, zn = states[k - 1], states[k]
-                sol.adjoint_step_cn(zp, zn, lam, fam.dt, fam.tol, fam.restart, 20000, mu_out=mu, grad_nu=grad_nu)
+                st = sol.adjoint_step_cn(zp, zn, lam, fam.dt, fam.tol, fam.restart, 20000, mu_out=mu,
+                                         grad_nu=grad_nu)
+                iters.append(int(st.iterations))
                 w = zp + zn
                 sol_p.apply(w, a)
                 sol_m.apply(w, b)
                 g_u1 += -0.5 * fam.dt * float(mu @ (a - b)) / (2 * eps)
+            t_rec += t1 - t0
+            t_adj += time.perf_counter() - t1
             end = s0
         for s in (sol, sol_p, sol_m):
             s.close()
+        fam.last_backward = {"total_s": time.perf_counter() - t_enter, "setup_s": t_setup,
+                             "recompute_s": t_rec, "adjoint_s": t_adj,
+                             "adjoint_iterations_per_step": sum(iters) / max(1, len(iters))}
         return grad_nu, torch.tensor(g_u1, dtype=torch.float64), None
 
 
