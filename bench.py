@@ -159,6 +159,25 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------------
+# rank aggregation (replicas: no collective on the data path, only the timing reduction)
+# ------------------------------------------------------------------------------------------------
+def max_over_ranks(t: float, world: int, device: str = "cuda") -> float:
+    """The job's time: the largest of the ranks' timed regions (all_reduce MAX when world > 1)."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(n_per_rank: int, steps: int, world: int, t_max: float) -> float:
+    """Whole-job throughput: the DoF-updates of all ranks divided by the slowest rank's time."""
+    return n_per_rank * steps * world / t_max
+
+
+# ------------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------------
 def run_mine(args):
@@ -206,12 +225,8 @@ def run_mine(args):
         launches += st.kernel_launches
     barrier()
     clk = clocks.stop()
-    t_total = sum(t_steps)
-    if world > 1:
-        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    value = N * args.steps * world / t_total
+    t_total = max_over_ranks(sum(t_steps), world)
+    value = job_value(N, args.steps, world, t_total)
 
     # ---- end to end through the public API with host buffers -------------------------------------
     host = torch.empty(N, dtype=torch.float64, pin_memory=True)
@@ -230,11 +245,8 @@ def run_mine(args):
         e1.synchronize()
         t_e2e += e0.elapsed_time(e1) * 1e-3
     barrier()
-    if world > 1:
-        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e = {"value": N * args.steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": N * 8,
+    t_e2e = max_over_ranks(t_e2e, world)
+    e2e = {"value": job_value(N, args.steps, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": N * 8,
            "d2h_bytes_per_step": N * 8}
 
     # ---- dominant kernel: the operator apply, timed alone on the same stream ----------------------
