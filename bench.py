@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--instances", type=int, default=512, help="batched: number of shock instances")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare-single", type=int, default=16,
+                    help="batched: also run this many of the instances one at a time on the FP64 path")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--apply-reps", type=int, default=200)
     return ap.parse_args()
@@ -409,6 +411,33 @@ def run_batched(args):
     t_apply = e0.elapsed_time(e1) * 1e-3 / 5
     flops, abytes = batch.apply_cost()
     t = sum(times)
+    batch.close()
+    # the same instances run one at a time on the plain FP64 path (equal tolerance, same steps): every
+    # (count/K)-th instance, each from its own initial state with the same warm-up
+    single = None
+    if args.compare_single > 0:
+        idx = list(range(0, len(probs), max(1, len(probs) // args.compare_single)))[:args.compare_single]
+        dofs, t_single, its_single = 0, 0.0, []
+        for i in idx:
+            sol = sapgpu.Solver(probs[i], "fp64")
+            ys = sol.initial_state()
+            for _ in range(args.warmup):
+                sol.step_cn(ys, 1.0, 1, 1e-10, 30, 20000)
+            torch.cuda.synchronize()
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = sol.step_cn(ys, 1.0, 1, 1e-10, 30, 20000)
+                e1.record(stream)
+                e1.synchronize()
+                t_single += e0.elapsed_time(e1) * 1e-3
+                its_single.append(st.iterations)
+            dofs += sol.N
+            sol.close()
+        single = {"path": "one instance at a time, FP64 plain, tol 1e-10", "instances": len(idx),
+                  "instance_index_step": max(1, len(probs) // args.compare_single), "dofs": dofs,
+                  "value": dofs * args.steps / t_single, "unit": UNIT,
+                  "gmres_iterations_per_step": statistics.mean(its_single)}
     print(json.dumps({"metric": "phase-space DoF-updates/s per CN step (batched)", "value": N * args.steps / t,
                       "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -420,7 +449,7 @@ def run_batched(args):
                                  "lmax_counts": {str(l): sum(p.lmax == l for p in probs) for l in (1, 3, 5, 7)}},
                       "apply": {"us": t_apply * 1e6, "gbs": abytes / t_apply / 1e9,
                                 "hbm_frac": abytes / t_apply / 1e9 / 6746.3, "tflops": flops / t_apply / 1e12},
-                      "gpu_launches": int(launches), "clocks": clk}))
+                      "gpu_launches": int(launches), "clocks": clk, "single_instances": single}))
 
 
 def run_adjoint(args):
