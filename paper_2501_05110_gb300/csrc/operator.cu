@@ -1379,12 +1379,13 @@ __global__ void __launch_bounds__(KRY_THREADS) multidot_b_kernel(const TV* __res
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mt = m + (with_ww ? 1 : 0);
+  const bool pairs = ((ldv & 1) == 0) && ((k0 & 1) == 0);  // V_i + k0 stays 2-element aligned
   for (int i = warp; i < mt; i += KRY_THREADS / 32) {
-    double acc = 0.0;
+    double acc;
     if (i < m) {
-      const TV* a = V + i * ldv + k0;
-      for (int k = lane; k < len; k += 32) acc += double(__ldg(a + k)) * ws[k];
+      acc = dot_chunk<TV>(V + i * ldv + k0, ws, len, lane, pairs);
     } else {
+      acc = 0.0;
       for (int k = lane; k < len; k += 32) acc += ws[k] * ws[k];
     }
     acc = warp_sum(acc);
@@ -1423,7 +1424,9 @@ __global__ void __launch_bounds__(KRY_THREADS) update_b_kernel(const TV* __restr
   double nrm = 0.0;
   for (int k = threadIdx.x; k < len; k += KRY_THREADS) {
     double v = double(w[k0 + k]);
-    for (int i = 0; i < m; ++i) v -= hs[i] * double(__ldg(V + i * ldv + k0 + k));
+    const TV* vp = V + k0 + k;
+#pragma unroll 4
+    for (int i = 0; i < m; ++i) v -= hs[i] * double(__ldg(vp + i * ldv));
     const TV vs = TV(v);
     w[k0 + k] = vs;
     nrm += double(vs) * double(vs);
@@ -1448,7 +1451,9 @@ __global__ void scale_b_kernel(const TV* __restrict__ x, TV* __restrict__ y, con
   if (!(av > 0.0)) return;
   const double f = 1.0 / sqrt(av);
   const int64_t k0 = C.k0[blockIdx.x];
-  for (int k = threadIdx.x; k < C.len[blockIdx.x]; k += blockDim.x) y[k0 + k] = TV(f * double(x[k0 + k]));
+  const int len = C.len[blockIdx.x];  // in a register: the stores to y cannot change it
+#pragma unroll 4
+  for (int k = threadIdx.x; k < len; k += blockDim.x) y[k0 + k] = TV(f * double(x[k0 + k]));
 }
 
 // x (FP64) += sum_{i < mi[inst]} y[inst*stride + i] V_i
@@ -1462,9 +1467,12 @@ __global__ void combine_b_kernel(const TV* __restrict__ V, int64_t ldv, const in
   if (threadIdx.x < m) ys[threadIdx.x] = y[(size_t)inst * stride + threadIdx.x];
   __syncthreads();
   const int64_t k0 = C.k0[blockIdx.x];
-  for (int k = threadIdx.x; k < C.len[blockIdx.x]; k += blockDim.x) {
+  const int len = C.len[blockIdx.x];
+  for (int k = threadIdx.x; k < len; k += blockDim.x) {
     double v = x[k0 + k];
-    for (int i = 0; i < m; ++i) v += ys[i] * double(__ldg(V + i * ldv + k0 + k));
+    const TV* vp = V + k0 + k;
+#pragma unroll 4
+    for (int i = 0; i < m; ++i) v += ys[i] * double(__ldg(vp + i * ldv));
     x[k0 + k] = v;
   }
 }
@@ -1474,7 +1482,8 @@ __global__ void zero_b_kernel(double* __restrict__ x, BatchChunks C, const int* 
   const int inst = C.inst[blockIdx.x];
   if (!mask[inst]) return;
   const int64_t k0 = C.k0[blockIdx.x];
-  for (int k = threadIdx.x; k < C.len[blockIdx.x]; k += blockDim.x) x[k0 + k] = 0.0;
+  const int len = C.len[blockIdx.x];
+  for (int k = threadIdx.x; k < len; k += blockDim.x) x[k0 + k] = 0.0;
 }
 
 template <typename V>
