@@ -977,6 +977,60 @@ __device__ __forceinline__ bool kry_skip(const int* done, const int* need) {
 // dots of w with V_0..V_{m-1} (+ w.w) over chunks; the last block sums the partials in chunk order.
 // 16 warps per block, one basis vector per warp at a time, paired loads when the layout allows.
 constexpr int LB_THREADS = 512;
+// Double-float arithmetic on the FP32 units for the FP32 Krylov vectors of the precision form.  On
+// GB300 an FP64 instruction costs ~64 FP32 ones; the orthogonalisation keeps FP64-class accuracy
+// with exact products (p + pe = a b via FMA) and compensated sums (TwoSum): (s, c) carries a sum
+// with ~2^-48 relative error, converted to FP64 once per lane.
+// (The _rn intrinsics keep every rounding step as written: no contraction into FMAs.)
+__device__ __forceinline__ void df_fma(float& s, float& c, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = fmaf(a, b, -p);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, pe));
+}
+
+// V_i . w over one chunk by one warp, FP32 vectors, double-float sums (ws: the chunk of w in FP32)
+__device__ __forceinline__ double dot_chunk_df(const float* __restrict__ a, const float* ws, int len, int lane,
+                                               bool pairs) {
+  float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
+  int k = lane;
+  if (pairs) {
+    const float2* a2 = reinterpret_cast<const float2*>(a);
+    const int np = len >> 1;
+    for (int p = lane; p < np; p += 32) {
+      const float2 x = __ldg(a2 + p);
+      df_fma(s0, c0, x.x, ws[2 * p]);
+      df_fma(s1, c1, x.y, ws[2 * p + 1]);
+    }
+    k = 2 * np + lane;
+  }
+  for (; k < len; k += 32) df_fma(s0, c0, __ldg(a + k), ws[k]);
+  return (double(s0) + double(c0)) + (double(s1) + double(c1));
+}
+
+// w . w over one chunk by one warp, double-float sums
+__device__ __forceinline__ double dot_self_df(const float* ws, int len, int lane) {
+  float s = 0.0f, c = 0.0f;
+  for (int k = lane; k < len; k += 32) df_fma(s, c, ws[k], ws[k]);
+  return double(s) + double(c);
+}
+
+// w_k - sum_{i<m} h_i V_i[k] in double-float (h split into FP32 hi + lo parts), rounded to FP32
+__device__ __forceinline__ float update_df(float wk, const float* __restrict__ vp, int64_t ldv, int m,
+                                           const float* hh, const float* hl) {
+  float s = wk, c = 0.0f;
+#pragma unroll 4
+  for (int i = 0; i < m; ++i) {
+    const float v = __ldg(vp + i * ldv);
+    df_fma(s, c, -hh[i], v);
+    c = fmaf(-hl[i], v, c);
+  }
+  return s + c;
+}
+
 template <typename TV>
 __device__ __forceinline__ double dot_chunk(const TV* __restrict__ a, const double* ws, int len, int lane, bool pairs) {
   double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
@@ -1013,25 +1067,36 @@ __global__ void __launch_bounds__(LB_THREADS) multidot_lb_kernel(const TV* __res
                                                                  unsigned int* counter, double* out,
                                                                  const int* done, const int* need) {
   if (kry_skip(done, need)) return;
-  __shared__ double ws[KRY_CHUNK];
   __shared__ unsigned int ticket;
   const int64_t k0 = (int64_t)blockIdx.x * KRY_CHUNK;
   const int len = (int)((N - k0) < KRY_CHUNK ? (N - k0) : KRY_CHUNK);
-  for (int k = threadIdx.x; k < len; k += LB_THREADS) ws[k] = double(w[k0 + k]);
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mt = m + (with_ww ? 1 : 0);
   const bool pairs = ((ldv & 1) == 0);  // V_i + k0 stays 2-element aligned
-  for (int i = warp; i < mt; i += LB_THREADS / 32) {
-    double acc;
-    if (i < m) {
-      acc = dot_chunk<TV>(V + i * ldv + k0, ws, len, lane, pairs);
-    } else {
-      acc = 0.0;
-      for (int k = lane; k < len; k += 32) acc += ws[k] * ws[k];
+  if constexpr (sizeof(TV) == 4) {
+    __shared__ float wsf[KRY_CHUNK];
+    for (int k = threadIdx.x; k < len; k += LB_THREADS) wsf[k] = w[k0 + k];
+    __syncthreads();
+    for (int i = warp; i < mt; i += LB_THREADS / 32) {
+      double acc = i < m ? dot_chunk_df(V + i * ldv + k0, wsf, len, lane, pairs) : dot_self_df(wsf, len, lane);
+      acc = warp_sum(acc);
+      if (lane == 0) partial[(size_t)i * nchunks + blockIdx.x] = acc;
     }
-    acc = warp_sum(acc);
-    if (lane == 0) partial[(size_t)i * nchunks + blockIdx.x] = acc;
+  } else {
+    __shared__ double ws[KRY_CHUNK];
+    for (int k = threadIdx.x; k < len; k += LB_THREADS) ws[k] = double(w[k0 + k]);
+    __syncthreads();
+    for (int i = warp; i < mt; i += LB_THREADS / 32) {
+      double acc;
+      if (i < m) {
+        acc = dot_chunk<TV>(V + i * ldv + k0, ws, len, lane, pairs);
+      } else {
+        acc = 0.0;
+        for (int k = lane; k < len; k += 32) acc += ws[k] * ws[k];
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) partial[(size_t)i * nchunks + blockIdx.x] = acc;
+    }
   }
   __threadfence();
   __syncthreads();
@@ -1071,14 +1136,30 @@ __global__ void __launch_bounds__(LB_THREADS) update_lb_kernel(const TV* __restr
   const int64_t k0 = (int64_t)blockIdx.x * KRY_CHUNK;
   const int len = (int)((N - k0) < KRY_CHUNK ? (N - k0) : KRY_CHUNK);
   double nrm = 0.0;
-  for (int k = threadIdx.x; k < len; k += LB_THREADS) {
-    double v = double(w[k0 + k]);
-    const TV* vp = V + k0 + k;
+  if constexpr (sizeof(TV) == 4) {
+    __shared__ float hh[KRY_MAXV], hl[KRY_MAXV];
+    if (threadIdx.x < m) {
+      hh[threadIdx.x] = float(hs[threadIdx.x]);
+      hl[threadIdx.x] = float(hs[threadIdx.x] - double(float(hs[threadIdx.x])));
+    }
+    __syncthreads();
+    float ns = 0.0f, nc = 0.0f;
+    for (int k = threadIdx.x; k < len; k += LB_THREADS) {
+      const float vs = update_df(w[k0 + k], V + k0 + k, ldv, m, hh, hl);
+      w[k0 + k] = vs;
+      df_fma(ns, nc, vs, vs);
+    }
+    nrm = double(ns) + double(nc);
+  } else {
+    for (int k = threadIdx.x; k < len; k += LB_THREADS) {
+      double v = double(w[k0 + k]);
+      const TV* vp = V + k0 + k;
 #pragma unroll 4
-    for (int i = 0; i < m; ++i) v -= hs[i] * double(__ldg(vp + i * ldv));
-    const TV vs = TV(v);
-    w[k0 + k] = vs;
-    nrm += double(vs) * double(vs);
+      for (int i = 0; i < m; ++i) v -= hs[i] * double(__ldg(vp + i * ldv));
+      const TV vs = TV(v);
+      w[k0 + k] = vs;
+      nrm += double(vs) * double(vs);
+    }
   }
   nrm = warp_sum(nrm);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
@@ -1370,16 +1451,27 @@ __global__ void __launch_bounds__(KRY_THREADS) multidot_b_kernel(const TV* __res
                                                                  const TV* __restrict__ w, int with_ww,
                                                                  BatchChunks C, const int* __restrict__ active,
                                                                  double* __restrict__ partial) {
-  __shared__ double ws[KRY_CHUNK];
   const int inst = C.inst[blockIdx.x];
   if (!active[inst]) return;
   const int64_t k0 = C.k0[blockIdx.x];
   const int len = C.len[blockIdx.x];
-  for (int k = threadIdx.x; k < len; k += KRY_THREADS) ws[k] = double(w[k0 + k]);
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mt = m + (with_ww ? 1 : 0);
   const bool pairs = ((ldv & 1) == 0) && ((k0 & 1) == 0);  // V_i + k0 stays 2-element aligned
+  if constexpr (sizeof(TV) == 4) {
+    __shared__ float wsf[KRY_CHUNK];
+    for (int k = threadIdx.x; k < len; k += KRY_THREADS) wsf[k] = w[k0 + k];
+    __syncthreads();
+    for (int i = warp; i < mt; i += KRY_THREADS / 32) {
+      double acc = i < m ? dot_chunk_df(V + i * ldv + k0, wsf, len, lane, pairs) : dot_self_df(wsf, len, lane);
+      acc = warp_sum(acc);
+      if (lane == 0) partial[(size_t)i * C.nchunks + blockIdx.x] = acc;
+    }
+    return;
+  }
+  __shared__ double ws[KRY_CHUNK];
+  for (int k = threadIdx.x; k < len; k += KRY_THREADS) ws[k] = double(w[k0 + k]);
+  __syncthreads();
   for (int i = warp; i < mt; i += KRY_THREADS / 32) {
     double acc;
     if (i < m) {
@@ -1422,14 +1514,30 @@ __global__ void __launch_bounds__(KRY_THREADS) update_b_kernel(const TV* __restr
   const int64_t k0 = C.k0[blockIdx.x];
   const int len = C.len[blockIdx.x];
   double nrm = 0.0;
-  for (int k = threadIdx.x; k < len; k += KRY_THREADS) {
-    double v = double(w[k0 + k]);
-    const TV* vp = V + k0 + k;
+  if constexpr (sizeof(TV) == 4) {
+    __shared__ float hh[KRY_MAXV], hl[KRY_MAXV];
+    if (threadIdx.x < m) {
+      hh[threadIdx.x] = float(hs[threadIdx.x]);
+      hl[threadIdx.x] = float(hs[threadIdx.x] - double(float(hs[threadIdx.x])));
+    }
+    __syncthreads();
+    float ns = 0.0f, nc = 0.0f;
+    for (int k = threadIdx.x; k < len; k += KRY_THREADS) {
+      const float vs = update_df(w[k0 + k], V + k0 + k, ldv, m, hh, hl);
+      w[k0 + k] = vs;
+      df_fma(ns, nc, vs, vs);
+    }
+    nrm = double(ns) + double(nc);
+  } else {
+    for (int k = threadIdx.x; k < len; k += KRY_THREADS) {
+      double v = double(w[k0 + k]);
+      const TV* vp = V + k0 + k;
 #pragma unroll 4
-    for (int i = 0; i < m; ++i) v -= hs[i] * double(__ldg(vp + i * ldv));
-    const TV vs = TV(v);
-    w[k0 + k] = vs;
-    nrm += double(vs) * double(vs);
+      for (int i = 0; i < m; ++i) v -= hs[i] * double(__ldg(vp + i * ldv));
+      const TV vs = TV(v);
+      w[k0 + k] = vs;
+      nrm += double(vs) * double(vs);
+    }
   }
   nrm = warp_sum(nrm);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
