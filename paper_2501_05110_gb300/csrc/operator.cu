@@ -1467,21 +1467,21 @@ __global__ void __launch_bounds__(KRY_THREADS) multidot_b_kernel(const TV* __res
       acc = warp_sum(acc);
       if (lane == 0) partial[(size_t)i * C.nchunks + blockIdx.x] = acc;
     }
-    return;
-  }
-  __shared__ double ws[KRY_CHUNK];
-  for (int k = threadIdx.x; k < len; k += KRY_THREADS) ws[k] = double(w[k0 + k]);
-  __syncthreads();
-  for (int i = warp; i < mt; i += KRY_THREADS / 32) {
-    double acc;
-    if (i < m) {
-      acc = dot_chunk<TV>(V + i * ldv + k0, ws, len, lane, pairs);
-    } else {
-      acc = 0.0;
-      for (int k = lane; k < len; k += 32) acc += ws[k] * ws[k];
+  } else {
+    __shared__ double ws[KRY_CHUNK];
+    for (int k = threadIdx.x; k < len; k += KRY_THREADS) ws[k] = double(w[k0 + k]);
+    __syncthreads();
+    for (int i = warp; i < mt; i += KRY_THREADS / 32) {
+      double acc;
+      if (i < m) {
+        acc = dot_chunk<TV>(V + i * ldv + k0, ws, len, lane, pairs);
+      } else {
+        acc = 0.0;
+        for (int k = lane; k < len; k += 32) acc += ws[k] * ws[k];
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) partial[(size_t)i * C.nchunks + blockIdx.x] = acc;
     }
-    acc = warp_sum(acc);
-    if (lane == 0) partial[(size_t)i * C.nchunks + blockIdx.x] = acc;
   }
 }
 
