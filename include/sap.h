@@ -152,7 +152,9 @@ sap_status sap_step_erk(sap_handle h, double* state, double dt, int nsteps, sap_
  * (1 + dt/2 M^-1 D) zeta^n = (1 - dt/2 M^-1 D) zeta^(n-1) + dt M^-1 h, each solved by restarted
  * GMRES(restart) with point-Jacobi preconditioning to ||b - A zeta|| <= tol ||b|| (2-norm,
  * canonical nodal vector), at most maxit iterations per step.  With SAP_PREC_FP32 the inner GMRES
- * applies the operator in FP32 and an FP64 residual/refinement loop restores the tolerance.
+ * applies the operator in FP32 to FP32 Krylov vectors, orthogonalised with FP64-class accuracy
+ * (exact FP32 products and compensated sums, ~2^-48 relative), and an FP64 residual/refinement loop
+ * restores the tolerance.
  * Synchronous (reads the convergence status each restart).  `stats` may be NULL.
  * Errors: SAP_EINVAL, SAP_ENOCONV (state holds the last iterate), SAP_ECUDA. */
 sap_status sap_step_cn(sap_handle h, double* state, double dt, int nsteps, double tol, int restart,
