@@ -33,7 +33,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e-3  # SMs x DFMA/clk/SM x 2 flop x max GH
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3  # SMs x FFMA/clk/SM x 2 flop x max GHz = 80.5 TFLOP/s (FP32)
 # DRAM bytes (read + write) per apply launch from the ncu capture in profiles/rows_kernel_fp64_shock.md,
 # valid only for the kernel source it was taken on (first 16 hex of sha256 of csrc/apply_rows.cu)
-APPLY_TRAFFIC = {"56e6d9ca3804deab": 11001600.0}
+APPLY_TRAFFIC = {"29ab0aa921f8c3aa": 11002112.0}
 
 
 def parse():
