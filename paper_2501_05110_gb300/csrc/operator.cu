@@ -34,6 +34,12 @@ static thread_local int64_t g_launches = 0;
 int64_t launch_count() { return g_launches; }
 void note_launch() { ++g_launches; }
 
+void cn_graphs_release(sap_ctx* c) {
+  for (auto& gg : c->cn_graphs)
+    if (gg.exec) cudaGraphExecDestroy(gg.exec);
+  c->cn_graphs.clear();
+}
+
 template <typename T>
 __device__ __forceinline__ T csr_row(const Bank<T>& B, int mat, int r, const T* x, int stride) {
   if (mat == MAT_I) return x[r * stride];
@@ -1274,6 +1280,64 @@ static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, d
     cudaMemcpyAsync(Gh->misc, G->misc, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
     return cudaStreamSynchronize(s);
   };
+  // Arnoldi iterations j0 .. j0+cnt-1 (apply, Gram--Schmidt with selective second pass,
+  // normalisation; launches after convergence return at once) and the copy of the flags to the host
+  auto enqueue_group = [&](cudaStream_t cs, int j0, int cnt) -> cudaError_t {
+    for (int j = j0; j < j0 + cnt; ++j) {
+      TV* w = V + (size_t)(j + 1) * N;
+      Epi<TV> e{};
+      e.out = w; e.ax = TV(1); e.bl = TV(half); e.jacobi = 1; e.cj = TV(half); e.skip = &G->done;
+      e.axpost = TV(-1);
+      cudaError_t e1 = launch_apply<TV>(PV, V + (size_t)j * N, e, cs);
+      if (e1 != cudaSuccess) return e1;
+      multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j + 1, w, N, 1, partial, nchunks,
+                                                              &G->counter, G->h1, &G->done, nullptr);
+      update_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j, w, N, partial, nchunks, G, 1);
+      multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j + 1, w, N, 0, partial, nchunks,
+                                                              &G->counter, G->h2, &G->done, &G->reorth);
+      update_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j, w, N, partial, nchunks, G, 2);
+      scale_dev_kernel<TV><<<1024, KRY_THREADS, 0, cs>>>(w, w, &G->inv_norm, N, &G->done);
+      g_launches += 5;
+    }
+    cudaMemcpyAsync(&Gh->done, &G->done, sizeof(int) * 4, cudaMemcpyDeviceToHost, cs);
+    return cudaGetLastError();
+  };
+  // The group's launches as a CUDA graph (one launch instead of 6 per iteration), captured once on a
+  // private stream for this dt, field set and workspace; nullptr (direct launches) if capture fails.
+  auto group_graph = [&](int j0, int cnt) -> cudaGraphExec_t {
+    const void* ws = static_cast<const void*>(V);
+    if (!c->cn_graphs.empty()) {
+      const auto& g0 = c->cn_graphs.front();
+      if (g0.dt != dt || g0.fields_version != c->fields_version || g0.ws != ws) cn_graphs_release(c);
+    }
+    for (const auto& gg : c->cn_graphs)
+      if (gg.j0 == j0 && gg.cnt == cnt) return gg.exec;
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      c->cap_stream = nullptr;
+      cudaGetLastError();
+      return nullptr;
+    }
+    const int64_t l0 = g_launches;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    const cudaError_t e1 = enqueue_group(c->cap_stream, j0, cnt);
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+    g_launches = l0;
+    cudaGraphExec_t ex = nullptr;
+    if (e1 != cudaSuccess || e2 != cudaSuccess || !graph || cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return nullptr;
+    }
+    cudaGraphDestroy(graph);
+    sap_ctx::CnGraph gg;
+    gg.exec = ex; gg.j0 = j0; gg.cnt = cnt; gg.fields_version = c->fields_version; gg.dt = dt; gg.ws = ws;
+    c->cn_graphs.push_back(gg);
+    return ex;
+  };
 #define CK(x)                               \
   do {                                      \
     err = (x);                              \
@@ -1336,27 +1400,17 @@ static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, d
       ++g_launches;
       const int mm = Gh->m;
       int jd = 0;
-      for (int j = 0; j < mm; ++j) {
-        TV* w = V + (size_t)(j + 1) * N;
-        {
-          Epi<TV> e{};
-          e.out = w; e.ax = TV(1); e.bl = TV(half); e.jacobi = 1; e.cj = TV(half); e.skip = &G->done;
-          e.axpost = TV(-1);
-          CK(launch_apply<TV>(PV, V + (size_t)j * N, e, s));
+      for (int j0 = 0; j0 < mm; j0 += group) {
+        const int cnt = std::min(group, mm - j0);
+        cudaGraphExec_t ex = group_graph(j0, cnt);
+        if (ex) {
+          CK(cudaGraphLaunch(ex, s));
+          g_launches += 6 * cnt;
+        } else {
+          CK(enqueue_group(s, j0, cnt));
         }
-        multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, s>>>(V, N, j + 1, w, N, 1, partial, nchunks,
-                                                               &G->counter, G->h1, &G->done, nullptr);
-        update_lb_kernel<TV><<<nchunks, LB_THREADS, 0, s>>>(V, N, j, w, N, partial, nchunks, G, 1);
-        multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, s>>>(V, N, j + 1, w, N, 0, partial, nchunks,
-                                                               &G->counter, G->h2, &G->done, &G->reorth);
-        update_lb_kernel<TV><<<nchunks, LB_THREADS, 0, s>>>(V, N, j, w, N, partial, nchunks, G, 2);
-        scale_dev_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(w, w, &G->inv_norm, N, &G->done);
-        g_launches += 5;
-        if ((j + 1) % group == 0 || j + 1 == mm) {
-          CK(cudaMemcpyAsync(&Gh->done, &G->done, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
-          CK(cudaStreamSynchronize(s));
-          if (Gh->done) break;
-        }
+        CK(cudaStreamSynchronize(s));
+        if (Gh->done) break;
       }
       jd = Gh->jdone;
       // y = H^-1 g on the host, zeta += V y

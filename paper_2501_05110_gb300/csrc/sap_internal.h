@@ -197,6 +197,16 @@ struct sap_ctx {
   int* d_active = nullptr;                     // [ninst] device activity mask
   std::vector<int> h_active;
   sap_ctx* parent = nullptr;                   // set on the sub-contexts of a batch
+  // CUDA graphs of the GMRES iteration groups of sap_step_cn, replayed while the configuration they
+  // were captured for (dt, fields, workspace, group) holds
+  struct CnGraph {
+    cudaGraphExec_t exec = nullptr;
+    int j0 = -1, cnt = 0, fields_version = -1;
+    double dt = 0.0;
+    const void* ws = nullptr;
+  };
+  std::vector<CnGraph> cn_graphs;
+  cudaStream_t cap_stream = nullptr;           // private stream for the captures
 };
 
 namespace sap {
@@ -228,6 +238,7 @@ sap_status batch_cn(sap_ctx* c, double* state, double dt, int nsteps, double tol
                     sap_solver_stats* st, cudaStream_t s);
 sap_status batch_erk(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s);
 int64_t launch_count();
+void cn_graphs_release(sap_ctx* c);  // destroys the cached CN graphs and the capture stream
 int64_t krylov_scratch_doubles(int64_t N);
 size_t gmres_control_bytes();
 int64_t krylov_batch_scratch_doubles(const std::vector<int64_t>& Ns);

@@ -1100,6 +1100,8 @@ extern "C" sap_status sap_destroy(sap_handle c) {
   if (c->small_host) cudaFreeHost(c->small_host);
   if (c->gdev) cudaFree(c->gdev);
   if (c->gdev_host) cudaFreeHost(c->gdev_host);
+  cn_graphs_release(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return SAP_OK;
 }
