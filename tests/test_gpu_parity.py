@@ -132,6 +132,27 @@ def test_cn_tolerance_1e10(torch_cuda):
     assert err < 1e-8 and st.last_rel_residual <= 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cn_changing_dt_and_fields(torch_cuda, prec):
+    """CN calls with changing dt, and after new fields, match the oracle's LU CN run with the same
+    sequence: the iteration groups that the library replays from cached CUDA graphs are rebuilt
+    whenever dt or the fields change."""
+    prob = W.shock(nx=15, npc=7, lmax=3)
+    prob2 = W.shock(nx=15, npc=7, lmax=3, nu0=2.0)
+    sol = _solver(prob, prec)
+    y = sol.initial_state()
+    z = np.zeros(sol.N)
+    for dt, nsteps in [(1.0, 3), (0.5, 3), (1.0, 2)]:
+        sol.step_cn(y, dt, nsteps, tol=1e-13, restart=30, maxit=4000)
+        z = NodalOracle(prob).cn(z, dt, nsteps)
+    sol.set_fields(prob2)
+    sol.step_cn(y, 1.0, 3, tol=1e-13, restart=30, maxit=4000)
+    torch_cuda.cuda.synchronize()
+    want = NodalOracle(prob2).cn(z, 1.0, 3)
+    err = np.linalg.norm(y.cpu().numpy() - want) / np.linalg.norm(want)
+    assert err < (1e-11 if prec == "fp64" else 1e-8), err
+
+
 # ------------------------------------------------------------------------------------------------
 # precision form: FP32 operator apply (FP64 state in RK4)
 # ------------------------------------------------------------------------------------------------
