@@ -546,6 +546,7 @@ __device__ __forceinline__ void applyT_body(const OpParams<T>& P, const T* __res
     E.outj[dof] = o * jacobi_scale(E.cj, rdiag);
   }
   if (E.jacobi) o *= jacobi_scale(E.cj, rdiag);
+  if (E.axpost != T(0)) o += E.axpost * F[t];
   if (E.out) E.out[dof] = o;
 }
 
@@ -781,7 +782,7 @@ sap_status erk_steps(sap_ctx* c, double* state, double dt, int nsteps, cudaStrea
 }
 
 // ------------------------------------------------------------------------------------------------
-// Krylov kernels (FP64): multi-dot, update, norms
+// Krylov kernels: multi-dot, update, norms (FP64 sums)
 // ------------------------------------------------------------------------------------------------
 constexpr int KRY_THREADS = 256;
 constexpr int KRY_MAXV = 32;
@@ -791,83 +792,8 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Dot products of w with V_0..V_{m-1} (V_i = V + i*ldv) and, if `with_ww`, of w with itself.
-// Block b handles the chunk [b*KRY_CHUNK, (b+1)*KRY_CHUNK): it stages w in shared memory once, then
-// warp v sums V_i . w for i = v, v+8, ... ; partial[i][b] = the chunk's value (fixed order).
+// The Krylov kernels work on chunks of KRY_CHUNK entries, one thread block per chunk.
 constexpr int KRY_CHUNK = 2048;
-template <typename TV>
-__global__ void __launch_bounds__(KRY_THREADS) multidot_kernel(const TV* __restrict__ V, int64_t ldv, int m,
-                                                               const TV* __restrict__ w, int64_t N, int with_ww,
-                                                               double* __restrict__ partial, int nchunks) {
-  __shared__ double ws[KRY_CHUNK];
-  const int64_t k0 = (int64_t)blockIdx.x * KRY_CHUNK;
-  const int len = (int)((N - k0) < KRY_CHUNK ? (N - k0) : KRY_CHUNK);
-  for (int k = threadIdx.x; k < len; k += KRY_THREADS) ws[k] = double(w[k0 + k]);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int mt = m + (with_ww ? 1 : 0);
-  for (int i = warp; i < mt; i += KRY_THREADS / 32) {
-    const TV* a = (i < m) ? V + i * ldv + k0 : nullptr;
-    double acc = 0.0;
-    if (a) {
-      for (int k = lane; k < len; k += 32) acc += double(__ldg(a + k)) * ws[k];
-    } else {
-      for (int k = lane; k < len; k += 32) acc += ws[k] * ws[k];
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) partial[(size_t)i * nchunks + blockIdx.x] = acc;
-  }
-}
-
-// out[i] = sum_c partial[i][c], i < m: warp i strides over the chunks, then a fixed-order shuffle
-// reduction (deterministic for a given N).
-__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nchunks, int m, double* __restrict__ out) {
-  const int lane = threadIdx.x & 31, i = threadIdx.x >> 5;
-  if (i >= m) return;
-  double v = 0.0;
-  for (int c = lane; c < nchunks; c += 32) v += partial[(size_t)i * nchunks + c];
-  v = warp_sum(v);
-  if (lane == 0) out[i] = v;
-}
-
-// w -= sum_i h[i] V_i (FP64 arithmetic) ; partial[b] = this block's sum of the updated w^2
-template <typename TV>
-__global__ void __launch_bounds__(KRY_THREADS) update_kernel(const TV* __restrict__ V, int64_t ldv, int m,
-                                                             const double* __restrict__ h, TV* __restrict__ w,
-                                                             int64_t N, double* __restrict__ partial, int nchunks) {
-  __shared__ double hs[KRY_MAXV];
-  __shared__ double red[KRY_THREADS / 32];
-  if (threadIdx.x < m) hs[threadIdx.x] = h[threadIdx.x];
-  __syncthreads();
-  const int64_t k0 = (int64_t)blockIdx.x * KRY_CHUNK;
-  const int64_t k1 = (k0 + KRY_CHUNK < N) ? k0 + KRY_CHUNK : N;
-  double nrm = 0.0;
-  for (int64_t k = k0 + threadIdx.x; k < k1; k += KRY_THREADS) {
-    double v = double(w[k]);
-    for (int i = 0; i < m; ++i) v -= hs[i] * double(__ldg(V + i * ldv + k));
-    const TV vs = TV(v);
-    w[k] = vs;
-    nrm += double(vs) * double(vs);
-  }
-  nrm = warp_sum(nrm);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < KRY_THREADS / 32; ++q) t += red[q];
-    partial[blockIdx.x] = t;
-  }
-  (void)nchunks;
-}
-
-// y = a*x with a = 1/a_dev[0] (invert = 1), 1/sqrt(a_dev[0]) (invert = 2) or a_dev[0]
-template <typename TV>
-__global__ void scale_kernel(const TV* __restrict__ x, TV* __restrict__ y, const double* __restrict__ a_dev,
-                             int invert, int64_t N) {
-  const double a = invert == 1 ? 1.0 / a_dev[0] : (invert == 2 ? 1.0 / sqrt(a_dev[0]) : a_dev[0]);
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-    y[k] = TV(a * double(x[k]));
-}
 
 // x (FP64) += sum_i y[i] V_i
 template <typename TV>
@@ -889,40 +815,6 @@ __global__ void combine_kernel(const TV* __restrict__ V, int64_t ldv, int m, con
 // Crank--Nicolson step, restarted GMRES with left point-Jacobi preconditioning (FP64)
 // ------------------------------------------------------------------------------------------------
 namespace sap {
-
-struct KrylovCtx {
-  sap_ctx* c;
-  cudaStream_t s;
-  int nchunks;
-  double* partial;   // [KRY_MAXV + 1][nchunks]
-  double* dsc;       // device scalars [8 * KRY_MAXV]
-  double* hsc;       // pinned host mirror [8 * KRY_MAXV]
-};
-
-// dsc_out[i] = V_i . w for i < m, and dsc_out[m] = w . w if with_ww
-template <typename TV>
-static void dots(KrylovCtx& K, const TV* V, int m, const TV* w, int with_ww, double* dsc_out) {
-  const int64_t N = K.c->N;
-  multidot_kernel<TV><<<K.nchunks, KRY_THREADS, 0, K.s>>>(V, N, m, w, N, with_ww, K.partial, K.nchunks);
-  ++g_launches;
-  reduce_partials_kernel<<<1, 32 * (m + with_ww), 0, K.s>>>(K.partial, K.nchunks, m + with_ww, dsc_out);
-  ++g_launches;
-}
-
-// w -= V h (m vectors), then dsc_out[0] = |w|^2
-template <typename TV>
-static void update(KrylovCtx& K, const TV* V, int m, const double* h, TV* w, double* dsc_out) {
-  const int64_t N = K.c->N;
-  update_kernel<TV><<<K.nchunks, KRY_THREADS, 0, K.s>>>(V, N, m, h, w, N, K.partial, K.nchunks);
-  ++g_launches;
-  reduce_partials_kernel<<<1, 32, 0, K.s>>>(K.partial, K.nchunks, 1, dsc_out);
-  ++g_launches;
-}
-
-static cudaError_t fetch(KrylovCtx& K, int first, int count) {
-  cudaMemcpyAsync(K.hsc + first, K.dsc + first, sizeof(double) * count, cudaMemcpyDeviceToHost, K.s);
-  return cudaStreamSynchronize(K.s);
-}
 
 int64_t krylov_scratch_doubles(int64_t N) {
   const int64_t nchunks = (N + KRY_CHUNK - 1) / KRY_CHUNK;
@@ -1212,9 +1104,9 @@ __global__ void __launch_bounds__(LB_THREADS) update_lb_kernel(const TV* __restr
   }
 }
 
-// y = x * (*s)
+// y = x * (*s); called in place (y == x), so x and y are not restrict-qualified
 template <typename TV>
-__global__ void scale_dev_kernel(const TV* __restrict__ x, TV* __restrict__ y, const double* s, int64_t N,
+__global__ void scale_dev_kernel(const TV* x, TV* y, const double* s, int64_t N,
                                  const int* done) {
   if (done && *done) return;
   const double a = *s;
@@ -1233,10 +1125,164 @@ __global__ void extrapolate_kernel(double* __restrict__ x, double* __restrict__ 
   }
 }
 
+// G->misc[slot] = |v|^2 (one launch; its last block finishes the sum)
+template <typename TV>
+static void norm2_dev(sap_ctx* c, const TV* v, int slot, cudaStream_t s) {
+  const int64_t N = c->N;
+  const int nchunks = (int)((N + KRY_CHUNK - 1) / KRY_CHUNK);
+  GmresDev* G = reinterpret_cast<GmresDev*>(c->gdev);
+  multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, s>>>(nullptr, N, 0, v, N, 1, c->small, nchunks, &G->counter,
+                                                         &G->misc[slot], nullptr, nullptr);
+  ++g_launches;
+}
+
+static cudaError_t fetch_misc(sap_ctx* c, cudaStream_t s) {
+  GmresDev* G = reinterpret_cast<GmresDev*>(c->gdev);
+  GmresDev* Gh = reinterpret_cast<GmresDev*>(c->gdev_host);
+  cudaMemcpyAsync(Gh->misc, G->misc, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
+  return cudaStreamSynchronize(s);
+}
+
+// Arnoldi iterations j0 .. j0+cnt-1 of the device-controlled GMRES on P^-1 A - 1 (TRANS: on
+// P^-1 A^T - 1), A = 1 + dt/2 L, P its point-Jacobi diagonal (also that of A^T): apply,
+// Gram--Schmidt with selective second pass, normalisation; launches after convergence return at
+// once.  The group ends with the copy of the flags to the host.
+template <typename TV, bool TRANS>
+static cudaError_t enqueue_arnoldi(sap_ctx* c, const OpParams<TV>& PV, TV* V, double half, int j0, int cnt,
+                                   cudaStream_t cs) {
+  const int64_t N = c->N;
+  const int nchunks = (int)((N + KRY_CHUNK - 1) / KRY_CHUNK);
+  double* partial = c->small;
+  GmresDev* G = reinterpret_cast<GmresDev*>(c->gdev);
+  GmresDev* Gh = reinterpret_cast<GmresDev*>(c->gdev_host);
+  for (int j = j0; j < j0 + cnt; ++j) {
+    TV* w = V + (size_t)(j + 1) * N;
+    Epi<TV> e{};
+    e.out = w; e.ax = TV(1); e.bl = TV(half); e.jacobi = 1; e.cj = TV(half); e.skip = &G->done;
+    e.axpost = TV(-1);
+    cudaError_t e1;
+    if constexpr (TRANS) e1 = launch_applyT<TV>(PV, V + (size_t)j * N, e, cs);
+    else e1 = launch_apply<TV>(PV, V + (size_t)j * N, e, cs);
+    if (e1 != cudaSuccess) return e1;
+    multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j + 1, w, N, 1, partial, nchunks,
+                                                            &G->counter, G->h1, &G->done, nullptr);
+    update_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j, w, N, partial, nchunks, G, 1);
+    multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j + 1, w, N, 0, partial, nchunks,
+                                                            &G->counter, G->h2, &G->done, &G->reorth);
+    update_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j, w, N, partial, nchunks, G, 2);
+    scale_dev_kernel<TV><<<1024, KRY_THREADS, 0, cs>>>(w, w, &G->inv_norm, N, &G->done);
+    g_launches += 5;
+  }
+  cudaMemcpyAsync(&Gh->done, &G->done, sizeof(int) * 4, cudaMemcpyDeviceToHost, cs);
+  return cudaGetLastError();
+}
+
+// A group's launches as a CUDA graph (one launch instead of 6 per iteration), captured once on a
+// private stream for this operator (forward or transposed), dt, field set and workspace; nullptr
+// (direct launches) if capture fails.
+template <typename TV, bool TRANS>
+static cudaGraphExec_t arnoldi_graph(sap_ctx* c, const OpParams<TV>& PV, TV* V, double dt, int j0, int cnt) {
+  const int kind = TRANS ? 1 : 0;
+  const void* ws = static_cast<const void*>(V);
+  if (!c->cn_graphs.empty()) {
+    const auto& g0 = c->cn_graphs.front();
+    if (g0.dt != dt || g0.fields_version != c->fields_version || g0.ws != ws) cn_graphs_release(c);
+  }
+  for (const auto& gg : c->cn_graphs)
+    if (gg.kind == kind && gg.j0 == j0 && gg.cnt == cnt) return gg.exec;
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    c->cap_stream = nullptr;
+    cudaGetLastError();
+    return nullptr;
+  }
+  const int64_t l0 = g_launches;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const cudaError_t e1 = enqueue_arnoldi<TV, TRANS>(c, PV, V, 0.5 * dt, j0, cnt, c->cap_stream);
+  const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+  g_launches = l0;
+  cudaGraphExec_t ex = nullptr;
+  if (e1 != cudaSuccess || e2 != cudaSuccess || !graph || cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraphDestroy(graph);
+  sap_ctx::CnGraph gg;
+  gg.exec = ex; gg.kind = kind; gg.j0 = j0; gg.cnt = cnt; gg.fields_version = c->fields_version; gg.dt = dt;
+  gg.ws = ws;
+  c->cn_graphs.push_back(gg);
+  return ex;
+}
+
+// One restart cycle of the device-controlled GMRES, from V_0 = P^-1 r of norm beta (not yet
+// normalised): groups of Arnoldi iterations until the device flags convergence (|g_{j+1}| <= target)
+// or the cycle length mlen, then y = R^-1 g by back substitution on the host and x += V y.
+// *jd = the cycle's iterations.
+template <typename TV, bool TRANS>
+static cudaError_t gmres_cycle(sap_ctx* c, const OpParams<TV>& PV, TV* V, double dt, double beta, double target,
+                               int mlen, double* x, cudaStream_t s, int* jd) {
+  const int64_t N = c->N;
+  GmresDev* G = reinterpret_cast<GmresDev*>(c->gdev);
+  GmresDev* Gh = reinterpret_cast<GmresDev*>(c->gdev_host);
+  const int group = 6;  // iterations enqueued between host checks
+  cudaError_t err = cudaSuccess;
+  *jd = 0;
+  Gh->g[0] = beta;
+  Gh->beta = beta;
+  Gh->inv_norm = 1.0 / beta;
+  Gh->target = target;
+  Gh->done = 0;
+  Gh->reorth = 0;
+  Gh->jdone = 0;
+  Gh->m = mlen;
+  if ((err = cudaMemcpyAsync(&G->g[0], &Gh->g[0], sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return err;
+  if ((err = cudaMemcpyAsync(&G->inv_norm, &Gh->inv_norm, sizeof(double) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return err;
+  if ((err = cudaMemcpyAsync(&G->done, &Gh->done, sizeof(int) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return err;
+  scale_dev_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(V, V, &G->inv_norm, N, nullptr);
+  ++g_launches;
+  for (int j0 = 0; j0 < mlen; j0 += group) {
+    const int cnt = std::min(group, mlen - j0);
+    cudaGraphExec_t ex = arnoldi_graph<TV, TRANS>(c, PV, V, dt, j0, cnt);
+    if (ex) {
+      err = cudaGraphLaunch(ex, s);
+      g_launches += 6 * cnt;
+    } else {
+      err = enqueue_arnoldi<TV, TRANS>(c, PV, V, 0.5 * dt, j0, cnt, s);
+    }
+    if (err != cudaSuccess) return err;
+    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
+    if (Gh->done) break;
+  }
+  const int jdone = Gh->jdone;
+  cudaMemcpyAsync(Gh->H, G->H, sizeof(double) * KRY_MAXV * (KRY_MAXV + 1), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(Gh->g, G->g, sizeof(double) * (KRY_MAXV + 1), cudaMemcpyDeviceToHost, s);
+  if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
+  double y[KRY_MAXV];
+  for (int i2 = jdone - 1; i2 >= 0; --i2) {
+    double v = Gh->g[i2];
+    for (int k2 = i2 + 1; k2 < jdone; ++k2) v -= Gh->H[i2 * KRY_MAXV + k2] * y[k2];
+    y[i2] = v / Gh->H[i2 * KRY_MAXV + i2];
+  }
+  for (int i2 = 0; i2 < jdone; ++i2) Gh->h2[i2] = y[i2];
+  if ((err = cudaMemcpyAsync(G->h2, Gh->h2, sizeof(double) * jdone, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return err;
+  combine_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, G->h2, x, N);
+  ++g_launches;
+  *jd = jdone;
+  return cudaGetLastError();
+}
+
 // TV = double: FP64 operator and Krylov vectors (the plain path).  TV = float: precision form: the
-// Arnoldi process applies the FP32 operator to FP32 vectors (FP64 accumulation in dots and updates)
-// inside the FP64 residual / refinement loop, each cycle asking for no more than the FP32 operator
-// can deliver (1e-6).
+// Arnoldi process applies the FP32 operator to FP32 vectors (double-float accumulation in dots and
+// updates) inside the FP64 residual / refinement loop, each cycle asking for no more than the FP32
+// operator can deliver (1e-6).
 template <typename TV>
 static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
                              sap_solver_stats* st, cudaStream_t s) {
@@ -1248,95 +1294,18 @@ static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, d
   double* tmp = b + N;
   double* prev = c->ws64 + (size_t)(c->ws64_count - 1) * N;  // state before the last step
   const OpParams<TV>& PV = *reinterpret_cast<const OpParams<TV>*>(f64 ? (const void*)&c->p64 : (const void*)&c->p32);
-  const int nchunks = (int)((N + KRY_CHUNK - 1) / KRY_CHUNK);
-  double* partial = c->small;
-  GmresDev* G = reinterpret_cast<GmresDev*>(c->gdev);
   GmresDev* Gh = reinterpret_cast<GmresDev*>(c->gdev_host);
   const OpParams<double>& P = c->p64;
   const double half = 0.5 * dt;
-  const int group = 6;                       // iterations enqueued between host checks
   int64_t total_its = 0;
   const int64_t launches0 = g_launches;
   int max_its = 0;
   double last_rel = 0.0;
   cudaError_t err = cudaSuccess;
-  std::vector<double> y(m);
-  auto norm2 = [&](const double* v, int slot) {  // G->misc[slot] = |v|^2
-    multidot_lb_kernel<double><<<nchunks, LB_THREADS, 0, s>>>(nullptr, N, 0, v, N, 1, partial, nchunks, &G->counter,
-                                                               &G->misc[slot], nullptr, nullptr);
-    ++g_launches;
-  };
-  auto norm2v = [&](const TV* v, int slot) {
-    multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, s>>>(nullptr, N, 0, v, N, 1, partial, nchunks, &G->counter,
-                                                           &G->misc[slot], nullptr, nullptr);
-    ++g_launches;
-  };
   auto jcopy = [&](Epi<double>& e) {  // Jacobi-scaled copy of the residual into V_0
     if constexpr (f64) e.outj = reinterpret_cast<double*>(V);
     else e.out32 = reinterpret_cast<float*>(V);
     e.cj = half;
-  };
-  auto fetch_misc = [&]() -> cudaError_t {
-    cudaMemcpyAsync(Gh->misc, G->misc, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
-    return cudaStreamSynchronize(s);
-  };
-  // Arnoldi iterations j0 .. j0+cnt-1 (apply, Gram--Schmidt with selective second pass,
-  // normalisation; launches after convergence return at once) and the copy of the flags to the host
-  auto enqueue_group = [&](cudaStream_t cs, int j0, int cnt) -> cudaError_t {
-    for (int j = j0; j < j0 + cnt; ++j) {
-      TV* w = V + (size_t)(j + 1) * N;
-      Epi<TV> e{};
-      e.out = w; e.ax = TV(1); e.bl = TV(half); e.jacobi = 1; e.cj = TV(half); e.skip = &G->done;
-      e.axpost = TV(-1);
-      cudaError_t e1 = launch_apply<TV>(PV, V + (size_t)j * N, e, cs);
-      if (e1 != cudaSuccess) return e1;
-      multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j + 1, w, N, 1, partial, nchunks,
-                                                              &G->counter, G->h1, &G->done, nullptr);
-      update_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j, w, N, partial, nchunks, G, 1);
-      multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j + 1, w, N, 0, partial, nchunks,
-                                                              &G->counter, G->h2, &G->done, &G->reorth);
-      update_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j, w, N, partial, nchunks, G, 2);
-      scale_dev_kernel<TV><<<1024, KRY_THREADS, 0, cs>>>(w, w, &G->inv_norm, N, &G->done);
-      g_launches += 5;
-    }
-    cudaMemcpyAsync(&Gh->done, &G->done, sizeof(int) * 4, cudaMemcpyDeviceToHost, cs);
-    return cudaGetLastError();
-  };
-  // The group's launches as a CUDA graph (one launch instead of 6 per iteration), captured once on a
-  // private stream for this dt, field set and workspace; nullptr (direct launches) if capture fails.
-  auto group_graph = [&](int j0, int cnt) -> cudaGraphExec_t {
-    const void* ws = static_cast<const void*>(V);
-    if (!c->cn_graphs.empty()) {
-      const auto& g0 = c->cn_graphs.front();
-      if (g0.dt != dt || g0.fields_version != c->fields_version || g0.ws != ws) cn_graphs_release(c);
-    }
-    for (const auto& gg : c->cn_graphs)
-      if (gg.j0 == j0 && gg.cnt == cnt) return gg.exec;
-    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-      c->cap_stream = nullptr;
-      cudaGetLastError();
-      return nullptr;
-    }
-    const int64_t l0 = g_launches;
-    cudaGraph_t graph = nullptr;
-    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    const cudaError_t e1 = enqueue_group(c->cap_stream, j0, cnt);
-    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
-    g_launches = l0;
-    cudaGraphExec_t ex = nullptr;
-    if (e1 != cudaSuccess || e2 != cudaSuccess || !graph || cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      cudaGetLastError();
-      return nullptr;
-    }
-    cudaGraphDestroy(graph);
-    sap_ctx::CnGraph gg;
-    gg.exec = ex; gg.j0 = j0; gg.cnt = cnt; gg.fields_version = c->fields_version; gg.dt = dt; gg.ws = ws;
-    c->cn_graphs.push_back(gg);
-    return ex;
   };
 #define CK(x)                               \
   do {                                      \
@@ -1370,10 +1339,10 @@ static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, d
     c->cn_prev_valid = true;
     c->cn_prev_ptr = state;
     c->cn_prev_dt = dt;
-    norm2(b, 0);
-    norm2(tmp, 1);
-    norm2v(V, 2);
-    CK(fetch_misc());
+    norm2_dev<double>(c, b, 0, s);
+    norm2_dev<double>(c, tmp, 1, s);
+    norm2_dev<TV>(c, V, 2, s);
+    CK(fetch_misc(c, s));
     const double bnorm = std::sqrt(Gh->misc[0]);
     double rel = bnorm > 0 ? std::sqrt(Gh->misc[1]) / bnorm : 0.0;
     double beta = std::sqrt(Gh->misc[2]);
@@ -1384,48 +1353,9 @@ static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, d
     }
     if (!std::isfinite(bnorm)) rel = bnorm;  // reported as not converged below
     while (!(rel <= tol) && its < maxit && std::isfinite(rel)) {
-      // start a cycle: g = beta e_1, V_0 = P^-1 r / beta
-      Gh->g[0] = beta;
-      Gh->beta = beta;
-      Gh->inv_norm = 1.0 / beta;
-      Gh->target = f64 ? 0.5 * beta * (tol / rel) : beta * std::max(0.5 * tol / rel, 1e-6);
-      Gh->done = 0;
-      Gh->reorth = 0;
-      Gh->jdone = 0;
-      Gh->m = std::min(m, maxit - its);
-      CK(cudaMemcpyAsync(&G->g[0], &Gh->g[0], sizeof(double), cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(&G->inv_norm, &Gh->inv_norm, sizeof(double) * 4, cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(&G->done, &Gh->done, sizeof(int) * 4, cudaMemcpyHostToDevice, s));
-      scale_dev_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(V, V, &G->inv_norm, N, nullptr);
-      ++g_launches;
-      const int mm = Gh->m;
+      const double target = f64 ? 0.5 * beta * (tol / rel) : beta * std::max(0.5 * tol / rel, 1e-6);
       int jd = 0;
-      for (int j0 = 0; j0 < mm; j0 += group) {
-        const int cnt = std::min(group, mm - j0);
-        cudaGraphExec_t ex = group_graph(j0, cnt);
-        if (ex) {
-          CK(cudaGraphLaunch(ex, s));
-          g_launches += 6 * cnt;
-        } else {
-          CK(enqueue_group(s, j0, cnt));
-        }
-        CK(cudaStreamSynchronize(s));
-        if (Gh->done) break;
-      }
-      jd = Gh->jdone;
-      // y = H^-1 g on the host, zeta += V y
-      CK(cudaMemcpyAsync(Gh->H, G->H, sizeof(double) * KRY_MAXV * (KRY_MAXV + 1), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(Gh->g, G->g, sizeof(double) * (KRY_MAXV + 1), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      for (int i2 = jd - 1; i2 >= 0; --i2) {
-        double v = Gh->g[i2];
-        for (int k2 = i2 + 1; k2 < jd; ++k2) v -= Gh->H[i2 * KRY_MAXV + k2] * y[k2];
-        y[i2] = v / Gh->H[i2 * KRY_MAXV + i2];
-      }
-      for (int i2 = 0; i2 < jd; ++i2) Gh->h2[i2] = y[i2];
-      CK(cudaMemcpyAsync(G->h2, Gh->h2, sizeof(double) * jd, cudaMemcpyHostToDevice, s));
-      combine_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(V, N, jd, G->h2, state, N);
-      ++g_launches;
+      CK((gmres_cycle<TV, false>(c, PV, V, dt, beta, target, std::min(m, maxit - its), state, s, &jd)));
       its += jd;
       // true residual r = b - A zeta and its Jacobi-scaled copy (start of a further cycle)
       {
@@ -1434,9 +1364,9 @@ static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, d
         jcopy(e);
         CK(launch_apply<double>(P, state, e, s));
       }
-      norm2(tmp, 1);
-      norm2v(V, 2);
-      CK(fetch_misc());
+      norm2_dev<double>(c, tmp, 1, s);
+      norm2_dev<TV>(c, V, 2, s);
+      CK(fetch_misc(c, s));
       rel = std::sqrt(Gh->misc[1]) / bnorm;
       beta = std::sqrt(Gh->misc[2]);
       if (jd == 0) break;
@@ -1605,7 +1535,7 @@ __global__ void __launch_bounds__(KRY_THREADS) update_b_kernel(const TV* __restr
 
 // y = x / sqrt(a[inst*stride]) on the active instances
 template <typename TV>
-__global__ void scale_b_kernel(const TV* __restrict__ x, TV* __restrict__ y, const double* __restrict__ a, int stride,
+__global__ void scale_b_kernel(const TV* x, TV* y, const double* __restrict__ a, int stride,
                                BatchChunks C, const int* __restrict__ active) {
   const int inst = C.inst[blockIdx.x];
   if (!active[inst]) return;
@@ -2124,6 +2054,9 @@ __global__ void grad_nu_kernel(const double* __restrict__ mu, const double* __re
   }
 }
 
+// One reverse step: A^T mu = lambda (A = 1 + dt/2 L) by the device-controlled GMRES on P^-1 A^T from
+// the initial guess lambda, the same iteration groups (graph-replayed) as the forward solve; then
+// lambda <- B^T mu (B = 1 - dt/2 L) and the nu gradient of the collision term.
 sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, double* lambda, double dt, double tol,
                            int m, int maxit, double* mu_out, double* grad_nu, sap_solver_stats* st, cudaStream_t s) {
   const int64_t N = c->N;
@@ -2131,15 +2064,9 @@ sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, doubl
   double* b = V + (size_t)(m + 1) * N;       // right side (copy of lambda)
   double* tmp = b + N;
   double* mu = tmp + N;                      // solution
-  const int nchunks = (int)((N + KRY_CHUNK - 1) / KRY_CHUNK);
-  KrylovCtx K{c, s, nchunks, c->small, c->small + (size_t)(KRY_MAXV + 1) * nchunks, c->small_host};
-  double* const d_h1 = K.dsc;
-  double* const d_nrm = K.dsc + KRY_MAXV;
-  double* const d_h2 = K.dsc + 2 * KRY_MAXV;
-  double* const d_y = K.dsc + 3 * KRY_MAXV;
+  GmresDev* Gh = reinterpret_cast<GmresDev*>(c->gdev_host);
   const OpParams<double>& P = c->p64;
   const double half = 0.5 * dt;
-  std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), y(m);
   const int64_t launches0 = g_launches;
   int its = 0;
   double rel = 0.0;
@@ -2151,90 +2078,30 @@ sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, doubl
   } while (0)
   CK(cudaMemcpyAsync(b, lambda, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(mu, lambda, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));  // initial guess
+  norm2_dev<double>(c, b, 0, s);
+  CK(fetch_misc(c, s));
   {
-    dots<double>(K, nullptr, 0, b, 1, d_nrm);
-    CK(fetch(K, KRY_MAXV, 1));
-    const double bnorm = std::sqrt(K.hsc[KRY_MAXV]);
+    const double bnorm = std::sqrt(Gh->misc[0]);
     if (bnorm == 0.0) {
       CK(cudaMemsetAsync(mu, 0, sizeof(double) * N, s));
     } else {
       for (;;) {
-        {  // r = b - A^T mu
+        {  // r = b - A^T mu and its Jacobi-scaled copy in V_0
           Epi<double> e{};
-          e.out = tmp; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half;
+          e.out = tmp; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.outj = V; e.cj = half;
           CK(launch_applyT<double>(P, mu, e, s));
         }
-        dots<double>(K, nullptr, 0, tmp, 1, d_nrm);
-        CK(fetch(K, KRY_MAXV, 1));
-        rel = std::sqrt(K.hsc[KRY_MAXV]) / bnorm;
+        norm2_dev<double>(c, tmp, 1, s);
+        norm2_dev<double>(c, V, 2, s);
+        CK(fetch_misc(c, s));
+        rel = std::sqrt(Gh->misc[1]) / bnorm;
+        const double beta = std::sqrt(Gh->misc[2]);
         if (rel <= tol || its >= maxit || !std::isfinite(rel)) break;
-        {
-          Epi<double> e{};
-          e.out = V; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.jacobi = 1; e.cj = half;
-          CK(launch_applyT<double>(P, mu, e, s));
-        }
-        dots<double>(K, nullptr, 0, V, 1, d_nrm);
-        scale_kernel<double><<<1024, KRY_THREADS, 0, s>>>(V, V, d_nrm, 2, N);
-        ++g_launches;
-        CK(fetch(K, KRY_MAXV, 1));
-        const double beta = std::sqrt(K.hsc[KRY_MAXV]);
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        const double target = 0.5 * beta * (tol / rel);
-        int jdone = 0;
-        for (int j = 0; j < m && its < maxit; ++j) {
-          double* w = V + (size_t)(j + 1) * N;
-          {
-            Epi<double> e{};
-            e.out = w; e.ax = 1.0; e.bl = half; e.jacobi = 1; e.cj = half;
-            CK(launch_applyT<double>(P, V + (size_t)j * N, e, s));
-          }
-          dots<double>(K, V, j + 1, w, 1, d_h1);
-          update<double>(K, V, j + 1, d_h1, w, d_nrm);
-          CK(fetch(K, 0, KRY_MAXV + 1));
-          for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] = K.hsc[i2];
-          const double wn0 = std::sqrt(K.hsc[j + 1]);
-          double wn = std::sqrt(K.hsc[KRY_MAXV]);
-          if (wn < 0.7071067811865476 * wn0) {
-            dots<double>(K, V, j + 1, w, 0, d_h2);
-            update<double>(K, V, j + 1, d_h2, w, d_nrm);
-            CK(fetch(K, 2 * KRY_MAXV, j + 1));
-            CK(fetch(K, KRY_MAXV, 1));
-            for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] += K.hsc[2 * KRY_MAXV + i2];
-            wn = std::sqrt(K.hsc[KRY_MAXV]);
-          }
-          H[(size_t)(j + 1) * m + j] = wn;
-          if (wn > 0.0) {
-            scale_kernel<double><<<1024, KRY_THREADS, 0, s>>>(w, w, d_nrm, 2, N);
-            ++g_launches;
-          }
-          for (int i2 = 0; i2 < j; ++i2) {
-            const double a0 = H[(size_t)i2 * m + j], a1 = H[(size_t)(i2 + 1) * m + j];
-            H[(size_t)i2 * m + j] = cs[i2] * a0 + sn[i2] * a1;
-            H[(size_t)(i2 + 1) * m + j] = -sn[i2] * a0 + cs[i2] * a1;
-          }
-          const double a0 = H[(size_t)j * m + j], a1 = H[(size_t)(j + 1) * m + j];
-          const double den = std::hypot(a0, a1);
-          cs[j] = den > 0 ? a0 / den : 1.0;
-          sn[j] = den > 0 ? a1 / den : 0.0;
-          H[(size_t)j * m + j] = den;
-          H[(size_t)(j + 1) * m + j] = 0.0;
-          g[j + 1] = -sn[j] * g[j];
-          g[j] = cs[j] * g[j];
-          ++its;
-          jdone = j + 1;
-          if (std::fabs(g[j + 1]) <= target || wn == 0.0) break;
-        }
-        for (int i2 = jdone - 1; i2 >= 0; --i2) {
-          double v = g[i2];
-          for (int k2 = i2 + 1; k2 < jdone; ++k2) v -= H[(size_t)i2 * m + k2] * y[k2];
-          y[i2] = v / H[(size_t)i2 * m + i2];
-        }
-        for (int i2 = 0; i2 < jdone; ++i2) K.hsc[3 * KRY_MAXV + i2] = y[i2];
-        CK(cudaMemcpyAsync(d_y, K.hsc + 3 * KRY_MAXV, sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
-        combine_kernel<double><<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, d_y, mu, N);
-        ++g_launches;
-        CK(cudaGetLastError());
+        int jd = 0;
+        CK((gmres_cycle<double, true>(c, P, V, dt, beta, 0.5 * beta * (tol / rel), std::min(m, maxit - its), mu, s,
+                                      &jd)));
+        its += jd;
+        if (jd == 0) break;
       }
     }
   }

@@ -197,11 +197,11 @@ struct sap_ctx {
   int* d_active = nullptr;                     // [ninst] device activity mask
   std::vector<int> h_active;
   sap_ctx* parent = nullptr;                   // set on the sub-contexts of a batch
-  // CUDA graphs of the GMRES iteration groups of sap_step_cn, replayed while the configuration they
-  // were captured for (dt, fields, workspace, group) holds
+  // CUDA graphs of the GMRES iteration groups of sap_step_cn (kind 0) and of the adjoint step (kind 1),
+  // replayed while the configuration they were captured for (dt, fields, workspace, group) holds
   struct CnGraph {
     cudaGraphExec_t exec = nullptr;
-    int j0 = -1, cnt = 0, fields_version = -1;
+    int kind = 0, j0 = -1, cnt = 0, fields_version = -1;
     double dt = 0.0;
     const void* ws = nullptr;
   };
