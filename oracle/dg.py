@@ -362,19 +362,32 @@ class Discretisation:
             keep_hi = self.row_mask[c_hi] if c_hi is not None else None
             if (c_lo is None or not keep_lo.any()) and (c_hi is None or not keep_hi.any()):
                 continue
+            # only the faces of this plane that border an assembled row (all of them without a
+            # row restriction); every face point is evaluated on its own
+            touch = np.zeros(len(tgrid), dtype=bool)
+            if c_lo is not None:
+                touch |= keep_lo
+            if c_hi is not None:
+                touch |= keep_hi
+            tsel = np.nonzero(touch)[0]
+            nt = len(tsel)
+            if c_lo is not None:
+                c_lo, keep_lo = c_lo[tsel], keep_lo[tsel]
+            if c_hi is not None:
+                c_hi, keep_hi = c_hi[tsel], keep_hi[tsel]
             # face points and weights
             ref_cell = c_lo if c_lo is not None else c_hi
             _, lo, h = self._cell_geometry(ref_cell)
             xf = m.edges[ax][f]
-            coords = np.empty((len(tgrid), nfq, D))
+            coords = np.empty((nt, nfq, D))
             coords[:, :, ax] = xf
             for t, b in enumerate(tang):
                 coords[:, :, b] = lo[:, b][:, None] + h[:, b][:, None] * self.xg[fidx[:, t]][None, :]
-            Wf = np.prod(self.wg[fidx], axis=1)[None, :] * np.prod(h[:, tang], axis=1)[:, None] if tang else np.ones((len(tgrid), 1))
+            Wf = np.prod(self.wg[fidx], axis=1)[None, :] * np.prod(h[:, tang], axis=1)[:, None] if tang else np.ones((nt, 1))
             st = _point_state(prob, coords.reshape(-1, D))
             beta = advection_matrix(prob, T, m.axes[ax], st, self.terms)
             bp, bm = upwind_split(beta)
-            beta = beta.reshape(len(tgrid), nfq, n, n)
+            beta = beta.reshape(nt, nfq, n, n)
             bp = bp.reshape(beta.shape)
             bm = bm.reshape(beta.shape)
             # J = K_lo f_lo + K_hi f_hi; lo rows get +J, hi rows get -J

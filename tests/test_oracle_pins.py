@@ -413,13 +413,20 @@ def test_gmres_matches_direct_solve():
     assert 0 < its < 200
 
 
-def test_rows_of_cells_subset_matches_full_assembly():
-    prob = W.shock(nx=8, npc=6)
+@pytest.mark.parametrize("case", ["shock2d", "box3d"])
+def test_rows_of_cells_subset_matches_full_assembly(case):
+    """Assembling only the rows of some cells (faces evaluated only where they border those
+    cells) reproduces those rows of the full assembly: 2-D shock with boundaries, 3-D periodic box
+    (two tangential axes per face plane, wrap-around neighbours)."""
+    if case == "shock2d":
+        prob, cells = W.shock(nx=8, npc=6), np.array([0, 7, 9, 22, 47])
+    else:
+        prob, cells = W.box3d(ncells=4, k=1, lmax=2), np.array([0, 5, 21, 42, 63])
     full = dg.Discretisation(prob)
-    cells = np.array([0, 7, 9, 22, 47])
     part = dg.Discretisation(prob, rows_of_cells=cells)
     rows = np.concatenate([full.dof(c, 0, 0) + np.arange(full.n * full.mesh.nloc) for c in cells])
     np.testing.assert_allclose(part.D[rows].toarray(), full.D[rows].toarray(), atol=1e-15)
+    np.testing.assert_allclose(part.M[rows].toarray(), full.M[rows].toarray(), atol=1e-15)
     np.testing.assert_allclose(part.h[rows], full.h[rows])
 
 
