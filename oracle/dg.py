@@ -317,8 +317,12 @@ class Discretisation:
         for ax in range(D):
             self._assemble_faces(ax)
         Nn = self.N
-        self.D = sp.csr_matrix((np.concatenate(self._v), (np.concatenate(self._r), np.concatenate(self._c))), shape=(Nn, Nn))
-        self.M = sp.csr_matrix((np.concatenate(self._mv), (np.concatenate(self._mr), np.concatenate(self._mc))), shape=(Nn, Nn))
+
+        def cat(parts, dtype):  # no entries at all is valid: e.g. l_max = 0 with U = 0 gives D = 0
+            return np.concatenate(parts) if parts else np.zeros(0, dtype=dtype)
+
+        self.D = sp.csr_matrix((cat(self._v, float), (cat(self._r, np.int64), cat(self._c, np.int64))), shape=(Nn, Nn))
+        self.M = sp.csr_matrix((cat(self._mv, float), (cat(self._mr, np.int64), cat(self._mc, np.int64))), shape=(Nn, Nn))
         del self._r, self._c, self._v, self._mr, self._mc, self._mv
 
     def _assemble_faces(self, ax):

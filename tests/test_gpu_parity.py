@@ -221,7 +221,7 @@ def test_apply_full_box3d_sampled(torch_cuda, prec, tol):
     from paper_2501_05110_gb300 import sapgpu
     sol.apply(x, yv, sapgpu.APPLY_D)
     torch.cuda.synchronize()
-    cells = _sample_cells(48 ** 3, 12, 2)
+    cells = _sample_cells(48 ** 3, 40, 2)
     per = prob.n * 27
     idx = torch.from_numpy(np.concatenate([c * per + np.arange(per) for c in cells])).cuda()
     # the oracle needs the input of the sampled cells and of their neighbours: take it all on host
@@ -265,6 +265,64 @@ def test_cn_fp32_refined(torch_cuda, tol, bound):
     want = orc.cn(np.zeros(sol.N), 1.0, 12)
     err = np.linalg.norm(y.cpu().numpy() - want) / np.linalg.norm(want)
     assert st.last_rel_residual <= tol and err < bound, (err, st.last_rel_residual)
+
+
+# ------------------------------------------------------------------------------------------------
+# orders at the ends of the supported ranges, and degenerate systems
+# ------------------------------------------------------------------------------------------------
+_EDGE_ORDERS = {
+    "k0_periodic1d": lambda: W.periodic_1d(ncells=5, k=0, lmax=2),
+    "l0_periodic1d": lambda: W.periodic_1d(ncells=4, k=2, lmax=0),
+    "l0_shock": lambda: W.shock(nx=4, npc=3, k=1, lmax=0, xr=(-2.0, 2.0), lnpr=(0.0, 2.0)),
+    "l0_box_zero_operator": lambda: W.box3d(ncells=2, k=2, lmax=0),
+    "k0_box": lambda: W.box3d(ncells=3, k=0, lmax=2),
+    "l11_periodic1d": lambda: W.periodic_1d(ncells=2, k=1, lmax=11),
+    "k4_shock": lambda: W.shock(nx=2, npc=2, k=4, lmax=1, xr=(-2.0, 2.0), lnpr=(0.0, 2.0)),
+}
+
+
+@pytest.mark.parametrize("name", list(_EDGE_ORDERS))
+def test_apply_edge_orders(torch_cuda, name):
+    """k = 0 and 4, l_max = 0 and 11 (l_max = 0 with U = 0 gives D = 0): every column of M^-1 D and
+    of its transpose equals the oracle's, and the right-side mode M^-1 (h - D x) agrees."""
+    from paper_2501_05110_gb300 import sapgpu
+    torch = torch_cuda
+    prob = _EDGE_ORDERS[name]()
+    orc = NodalOracle(prob)
+    sol = _solver(prob)
+    N = sol.N
+    assert N == orc.disc.N
+    eye = np.eye(N)
+    O = np.stack([orc.apply(eye[:, j]) for j in range(N)], axis=1)
+    G = np.stack([_gpu_apply(torch, sol, eye[:, j]) for j in range(N)], axis=1)
+    GT = []
+    for j in range(N):
+        x = torch.from_numpy(eye[:, j]).cuda()
+        y = torch.empty_like(x)
+        sol.apply(x, y, sapgpu.APPLY_T)
+        GT.append(y.cpu().numpy())
+    GT = np.stack(GT, axis=1)
+    if not O.any():
+        assert not G.any() and not GT.any()
+    else:
+        assert _rel_max(G, O) < 1e-12
+        assert _rel_max(GT, O.T) < 1e-12
+    y = np.random.default_rng(4).standard_normal(N)
+    want = orc.apply(y, True)
+    got = _gpu_apply(torch, sol, y, True)
+    assert (not want.any() and not got.any()) or _rel_max(got, want) < 1e-12
+
+
+def test_cn_zero_right_side_stays_zero(torch_cuda):
+    """No source and a zero state: b = 0, so each CN step returns exactly zero without iterating."""
+    torch = torch_cuda
+    prob = W.shock(nx=15, npc=7, lmax=3, Q=0.0)
+    sol = _solver(prob)
+    y = torch.zeros(sol.N, dtype=torch.float64, device="cuda")
+    st = sol.step_cn(y, 1.0, 3, 1e-10, 30, 100)
+    torch.cuda.synchronize()
+    assert not y.any()
+    assert st.iterations == 0
 
 
 # ------------------------------------------------------------------------------------------------

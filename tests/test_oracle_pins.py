@@ -413,6 +413,22 @@ def test_gmres_matches_direct_solve():
     assert 0 < its < 200
 
 
+def test_lmax0_reductions():
+    """l_max = 0 keeps only f_000: A^a couples l = 0 to l = 1 only and the collision rate
+    nu l(l+1)/2 vanishes at l = 0 (Sec. 2.1).  (a) 1-D periodic, constant U > 0, k = 0: the dG
+    operator is first-order upwind finite volumes, M^-1 D = (U/h)(I - S) with S the periodic shift
+    i-1 -> i.  (b) 3-D box with U = 0: D = 0 exactly."""
+    U, nc = 0.3, 7
+    prob = W.periodic_1d(ncells=nc, k=0, lmax=0, U=U)
+    d = dg.Discretisation(prob)
+    h = 20.0 / nc
+    got = spla.spsolve(d.M.tocsc(), d.D.toarray())
+    S = np.roll(np.eye(nc), 1, axis=0)  # (S z)_i = z_{i-1}
+    np.testing.assert_allclose(got, (U / h) * (np.eye(nc) - S), rtol=0, atol=1e-14)
+    box = dg.Discretisation(W.box3d(ncells=2, k=2, lmax=0))
+    assert box.D.nnz == 0 and box.N == 8 * 27
+
+
 @pytest.mark.parametrize("case", ["shock2d", "box3d"])
 def test_rows_of_cells_subset_matches_full_assembly(case):
     """Assembling only the rows of some cells (faces evaluated only where they border those
