@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY: part of the FP64 CPU oracle (see ``oracle/__init__.py``).
 
-* classical explicit fourth-order Runge--Kutta (ERK4, Sec. 3.4, last paragraph);
+* classical explicit fourth-order Runge--Kutta (ERK4, Sec. 3.4, last paragraph), its
+  tangent-linear trajectory and the transpose of one step (for the discrete adjoint);
 * the theta-method (M + dt theta D) zeta^n = (M - dt (1-theta) D) zeta^(n-1) + dt h
   (Eq. theta-method, Eq. system-matrix-rhs) with a time-independent D and h; theta = 0, 1, 1/2
   give forward Euler, backward Euler and Crank--Nicolson.  The linear system is solved exactly by a
@@ -32,6 +33,43 @@ def rk4(M, D, h, zeta0, dt, nsteps, callback=None):
         if callback is not None:
             callback(i + 1, z)
     return z
+
+
+def rk4_tangent(M, D, h, dD, zeta0, dt, nsteps):
+    """Tangent of the RK4 trajectory along a parameter direction with dD = dD/dtheta.  Each stage
+    derivative k_i = F(Y_i), F(z) = M^-1 (h - D z), has the tangent dk_i = -M^-1 (dD Y_i + D dY_i),
+    with dY_1 = d, dY_2 = d + dt/2 dk_1, dY_3 = d + dt/2 dk_2, dY_4 = d + dt dk_3, and the step gives
+    d <- d + dt/6 (dk_1 + 2 dk_2 + 2 dk_3 + dk_4), d^0 = 0.  Returns (z^N, d^N)."""
+    Mlu = spla.splu(sp.csc_matrix(M))
+    F = lambda z: Mlu.solve(h - D @ z)
+    dF = lambda z, dz: -Mlu.solve(dD @ z + D @ dz)
+    z = np.array(zeta0, dtype=float)
+    d = np.zeros_like(z)
+    for _ in range(nsteps):
+        Y1, dY1 = z, d
+        k1, dk1 = F(Y1), dF(Y1, dY1)
+        Y2, dY2 = z + 0.5 * dt * k1, d + 0.5 * dt * dk1
+        k2, dk2 = F(Y2), dF(Y2, dY2)
+        Y3, dY3 = z + 0.5 * dt * k2, d + 0.5 * dt * dk2
+        k3, dk3 = F(Y3), dF(Y3, dY3)
+        Y4, dY4 = z + dt * k3, d + dt * dk3
+        k4, dk4 = F(Y4), dF(Y4, dY4)
+        z = z + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+        d = d + dt / 6.0 * (dk1 + 2 * dk2 + 2 * dk3 + dk4)
+    return z, d
+
+
+def rk4_step_transpose(LT, dt, lam):
+    """Transpose of the linear part of one RK4 step.  For zeta' = s - L zeta with a constant
+    operator L, the classical RK4 step maps zeta to R zeta + const, with R the stability polynomial
+    sum_{j=0..4} (-dt L)^j / j!, so dJ/dzeta = R^T dJ/dzeta' = sum_j (-dt L^T)^j / j! lam.  ``LT``
+    applies L^T; the sum is taken by Horner's rule:
+    lam + (-dt L^T)(lam + (-dt L^T)/2 (lam + (-dt L^T)/3 (lam + (-dt L^T)/4 lam)))."""
+    lam = np.asarray(lam, dtype=float)
+    v = lam.copy()
+    for j in (4, 3, 2, 1):
+        v = lam + (-dt / j) * LT(v)
+    return v
 
 
 def theta_method(M, D, h, zeta0, dt, nsteps, theta=0.5, callback=None):

@@ -446,6 +446,65 @@ def test_rows_of_cells_subset_matches_full_assembly(case):
     np.testing.assert_allclose(part.h[rows], full.h[rows])
 
 
+def _shock_nu_family():
+    """Small shock with a per-cell log-normal nu, a per-cell direction v, and discretisations of
+    nu0 + t v (or of v alone as a pure collision term)."""
+    rng = np.random.default_rng(3)
+    base = W.shock(nx=6, npc=4, lmax=2, xr=(-12.0, 12.0), lnpr=(0.0, 3.0))
+    xe, pe = base.edges
+    v = rng.standard_normal((len(pe) - 1, len(xe) - 1))
+    nu0, _ = W.lognormal_cell_nu(xe, pe, seed=6)
+
+    def cellfun(vals):
+        def f(xs, p):
+            ix = np.clip(np.searchsorted(xe, xs[:, 0], side="right") - 1, 0, len(xe) - 2)
+            ip = np.clip(np.searchsorted(pe, np.log(p), side="right") - 1, 0, len(pe) - 2)
+            return vals[ip, ix]
+        return f
+
+    def disc_with(nu_fun, terms=None):
+        p = W.shock(nx=6, npc=4, lmax=2, xr=(-12.0, 12.0), lnpr=(0.0, 3.0), nu_field=nu_fun)
+        if terms is not None:
+            p.terms = frozenset(terms)
+        return dg.Discretisation(p)
+
+    return nu0, v, cellfun, disc_with
+
+
+def test_rk4_tangent_matches_trajectory_differences():
+    """The oracle's RK4 tangent (d zeta^N / d nu along a per-cell direction) equals a central
+    difference of its own RK4 trajectories (dt = 0.02, inside RK4's stability region for the
+    spectral radius 63 of M^-1 D here; the trajectory is a polynomial in nu)."""
+    nu0, v, cellfun, disc_with = _shock_nu_family()
+    d0 = disc_with(nu0)
+    dD = disc_with(cellfun(v), terms={"coll"}).D
+    dt, nsteps = 0.02, 5
+    z, dz = steppers.rk4_tangent(d0.M, d0.D, d0.h, dD, np.zeros(d0.N), dt, nsteps)
+    np.testing.assert_allclose(z, steppers.rk4(d0.M, d0.D, d0.h, np.zeros(d0.N), dt, nsteps), rtol=0, atol=0)
+    eps = 1e-4
+    zs = []
+    for sgn in (1, -1):
+        d = disc_with(lambda xs, p, s=sgn: nu0(xs, p) + s * eps * cellfun(v)(xs, p))
+        zs.append(steppers.rk4(d.M, d.D, d.h, np.zeros(d.N), dt, nsteps))
+    fd = (zs[0] - zs[1]) / (2 * eps)
+    assert np.abs(fd - dz).max() < 1e-7 * np.abs(dz).max()
+
+
+def test_rk4_step_transpose_dot_product():
+    """<lam, Phi x> = <Phi^T lam, x> for the linear part Phi of one RK4 step (the oracle's stage
+    form with h = 0) and the transpose from the stability polynomial in L^T = D^T M^-1."""
+    nu0, _, _, disc_with = _shock_nu_family()
+    d = disc_with(nu0)
+    Mlu = spla.splu(d.M.tocsc())
+    LT = lambda x: d.D.T @ Mlu.solve(x)
+    rng = np.random.default_rng(8)
+    for dt in (0.02, 0.5):
+        x, lam = rng.standard_normal(d.N), rng.standard_normal(d.N)
+        Phi_x = steppers.rk4(d.M, d.D, np.zeros(d.N), x, dt, 1)
+        a, b = lam @ Phi_x, steppers.rk4_step_transpose(LT, dt, lam) @ x
+        assert abs(a - b) < 1e-12 * (np.abs(lam) @ np.abs(Phi_x)), (dt, a, b)
+
+
 def test_cn_tangent_matches_trajectory_differences():
     """The oracle's CN tangent (d zeta^N / d nu along a per-cell direction) equals a central
     difference of its own CN trajectories; D is linear in nu, so the difference is exact up to
