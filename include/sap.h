@@ -174,6 +174,22 @@ sap_status sap_adjoint_step_cn(sap_handle h, const double* zeta_prev, const doub
                                double dt, double tol, int restart, int maxit, double* mu_out, double* grad_nu,
                                sap_solver_stats* stats, sap_stream stream);
 
+/* One step of the discrete adjoint of the classical RK4 step of sap_step_erk (Sec. 3.4, last
+ * paragraph) on zeta' = s - L zeta, L = M^-1 D.  On entry `lambda` (device, N doubles) holds
+ * dJ/dzeta_next for the step that starts from `zeta_prev` (device, N doubles); on return it holds
+ * dJ/dzeta_prev.  The call recomputes the stage inputs Y_1 = zeta_prev, Y_2 = Y_1 + dt/2 k_1,
+ * Y_3 = Y_1 + dt/2 k_2, Y_4 = Y_1 + dt k_3 (k_i = s - L Y_i), forms the stage adjoints in reverse
+ * order, kb_4 = dt/6 lambda, kb_3 = dt/3 lambda - dt L^T kb_4, kb_2 = dt/3 lambda - dt/2 L^T kb_3,
+ * kb_1 = dt/6 lambda - dt/2 L^T kb_2, and sets lambda <- lambda - L^T (kb_1 + kb_2 + kb_3 + kb_4).
+ * When `grad_nu` (device, one double per phase-space node) is not NULL it adds dJ/dnu there:
+ * -sum_i sum_j kb_i,j l_j(l_j+1)/2 Y_i,j (the collision term is pointwise in the nodal basis).
+ * When `stages_out` (device, 7 N doubles, caller-owned) is not NULL the call keeps Y_2, Y_3, Y_4,
+ * kb_1, kb_2, kb_3, kb_4 there, in that order, for derivatives the caller forms itself (a parameter
+ * theta adds sum_i kb_i . dF/dtheta(Y_i)).  Synchronous.  `stats` may be NULL.
+ * Errors: SAP_EINVAL, SAP_ENOMEM, SAP_ECUDA, SAP_EUNSUPPORTED (batch handles, FP32 contexts). */
+sap_status sap_adjoint_step_erk(sap_handle h, const double* zeta_prev, double* lambda, double dt, double* grad_nu,
+                                double* stages_out, sap_solver_stats* stats, sap_stream stream);
+
 /* Largest N (degrees of freedom) that sap_step_erk_noalloc accepts. */
 #define SAP_NOALLOC_MAX_DOFS 262144
 

@@ -1,4 +1,4 @@
-"""Discrete adjoint of Crank--Nicolson trajectories as a torch.autograd.Function.
+"""Discrete adjoints of Crank--Nicolson and RK4 trajectories as torch.autograd.Functions.
 
 The forward pass runs CN steps in the library (sap_step_cn) and keeps the state every
 `checkpoint` steps.  The backward pass walks the segments from the end: it recomputes a segment's
@@ -8,6 +8,13 @@ the last term being exact (nu enters the operator only through the pointwise col
 shock speed U1 enters through every field (U, grad U, dU/dt) and the upwind splits; its term
 -dt/2 mu . (dL/dU1)(zeta_{n-1} + zeta_n) uses the operator's central difference in U1,
 (L(U1 + e) - L(U1 - e)) / (2e) with e = 1e-6 U1, applied by the library.
+
+RK4 (ERKTrajectory) follows the same pattern with the library's RK4 adjoint step
+(sap_adjoint_step_erk): per step it recomputes the stage inputs Y_i, forms the stage adjoints kb_i
+and returns lambda_{n-1} = R^T lambda_n (R the RK4 stability polynomial in -dt L) and the exact nu
+term -sum_i kb_i . (dL/dnu) Y_i; the U1 term -sum_i kb_i . (dL/dU1) Y_i uses the same central
+difference in U1 on the stage pairs the library hands back.  RK4 is explicit, so recomputed segments
+reproduce the forward states exactly.
 
 Only argument marshalling and the per-step bookkeeping live here; every operator apply, linear
 solve and gradient accumulation runs in libsapgpu.so.
@@ -26,7 +33,8 @@ from . import sapgpu
 
 @dataclasses.dataclass
 class CNProblemFamily:
-    """A CN problem parametrised by a per-node nu (library phase-node order) and the shock speed."""
+    """A problem parametrised by a per-node nu (library phase-node order) and the shock speed, with
+    the time stepping of a trajectory (tol and restart apply to CN only)."""
     make_problem: Callable  # (nu_nodes_numpy or None, U1) -> workloads.Problem
     nsteps: int
     dt: float
@@ -117,6 +125,63 @@ class CNTrajectory(torch.autograd.Function):
                              "recompute_s": t_rec, "adjoint_s": t_adj,
                              "adjoint_iterations_per_step": sum(iters) / max(1, len(iters))}
         return grad_nu, torch.tensor(g_u1, dtype=torch.float64), None
+
+
+class ERKTrajectory(torch.autograd.Function):
+    """zeta_N = RK4^N(zeta_0 = initial state; nu, U1).  Inputs: nu_nodes (npv, float64, cuda),
+    U1 (0-d float64 tensor).  Returns the final state (N, float64, cuda)."""
+
+    @staticmethod
+    def forward(ctx, nu_nodes, U1, fam: CNProblemFamily):
+        u1 = float(U1)
+        nu_np = nu_nodes.detach().cpu().numpy()
+        sol = fam.solver(nu_np, u1)
+        state = sol.initial_state()
+        ckpts = {0: state.clone()}
+        for n in range(1, fam.nsteps + 1):
+            sol.step_erk(state, fam.dt, 1)
+            if n % fam.checkpoint == 0 and n < fam.nsteps:
+                ckpts[n] = state.clone()
+        ctx.fam, ctx.ckpts, ctx.nu_np, ctx.u1 = fam, ckpts, nu_np, u1
+        ctx.npv = nu_nodes.numel()
+        sol.close()
+        return state.clone()
+
+    @staticmethod
+    def backward(ctx, gL):
+        fam, ckpts, nu_np, u1 = ctx.fam, ctx.ckpts, ctx.nu_np, ctx.u1
+        sol = fam.solver(nu_np, u1)
+        eps = fam.u1_rel_eps * abs(u1)
+        sol_p = fam.solver(nu_np, u1 + eps)
+        sol_m = fam.solver(nu_np, u1 - eps)
+        lam = gL.detach().to(torch.float64).contiguous().clone()
+        N = lam.numel()
+        grad_nu = torch.zeros(ctx.npv, dtype=torch.float64, device=lam.device)
+        stages = torch.empty(7 * N, dtype=torch.float64, device=lam.device)
+        a = torch.empty_like(lam)
+        b = torch.empty_like(lam)
+        g_u1 = torch.zeros((), dtype=torch.float64, device=lam.device)
+        end = fam.nsteps
+        for s0 in reversed(sorted(ckpts)):
+            # the states that start the steps of [s0, end)
+            states = [ckpts[s0].clone()]
+            x = ckpts[s0].clone()
+            for _ in range(s0, end - 1):
+                sol.step_erk(x, fam.dt, 1)
+                states.append(x.clone())
+            for k in range(end - s0 - 1, -1, -1):
+                y = states[k]
+                sol.adjoint_step_erk(y, lam, fam.dt, grad_nu=grad_nu, stages_out=stages)
+                Y = [y, stages[:N], stages[N:2 * N], stages[2 * N:3 * N]]
+                for i in range(4):
+                    kb = stages[(3 + i) * N:(4 + i) * N]
+                    sol_p.apply(Y[i], a)
+                    sol_m.apply(Y[i], b)
+                    g_u1 -= kb @ (a - b) / (2 * eps)
+            end = s0
+        for s in (sol, sol_p, sol_m):
+            s.close()
+        return grad_nu, g_u1.cpu(), None
 
 
 def spectrum_loss(state, prob, target, mask, x_range=(50.0, 150.0)):

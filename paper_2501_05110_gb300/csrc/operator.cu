@@ -2035,7 +2035,15 @@ sap_status batch_cn(sap_ctx* c, double* state, double dt, int nsteps, double tol
 // ================================================================================================
 // Discrete adjoint of the Crank--Nicolson step
 // ================================================================================================
-// grad[node] += coef * sum_r mu[r,node] * l_r(l_r+1)/2 * (zp + zn)[r,node]   (l_r = floor(sqrt(r)))
+// l(l+1)/2 of expansion coefficient r (l = floor(sqrt(r))): the collision rate per unit nu
+__device__ __forceinline__ double coll_rate(int r) {
+  int l = (int)sqrt((double)r);
+  while ((l + 1) * (l + 1) <= r) ++l;
+  while (l * l > r) --l;
+  return 0.5 * l * (l + 1);
+}
+
+// grad[node] += coef * sum_r mu[r,node] * l_r(l_r+1)/2 * (zp + zn)[r,node]
 __global__ void grad_nu_kernel(const double* __restrict__ mu, const double* __restrict__ zp,
                                const double* __restrict__ zn, int n, int nloc, int64_t npv, double coef,
                                double* __restrict__ grad) {
@@ -2044,11 +2052,8 @@ __global__ void grad_nu_kernel(const double* __restrict__ mu, const double* __re
     const int i = (int)(p - cell * nloc);
     double acc = 0.0;
     for (int r = 1; r < n; ++r) {
-      int l = (int)sqrt((double)r);
-      while ((l + 1) * (l + 1) <= r) ++l;
-      while (l * l > r) --l;
       const size_t k = ((size_t)cell * n + r) * nloc + i;
-      acc += 0.5 * l * (l + 1) * mu[k] * (zp[k] + zn[k]);
+      acc += coll_rate(r) * mu[k] * (zp[k] + zn[k]);
     }
     grad[p] += coef * acc;
   }
@@ -2131,6 +2136,117 @@ sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, doubl
   return SAP_OK;
 cuda_fail:
   c->err = std::string("adjoint cn: ") + cudaGetErrorString(err);
+  return SAP_ECUDA;
+#undef CK
+}
+
+
+// ================================================================================================
+// Discrete adjoint of the RK4 step
+// ================================================================================================
+// grad[node] += coef * sum_r l_r(l_r+1)/2 * sum_i kb_i[r,node] Y_i[r,node] over the four stages
+__global__ void grad_nu_erk_kernel(const double* __restrict__ y, const double* __restrict__ S, int64_t N, int n,
+                                   int nloc, int64_t npv, double coef, double* __restrict__ grad) {
+  const double* Y2 = S;
+  const double* Y3 = S + N;
+  const double* Y4 = S + 2 * N;
+  const double* kb1 = S + 3 * N;
+  const double* kb2 = S + 4 * N;
+  const double* kb3 = S + 5 * N;
+  const double* kb4 = S + 6 * N;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npv; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = p / nloc;
+    const int i = (int)(p - cell * nloc);
+    double acc = 0.0;
+    for (int r = 1; r < n; ++r) {
+      const size_t k = ((size_t)cell * n + r) * nloc + i;
+      acc += coll_rate(r) * (kb1[k] * y[k] + kb2[k] * Y2[k] + kb3[k] * Y3[k] + kb4[k] * Y4[k]);
+    }
+    grad[p] += coef * acc;
+  }
+}
+
+// kb4 = c4 lam, ksum = kb1 + kb2 + kb3 + kb4
+__global__ void erk_adj_sum_kernel(const double* __restrict__ kb1, const double* __restrict__ kb2,
+                                   const double* __restrict__ kb3, const double* __restrict__ lam, double c4,
+                                   double* __restrict__ kb4, double* __restrict__ ksum, int64_t N) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const double k4 = c4 * lam[k];
+    kb4[k] = k4;
+    ksum[k] = (kb1[k] + kb2[k]) + (kb3[k] + k4);
+  }
+}
+
+// One reverse step of classical RK4 on zeta' = s - L zeta (L = M^-1 D).  The stage inputs
+// Y_1 = y, Y_2 = y + dt/2 k_1, Y_3 = y + dt/2 k_2, Y_4 = y + dt k_3 (k_i = s - L Y_i) are recomputed
+// from y; the stage adjoints, in reverse order, are
+//   kb4 = dt/6 lam,  kb3 = dt/3 lam - dt L^T kb4,  kb2 = dt/3 lam - dt/2 L^T kb3,
+//   kb1 = dt/6 lam - dt/2 L^T kb2,
+// and lam <- lam - L^T (kb1 + kb2 + kb3 + kb4).  A parameter theta adds sum_i kb_i . dF/dtheta(Y_i);
+// for nu that is -sum_i kb_i . (dL/dnu) Y_i, pointwise in the nodal basis.
+// S (7 N): Y2, Y3, Y4, kb1, kb2, kb3, kb4 (the caller's buffer or the workspace).
+sap_status adjoint_erk_step(sap_ctx* c, const double* y, double* lambda, double dt, double* grad_nu, double* stages,
+                            sap_solver_stats* st, cudaStream_t s) {
+  const int64_t N = c->N;
+  double* S = stages ? stages : c->ws64;
+  double* Y2 = S;
+  double* Y3 = S + N;
+  double* Y4 = S + 2 * N;
+  double* kb1 = S + 3 * N;
+  double* kb2 = S + 4 * N;
+  double* kb3 = S + 5 * N;
+  double* kb4 = S + 6 * N;
+  double* ksum = c->ws64 + 7 * N;
+  const OpParams<double>& P = c->p64;
+  const int64_t launches0 = g_launches;
+  cudaError_t err = cudaSuccess;
+#define CK(x)                               \
+  do {                                      \
+    err = (x);                              \
+    if (err != cudaSuccess) goto cuda_fail; \
+  } while (0)
+  {  // stage inputs of the forward step
+    Epi<double> e2{};
+    e2.out = Y2; e2.ax = 1.0; e2.bl = -0.5 * dt; e2.gs = 0.5 * dt;
+    CK(launch_apply<double>(P, y, e2, s));
+    Epi<double> e3{};
+    e3.out = Y3; e3.bvec = y; e3.wb = 1.0; e3.bl = -0.5 * dt; e3.gs = 0.5 * dt;
+    CK(launch_apply<double>(P, Y2, e3, s));
+    Epi<double> e4{};
+    e4.out = Y4; e4.bvec = y; e4.wb = 1.0; e4.bl = -dt; e4.gs = dt;
+    CK(launch_apply<double>(P, Y3, e4, s));
+  }
+  {  // stage adjoints (kb4 = dt/6 lam enters kb3 directly)
+    Epi<double> a3{};
+    a3.out = kb3; a3.ax = dt / 3.0; a3.bl = -dt * dt / 6.0;
+    CK(launch_applyT<double>(P, lambda, a3, s));
+    Epi<double> a2{};
+    a2.out = kb2; a2.bvec = lambda; a2.wb = dt / 3.0; a2.bl = -0.5 * dt;
+    CK(launch_applyT<double>(P, kb3, a2, s));
+    Epi<double> a1{};
+    a1.out = kb1; a1.bvec = lambda; a1.wb = dt / 6.0; a1.bl = -0.5 * dt;
+    CK(launch_applyT<double>(P, kb2, a1, s));
+  }
+  erk_adj_sum_kernel<<<1024, 256, 0, s>>>(kb1, kb2, kb3, lambda, dt / 6.0, kb4, ksum, N);
+  ++g_launches;
+  if (grad_nu && (c->desc.terms & SAP_TERM_COLL)) {
+    grad_nu_erk_kernel<<<1024, 256, 0, s>>>(y, S, N, c->n, c->nloc, (int64_t)c->npv, -1.0, grad_nu);
+    ++g_launches;
+  }
+  {  // lam <- lam - L^T (kb1 + kb2 + kb3 + kb4); each entry of lam is read, then written, by one thread
+    Epi<double> e{};
+    e.out = lambda; e.bvec = lambda; e.wb = 1.0; e.bl = -1.0;
+    CK(launch_applyT<double>(P, ksum, e, s));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  if (st) {
+    st->steps = 1; st->iterations = 0; st->max_iterations = 0; st->last_rel_residual = 0.0;
+    st->kernel_launches = g_launches - launches0;
+  }
+  return SAP_OK;
+cuda_fail:
+  c->err = std::string("adjoint erk: ") + cudaGetErrorString(err);
   return SAP_ECUDA;
 #undef CK
 }

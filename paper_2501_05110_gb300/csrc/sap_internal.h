@@ -219,6 +219,8 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
                     sap_solver_stats* st, cudaStream_t s);
 sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, double* lambda, double dt, double tol,
                            int m, int maxit, double* mu_out, double* grad_nu, sap_solver_stats* st, cudaStream_t s);
+sap_status adjoint_erk_step(sap_ctx* c, const double* y, double* lambda, double dt, double* grad_nu, double* stages,
+                            sap_solver_stats* st, cudaStream_t s);
 int apply_cells_per_block(int n, int nloc);
 // row-per-thread apply (apply_rows.cu) for the compiled shapes (D, q) = (1, 3), (2, 2), (3, 3)
 bool rows_supported(int D, int q);

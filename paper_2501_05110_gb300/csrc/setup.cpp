@@ -1078,6 +1078,26 @@ extern "C" sap_status sap_adjoint_step_cn(sap_handle c, const double* zeta_prev,
                          (cudaStream_t)stream);
 }
 
+extern "C" sap_status sap_adjoint_step_erk(sap_handle c, const double* zeta_prev, double* lambda, double dt,
+                                           double* grad_nu, double* stages_out, sap_solver_stats* stats,
+                                           sap_stream stream) {
+  if (!c || !zeta_prev || !lambda || !std::isfinite(dt)) return SAP_EINVAL;
+  if (!c->sub.empty() || c->prec != SAP_PREC_FP64) {
+    c->err = "adjoint: FP64 single-problem contexts only";
+    return SAP_EUNSUPPORTED;
+  }
+  if (!c->fields_set) {
+    c->err = "fields not set";
+    return SAP_EINVAL;
+  }
+  if (!ensure_ws64(c, 8)) {
+    c->err = "adjoint: workspace allocation failed";
+    return SAP_ENOMEM;
+  }
+  c->cn_prev_valid = false;  // the adjoint step shares the workspace
+  return adjoint_erk_step(c, zeta_prev, lambda, dt, grad_nu, stages_out, stats, (cudaStream_t)stream);
+}
+
 extern "C" sap_status sap_destroy(sap_handle c) {
   if (!c) return SAP_OK;
   if (c->parent) return SAP_EINVAL;  // sub-handles belong to their batch

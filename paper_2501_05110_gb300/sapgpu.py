@@ -23,7 +23,7 @@ APPLY_D, APPLY_RHS, APPLY_T = 0, 1, 2
 PTS_SPATIAL, PTS_FACE_X, PTS_FACE_Y, PTS_FACE_Z, PTS_PHASE = range(5)
 
 EXPORTS = ["sap_create", "sap_create_batch", "sap_batch_instance", "sap_field_points", "sap_set_fields", "sap_num_dofs", "sap_apply_operator",
-           "sap_step_erk", "sap_step_erk_noalloc", "sap_step_cn", "sap_adjoint_step_cn", "sap_apply_cost", "sap_destroy", "sap_last_error",
+           "sap_step_erk", "sap_step_erk_noalloc", "sap_step_cn", "sap_adjoint_step_cn", "sap_adjoint_step_erk", "sap_apply_cost", "sap_destroy", "sap_last_error",
            "sap_coupling_matrix"]
 
 
@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH):
     lib.sap_apply_cost.argtypes = [vp, dp, dp]
     lib.sap_adjoint_step_cn.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int, C.c_int, vp, vp,
                                         C.POINTER(SolverStats), vp]
+    lib.sap_adjoint_step_erk.argtypes = [vp, vp, vp, C.c_double, vp, vp, C.POINTER(SolverStats), vp]
     lib.sap_destroy.argtypes = [vp]
     lib.sap_last_error.argtypes = [vp]
     lib.sap_last_error.restype = C.c_char_p
@@ -228,6 +229,16 @@ class Solver:
         self._check(self.lib.sap_adjoint_step_cn(self.h, ptr(zeta_prev), ptr(zeta_next), ptr(lam), dt, tol, restart,
                                                  maxit, ptr(mu_out), ptr(grad_nu), C.byref(st),
                                                  _stream_handle(stream)))
+        return st
+
+    def adjoint_step_erk(self, zeta_prev, lam, dt: float, grad_nu=None, stages_out=None,
+                         stream=None) -> SolverStats:
+        """lam <- dJ/dzeta_prev given dJ/dzeta_next (in place) for the RK4 step from zeta_prev;
+        optional nodal nu-gradient and the stage inputs / stage adjoints (7 N doubles)."""
+        st = SolverStats()
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        self._check(self.lib.sap_adjoint_step_erk(self.h, ptr(zeta_prev), ptr(lam), dt, ptr(grad_nu),
+                                                  ptr(stages_out), C.byref(st), _stream_handle(stream)))
         return st
 
     def apply_cost(self):
