@@ -816,9 +816,10 @@ __global__ void combine_kernel(const TV* __restrict__ V, int64_t ldv, int m, con
 // ------------------------------------------------------------------------------------------------
 namespace sap {
 
+// partial[i][chunk], i <= KRY_MAXV (the dots of w with up to KRY_MAXV basis vectors and w . w)
 int64_t krylov_scratch_doubles(int64_t N) {
   const int64_t nchunks = (N + KRY_CHUNK - 1) / KRY_CHUNK;
-  return (KRY_MAXV + 1) * nchunks + 8 * KRY_MAXV;
+  return (KRY_MAXV + 1) * nchunks;
 }
 
 int64_t krylov_batch_scratch_doubles(const std::vector<int64_t>& Ns) {

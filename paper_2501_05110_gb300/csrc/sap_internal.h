@@ -171,8 +171,8 @@ struct sap_ctx {
   int ws64_count = 0;
   float* ws32 = nullptr;
   int ws32_count = 0;
-  double* small = nullptr;                     // small device scratch for reductions/scalars
-  double* small_host = nullptr;                // pinned mirror
+  double* small = nullptr;                     // block partial sums of the Krylov reductions (+ batch scalars)
+  double* small_host = nullptr;                // pinned mirror of the batch scalars (batch handles only)
   void* gdev = nullptr;                        // device Arnoldi control block
   void* gdev_host = nullptr;                   // pinned mirror
   int krylov_restart = 0;

@@ -321,9 +321,8 @@ extern "C" sap_status sap_create(const sap_desc* desc, int prec, sap_handle* out
     };
     base(c->p64, d_ih64, d_pn64, d_pf64, d_mfn64, d_mff64);
     base(c->p32, d_ih32, d_pn32, d_pf32, d_mfn32, d_mff32);
-    // small reduction scratch
+    // block partial sums of the Krylov reductions
     if (cudaMalloc(&c->small, sizeof(double) * krylov_scratch_doubles(c->N)) != cudaSuccess) throw std::string("cudaMalloc failed");
-    if (cudaMallocHost(&c->small_host, sizeof(double) * 8 * 32) != cudaSuccess) throw std::string("cudaMallocHost failed");
     if (cudaMalloc(&c->gdev, gmres_control_bytes()) != cudaSuccess ||
         cudaMemset(c->gdev, 0, gmres_control_bytes()) != cudaSuccess)
       throw std::string("cudaMalloc failed");
