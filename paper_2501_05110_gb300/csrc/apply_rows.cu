@@ -520,13 +520,8 @@ void rows_config_shape(const OpParams<T>& P, int target, int* cells, size_t* sme
 
 template <typename T, int D, int Q>
 cudaError_t launch_rows_shape(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(rows_kernel<T, D, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)kRowsSmemMax);
-    if (err != cudaSuccess) return err;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> opted{0};
+  if (cudaError_t err = smem_opt_in(rows_kernel<T, D, Q>, (int)kRowsSmemMax, opted); err != cudaSuccess) return err;
   int C;
   size_t smem;
   // threads per block measured best on GB300: FP64 rows need many registers (3-D: ~190), so
@@ -544,13 +539,9 @@ cudaError_t launch_rows_shape(const OpParams<T>& P, const T* x, const Epi<T>& e,
 template <typename T, int D, int Q>
 cudaError_t launch_rows_batched_shape(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e,
                                       cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(rows_kernel_batched<T, D, Q>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowsSmemMax);
-    if (err != cudaSuccess) return err;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> opted{0};
+  if (cudaError_t err = smem_opt_in(rows_kernel_batched<T, D, Q>, (int)kRowsSmemMax, opted); err != cudaSuccess)
+    return err;
   if (B.smem > kRowsSmemMax || B.threads > Shape<T, D, Q>::MAXT) return cudaErrorInvalidConfiguration;
   rows_kernel_batched<T, D, Q><<<B.nblocks, B.threads, B.smem, s>>>(B.P, B.doff, B.cpb, B.blocks, active, x, e);
   note_launch();

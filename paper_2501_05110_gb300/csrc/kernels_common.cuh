@@ -3,11 +3,27 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "sap_internal.h"
 
 namespace sap {
 
 void note_launch();  // counts a kernel launch of this host thread (sap_solver_stats.kernel_launches)
+
+// Raise `kernel`'s dynamic shared-memory limit to `bytes` on the current device.  The attribute is
+// per device, so `done` (one per call site) records the devices already set, one bit each.
+template <typename K>
+inline cudaError_t smem_opt_in(K kernel, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (err == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return err;
+}
 
 // ------------------------------------------------------------------------------------------------
 // epilogue: out = d .* (wb*b + ax*x + bl*(Lx) + gs*s), and/or ERK bookkeeping

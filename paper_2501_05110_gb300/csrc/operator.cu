@@ -610,12 +610,8 @@ static int cell_stride_elems(const OpParams<T>& P) {
 template <typename T, int DT, int QT>
 static cudaError_t launch_apply_shape(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s, int cpb,
                                       int stride, size_t smem) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(apply_kernel<T, DT, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (err != cudaSuccess) return err;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> opted{0};
+  if (cudaError_t err = smem_opt_in(apply_kernel<T, DT, QT>, 200 * 1024, opted); err != cudaSuccess) return err;
   const int blocks = (P.ncell + cpb - 1) / cpb;
   apply_kernel<T, DT, QT><<<blocks, cpb * P.n * P.nloc, smem, s>>>(P, x, e, cpb, stride);
   ++g_launches;
@@ -643,13 +639,8 @@ static cudaError_t launch_applyT(const OpParams<T>& P, const T* x, const Epi<T>&
   const int cpb = apply_cells_per_block(P.n, P.nloc);
   const int stride = cell_stride_elems(P);
   const size_t smem = (size_t)cpb * stride * sizeof(T);
-  static bool attr_set[2] = {false, false};
-  const int idx = sizeof(T) == 8 ? 0 : 1;
-  if (!attr_set[idx]) {
-    cudaError_t err = cudaFuncSetAttribute(applyT_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (err != cudaSuccess) return err;
-    attr_set[idx] = true;
-  }
+  static std::atomic<unsigned long long> opted{0};  // one per instantiation (T)
+  if (cudaError_t err = smem_opt_in(applyT_kernel<T>, 200 * 1024, opted); err != cudaSuccess) return err;
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   const int blocks = (P.ncell + cpb - 1) / cpb;
   applyT_kernel<T><<<blocks, cpb * per, smem, s>>>(P, x, e, cpb, stride);
@@ -1410,13 +1401,9 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
 template <typename T, int DT, int QT>
 static cudaError_t launch_apply_batched_shape(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e,
                                               cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(apply_kernel_batched<T, DT, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           200 * 1024);
-    if (err != cudaSuccess) return err;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> opted{0};
+  if (cudaError_t err = smem_opt_in(apply_kernel_batched<T, DT, QT>, 200 * 1024, opted); err != cudaSuccess)
+    return err;
   apply_kernel_batched<T, DT, QT><<<B.nblocks, B.threads, B.smem, s>>>(B.P, B.doff, B.cpb, B.stride, B.blocks, active, x, e);
   ++g_launches;
   return cudaGetLastError();
