@@ -11,7 +11,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <map>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -20,6 +22,31 @@
 using namespace sap;
 
 static std::string g_create_error;
+
+// Every entry point returns a status: host exceptions (allocation failures of host containers and
+// the like) become status codes here instead of crossing the C boundary.  Errors of a call without
+// a handle go to the creation-error text.
+template <typename F>
+static sap_status guarded(sap_ctx* c, const char* what, F&& body) {
+  auto note = [&](const std::string& msg) {
+    try {
+      (c ? c->err : g_create_error) = std::string(what) + ": " + msg;
+    } catch (...) {
+    }
+  };
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    note("host allocation failed");
+    return SAP_ENOMEM;
+  } catch (const std::exception& e) {
+    note(e.what());
+    return SAP_EINVAL;
+  } catch (const std::string& e) {
+    note(e);
+    return SAP_EINVAL;
+  }
+}
 
 // ------------------------------------------------------------------------------------------------
 // 1-D Gauss--Legendre rule on [0,1] (Newton on the three-term recurrence) and Lagrange tables
@@ -173,205 +200,212 @@ static void fill_1d_tables(sap_ctx* c, OpParams<T>& P) {
 }
 
 extern "C" sap_status sap_create(const sap_desc* desc, int prec, sap_handle* out) {
-  if (!out) {
-    g_create_error = "null output handle";
-    return SAP_EINVAL;
-  }
-  *out = nullptr;
-  std::string v = validate(desc);
-  if (!v.empty()) {
-    g_create_error = v;
-    return SAP_EINVAL;
-  }
-  if (prec != SAP_PREC_FP64 && prec != SAP_PREC_FP32) {
-    g_create_error = "unknown precision";
-    return SAP_EINVAL;
-  }
-  sap_ctx* c = new sap_ctx();
-  try {
-    c->desc = *desc;
-    c->prec = prec;
-    c->D = desc->ndim;
-    c->q = desc->degree + 1;
-    c->n = (desc->lmax + 1) * (desc->lmax + 1);
-    c->nloc = 1;
-    for (int a = 0; a < c->D; ++a) c->nloc *= c->q;
-    c->nfp = c->nloc / c->q;
-    c->has_mom = !is_spatial(desc->axis_kind[c->D - 1]);
-    c->dx = c->D - c->has_mom;
-    c->qdx = 1;
-    for (int a = 0; a < c->dx; ++a) c->qdx *= c->q;
-    c->ncell = 1;
-    for (int a = 0; a < c->D; ++a) {
-      c->nc[a] = desc->ncells[a];
-      c->ncell *= desc->ncells[a];
-      c->edges[a].assign(desc->edges[a], desc->edges[a] + desc->ncells[a] + 1);
-      c->desc.edges[a] = c->edges[a].data();
+  return guarded(nullptr, "sap_create", [&]() -> sap_status {
+    if (!out) {
+      g_create_error = "null output handle";
+      return SAP_EINVAL;
     }
-    c->N = (int64_t)c->ncell * c->n * c->nloc;
-    c->nscell = 1;
-    for (int a = 0; a < c->dx; ++a) c->nscell *= c->nc[a];
-    c->npc = c->has_mom ? c->nc[c->D - 1] : 1;
-    c->nsv = c->nscell * c->qdx;
-    c->npv = c->ncell * c->nloc;
-    gauss_legendre01(c->q, c->xg, c->wg);
-    c->T = build_sh_tables(desc->lmax);
-    // momentum node and face values
-    if (c->has_mom) {
-      const int a = c->D - 1;
-      const bool lg = desc->axis_kind[a] == SAP_AXIS_LNP;
-      for (int pc = 0; pc < c->npc; ++pc)
-        for (int j = 0; j < c->q; ++j) {
-          double crd = c->edges[a][pc] + (c->edges[a][pc + 1] - c->edges[a][pc]) * c->xg[j];
-          c->pnode.push_back(lg ? std::exp(crd) : crd);
+    *out = nullptr;
+    std::string v = validate(desc);
+    if (!v.empty()) {
+      g_create_error = v;
+      return SAP_EINVAL;
+    }
+    if (prec != SAP_PREC_FP64 && prec != SAP_PREC_FP32) {
+      g_create_error = "unknown precision";
+      return SAP_EINVAL;
+    }
+    sap_ctx* c = new sap_ctx();
+    try {
+      c->desc = *desc;
+      c->prec = prec;
+      c->D = desc->ndim;
+      c->q = desc->degree + 1;
+      c->n = (desc->lmax + 1) * (desc->lmax + 1);
+      c->nloc = 1;
+      for (int a = 0; a < c->D; ++a) c->nloc *= c->q;
+      c->nfp = c->nloc / c->q;
+      c->has_mom = !is_spatial(desc->axis_kind[c->D - 1]);
+      c->dx = c->D - c->has_mom;
+      c->qdx = 1;
+      for (int a = 0; a < c->dx; ++a) c->qdx *= c->q;
+      c->ncell = 1;
+      for (int a = 0; a < c->D; ++a) {
+        c->nc[a] = desc->ncells[a];
+        c->ncell *= desc->ncells[a];
+        c->edges[a].assign(desc->edges[a], desc->edges[a] + desc->ncells[a] + 1);
+        c->desc.edges[a] = c->edges[a].data();
+      }
+      c->N = (int64_t)c->ncell * c->n * c->nloc;
+      c->nscell = 1;
+      for (int a = 0; a < c->dx; ++a) c->nscell *= c->nc[a];
+      c->npc = c->has_mom ? c->nc[c->D - 1] : 1;
+      c->nsv = c->nscell * c->qdx;
+      c->npv = c->ncell * c->nloc;
+      gauss_legendre01(c->q, c->xg, c->wg);
+      c->T = build_sh_tables(desc->lmax);
+      // momentum node and face values
+      if (c->has_mom) {
+        const int a = c->D - 1;
+        const bool lg = desc->axis_kind[a] == SAP_AXIS_LNP;
+        for (int pc = 0; pc < c->npc; ++pc)
+          for (int j = 0; j < c->q; ++j) {
+            double crd = c->edges[a][pc] + (c->edges[a][pc + 1] - c->edges[a][pc]) * c->xg[j];
+            c->pnode.push_back(lg ? std::exp(crd) : crd);
+          }
+        for (int f = 0; f <= c->npc; ++f) c->pface.push_back(lg ? std::exp(c->edges[a][f]) : c->edges[a][f]);
+      } else {
+        c->pnode.assign(c->q, 1.0);
+        c->pface.assign(2, 1.0);
+      }
+      // mesh connectivity
+      std::vector<int> nb((size_t)c->ncell * 2 * c->D), scell(c->ncell), pcell(c->ncell);
+      std::vector<double> invh((size_t)c->ncell * c->D);
+      for (int cell = 0; cell < c->ncell; ++cell) {
+        int idx[3] = {0, 0, 0}, rest = cell, stride[3];
+        int st = 1;
+        for (int a = 0; a < c->D; ++a) {
+          idx[a] = rest % c->nc[a];
+          rest /= c->nc[a];
+          stride[a] = st;
+          st *= c->nc[a];
         }
-      for (int f = 0; f <= c->npc; ++f) c->pface.push_back(lg ? std::exp(c->edges[a][f]) : c->edges[a][f]);
-    } else {
-      c->pnode.assign(c->q, 1.0);
-      c->pface.assign(2, 1.0);
-    }
-    // mesh connectivity
-    std::vector<int> nb((size_t)c->ncell * 2 * c->D), scell(c->ncell), pcell(c->ncell);
-    std::vector<double> invh((size_t)c->ncell * c->D);
-    for (int cell = 0; cell < c->ncell; ++cell) {
-      int idx[3] = {0, 0, 0}, rest = cell, stride[3];
-      int st = 1;
-      for (int a = 0; a < c->D; ++a) {
-        idx[a] = rest % c->nc[a];
-        rest /= c->nc[a];
-        stride[a] = st;
-        st *= c->nc[a];
+        for (int a = 0; a < c->D; ++a) {
+          invh[(size_t)cell * c->D + a] = 1.0 / (c->edges[a][idx[a] + 1] - c->edges[a][idx[a]]);
+          bool per = desc->bc_lo[a] == SAP_BC_PERIODIC;
+          int lo = idx[a] > 0 ? cell - stride[a] : (per ? cell + (c->nc[a] - 1) * stride[a] : -1);
+          int hi = idx[a] < c->nc[a] - 1 ? cell + stride[a] : (per ? cell - (c->nc[a] - 1) * stride[a] : -1);
+          nb[(size_t)cell * 2 * c->D + 2 * a] = lo;
+          nb[(size_t)cell * 2 * c->D + 2 * a + 1] = hi;
+        }
+        int sc = 0, sst = 1;
+        for (int a = 0; a < c->dx; ++a) {
+          sc += idx[a] * sst;
+          sst *= c->nc[a];
+        }
+        scell[cell] = sc;
+        pcell[cell] = c->has_mom ? idx[c->D - 1] : 0;
       }
-      for (int a = 0; a < c->D; ++a) {
-        invh[(size_t)cell * c->D + a] = 1.0 / (c->edges[a][idx[a] + 1] - c->edges[a][idx[a]]);
-        bool per = desc->bc_lo[a] == SAP_BC_PERIODIC;
-        int lo = idx[a] > 0 ? cell - stride[a] : (per ? cell + (c->nc[a] - 1) * stride[a] : -1);
-        int hi = idx[a] < c->nc[a] - 1 ? cell + stride[a] : (per ? cell - (c->nc[a] - 1) * stride[a] : -1);
-        nb[(size_t)cell * 2 * c->D + 2 * a] = lo;
-        nb[(size_t)cell * 2 * c->D + 2 * a + 1] = hi;
-      }
-      int sc = 0, sst = 1;
+      // spatial face point bases: faces along spatial axis a, ordered (face position, tangential
+      // spatial cell with lower axes fastest, tangential spatial node)
+      const int qt = c->qdx / c->q;  // tangential spatial nodes per face
+      c->scell_face_h.assign((size_t)c->nscell * 2 * std::max(c->dx, 1), 0);
       for (int a = 0; a < c->dx; ++a) {
-        sc += idx[a] * sst;
-        sst *= c->nc[a];
-      }
-      scell[cell] = sc;
-      pcell[cell] = c->has_mom ? idx[c->D - 1] : 0;
-    }
-    // spatial face point bases: faces along spatial axis a, ordered (face position, tangential
-    // spatial cell with lower axes fastest, tangential spatial node)
-    const int qt = c->qdx / c->q;  // tangential spatial nodes per face
-    c->scell_face_h.assign((size_t)c->nscell * 2 * std::max(c->dx, 1), 0);
-    for (int a = 0; a < c->dx; ++a) {
-      int ntang = c->nscell / c->nc[a];
-      c->nsf[a] = (c->nc[a] + 1) * ntang * qt;
-      for (int sc = 0; sc < c->nscell; ++sc) {
-        int idx[3] = {0, 0, 0}, rest = sc;
-        for (int b = 0; b < c->dx; ++b) {
-          idx[b] = rest % c->nc[b];
-          rest /= c->nc[b];
+        int ntang = c->nscell / c->nc[a];
+        c->nsf[a] = (c->nc[a] + 1) * ntang * qt;
+        for (int sc = 0; sc < c->nscell; ++sc) {
+          int idx[3] = {0, 0, 0}, rest = sc;
+          for (int b = 0; b < c->dx; ++b) {
+            idx[b] = rest % c->nc[b];
+            rest /= c->nc[b];
+          }
+          int tc = 0, tst = 1;
+          for (int b = 0; b < c->dx; ++b) {
+            if (b == a) continue;
+            tc += idx[b] * tst;
+            tst *= c->nc[b];
+          }
+          bool per = desc->bc_lo[a] == SAP_BC_PERIODIC;
+          int flo = (idx[a] == 0 && per) ? c->nc[a] : idx[a];
+          int fhi = idx[a] + 1;
+          c->scell_face_h[(size_t)sc * 2 * c->dx + 2 * a] = (flo * ntang + tc) * qt;
+          c->scell_face_h[(size_t)sc * 2 * c->dx + 2 * a + 1] = (fhi * ntang + tc) * qt;
         }
-        int tc = 0, tst = 1;
-        for (int b = 0; b < c->dx; ++b) {
-          if (b == a) continue;
-          tc += idx[b] * tst;
-          tst *= c->nc[b];
-        }
-        bool per = desc->bc_lo[a] == SAP_BC_PERIODIC;
-        int flo = (idx[a] == 0 && per) ? c->nc[a] : idx[a];
-        int fhi = idx[a] + 1;
-        c->scell_face_h[(size_t)sc * 2 * c->dx + 2 * a] = (flo * ntang + tc) * qt;
-        c->scell_face_h[(size_t)sc * 2 * c->dx + 2 * a + 1] = (fhi * ntang + tc) * qt;
       }
+      // A^x blocks for the eigen route
+      c->Ablocks = connected_blocks(c->T.A[0]);
+      // device mesh tables (both precisions share the integer tables)
+      auto& own = c->owned;
+      int* d_nb = (int*)upload(c, nb, own);
+      int* d_sc = (int*)upload(c, scell, own);
+      int* d_pc = (int*)upload(c, pcell, own);
+      int* d_sf = (int*)upload(c, c->scell_face_h, own);
+      double* d_ih64 = (double*)upload(c, invh, own);
+      float* d_ih32 = (float*)upload(c, to_f32(invh), own);
+      double* d_pn64 = (double*)upload(c, c->pnode, own);
+      float* d_pn32 = (float*)upload(c, to_f32(c->pnode), own);
+      double* d_pf64 = (double*)upload(c, c->pface, own);
+      float* d_pf32 = (float*)upload(c, to_f32(c->pface), own);
+      // momentum factor tables (MF_*) at nodes and faces
+      const int npn = (int)c->pnode.size(), npf = (int)c->pface.size();
+      std::vector<double> mfn((size_t)MF_COUNT * npn), mff((size_t)MF_COUNT * npf);
+      for (int mf = 0; mf < MF_COUNT; ++mf) {
+        for (int i = 0; i < npn; ++i) mfn[(size_t)mf * npn + i] = mom_factor_h(mf, c->pnode[i], c->has_mom, desc->V);
+        for (int i = 0; i < npf; ++i) mff[(size_t)mf * npf + i] = mom_factor_h(mf, c->pface[i], c->has_mom, desc->V);
+      }
+      double* d_mfn64 = (double*)upload(c, mfn, own);
+      float* d_mfn32 = (float*)upload(c, to_f32(mfn), own);
+      double* d_mff64 = (double*)upload(c, mff, own);
+      float* d_mff32 = (float*)upload(c, to_f32(mff), own);
+      auto base = [&](auto& P, auto* ih, auto* pn, auto* pf, auto* mn, auto* mfc) {
+        P.D = c->D; P.dx = c->dx; P.q = c->q; P.nloc = c->nloc; P.nfp = c->nfp; P.n = c->n;
+        P.ncell = c->ncell; P.has_mom = c->has_mom; P.qdx = c->qdx;
+        for (int a = 0; a < 3; ++a) P.nc[a] = c->nc[a];
+        P.cell_nb = d_nb; P.cell_scell = d_sc; P.cell_pcell = d_pc; P.scell_face = d_sf;
+        P.cell_invh = ih; P.pnode = pn; P.pface = pf; P.npface = npf; P.mfn = mn; P.mff = mfc; P.npn = npn;
+        P.nsv = c->nsv;
+        P.Vmono = c->has_mom ? 1 : desc->V;
+        fill_1d_tables(c, P);
+      };
+      base(c->p64, d_ih64, d_pn64, d_pf64, d_mfn64, d_mff64);
+      base(c->p32, d_ih32, d_pn32, d_pf32, d_mfn32, d_mff32);
+      // block partial sums of the Krylov reductions
+      if (cudaMalloc(&c->small, sizeof(double) * krylov_scratch_doubles(c->N)) != cudaSuccess) throw std::string("cudaMalloc failed");
+      if (cudaMalloc(&c->gdev, gmres_control_bytes()) != cudaSuccess ||
+          cudaMemset(c->gdev, 0, gmres_control_bytes()) != cudaSuccess)
+        throw std::string("cudaMalloc failed");
+      if (cudaMallocHost(&c->gdev_host, gmres_control_bytes()) != cudaSuccess) throw std::string("cudaMallocHost failed");
+      std::memset(c->gdev_host, 0, gmres_control_bytes());
+    } catch (const std::string& e) {
+      g_create_error = "sap_create: " + e;
+      sap_destroy(c);
+      return SAP_ENOMEM;
+    } catch (const std::exception& e) {
+      sap_destroy(c);
+      throw;  // reported by the guard
     }
-    // A^x blocks for the eigen route
-    c->Ablocks = connected_blocks(c->T.A[0]);
-    // device mesh tables (both precisions share the integer tables)
-    auto& own = c->owned;
-    int* d_nb = (int*)upload(c, nb, own);
-    int* d_sc = (int*)upload(c, scell, own);
-    int* d_pc = (int*)upload(c, pcell, own);
-    int* d_sf = (int*)upload(c, c->scell_face_h, own);
-    double* d_ih64 = (double*)upload(c, invh, own);
-    float* d_ih32 = (float*)upload(c, to_f32(invh), own);
-    double* d_pn64 = (double*)upload(c, c->pnode, own);
-    float* d_pn32 = (float*)upload(c, to_f32(c->pnode), own);
-    double* d_pf64 = (double*)upload(c, c->pface, own);
-    float* d_pf32 = (float*)upload(c, to_f32(c->pface), own);
-    // momentum factor tables (MF_*) at nodes and faces
-    const int npn = (int)c->pnode.size(), npf = (int)c->pface.size();
-    std::vector<double> mfn((size_t)MF_COUNT * npn), mff((size_t)MF_COUNT * npf);
-    for (int mf = 0; mf < MF_COUNT; ++mf) {
-      for (int i = 0; i < npn; ++i) mfn[(size_t)mf * npn + i] = mom_factor_h(mf, c->pnode[i], c->has_mom, desc->V);
-      for (int i = 0; i < npf; ++i) mff[(size_t)mf * npf + i] = mom_factor_h(mf, c->pface[i], c->has_mom, desc->V);
-    }
-    double* d_mfn64 = (double*)upload(c, mfn, own);
-    float* d_mfn32 = (float*)upload(c, to_f32(mfn), own);
-    double* d_mff64 = (double*)upload(c, mff, own);
-    float* d_mff32 = (float*)upload(c, to_f32(mff), own);
-    auto base = [&](auto& P, auto* ih, auto* pn, auto* pf, auto* mn, auto* mfc) {
-      P.D = c->D; P.dx = c->dx; P.q = c->q; P.nloc = c->nloc; P.nfp = c->nfp; P.n = c->n;
-      P.ncell = c->ncell; P.has_mom = c->has_mom; P.qdx = c->qdx;
-      for (int a = 0; a < 3; ++a) P.nc[a] = c->nc[a];
-      P.cell_nb = d_nb; P.cell_scell = d_sc; P.cell_pcell = d_pc; P.scell_face = d_sf;
-      P.cell_invh = ih; P.pnode = pn; P.pface = pf; P.npface = npf; P.mfn = mn; P.mff = mfc; P.npn = npn;
-      P.nsv = c->nsv;
-      P.Vmono = c->has_mom ? 1 : desc->V;
-      fill_1d_tables(c, P);
-    };
-    base(c->p64, d_ih64, d_pn64, d_pf64, d_mfn64, d_mff64);
-    base(c->p32, d_ih32, d_pn32, d_pf32, d_mfn32, d_mff32);
-    // block partial sums of the Krylov reductions
-    if (cudaMalloc(&c->small, sizeof(double) * krylov_scratch_doubles(c->N)) != cudaSuccess) throw std::string("cudaMalloc failed");
-    if (cudaMalloc(&c->gdev, gmres_control_bytes()) != cudaSuccess ||
-        cudaMemset(c->gdev, 0, gmres_control_bytes()) != cudaSuccess)
-      throw std::string("cudaMalloc failed");
-    if (cudaMallocHost(&c->gdev_host, gmres_control_bytes()) != cudaSuccess) throw std::string("cudaMallocHost failed");
-    std::memset(c->gdev_host, 0, gmres_control_bytes());
-  } catch (const std::string& e) {
-    g_create_error = "sap_create: " + e;
-    sap_destroy(c);
-    return SAP_ENOMEM;
-  }
-  *out = c;
-  return SAP_OK;
+    *out = c;
+    return SAP_OK;
+  });
 }
 
 extern "C" sap_status sap_create_batch(int ninst, const sap_desc* descs, int prec, sap_handle* out) {
-  if (!out || !descs || ninst < 1) {
-    g_create_error = "sap_create_batch: bad arguments";
-    return SAP_EINVAL;
-  }
-  *out = nullptr;
-  sap_ctx* c = new sap_ctx();
-  c->prec = prec;
-  std::vector<int64_t> Ns;
-  for (int i = 0; i < ninst; ++i) {
-    sap_handle sub = nullptr;
-    sap_status st = sap_create(&descs[i], prec, &sub);
-    if (st != SAP_OK) {
-      g_create_error = "sap_create_batch: instance " + std::to_string(i) + ": " + g_create_error;
-      for (auto* s2 : c->sub) {
-        s2->parent = nullptr;
-        sap_destroy(s2);
-      }
-      delete c;
-      return st;
+  return guarded(nullptr, "sap_create_batch", [&]() -> sap_status {
+    if (!out || !descs || ninst < 1) {
+      g_create_error = "sap_create_batch: bad arguments";
+      return SAP_EINVAL;
     }
-    sub->parent = c;
-    c->inst_off.push_back(c->N);
-    c->N += sub->N;
-    Ns.push_back(sub->N);
-    c->sub.push_back(sub);
-  }
-  if (cudaMalloc(&c->small, sizeof(double) * krylov_batch_scratch_doubles(Ns)) != cudaSuccess ||
-      cudaMallocHost(&c->small_host, sizeof(double) * 4 * 32 * (size_t)ninst) != cudaSuccess) {
-    g_create_error = "sap_create_batch: allocation failed";
-    sap_destroy(c);
-    return SAP_ENOMEM;
-  }
-  *out = c;
-  return SAP_OK;
+    *out = nullptr;
+    sap_ctx* c = new sap_ctx();
+    c->prec = prec;
+    std::vector<int64_t> Ns;
+    for (int i = 0; i < ninst; ++i) {
+      sap_handle sub = nullptr;
+      sap_status st = sap_create(&descs[i], prec, &sub);
+      if (st != SAP_OK) {
+        g_create_error = "sap_create_batch: instance " + std::to_string(i) + ": " + g_create_error;
+        for (auto* s2 : c->sub) {
+          s2->parent = nullptr;
+          sap_destroy(s2);
+        }
+        delete c;
+        return st;
+      }
+      sub->parent = c;
+      c->inst_off.push_back(c->N);
+      c->N += sub->N;
+      Ns.push_back(sub->N);
+      c->sub.push_back(sub);
+    }
+    if (cudaMalloc(&c->small, sizeof(double) * krylov_batch_scratch_doubles(Ns)) != cudaSuccess ||
+        cudaMallocHost(&c->small_host, sizeof(double) * 4 * 32 * (size_t)ninst) != cudaSuccess) {
+      g_create_error = "sap_create_batch: allocation failed";
+      sap_destroy(c);
+      return SAP_ENOMEM;
+    }
+    *out = c;
+    return SAP_OK;
+  });
 }
 
 extern "C" sap_status sap_batch_instance(sap_handle c, int inst, sap_handle* sub, int64_t* offset) {
@@ -385,89 +419,91 @@ extern "C" sap_status sap_batch_instance(sap_handle c, int inst, sap_handle* sub
 // points
 // ------------------------------------------------------------------------------------------------
 extern "C" sap_status sap_field_points(sap_handle c, int which, double* coords, int64_t* count) {
-  if (!c || !count) return SAP_EINVAL;
-  const int q = c->q;
-  std::vector<double> out;
-  if (which == SAP_PTS_SPATIAL) {
-    *count = c->nsv;
-    if (!coords) return SAP_OK;
-    for (int sc = 0; sc < c->nscell; ++sc) {
-      int idx[3] = {0, 0, 0}, rest = sc;
-      for (int a = 0; a < c->dx; ++a) {
-        idx[a] = rest % c->nc[a];
-        rest /= c->nc[a];
-      }
-      for (int nd = 0; nd < c->qdx; ++nd) {
-        int r2 = nd;
+  return guarded(c, "sap_field_points", [&]() -> sap_status {
+    if (!c || !count) return SAP_EINVAL;
+    const int q = c->q;
+    std::vector<double> out;
+    if (which == SAP_PTS_SPATIAL) {
+      *count = c->nsv;
+      if (!coords) return SAP_OK;
+      for (int sc = 0; sc < c->nscell; ++sc) {
+        int idx[3] = {0, 0, 0}, rest = sc;
         for (int a = 0; a < c->dx; ++a) {
-          int j = r2 % q;
-          r2 /= q;
-          double lo = c->edges[a][idx[a]], h = c->edges[a][idx[a] + 1] - lo;
-          coords[((size_t)sc * c->qdx + nd) * c->dx + a] = lo + h * c->xg[j];
+          idx[a] = rest % c->nc[a];
+          rest /= c->nc[a];
         }
-      }
-    }
-    return SAP_OK;
-  }
-  if (which >= SAP_PTS_FACE_X && which <= SAP_PTS_FACE_Z) {
-    int a = which - SAP_PTS_FACE_X;
-    if (a >= c->dx) {
-      *count = 0;
-      return SAP_OK;
-    }
-    *count = c->nsf[a];
-    if (!coords) return SAP_OK;
-    const int qt = c->qdx / q;
-    const int ntang = c->nscell / c->nc[a];
-    for (int f = 0; f <= c->nc[a]; ++f)
-      for (int tc = 0; tc < ntang; ++tc) {
-        int tidx[3] = {0, 0, 0}, rest = tc;
-        for (int b = 0; b < c->dx; ++b) {
-          if (b == a) continue;
-          tidx[b] = rest % c->nc[b];
-          rest /= c->nc[b];
-        }
-        for (int nd = 0; nd < qt; ++nd) {
-          size_t pidx = ((size_t)f * ntang + tc) * qt + nd;
+        for (int nd = 0; nd < c->qdx; ++nd) {
           int r2 = nd;
-          for (int b = 0; b < c->dx; ++b) {
-            double v;
-            if (b == a) {
-              v = c->edges[a][f];
-            } else {
-              int j = r2 % q;
-              r2 /= q;
-              double lo = c->edges[b][tidx[b]], h = c->edges[b][tidx[b] + 1] - lo;
-              v = lo + h * c->xg[j];
-            }
-            coords[pidx * c->dx + b] = v;
+          for (int a = 0; a < c->dx; ++a) {
+            int j = r2 % q;
+            r2 /= q;
+            double lo = c->edges[a][idx[a]], h = c->edges[a][idx[a] + 1] - lo;
+            coords[((size_t)sc * c->qdx + nd) * c->dx + a] = lo + h * c->xg[j];
           }
         }
       }
-    return SAP_OK;
-  }
-  if (which == SAP_PTS_PHASE) {
-    *count = c->npv;
-    if (!coords) return SAP_OK;
-    for (int cell = 0; cell < c->ncell; ++cell) {
-      int idx[3] = {0, 0, 0}, rest = cell;
-      for (int a = 0; a < c->D; ++a) {
-        idx[a] = rest % c->nc[a];
-        rest /= c->nc[a];
+      return SAP_OK;
+    }
+    if (which >= SAP_PTS_FACE_X && which <= SAP_PTS_FACE_Z) {
+      int a = which - SAP_PTS_FACE_X;
+      if (a >= c->dx) {
+        *count = 0;
+        return SAP_OK;
       }
-      for (int nd = 0; nd < c->nloc; ++nd) {
-        int r2 = nd;
+      *count = c->nsf[a];
+      if (!coords) return SAP_OK;
+      const int qt = c->qdx / q;
+      const int ntang = c->nscell / c->nc[a];
+      for (int f = 0; f <= c->nc[a]; ++f)
+        for (int tc = 0; tc < ntang; ++tc) {
+          int tidx[3] = {0, 0, 0}, rest = tc;
+          for (int b = 0; b < c->dx; ++b) {
+            if (b == a) continue;
+            tidx[b] = rest % c->nc[b];
+            rest /= c->nc[b];
+          }
+          for (int nd = 0; nd < qt; ++nd) {
+            size_t pidx = ((size_t)f * ntang + tc) * qt + nd;
+            int r2 = nd;
+            for (int b = 0; b < c->dx; ++b) {
+              double v;
+              if (b == a) {
+                v = c->edges[a][f];
+              } else {
+                int j = r2 % q;
+                r2 /= q;
+                double lo = c->edges[b][tidx[b]], h = c->edges[b][tidx[b] + 1] - lo;
+                v = lo + h * c->xg[j];
+              }
+              coords[pidx * c->dx + b] = v;
+            }
+          }
+        }
+      return SAP_OK;
+    }
+    if (which == SAP_PTS_PHASE) {
+      *count = c->npv;
+      if (!coords) return SAP_OK;
+      for (int cell = 0; cell < c->ncell; ++cell) {
+        int idx[3] = {0, 0, 0}, rest = cell;
         for (int a = 0; a < c->D; ++a) {
-          int j = r2 % q;
-          r2 /= q;
-          double lo = c->edges[a][idx[a]], h = c->edges[a][idx[a] + 1] - lo;
-          coords[((size_t)cell * c->nloc + nd) * c->D + a] = lo + h * c->xg[j];
+          idx[a] = rest % c->nc[a];
+          rest /= c->nc[a];
+        }
+        for (int nd = 0; nd < c->nloc; ++nd) {
+          int r2 = nd;
+          for (int a = 0; a < c->D; ++a) {
+            int j = r2 % q;
+            r2 /= q;
+            double lo = c->edges[a][idx[a]], h = c->edges[a][idx[a] + 1] - lo;
+            coords[((size_t)cell * c->nloc + nd) * c->D + a] = lo + h * c->xg[j];
+          }
         }
       }
+      return SAP_OK;
     }
-    return SAP_OK;
-  }
-  return SAP_EINVAL;
+    return SAP_EINVAL;
+  });
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -564,326 +600,331 @@ static void set_bank(OpParams<T>& P, const BankBuilder& B, sap_ctx* c, std::vect
 extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double* gradU, const double* DUDt,
                                      const double* Bw, const double* const Uface[3], const double* nu,
                                      const double* s000) {
-  if (!c) return SAP_EINVAL;
-  try {
-    FieldStore& fs = g_fields[c];
-    free_bufs(fs.bufs);
-    const sap_desc& d = c->desc;
-    const int n = c->n, nsv = c->nsv;
-    const unsigned terms = d.terms;
-    // spatial field components [SF_NCOMP][nsv]
-    std::vector<double> sf((size_t)SF_NCOMP * nsv, 0.0);
-    for (int p = 0; p < nsv; ++p) {
-      for (int a = 0; a < 3; ++a) {
-        if (U) sf[(size_t)(SF_U + a) * nsv + p] = U[(size_t)p * 3 + a];
-        if (DUDt) sf[(size_t)(SF_DU + a) * nsv + p] = DUDt[(size_t)p * 3 + a];
-        if (Bw) sf[(size_t)(SF_B + a) * nsv + p] = Bw[(size_t)p * 3 + a];
-        for (int b = 0; b < 3; ++b)
-          if (gradU) sf[(size_t)(SF_G + 3 * a + b) * nsv + p] = gradU[(size_t)p * 9 + 3 * a + b];
-      }
-    }
-    bool nonzero[SF_NCOMP], uni[SF_NCOMP];
-    double uval[SF_NCOMP];
-    for (int k = 0; k < SF_NCOMP; ++k) {
-      nonzero[k] = false;
-      uni[k] = true;
-      uval[k] = nsv ? sf[(size_t)k * nsv] : 0.0;
+  return guarded(c, "sap_set_fields", [&]() -> sap_status {
+    if (!c) return SAP_EINVAL;
+    try {
+      FieldStore& fs = g_fields[c];
+      // the old field buffers go now: until this call succeeds the context has no fields, so no
+      // compute call can read a freed buffer after a failure part-way
+      c->fields_set = false;
+      free_bufs(fs.bufs);
+      const sap_desc& d = c->desc;
+      const int n = c->n, nsv = c->nsv;
+      const unsigned terms = d.terms;
+      // spatial field components [SF_NCOMP][nsv]
+      std::vector<double> sf((size_t)SF_NCOMP * nsv, 0.0);
       for (int p = 0; p < nsv; ++p) {
-        double v = sf[(size_t)k * nsv + p];
-        if (v != 0.0) nonzero[k] = true;
-        if (v != uval[k]) uni[k] = false;
+        for (int a = 0; a < 3; ++a) {
+          if (U) sf[(size_t)(SF_U + a) * nsv + p] = U[(size_t)p * 3 + a];
+          if (DUDt) sf[(size_t)(SF_DU + a) * nsv + p] = DUDt[(size_t)p * 3 + a];
+          if (Bw) sf[(size_t)(SF_B + a) * nsv + p] = Bw[(size_t)p * 3 + a];
+          for (int b = 0; b < 3; ++b)
+            if (gradU) sf[(size_t)(SF_G + 3 * a + b) * nsv + p] = gradU[(size_t)p * 9 + 3 * a + b];
+        }
       }
-    }
-    const bool has_mom = c->has_mom;
-    const bool lnp = has_mom && d.axis_kind[c->D - 1] == SAP_AXIS_LNP;
-    BankBuilder B;
-    const SHTables& Tb = c->T;
-    auto A_id = [&](int a) { return B.add("A" + std::to_string(a), Tb.A[a]); };
-    auto AA_id = [&](int a, int b) { return B.add("AA" + std::to_string(a) + std::to_string(b), Tb.AA[a][b]); };
-    std::vector<Term> react;
-    auto add_term = [&](std::vector<Term>& v, int mat, int sfc, int mf, int nuf, double sc) {
-      int matT = MAT_I;
-      if (mat != MAT_I) {
-        std::string key;
-        for (auto& kv : B.ids)
-          if (kv.second == mat) key = kv.first;
-        Mat m(n);
-        const HostCSR& h = B.mats[mat];
-        for (int i = 0; i < n; ++i)
-          for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) m(h.col[k], i) = h.val[k];
-        matT = B.add(key + "^T", m);
+      bool nonzero[SF_NCOMP], uni[SF_NCOMP];
+      double uval[SF_NCOMP];
+      for (int k = 0; k < SF_NCOMP; ++k) {
+        nonzero[k] = false;
+        uni[k] = true;
+        uval[k] = nsv ? sf[(size_t)k * nsv] : 0.0;
+        for (int p = 0; p < nsv; ++p) {
+          double v = sf[(size_t)k * nsv + p];
+          if (v != 0.0) nonzero[k] = true;
+          if (v != uval[k]) uni[k] = false;
+        }
       }
-      v.push_back(Term{mat, matT, sfc, mf, nuf, sc});
-    };
-    // reaction matrix R - div(beta)  (Eq. definitions-advection-reaction-eq, Eq. linear-system-...)
-    if (terms & SAP_TERM_MOM) {
-      for (int a = 0; a < 3; ++a)
-        if (nonzero[SF_DU + a]) add_term(react, B.add("E" + std::to_string(a), Tb.E[a]), SF_DU + a, MF_INV_V, 0, 1.0);
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-          if (nonzero[SF_G + 3 * a + b])
-            add_term(react, B.add("F" + std::to_string(a) + std::to_string(b), Tb.F[a][b]), SF_G + 3 * a + b, MF_ONE, 0, 1.0);
-    }
-    if (terms & SAP_TERM_ROT)
-      for (int a = 0; a < 3; ++a)
-        if (nonzero[SF_B + a])
-          add_term(react, B.add("Om" + std::to_string(a), Tb.Om[a]), SF_B + a, has_mom ? MF_INV_GM : MF_ONE, 0, -1.0);
-    if (terms & SAP_TERM_COLL) add_term(react, B.add("C", Tb.C), SF_ONE, MF_ONE, 1, 1.0);
-    if (terms & SAP_TERM_ADV)
-      for (int a = 0; a < c->dx; ++a)
-        if (nonzero[SF_G + 3 * a + a]) add_term(react, MAT_I, SF_G + 3 * a + a, MF_ONE, 0, -1.0);
-    if ((terms & SAP_TERM_MOM) && has_mom) {
-      if (!lnp) {  // -d/dp beta^p = +V DU_a A^a + dU_b/dx^a A^a A^b
+      const bool has_mom = c->has_mom;
+      const bool lnp = has_mom && d.axis_kind[c->D - 1] == SAP_AXIS_LNP;
+      BankBuilder B;
+      const SHTables& Tb = c->T;
+      auto A_id = [&](int a) { return B.add("A" + std::to_string(a), Tb.A[a]); };
+      auto AA_id = [&](int a, int b) { return B.add("AA" + std::to_string(a) + std::to_string(b), Tb.AA[a][b]); };
+      std::vector<Term> react;
+      auto add_term = [&](std::vector<Term>& v, int mat, int sfc, int mf, int nuf, double sc) {
+        int matT = MAT_I;
+        if (mat != MAT_I) {
+          std::string key;
+          for (auto& kv : B.ids)
+            if (kv.second == mat) key = kv.first;
+          Mat m(n);
+          const HostCSR& h = B.mats[mat];
+          for (int i = 0; i < n; ++i)
+            for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) m(h.col[k], i) = h.val[k];
+          matT = B.add(key + "^T", m);
+        }
+        v.push_back(Term{mat, matT, sfc, mf, nuf, sc});
+      };
+      // reaction matrix R - div(beta)  (Eq. definitions-advection-reaction-eq, Eq. linear-system-...)
+      if (terms & SAP_TERM_MOM) {
         for (int a = 0; a < 3; ++a)
-          if (nonzero[SF_DU + a]) add_term(react, A_id(a), SF_DU + a, MF_V, 0, 1.0);
+          if (nonzero[SF_DU + a]) add_term(react, B.add("E" + std::to_string(a), Tb.E[a]), SF_DU + a, MF_INV_V, 0, 1.0);
         for (int a = 0; a < 3; ++a)
           for (int b = 0; b < 3; ++b)
-            if (nonzero[SF_G + 3 * a + b]) add_term(react, AA_id(a, b), SF_G + 3 * a + b, MF_ONE, 0, 1.0);
-      } else {  // -p d/dp (beta^p/p) = -DU_a A^a / (gamma m p)
+            if (nonzero[SF_G + 3 * a + b])
+              add_term(react, B.add("F" + std::to_string(a) + std::to_string(b), Tb.F[a][b]), SF_G + 3 * a + b, MF_ONE, 0, 1.0);
+      }
+      if (terms & SAP_TERM_ROT)
         for (int a = 0; a < 3; ++a)
-          if (nonzero[SF_DU + a]) add_term(react, A_id(a), SF_DU + a, MF_INV_GMP, 0, -1.0);
-      }
-    }
-    if ((int)react.size() > MAXTERMS) throw std::string("too many reaction terms");
-    // advection terms per axis
-    AxisInfo ax[MAXD];
-    std::memset(ax, 0, sizeof(ax));
-    for (int a = 0; a < c->D; ++a) {
-      AxisInfo& A = ax[a];
-      A.kind = d.axis_kind[a];
-      A.bc_lo = d.bc_lo[a];
-      A.bc_hi = d.bc_hi[a];
-      std::vector<Term> adv;
-      if (is_spatial(A.kind)) {
-        if (terms & SAP_TERM_ADV) {
-          adv.push_back(Term{MAT_I, MAT_I, SF_U + a, MF_ONE, 0, 1.0});
-          adv.push_back(Term{A_id(a), A_id(a), SF_ONE, MF_V, 0, 1.0});
+          if (nonzero[SF_B + a])
+            add_term(react, B.add("Om" + std::to_string(a), Tb.Om[a]), SF_B + a, has_mom ? MF_INV_GM : MF_ONE, 0, -1.0);
+      if (terms & SAP_TERM_COLL) add_term(react, B.add("C", Tb.C), SF_ONE, MF_ONE, 1, 1.0);
+      if (terms & SAP_TERM_ADV)
+        for (int a = 0; a < c->dx; ++a)
+          if (nonzero[SF_G + 3 * a + a]) add_term(react, MAT_I, SF_G + 3 * a + a, MF_ONE, 0, -1.0);
+      if ((terms & SAP_TERM_MOM) && has_mom) {
+        if (!lnp) {  // -d/dp beta^p = +V DU_a A^a + dU_b/dx^a A^a A^b
+          for (int a = 0; a < 3; ++a)
+            if (nonzero[SF_DU + a]) add_term(react, A_id(a), SF_DU + a, MF_V, 0, 1.0);
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+              if (nonzero[SF_G + 3 * a + b]) add_term(react, AA_id(a, b), SF_G + 3 * a + b, MF_ONE, 0, 1.0);
+        } else {  // -p d/dp (beta^p/p) = -DU_a A^a / (gamma m p)
+          for (int a = 0; a < 3; ++a)
+            if (nonzero[SF_DU + a]) add_term(react, A_id(a), SF_DU + a, MF_INV_GMP, 0, -1.0);
         }
-      } else if (terms & SAP_TERM_MOM) {
-        for (int b = 0; b < 3; ++b)
-          if (nonzero[SF_DU + b]) adv.push_back(Term{A_id(b), A_id(b), SF_DU + b, lnp ? MF_GM_OVER_P : MF_GM, 0, -1.0});
-        for (int b = 0; b < 3; ++b)
-          for (int e = 0; e < 3; ++e)
-            if (nonzero[SF_G + 3 * b + e]) adv.push_back(Term{AA_id(b, e), AA_id(b, e), SF_G + 3 * b + e, lnp ? MF_ONE : MF_P, 0, -1.0});
       }
-      if ((int)adv.size() > MAXADV) throw std::string("too many advection terms");
-      A.nadv = (int)adv.size();
-      for (int t = 0; t < A.nadv; ++t) A.adv[t] = adv[t];
-      A.active = A.nadv > 0;
-    }
-    // eigen-pairs of A^x once, rotated for y and z (Sec. 3.2)
-    Mat Wx;
-    std::vector<double> lam;
-    sym_eig_blocks(Tb.A[0], c->Ablocks, Wx, lam);
-    Mat Wa[3];
-    Wa[0] = Wx;
-    Wa[1] = matmul(transpose(Tb.Uz), Wx);
-    Wa[2] = matmul(transpose(Tb.Ux), Wa[1]);
-    for (int a = 0; a < 3; ++a)
-      for (auto& v : Wa[a].a)
-        if (std::fabs(v) < 1e-14) v = 0.0;
-    // face |beta| data
-    std::vector<double> uface_vals[3];
-    bool uface_uni[3] = {true, true, true};
-    double uface_u[3] = {0, 0, 0};
-    for (int a = 0; a < c->dx; ++a) {
-      if (Uface && Uface[a]) uface_vals[a].assign(Uface[a], Uface[a] + c->nsf[a]);
-      else uface_vals[a].assign(c->nsf[a], 0.0);
-      uface_u[a] = uface_vals[a].empty() ? 0.0 : uface_vals[a][0];
-      for (double v : uface_vals[a])
-        if (v != uface_u[a]) uface_uni[a] = false;
-    }
-    std::vector<int> pslot(nsv, -1);
-    std::vector<double> pabs;
-    int npface = c->npc + 1;
-    for (int a = 0; a < c->D; ++a) {
-      AxisInfo& A = ax[a];
-      if (!A.active) continue;
-      if (is_spatial(A.kind)) {
-        if (uface_uni[a] && !has_mom) {  // constant beta: |beta| = W |U + lam V| W^T as one matrix
-          A.route = ABS_CONST;
-          Mat Ab(n);
-          for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n; ++j) {
-              double s = 0.0;
-              for (int k = 0; k < n; ++k) s += Wa[a](i, k) * std::fabs(uface_u[a] + lam[k] * d.V) * Wa[a](j, k);
-              Ab(i, j) = std::fabs(s) < 1e-15 ? 0.0 : s;
-            }
-          A.absmat = B.add("abs" + std::to_string(a), Ab);
+      if ((int)react.size() > MAXTERMS) throw std::string("too many reaction terms");
+      // advection terms per axis
+      AxisInfo ax[MAXD];
+      std::memset(ax, 0, sizeof(ax));
+      for (int a = 0; a < c->D; ++a) {
+        AxisInfo& A = ax[a];
+        A.kind = d.axis_kind[a];
+        A.bc_lo = d.bc_lo[a];
+        A.bc_hi = d.bc_hi[a];
+        std::vector<Term> adv;
+        if (is_spatial(A.kind)) {
+          if (terms & SAP_TERM_ADV) {
+            adv.push_back(Term{MAT_I, MAT_I, SF_U + a, MF_ONE, 0, 1.0});
+            adv.push_back(Term{A_id(a), A_id(a), SF_ONE, MF_V, 0, 1.0});
+          }
+        } else if (terms & SAP_TERM_MOM) {
+          for (int b = 0; b < 3; ++b)
+            if (nonzero[SF_DU + b]) adv.push_back(Term{A_id(b), A_id(b), SF_DU + b, lnp ? MF_GM_OVER_P : MF_GM, 0, -1.0});
+          for (int b = 0; b < 3; ++b)
+            for (int e = 0; e < 3; ++e)
+              if (nonzero[SF_G + 3 * b + e]) adv.push_back(Term{AA_id(b, e), AA_id(b, e), SF_G + 3 * b + e, lnp ? MF_ONE : MF_P, 0, -1.0});
+        }
+        if ((int)adv.size() > MAXADV) throw std::string("too many advection terms");
+        A.nadv = (int)adv.size();
+        for (int t = 0; t < A.nadv; ++t) A.adv[t] = adv[t];
+        A.active = A.nadv > 0;
+      }
+      // eigen-pairs of A^x once, rotated for y and z (Sec. 3.2)
+      Mat Wx;
+      std::vector<double> lam;
+      sym_eig_blocks(Tb.A[0], c->Ablocks, Wx, lam);
+      Mat Wa[3];
+      Wa[0] = Wx;
+      Wa[1] = matmul(transpose(Tb.Uz), Wx);
+      Wa[2] = matmul(transpose(Tb.Ux), Wa[1]);
+      for (int a = 0; a < 3; ++a)
+        for (auto& v : Wa[a].a)
+          if (std::fabs(v) < 1e-14) v = 0.0;
+      // face |beta| data
+      std::vector<double> uface_vals[3];
+      bool uface_uni[3] = {true, true, true};
+      double uface_u[3] = {0, 0, 0};
+      for (int a = 0; a < c->dx; ++a) {
+        if (Uface && Uface[a]) uface_vals[a].assign(Uface[a], Uface[a] + c->nsf[a]);
+        else uface_vals[a].assign(c->nsf[a], 0.0);
+        uface_u[a] = uface_vals[a].empty() ? 0.0 : uface_vals[a][0];
+        for (double v : uface_vals[a])
+          if (v != uface_u[a]) uface_uni[a] = false;
+      }
+      std::vector<int> pslot(nsv, -1);
+      std::vector<double> pabs;
+      int npface = c->npc + 1;
+      for (int a = 0; a < c->D; ++a) {
+        AxisInfo& A = ax[a];
+        if (!A.active) continue;
+        if (is_spatial(A.kind)) {
+          if (uface_uni[a] && !has_mom) {  // constant beta: |beta| = W |U + lam V| W^T as one matrix
+            A.route = ABS_CONST;
+            Mat Ab(n);
+            for (int i = 0; i < n; ++i)
+              for (int j = 0; j < n; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < n; ++k) s += Wa[a](i, k) * std::fabs(uface_u[a] + lam[k] * d.V) * Wa[a](j, k);
+                Ab(i, j) = std::fabs(s) < 1e-15 ? 0.0 : s;
+              }
+            A.absmat = B.add("abs" + std::to_string(a), Ab);
+          } else {
+            A.route = ABS_EIGEN;
+            A.Wmat = B.add("W" + std::to_string(a), Wa[a]);
+            A.WTmat = B.add("WT" + std::to_string(a), transpose(Wa[a]));
+          }
         } else {
-          A.route = ABS_EIGEN;
-          A.Wmat = B.add("W" + std::to_string(a), Wa[a]);
-          A.WTmat = B.add("WT" + std::to_string(a), transpose(Wa[a]));
-        }
-      } else {
-        // momentum faces: eigen-decomposition of beta^p at every (spatial node, p face) point
-        A.route = ABS_POINT;
-        Mat pat(n);
-        for (int t = 0; t < A.nadv; ++t) {
-          const HostCSR& h = B.mats[A.adv[t].mat];
-          for (int i = 0; i < n; ++i)
-            for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) pat(i, h.col[k]) = 1.0;
-        }
-        auto blocks = connected_blocks(pat);
-        Mat full(n);  // block pattern: dense within each block
-        for (auto& b : blocks)
-          for (int i : b)
-            for (int j : b) full(i, j) = 1.0;
-        HostCSR pc = to_csr(full);
-        const int nnzp = (int)pc.col.size();
-        A.absmat = B.add_csr("pabs_pattern", pc);
-        // each term's entries scattered into the block pattern once
-        std::vector<std::vector<std::pair<int, double>>> tpos(A.nadv);
-        for (int t = 0; t < A.nadv; ++t) {
-          const HostCSR& h = B.mats[A.adv[t].mat];
-          for (int i = 0; i < n; ++i)
-            for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) {
-              const int j = h.col[k];
-              int pos = -1;
-              for (int e = pc.rp[i]; e < pc.rp[i + 1]; ++e)
-                if (pc.col[e] == j) pos = e;
-              tpos[t].push_back({pos, h.val[k]});
-            }
-        }
-        std::vector<double> pv(nnzp);
-        auto build_beta = [&](int sp, double p) {  // beta^p at (spatial node, momentum) in the pattern
-          std::fill(pv.begin(), pv.end(), 0.0);
+          // momentum faces: eigen-decomposition of beta^p at every (spatial node, p face) point
+          A.route = ABS_POINT;
+          Mat pat(n);
           for (int t = 0; t < A.nadv; ++t) {
-            const Term& tm = A.adv[t];
-            const double cf = tm.scale * (tm.sf == SF_ONE ? 1.0 : sf[(size_t)tm.sf * nsv + sp]) *
-                              mom_factor_h(tm.mf, p, has_mom, d.V);
-            for (const auto& pr : tpos[t]) pv[pr.first] += cf * pr.second;
-          }
-        };
-        double gmax = 0.0;
-        std::vector<double> pmax(nsv, 0.0);
-        for (int sp = 0; sp < nsv; ++sp)
-          for (int f = 0; f < npface; ++f) {
-            build_beta(sp, c->pface[f]);
-            double mx = 0.0;
-            for (double v : pv) mx = std::max(mx, std::fabs(v));
-            pmax[sp] = std::max(pmax[sp], mx);
-            gmax = std::max(gmax, mx);
-          }
-        // points where |beta^p| stays below 1e-15 of its largest value carry no upwinding term
-        // beyond FP64 rounding of the largest momentum flux; they are skipped
-        int nslot = 0;
-        for (int sp = 0; sp < nsv; ++sp)
-          if (gmax > 0.0 && pmax[sp] > 1e-15 * gmax) pslot[sp] = nslot++;
-        pabs.assign((size_t)nslot * npface * nnzp, 0.0);
-        Mat bm(n), Wb;
-        std::vector<double> lb;
-        for (int sp = 0; sp < nsv; ++sp) {
-          if (pslot[sp] < 0) continue;
-          for (int f = 0; f < npface; ++f) {
-            build_beta(sp, c->pface[f]);
+            const HostCSR& h = B.mats[A.adv[t].mat];
             for (int i = 0; i < n; ++i)
-              for (int e = pc.rp[i]; e < pc.rp[i + 1]; ++e) bm(i, pc.col[e]) = pv[e];
-            sym_eig_blocks(bm, blocks, Wb, lb);
-            double* dst = &pabs[((size_t)pslot[sp] * npface + f) * nnzp];
+              for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) pat(i, h.col[k]) = 1.0;
+          }
+          auto blocks = connected_blocks(pat);
+          Mat full(n);  // block pattern: dense within each block
+          for (auto& b : blocks)
+            for (int i : b)
+              for (int j : b) full(i, j) = 1.0;
+          HostCSR pc = to_csr(full);
+          const int nnzp = (int)pc.col.size();
+          A.absmat = B.add_csr("pabs_pattern", pc);
+          // each term's entries scattered into the block pattern once
+          std::vector<std::vector<std::pair<int, double>>> tpos(A.nadv);
+          for (int t = 0; t < A.nadv; ++t) {
+            const HostCSR& h = B.mats[A.adv[t].mat];
             for (int i = 0; i < n; ++i)
-              for (int k = pc.rp[i]; k < pc.rp[i + 1]; ++k) {
-                int j = pc.col[k];
-                double s2 = 0.0;
-                for (int e = 0; e < n; ++e) s2 += Wb(i, e) * std::fabs(lb[e]) * Wb(j, e);
-                dst[k] = s2;
+              for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) {
+                const int j = h.col[k];
+                int pos = -1;
+                for (int e = pc.rp[i]; e < pc.rp[i + 1]; ++e)
+                  if (pc.col[e] == j) pos = e;
+                tpos[t].push_back({pos, h.val[k]});
               }
           }
+          std::vector<double> pv(nnzp);
+          auto build_beta = [&](int sp, double p) {  // beta^p at (spatial node, momentum) in the pattern
+            std::fill(pv.begin(), pv.end(), 0.0);
+            for (int t = 0; t < A.nadv; ++t) {
+              const Term& tm = A.adv[t];
+              const double cf = tm.scale * (tm.sf == SF_ONE ? 1.0 : sf[(size_t)tm.sf * nsv + sp]) *
+                                mom_factor_h(tm.mf, p, has_mom, d.V);
+              for (const auto& pr : tpos[t]) pv[pr.first] += cf * pr.second;
+            }
+          };
+          double gmax = 0.0;
+          std::vector<double> pmax(nsv, 0.0);
+          for (int sp = 0; sp < nsv; ++sp)
+            for (int f = 0; f < npface; ++f) {
+              build_beta(sp, c->pface[f]);
+              double mx = 0.0;
+              for (double v : pv) mx = std::max(mx, std::fabs(v));
+              pmax[sp] = std::max(pmax[sp], mx);
+              gmax = std::max(gmax, mx);
+            }
+          // points where |beta^p| stays below 1e-15 of its largest value carry no upwinding term
+          // beyond FP64 rounding of the largest momentum flux; they are skipped
+          int nslot = 0;
+          for (int sp = 0; sp < nsv; ++sp)
+            if (gmax > 0.0 && pmax[sp] > 1e-15 * gmax) pslot[sp] = nslot++;
+          pabs.assign((size_t)nslot * npface * nnzp, 0.0);
+          Mat bm(n), Wb;
+          std::vector<double> lb;
+          for (int sp = 0; sp < nsv; ++sp) {
+            if (pslot[sp] < 0) continue;
+            for (int f = 0; f < npface; ++f) {
+              build_beta(sp, c->pface[f]);
+              for (int i = 0; i < n; ++i)
+                for (int e = pc.rp[i]; e < pc.rp[i + 1]; ++e) bm(i, pc.col[e]) = pv[e];
+              sym_eig_blocks(bm, blocks, Wb, lb);
+              double* dst = &pabs[((size_t)pslot[sp] * npface + f) * nnzp];
+              for (int i = 0; i < n; ++i)
+                for (int k = pc.rp[i]; k < pc.rp[i + 1]; ++k) {
+                  int j = pc.col[k];
+                  double s2 = 0.0;
+                  for (int e = 0; e < n; ++e) s2 += Wb(i, e) * std::fabs(lb[e]) * Wb(j, e);
+                  dst[k] = s2;
+                }
+            }
+          }
         }
       }
-    }
-    // upload: bank, fields, term lists
-    std::vector<double> sf_nonuni;  // [SF_NCOMP][nsv], only used for non-uniform components
-    sf_nonuni = sf;
-    std::vector<double> nu_v, s_v;
-    bool nu_uni = true, s_uni = true;
-    double nu_u = nu ? nu[0] : 0.0, s_u = s000 ? s000[0] : 0.0;
-    if (nu)
-      for (int p = 0; p < c->npv; ++p)
-        if (nu[p] != nu_u) { nu_uni = false; break; }
-    if (s000)
-      for (int p = 0; p < c->npv; ++p)
-        if (s000[p] != s_u) { s_uni = false; break; }
-    if (!(terms & SAP_TERM_SRC)) { s_uni = true; s_u = 0.0; }
-    if (!nu_uni) nu_v.assign(nu, nu + c->npv);
-    if (!s_uni) s_v.assign(s000, s000 + c->npv);
-    auto fill = [&](auto& P, auto tag) {
-      using T = decltype(tag);
-      set_bank<T>(P, B, c, fs.bufs);
-      P.nreact = (int)react.size();
-      for (int t = 0; t < P.nreact; ++t) P.react[t] = react[t];
-      for (int a = 0; a < MAXD; ++a) P.ax[a] = ax[a];
-      bool any_nonuni = false;
-      for (int k = 0; k < SF_NCOMP; ++k) {
-        P.sf_is_uni[k] = uni[k];
-        P.sf_uni[k] = T(uval[k]);
-        if (!uni[k]) any_nonuni = true;
-      }
-      if (any_nonuni) {
-        if (sizeof(T) == 8) P.sfield = (const T*)upload(c, sf_nonuni, fs.bufs);
-        else P.sfield = (const T*)upload(c, to_f32(sf_nonuni), fs.bufs);
-      } else {
-        P.sfield = nullptr;
-      }
-      for (int a = 0; a < MAXD; ++a) {
-        P.uface_is_uni[a] = a < c->dx ? uface_uni[a] : 1;
-        P.uface_uni[a] = T(a < c->dx ? uface_u[a] : 0.0);
-        P.uface[a] = nullptr;
-        if (a < c->dx && !uface_uni[a]) {
-          if (sizeof(T) == 8) P.uface[a] = (const T*)upload(c, uface_vals[a], fs.bufs);
-          else P.uface[a] = (const T*)upload(c, to_f32(uface_vals[a]), fs.bufs);
+      // upload: bank, fields, term lists
+      std::vector<double> sf_nonuni;  // [SF_NCOMP][nsv], only used for non-uniform components
+      sf_nonuni = sf;
+      std::vector<double> nu_v, s_v;
+      bool nu_uni = true, s_uni = true;
+      double nu_u = nu ? nu[0] : 0.0, s_u = s000 ? s000[0] : 0.0;
+      if (nu)
+        for (int p = 0; p < c->npv; ++p)
+          if (nu[p] != nu_u) { nu_uni = false; break; }
+      if (s000)
+        for (int p = 0; p < c->npv; ++p)
+          if (s000[p] != s_u) { s_uni = false; break; }
+      if (!(terms & SAP_TERM_SRC)) { s_uni = true; s_u = 0.0; }
+      if (!nu_uni) nu_v.assign(nu, nu + c->npv);
+      if (!s_uni) s_v.assign(s000, s000 + c->npv);
+      auto fill = [&](auto& P, auto tag) {
+        using T = decltype(tag);
+        set_bank<T>(P, B, c, fs.bufs);
+        P.nreact = (int)react.size();
+        for (int t = 0; t < P.nreact; ++t) P.react[t] = react[t];
+        for (int a = 0; a < MAXD; ++a) P.ax[a] = ax[a];
+        bool any_nonuni = false;
+        for (int k = 0; k < SF_NCOMP; ++k) {
+          P.sf_is_uni[k] = uni[k];
+          P.sf_uni[k] = T(uval[k]);
+          if (!uni[k]) any_nonuni = true;
         }
-      }
-      P.nu_uni = T(nu_u);
-      P.nu = nullptr;
-      if (!nu_uni) P.nu = (sizeof(T) == 8) ? (const T*)upload(c, nu_v, fs.bufs) : (const T*)upload(c, to_f32(nu_v), fs.bufs);
-      P.s_uni = T(s_u);
-      P.s000 = nullptr;
-      if (!s_uni) P.s000 = (sizeof(T) == 8) ? (const T*)upload(c, s_v, fs.bufs) : (const T*)upload(c, to_f32(s_v), fs.bufs);
-      P.pslot = (const int*)upload(c, pslot, fs.bufs);
-      if (!pabs.empty())
-        P.pabs = (sizeof(T) == 8) ? (const T*)upload(c, pabs, fs.bufs) : (const T*)upload(c, to_f32(pabs), fs.bufs);
-      else
-        P.pabs = nullptr;
-      P.lam = (sizeof(T) == 8) ? (const T*)upload(c, lam, fs.bufs) : (const T*)upload(c, to_f32(lam), fs.bufs);
-      // the momentum-face |beta| values again in the ELL order of their pattern matrix
-      P.pabs_ell = nullptr;
-      for (int a = 0; a < c->D; ++a) {
-        const AxisInfo& A = ax[a];
-        if (!A.active || A.route != ABS_POINT || pabs.empty()) continue;
-        const HostCSR& pc = B.mats[A.absmat];
-        const int w = P.bank.ell_w[A.absmat];
-        const int nnzp = (int)pc.col.size();
-        const size_t npts = pabs.size() / nnzp;  // slots x momentum faces
-        std::vector<double> pe(npts * w * n, 0.0);
-        for (size_t sp = 0; sp < npts; ++sp)
-          for (int i = 0; i < n; ++i)
-            for (int k = 0; pc.rp[i] + k < pc.rp[i + 1]; ++k) pe[(sp * w + k) * n + i] = pabs[sp * nnzp + pc.rp[i] + k];
-        P.pabs_ell = (sizeof(T) == 8) ? (const T*)upload(c, pe, fs.bufs) : (const T*)upload(c, to_f32(pe), fs.bufs);
-      }
-      // terms whose coefficient is one number for the whole problem
-      auto term_uni = [&](const Term& tm) {
-        return (tm.sf == SF_ONE || uni[tm.sf]) && (tm.mf == MF_ONE || !has_mom) && (!tm.nu || nu_uni);
+        if (any_nonuni) {
+          if (sizeof(T) == 8) P.sfield = (const T*)upload(c, sf_nonuni, fs.bufs);
+          else P.sfield = (const T*)upload(c, to_f32(sf_nonuni), fs.bufs);
+        } else {
+          P.sfield = nullptr;
+        }
+        for (int a = 0; a < MAXD; ++a) {
+          P.uface_is_uni[a] = a < c->dx ? uface_uni[a] : 1;
+          P.uface_uni[a] = T(a < c->dx ? uface_u[a] : 0.0);
+          P.uface[a] = nullptr;
+          if (a < c->dx && !uface_uni[a]) {
+            if (sizeof(T) == 8) P.uface[a] = (const T*)upload(c, uface_vals[a], fs.bufs);
+            else P.uface[a] = (const T*)upload(c, to_f32(uface_vals[a]), fs.bufs);
+          }
+        }
+        P.nu_uni = T(nu_u);
+        P.nu = nullptr;
+        if (!nu_uni) P.nu = (sizeof(T) == 8) ? (const T*)upload(c, nu_v, fs.bufs) : (const T*)upload(c, to_f32(nu_v), fs.bufs);
+        P.s_uni = T(s_u);
+        P.s000 = nullptr;
+        if (!s_uni) P.s000 = (sizeof(T) == 8) ? (const T*)upload(c, s_v, fs.bufs) : (const T*)upload(c, to_f32(s_v), fs.bufs);
+        P.pslot = (const int*)upload(c, pslot, fs.bufs);
+        if (!pabs.empty())
+          P.pabs = (sizeof(T) == 8) ? (const T*)upload(c, pabs, fs.bufs) : (const T*)upload(c, to_f32(pabs), fs.bufs);
+        else
+          P.pabs = nullptr;
+        P.lam = (sizeof(T) == 8) ? (const T*)upload(c, lam, fs.bufs) : (const T*)upload(c, to_f32(lam), fs.bufs);
+        // the momentum-face |beta| values again in the ELL order of their pattern matrix
+        P.pabs_ell = nullptr;
+        for (int a = 0; a < c->D; ++a) {
+          const AxisInfo& A = ax[a];
+          if (!A.active || A.route != ABS_POINT || pabs.empty()) continue;
+          const HostCSR& pc = B.mats[A.absmat];
+          const int w = P.bank.ell_w[A.absmat];
+          const int nnzp = (int)pc.col.size();
+          const size_t npts = pabs.size() / nnzp;  // slots x momentum faces
+          std::vector<double> pe(npts * w * n, 0.0);
+          for (size_t sp = 0; sp < npts; ++sp)
+            for (int i = 0; i < n; ++i)
+              for (int k = 0; pc.rp[i] + k < pc.rp[i + 1]; ++k) pe[(sp * w + k) * n + i] = pabs[sp * nnzp + pc.rp[i] + k];
+          P.pabs_ell = (sizeof(T) == 8) ? (const T*)upload(c, pe, fs.bufs) : (const T*)upload(c, to_f32(pe), fs.bufs);
+        }
+        // terms whose coefficient is one number for the whole problem
+        auto term_uni = [&](const Term& tm) {
+          return (tm.sf == SF_ONE || uni[tm.sf]) && (tm.mf == MF_ONE || !has_mom) && (!tm.nu || nu_uni);
+        };
+        P.react_uni = 0u;
+        for (int t = 0; t < P.nreact; ++t)
+          if (term_uni(P.react[t])) P.react_uni |= 1u << t;
+        for (int a = 0; a < MAXD; ++a) {
+          P.adv_uni[a] = 0u;
+          for (int t = 0; t < P.ax[a].nadv; ++t)
+            if (term_uni(P.ax[a].adv[t])) P.adv_uni[a] |= 1u << t;
+        }
       };
-      P.react_uni = 0u;
-      for (int t = 0; t < P.nreact; ++t)
-        if (term_uni(P.react[t])) P.react_uni |= 1u << t;
-      for (int a = 0; a < MAXD; ++a) {
-        P.adv_uni[a] = 0u;
-        for (int t = 0; t < P.ax[a].nadv; ++t)
-          if (term_uni(P.ax[a].adv[t])) P.adv_uni[a] |= 1u << t;
-      }
-    };
-    fill(c->p64, double{});
-    fill(c->p32, float{});
-    c->fields_set = true;
-    c->fields_version += 1;
-    c->cn_prev_valid = false;
-  } catch (const std::string& e) {
-    c->err = "sap_set_fields: " + e;
-    return SAP_ENOMEM;
-  }
-  return SAP_OK;
+      fill(c->p64, double{});
+      fill(c->p32, float{});
+      c->fields_set = true;
+      c->fields_version += 1;
+      c->cn_prev_valid = false;
+    } catch (const std::string& e) {
+      c->err = "sap_set_fields: " + e;
+      return SAP_ENOMEM;
+    }
+    return SAP_OK;
+  });
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -917,184 +958,198 @@ static bool ensure_ws32(sap_ctx* c, int count) {
 }
 
 extern "C" sap_status sap_apply_operator(sap_handle c, const void* x, void* y, int mode, sap_stream stream) {
-  if (!c || !x || !y || x == y) return SAP_EINVAL;
-  if (!c->sub.empty()) {
-    if (mode != SAP_APPLY_D && mode != SAP_APPLY_RHS) return SAP_EUNSUPPORTED;
-    return batch_apply(c, x, y, mode, (cudaStream_t)stream);
-  }
-  if (!c->fields_set) {
-    c->err = "fields not set";
-    return SAP_EINVAL;
-  }
-  if (mode != SAP_APPLY_D && mode != SAP_APPLY_RHS && mode != SAP_APPLY_T) {
-    c->err = "unsupported apply mode";
-    return SAP_EUNSUPPORTED;
-  }
-  cudaError_t e = c->prec == SAP_PREC_FP64
-                      ? launch_apply64(c->p64, (const double*)x, (double*)y, mode, (cudaStream_t)stream)
-                      : launch_apply32(c->p32, (const float*)x, (float*)y, mode, (cudaStream_t)stream);
-  if (e != cudaSuccess) {
-    c->err = std::string("apply: ") + cudaGetErrorString(e);
-    return SAP_ECUDA;
-  }
-  return SAP_OK;
+  return guarded(c, "sap_apply_operator", [&]() -> sap_status {
+    if (!c || !x || !y || x == y) return SAP_EINVAL;
+    if (!c->sub.empty()) {
+      if (mode != SAP_APPLY_D && mode != SAP_APPLY_RHS) return SAP_EUNSUPPORTED;
+      return batch_apply(c, x, y, mode, (cudaStream_t)stream);
+    }
+    if (!c->fields_set) {
+      c->err = "fields not set";
+      return SAP_EINVAL;
+    }
+    if (mode != SAP_APPLY_D && mode != SAP_APPLY_RHS && mode != SAP_APPLY_T) {
+      c->err = "unsupported apply mode";
+      return SAP_EUNSUPPORTED;
+    }
+    cudaError_t e = c->prec == SAP_PREC_FP64
+                        ? launch_apply64(c->p64, (const double*)x, (double*)y, mode, (cudaStream_t)stream)
+                        : launch_apply32(c->p32, (const float*)x, (float*)y, mode, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+      c->err = std::string("apply: ") + cudaGetErrorString(e);
+      return SAP_ECUDA;
+    }
+    return SAP_OK;
+  });
 }
 
 extern "C" sap_status sap_step_erk(sap_handle c, double* state, double dt, int nsteps, sap_stream stream) {
-  if (!c || !state || nsteps < 0) return SAP_EINVAL;
-  c->cn_prev_valid = false;  // the RK4 stage buffers share the workspace
-  if (!c->sub.empty()) {
+  return guarded(c, "sap_step_erk", [&]() -> sap_status {
+    if (!c || !state || nsteps < 0) return SAP_EINVAL;
+    c->cn_prev_valid = false;  // the RK4 stage buffers share the workspace
+    if (!c->sub.empty()) {
+      if (c->prec == SAP_PREC_FP64 ? !ensure_ws64(c, 3) : (!ensure_ws32(c, 2) || !ensure_ws64(c, 1))) {
+        c->err = "erk: workspace allocation failed";
+        return SAP_ENOMEM;
+      }
+      return batch_erk(c, state, dt, nsteps, (cudaStream_t)stream);
+    }
+    if (!c->fields_set) {
+      c->err = "fields not set";
+      return SAP_EINVAL;
+    }
     if (c->prec == SAP_PREC_FP64 ? !ensure_ws64(c, 3) : (!ensure_ws32(c, 2) || !ensure_ws64(c, 1))) {
       c->err = "erk: workspace allocation failed";
       return SAP_ENOMEM;
     }
-    return batch_erk(c, state, dt, nsteps, (cudaStream_t)stream);
-  }
-  if (!c->fields_set) {
-    c->err = "fields not set";
-    return SAP_EINVAL;
-  }
-  if (c->prec == SAP_PREC_FP64 ? !ensure_ws64(c, 3) : (!ensure_ws32(c, 2) || !ensure_ws64(c, 1))) {
-    c->err = "erk: workspace allocation failed";
-    return SAP_ENOMEM;
-  }
-  return erk_steps(c, state, dt, nsteps, (cudaStream_t)stream);
+    return erk_steps(c, state, dt, nsteps, (cudaStream_t)stream);
+  });
 }
 
 extern "C" sap_status sap_step_erk_noalloc(sap_handle c, double* state, double dt, int nsteps, sap_stream stream) {
-  if (!c || !state || nsteps < 0) return SAP_EINVAL;
-  if (!c->fields_set) {
-    c->err = "fields not set";
-    return SAP_EINVAL;
-  }
-  return erk_steps_noalloc(c, state, dt, nsteps, (cudaStream_t)stream);
+  return guarded(c, "sap_step_erk_noalloc", [&]() -> sap_status {
+    if (!c || !state || nsteps < 0) return SAP_EINVAL;
+    if (!c->fields_set) {
+      c->err = "fields not set";
+      return SAP_EINVAL;
+    }
+    return erk_steps_noalloc(c, state, dt, nsteps, (cudaStream_t)stream);
+  });
 }
 
 extern "C" sap_status sap_step_cn(sap_handle c, double* state, double dt, int nsteps, double tol, int restart,
                                   int maxit, sap_solver_stats* stats, sap_stream stream) {
-  if (!c || !state || nsteps < 0 || restart < 1 || restart > 31 || maxit < 1 || !(tol > 0)) return SAP_EINVAL;
-  if (!c->sub.empty()) {
-    const bool ok = c->prec == SAP_PREC_FP64 ? ensure_ws64(c, restart + 3) : (ensure_ws32(c, restart + 1) && ensure_ws64(c, 2));
-    if (!ok) {
-      c->err = "cn: workspace allocation failed";
-      return SAP_ENOMEM;
+  return guarded(c, "sap_step_cn", [&]() -> sap_status {
+    if (!c || !state || nsteps < 0 || restart < 1 || restart > 31 || maxit < 1 || !(tol > 0)) return SAP_EINVAL;
+    if (!c->sub.empty()) {
+      const bool ok = c->prec == SAP_PREC_FP64 ? ensure_ws64(c, restart + 3) : (ensure_ws32(c, restart + 1) && ensure_ws64(c, 2));
+      if (!ok) {
+        c->err = "cn: workspace allocation failed";
+        return SAP_ENOMEM;
+      }
+      return batch_cn(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
     }
-    return batch_cn(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
-  }
-  if (!c->fields_set) {
-    c->err = "fields not set";
-    return SAP_EINVAL;
-  }
-  if (c->prec == SAP_PREC_FP32) {
-    if (c->ws64_count < 3) c->cn_prev_valid = false;
-    if (!ensure_ws32(c, restart + 1) || !ensure_ws64(c, 3)) {
+    if (!c->fields_set) {
+      c->err = "fields not set";
+      return SAP_EINVAL;
+    }
+    if (c->prec == SAP_PREC_FP32) {
+      if (c->ws64_count < 3) c->cn_prev_valid = false;
+      if (!ensure_ws32(c, restart + 1) || !ensure_ws64(c, 3)) {
+        c->err = "cn: workspace allocation failed";
+        return SAP_ENOMEM;
+      }
+      return cn_steps(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
+    }
+    if (c->ws64_count < restart + 4) c->cn_prev_valid = false;  // the history lives in the workspace
+    if (!ensure_ws64(c, restart + 4)) {
       c->err = "cn: workspace allocation failed";
       return SAP_ENOMEM;
     }
     return cn_steps(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
-  }
-  if (c->ws64_count < restart + 4) c->cn_prev_valid = false;  // the history lives in the workspace
-  if (!ensure_ws64(c, restart + 4)) {
-    c->err = "cn: workspace allocation failed";
-    return SAP_ENOMEM;
-  }
-  return cn_steps(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
+  });
 }
 
 extern "C" sap_status sap_apply_cost(sap_handle c, double* flops, double* bytes) {
-  if (!c || !flops || !bytes) return SAP_EINVAL;
-  if (!c->sub.empty()) {
-    double f = 0, b = 0;
-    for (auto* s2 : c->sub) {
-      double f1, b1;
-      sap_status st = sap_apply_cost(s2, &f1, &b1);
-      if (st != SAP_OK) return st;
-      f += f1;
-      b += b1;
+  return guarded(c, "sap_apply_cost", [&]() -> sap_status {
+    if (!c || !flops || !bytes) return SAP_EINVAL;
+    if (!c->sub.empty()) {
+      double f = 0, b = 0;
+      for (auto* s2 : c->sub) {
+        double f1, b1;
+        sap_status st = sap_apply_cost(s2, &f1, &b1);
+        if (st != SAP_OK) return st;
+        f += f1;
+        b += b1;
+      }
+      *flops = f;
+      *bytes = b;
+      return SAP_OK;
     }
-    *flops = f;
-    *bytes = b;
+    if (!c->fields_set) return SAP_EINVAL;
+    const OpParams<double>& P = c->p64;
+    const int n = c->n, nloc = c->nloc, nfp = c->nfp, q = c->q, D = c->D;
+    auto nnz_row_avg = [&](int mat) -> double {
+      if (mat == MAT_I) return 1.0;
+      const std::vector<int>* rp = nullptr;
+      (void)rp;
+      return c->bank_nnz[mat] / double(n);
+    };
+    double per_cell = 0.0;
+    int nvt = P.nreact;
+    for (int a = 0; a < D; ++a) nvt += P.ax[a].nadv;
+    per_cell += 4.0 * nvt * nloc;                       // coefficient tables
+    const double faces = 2.0 * D * n * nfp;            // face entries per cell
+    per_cell += 2.0 * faces * 2.0 * q;                  // own + neighbour traces
+    per_cell += 2.0 * faces;                            // sum / difference
+    for (int a = 0; a < D; ++a) {
+      const AxisInfo& A = P.ax[a];
+      if (!A.active) continue;
+      const double fe = 2.0 * n * nfp;  // this axis' face entries per cell
+      double f = 1.0;
+      for (int t = 0; t < A.nadv; ++t) f += 2.0 * nnz_row_avg(A.adv[t].mat) + 2.0;
+      if (A.route == ABS_EIGEN) f += 2.0 * nnz_row_avg(A.WTmat) + 3.0 + 2.0 * nnz_row_avg(A.Wmat) + 2.0;
+      else f += 2.0 * nnz_row_avg(A.absmat) + 1.0;
+      per_cell += fe * f;
+      double v = 0.0;  // volume advection per DoF
+      for (int t = 0; t < A.nadv; ++t) v += 2.0 * nnz_row_avg(A.adv[t].mat) + 2.0;
+      v += 2.0 * q + 6.0;  // derivative and lifts
+      per_cell += v * n * nloc;
+    }
+    double rx = 0.0;
+    for (int t = 0; t < P.nreact; ++t) rx += 2.0 * nnz_row_avg(P.react[t].mat) + 2.0;
+    per_cell += (rx + 4.0) * n * nloc;
+    *flops = per_cell * c->ncell;
+    *bytes = 2.0 * (double)c->N * (c->prec == SAP_PREC_FP64 ? 8.0 : 4.0);
     return SAP_OK;
-  }
-  if (!c->fields_set) return SAP_EINVAL;
-  const OpParams<double>& P = c->p64;
-  const int n = c->n, nloc = c->nloc, nfp = c->nfp, q = c->q, D = c->D;
-  auto nnz_row_avg = [&](int mat) -> double {
-    if (mat == MAT_I) return 1.0;
-    const std::vector<int>* rp = nullptr;
-    (void)rp;
-    return c->bank_nnz[mat] / double(n);
-  };
-  double per_cell = 0.0;
-  int nvt = P.nreact;
-  for (int a = 0; a < D; ++a) nvt += P.ax[a].nadv;
-  per_cell += 4.0 * nvt * nloc;                       // coefficient tables
-  const double faces = 2.0 * D * n * nfp;            // face entries per cell
-  per_cell += 2.0 * faces * 2.0 * q;                  // own + neighbour traces
-  per_cell += 2.0 * faces;                            // sum / difference
-  for (int a = 0; a < D; ++a) {
-    const AxisInfo& A = P.ax[a];
-    if (!A.active) continue;
-    const double fe = 2.0 * n * nfp;  // this axis' face entries per cell
-    double f = 1.0;
-    for (int t = 0; t < A.nadv; ++t) f += 2.0 * nnz_row_avg(A.adv[t].mat) + 2.0;
-    if (A.route == ABS_EIGEN) f += 2.0 * nnz_row_avg(A.WTmat) + 3.0 + 2.0 * nnz_row_avg(A.Wmat) + 2.0;
-    else f += 2.0 * nnz_row_avg(A.absmat) + 1.0;
-    per_cell += fe * f;
-    double v = 0.0;  // volume advection per DoF
-    for (int t = 0; t < A.nadv; ++t) v += 2.0 * nnz_row_avg(A.adv[t].mat) + 2.0;
-    v += 2.0 * q + 6.0;  // derivative and lifts
-    per_cell += v * n * nloc;
-  }
-  double rx = 0.0;
-  for (int t = 0; t < P.nreact; ++t) rx += 2.0 * nnz_row_avg(P.react[t].mat) + 2.0;
-  per_cell += (rx + 4.0) * n * nloc;
-  *flops = per_cell * c->ncell;
-  *bytes = 2.0 * (double)c->N * (c->prec == SAP_PREC_FP64 ? 8.0 : 4.0);
-  return SAP_OK;
+  });
 }
 
 extern "C" sap_status sap_adjoint_step_cn(sap_handle c, const double* zeta_prev, const double* zeta_next,
                                           double* lambda, double dt, double tol, int restart, int maxit,
                                           double* mu_out, double* grad_nu, sap_solver_stats* stats,
                                           sap_stream stream) {
-  if (!c || !zeta_prev || !zeta_next || !lambda || restart < 1 || restart > 31 || maxit < 1 || !(tol > 0))
-    return SAP_EINVAL;
-  if (!c->sub.empty() || c->prec != SAP_PREC_FP64) {
-    c->err = "adjoint: FP64 single-problem contexts only";
-    return SAP_EUNSUPPORTED;
-  }
-  if (!c->fields_set) {
-    c->err = "fields not set";
-    return SAP_EINVAL;
-  }
-  if (!ensure_ws64(c, restart + 4)) {
-    c->err = "adjoint: workspace allocation failed";
-    return SAP_ENOMEM;
-  }
-  c->cn_prev_valid = false;  // the adjoint solve shares the workspace
-  return adjoint_cn_step(c, zeta_prev, zeta_next, lambda, dt, tol, restart, maxit, mu_out, grad_nu, stats,
-                         (cudaStream_t)stream);
+  return guarded(c, "sap_adjoint_step_cn", [&]() -> sap_status {
+    if (!c || !zeta_prev || !zeta_next || !lambda || restart < 1 || restart > 31 || maxit < 1 || !(tol > 0))
+      return SAP_EINVAL;
+    if (!c->sub.empty() || c->prec != SAP_PREC_FP64) {
+      c->err = "adjoint: FP64 single-problem contexts only";
+      return SAP_EUNSUPPORTED;
+    }
+    if (!c->fields_set) {
+      c->err = "fields not set";
+      return SAP_EINVAL;
+    }
+    if (!ensure_ws64(c, restart + 4)) {
+      c->err = "adjoint: workspace allocation failed";
+      return SAP_ENOMEM;
+    }
+    c->cn_prev_valid = false;  // the adjoint solve shares the workspace
+    return adjoint_cn_step(c, zeta_prev, zeta_next, lambda, dt, tol, restart, maxit, mu_out, grad_nu, stats,
+                           (cudaStream_t)stream);
+  });
 }
 
 extern "C" sap_status sap_adjoint_step_erk(sap_handle c, const double* zeta_prev, double* lambda, double dt,
                                            double* grad_nu, double* stages_out, sap_solver_stats* stats,
                                            sap_stream stream) {
-  if (!c || !zeta_prev || !lambda || !std::isfinite(dt)) return SAP_EINVAL;
-  if (!c->sub.empty() || c->prec != SAP_PREC_FP64) {
-    c->err = "adjoint: FP64 single-problem contexts only";
-    return SAP_EUNSUPPORTED;
-  }
-  if (!c->fields_set) {
-    c->err = "fields not set";
-    return SAP_EINVAL;
-  }
-  if (!ensure_ws64(c, 8)) {
-    c->err = "adjoint: workspace allocation failed";
-    return SAP_ENOMEM;
-  }
-  c->cn_prev_valid = false;  // the adjoint step shares the workspace
-  return adjoint_erk_step(c, zeta_prev, lambda, dt, grad_nu, stages_out, stats, (cudaStream_t)stream);
+  return guarded(c, "sap_adjoint_step_erk", [&]() -> sap_status {
+    if (!c || !zeta_prev || !lambda || !std::isfinite(dt)) return SAP_EINVAL;
+    if (!c->sub.empty() || c->prec != SAP_PREC_FP64) {
+      c->err = "adjoint: FP64 single-problem contexts only";
+      return SAP_EUNSUPPORTED;
+    }
+    if (!c->fields_set) {
+      c->err = "fields not set";
+      return SAP_EINVAL;
+    }
+    if (!ensure_ws64(c, 8)) {
+      c->err = "adjoint: workspace allocation failed";
+      return SAP_ENOMEM;
+    }
+    c->cn_prev_valid = false;  // the adjoint step shares the workspace
+    return adjoint_erk_step(c, zeta_prev, lambda, dt, grad_nu, stages_out, stats, (cudaStream_t)stream);
+  });
 }
 
 extern "C" sap_status sap_destroy(sap_handle c) {
@@ -1131,18 +1186,20 @@ extern "C" const char* sap_last_error(sap_handle c) {
 }
 
 extern "C" sap_status sap_coupling_matrix(int lmax, int which, int a, int b, double* out) {
-  if (lmax < 0 || lmax > 11 || !out || a < 0 || a > 2 || b < 0 || b > 2) return SAP_EINVAL;
-  SHTables T = build_sh_tables(lmax);
-  const Mat* m = nullptr;
-  switch (which) {
-    case 0: m = &T.A[a]; break;
-    case 1: m = &T.Om[a]; break;
-    case 2: m = &T.C; break;
-    case 3: m = &T.AA[a][b]; break;
-    case 4: m = &T.E[a]; break;
-    case 5: m = &T.F[a][b]; break;
-    default: return SAP_EINVAL;
-  }
-  std::memcpy(out, m->a.data(), sizeof(double) * m->a.size());
-  return SAP_OK;
+  return guarded(nullptr, "sap_coupling_matrix", [&]() -> sap_status {
+    if (lmax < 0 || lmax > 11 || !out || a < 0 || a > 2 || b < 0 || b > 2) return SAP_EINVAL;
+    SHTables T = build_sh_tables(lmax);
+    const Mat* m = nullptr;
+    switch (which) {
+      case 0: m = &T.A[a]; break;
+      case 1: m = &T.Om[a]; break;
+      case 2: m = &T.C; break;
+      case 3: m = &T.AA[a][b]; break;
+      case 4: m = &T.E[a]; break;
+      case 5: m = &T.F[a][b]; break;
+      default: return SAP_EINVAL;
+    }
+    std::memcpy(out, m->a.data(), sizeof(double) * m->a.size());
+    return SAP_OK;
+  });
 }
