@@ -137,3 +137,30 @@ def test_adjoint_erk_U1_gradient_vs_finite_differences(setup):
     e = 1e-5 * 0.1
     fd = (_J_forward(S, None, 0.1 + e) - _J_forward(S, None, 0.1 - e)) / (2 * e)
     assert abs(fd - g_u1) < 1e-5 * abs(fd), (fd, g_u1)
+
+
+def test_adjoint_steps_degenerate_inputs(setup):
+    """lambda = 0: the CN adjoint solve has a zero right side (mu = 0 without iterating) and both
+    steps return lambda = 0 and leave the nu-gradient unchanged; dt = 0: the RK4 step is the
+    identity, so its adjoint returns lambda unchanged."""
+    torch = setup["torch"]
+    sol = setup["sapgpu"].Solver(setup["make"](None, 0.1))
+    N = sol.N
+    g = torch.Generator(device="cuda").manual_seed(9)
+    zp = torch.randn(N, device="cuda", dtype=torch.float64, generator=g)
+    zn = torch.randn(N, device="cuda", dtype=torch.float64, generator=g)
+    grad = torch.randn(len(setup["nu_nodes"]), device="cuda", dtype=torch.float64, generator=g)
+    grad0 = grad.clone()
+    lam = torch.zeros(N, device="cuda", dtype=torch.float64)
+    mu = torch.full((N,), 7.0, device="cuda", dtype=torch.float64)
+    st = sol.adjoint_step_cn(zp, zn, lam, 1.0, 1e-12, 30, 100, mu_out=mu, grad_nu=grad)
+    assert st.iterations == 0 and not lam.any() and not mu.any()
+    sol.adjoint_step_erk(zp, lam, DT, grad_nu=grad)
+    torch.cuda.synchronize()
+    assert not lam.any() and torch.equal(grad, grad0)
+    lam1 = torch.randn(N, device="cuda", dtype=torch.float64, generator=g)
+    lam2 = lam1.clone()
+    sol.adjoint_step_erk(zp, lam2, 0.0)
+    torch.cuda.synchronize()
+    assert torch.equal(lam1, lam2)
+    sol.close()
