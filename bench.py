@@ -121,7 +121,8 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        logdir = os.environ.get("SAP_BENCH_LOGDIR", os.path.join(ROOT, "bench_logs"))
+        self.path = os.path.join(logdir, f"clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
