@@ -26,7 +26,11 @@
  *    f^0 at the nodes.
  *  - Streams: compute entry points take a cudaStream_t (0 = legacy default stream) and are
  *    asynchronous with respect to the host unless stated otherwise.
- *  - Thread safety: one handle must not be used from two host threads at once.
+ *  - Thread safety: one handle must not be used from two host threads at once.  Different
+ *    handles may be used from different threads and on different devices (each handle lives on
+ *    the device that was current at sap_create; make that device current for its calls).
+ *  - Aliasing: device buffers passed to one call must not overlap unless the call says so (a
+ *    vector updated in place, such as `state` or `lambda`, is one buffer).
  */
 #ifndef SAP_H
 #define SAP_H
