@@ -36,10 +36,11 @@ def rk4(M, D, h, zeta0, dt, nsteps, callback=None):
 
 
 def rk4_tangent(M, D, h, dD, zeta0, dt, nsteps):
-    """Tangent of the RK4 trajectory along a parameter direction with dD = dD/dtheta.  Each stage
-    derivative k_i = F(Y_i), F(z) = M^-1 (h - D z), has the tangent dk_i = -M^-1 (dD Y_i + D dY_i),
-    with dY_1 = d, dY_2 = d + dt/2 dk_1, dY_3 = d + dt/2 dk_2, dY_4 = d + dt dk_3, and the step gives
-    d <- d + dt/6 (dk_1 + 2 dk_2 + 2 dk_3 + dk_4), d^0 = 0.  Returns (z^N, d^N)."""
+    """Tangent of the RK4 trajectory (Sec. 3.4) along a parameter direction with dD = dD/dtheta.
+    Each stage derivative k_i = F(Y_i), F(z) = M^-1 (h - D z), has the tangent
+    dk_i = -M^-1 (dD Y_i + D dY_i), with dY_1 = d, dY_2 = d + dt/2 dk_1, dY_3 = d + dt/2 dk_2,
+    dY_4 = d + dt dk_3, and the step gives d <- d + dt/6 (dk_1 + 2 dk_2 + 2 dk_3 + dk_4), d^0 = 0.
+    Returns (z^N, d^N)."""
     Mlu = spla.splu(sp.csc_matrix(M))
     F = lambda z: Mlu.solve(h - D @ z)
     dF = lambda z, dz: -Mlu.solve(dD @ z + D @ dz)
@@ -60,10 +61,10 @@ def rk4_tangent(M, D, h, dD, zeta0, dt, nsteps):
 
 
 def rk4_step_transpose(LT, dt, lam):
-    """Transpose of the linear part of one RK4 step.  For zeta' = s - L zeta with a constant
-    operator L, the classical RK4 step maps zeta to R zeta + const, with R the stability polynomial
-    sum_{j=0..4} (-dt L)^j / j!, so dJ/dzeta = R^T dJ/dzeta' = sum_j (-dt L^T)^j / j! lam.  ``LT``
-    applies L^T; the sum is taken by Horner's rule:
+    """Transpose of the linear part of one RK4 step (Sec. 3.4).  For zeta' = s - L zeta with a
+    constant operator L, the classical RK4 step maps zeta to R zeta + const, with R the stability
+    polynomial sum_{j=0..4} (-dt L)^j / j!, so dJ/dzeta = R^T dJ/dzeta' = sum_j (-dt L^T)^j / j! lam.
+    ``LT`` applies L^T; the sum is taken by Horner's rule:
     lam + (-dt L^T)(lam + (-dt L^T)/2 (lam + (-dt L^T)/3 (lam + (-dt L^T)/4 lam)))."""
     lam = np.asarray(lam, dtype=float)
     v = lam.copy()
