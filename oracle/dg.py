@@ -460,3 +460,18 @@ def project_initial(disc: Discretisation, f0):
     fv = f0(pts.reshape(-1, m.D)).reshape(m.ncell, -1, n)  # (ncell, nq, n)
     b = np.einsum("cq,cqr,qa->cra", W, fv, Phi).ravel()
     return spla.spsolve(disc.M.tocsc(), b)
+
+
+def parameter_derivative(make_problem, theta, step):
+    """dD/dtheta of the assembled dG matrix D (Eq. definition-mass-and-dg-matrix) for a family of
+    problems ``theta -> make_problem(theta)``, by the fourth-order Richardson central difference
+
+        dD ~ (8 [D(theta + s) - D(theta - s)] - [D(theta + 2 s) - D(theta - 2 s)]) / (12 s).
+
+    Used for parameters that enter D non-linearly (the shock speed U1 enters U, grad U, dU/dt and,
+    through the eigen-decompositions of n.beta, the upwind splits of Eq. definition-upwind-flux).
+    The upwind split |beta| has a kink where an eigenvalue changes sign; away from such points the
+    difference is accurate to O(s^4).  M does not depend on the fields."""
+    Ds = {k: Discretisation(make_problem(theta + k * step)).D for k in (-2, -1, 1, 2)}
+    return (8.0 * (Ds[1] - Ds[-1]) - (Ds[2] - Ds[-2])) / (12.0 * step)
+

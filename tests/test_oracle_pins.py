@@ -538,3 +538,64 @@ def test_cn_tangent_matches_trajectory_differences():
         zs.append(steppers.theta_method(d.M, d.D, d.h, np.zeros(d.N), 1.0, 5))
     fd = (zs[0] - zs[1]) / (2 * eps)
     assert np.abs(fd - dz).max() < 1e-7 * np.abs(dz).max()
+
+
+def _shock_u1_family():
+    def make(U1):
+        return W.shock(nx=8, npc=5, lmax=2, xr=(-6.0, 6.0), lnpr=(0.0, 3.0), U1=U1, Ls=1.0)
+    return make
+
+
+@pytest.mark.parametrize("scheme", ["cn", "rk4"])
+def test_u1_tangent_matches_trajectory_differences(scheme):
+    """The oracle's tangent of the trajectory with respect to the shock speed U1 (Richardson
+    difference of the assembled D fed through the CN / RK4 tangent recursions) equals a central
+    difference of the oracle's own trajectories at U1 +- e.  U1 enters U, grad U, dU/dt and the
+    upwind splits, so neither side is exact: the bound is the O(e^2) truncation of the trajectory
+    difference.  A wrong Richardson weight (planted in a copy below) fails the same bound."""
+    make = _shock_u1_family()
+    u1 = 0.1
+    d0 = dg.Discretisation(make(u1))
+    dD = dg.parameter_derivative(make, u1, 1e-3 * u1)
+    dt, nsteps = (1.0, 5) if scheme == "cn" else (0.01, 5)
+    if scheme == "cn":
+        _, dz = steppers.cn_tangent(d0.M, d0.D, d0.h, dD, np.zeros(d0.N), dt, nsteps)
+        run = lambda d: steppers.theta_method(d.M, d.D, d.h, np.zeros(d.N), dt, nsteps)
+    else:
+        _, dz = steppers.rk4_tangent(d0.M, d0.D, d0.h, dD, np.zeros(d0.N), dt, nsteps)
+        run = lambda d: steppers.rk4(d.M, d.D, d.h, np.zeros(d.N), dt, nsteps)
+    e = 1e-4 * u1
+    fd = (run(dg.Discretisation(make(u1 + e))) - run(dg.Discretisation(make(u1 - e)))) / (2 * e)
+    scale = np.abs(dz).max()
+    assert scale > 0
+    assert np.abs(fd - dz).max() < 1e-8 * scale
+    # planted mistake: a wrong Richardson weight (7 instead of 8) is detected
+    Ds = {k: dg.Discretisation(make(u1 + k * 1e-3 * u1)).D for k in (-2, -1, 1, 2)}
+    bad = (7.0 * (Ds[1] - Ds[-1]) - (Ds[2] - Ds[-2])) / (12.0 * 1e-3 * u1)
+    if scheme == "cn":
+        _, dz_bad = steppers.cn_tangent(d0.M, d0.D, d0.h, bad, np.zeros(d0.N), dt, nsteps)
+    else:
+        _, dz_bad = steppers.rk4_tangent(d0.M, d0.D, d0.h, bad, np.zeros(d0.N), dt, nsteps)
+    assert np.abs(fd - dz_bad).max() > 1e-3 * scale
+
+
+def test_c_driver_cn_matches_lu():
+    """The oracle's multi-threaded C driver of the CN step (GMRES(30), right point-Jacobi, the
+    algorithm of steppers.gmres) reaches the sparse-LU trajectory within its tolerance, and its
+    iteration counts match the Python GMRES to within one per step (rounding order differs)."""
+    from oracle import native
+    prob = W.shock(nx=12, npc=6, lmax=3)
+    d = dg.Discretisation(prob)
+    want = steppers.theta_method(d.M, d.D, d.h, np.zeros(d.N), 1.0, 4)
+    drv = native.CNDriver(d, 1.0)
+    z = np.zeros(d.N)
+    nt, its = drv.steps(z, 4, tol=1e-12, threads=2)
+    assert nt == 2
+    assert np.linalg.norm(z - want) < 1e-9 * np.linalg.norm(want)
+    A = (d.M + 0.5 * d.D).tocsr()
+    B = (d.M - 0.5 * d.D).tocsr()
+    zp, its_py = np.zeros(d.N), 0
+    for _ in range(4):
+        zp, k = steppers.gmres(A, B @ zp + d.h, zp, tol=1e-12)
+        its_py += k
+    assert abs(its - its_py) <= 4, (its, its_py)
