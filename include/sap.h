@@ -194,6 +194,45 @@ sap_status sap_adjoint_step_cn(sap_handle h, const double* zeta_prev, const doub
 sap_status sap_adjoint_step_erk(sap_handle h, const double* zeta_prev, double* lambda, double dt, double* grad_nu,
                                 double* stages_out, sap_solver_stats* stats, sap_stream stream);
 
+/* Time-stepping schemes of sap_adjoint_step */
+enum { SAP_SCHEME_ERK4 = 0, SAP_SCHEME_CN = 1 };
+
+/* Gradient accumulators of sap_adjoint_step: device arrays (caller-owned, FP64) with the shapes and
+ * layouts of the field arrays of sap_set_fields; each call ADDS its contribution.  Any pointer may
+ * be NULL (that gradient is not formed). */
+typedef struct {
+  double* U;          /* [nsv * 3]   dJ/dU_a at the spatial points                                  */
+  double* gradU;      /* [nsv * 9]   dJ/d(dU_b/dx^a), index p*9 + 3a + b                             */
+  double* DUDt;       /* [nsv * 3]   dJ/d(DU_a/Dt)                                                   */
+  double* Bw;         /* [nsv * 3]   dJ/dB_a (momentum axis) or dJ/domega_a (no momentum axis)       */
+  double* Uface[3];   /* [nsf_a]     dJ/dU_a at the spatial face points normal to axis a             */
+  double* nu;         /* [npv]       dJ/dnu at the phase-space nodes                                 */
+  double* s000;       /* [npv]       dJ/ds_000 at the phase-space nodes                              */
+} sap_field_grads;
+
+/* One step of the discrete adjoint of sap_step_cn (scheme SAP_SCHEME_CN: theta = 1/2 of Eq.
+ * theta-method, solved as in sap_adjoint_step_cn) or of sap_step_erk (SAP_SCHEME_ERK4: the stage
+ * adjoints of sap_adjoint_step_erk), with the gradients of J with respect to every prescribed field
+ * at the points where it is sampled.  On entry `lambda` (device, N doubles) holds dJ/dzeta_next;
+ * on return dJ/dzeta_prev.  zeta_prev (and, for CN, zeta_next) are the forward states (device).
+ * A field theta enters the CN step through -dt/2 mu^T (dL/dtheta)(zeta_prev + zeta_next) + dt mu^T
+ * ds/dtheta (mu = A^-T lambda) and the RK4 step through sum_i kb_i^T (ds/dtheta - (dL/dtheta) Y_i),
+ * L = M^-1 D (Eq. definition-mass-and-dg-matrix).  dL/dtheta is exact: L is linear in the
+ * coefficients of its volume and face terms (Eq. definitions-advection-reaction-eq, Eq.
+ * definition-upwind-flux); the upwind matrices |beta| are differentiated by the Daleckii--Krein
+ * formula d|beta|[dB] = W (Gamma o (W^T dB W)) W^T with Gamma_ij = (|l_i| - |l_j|)/(l_i - l_j) (sign
+ * for equal signs, 0 where both eigenvalues vanish: the zero subgradient at the kink of |.|).
+ * Gradients are formed for the field components that are non-zero somewhere at sap_set_fields (the
+ * components whose terms the operator contains); a component that is identically zero there adds
+ * nothing.  Points where |beta^p| was dropped as negligible add nothing to the momentum-face part.
+ * The first call after sap_set_fields builds the derivative tables of |beta^p| on the host.
+ * Synchronous.  tol, restart, maxit: the adjoint GMRES of the CN scheme (ignored for RK4).
+ * Errors: SAP_EINVAL, SAP_ENOCONV, SAP_ENOMEM, SAP_ECUDA, SAP_EUNSUPPORTED (batch handles, FP32
+ * contexts, a cell too large for the gradient kernel's shared memory). */
+sap_status sap_adjoint_step(sap_handle h, int scheme, const double* zeta_prev, const double* zeta_next,
+                            double* lambda, double dt, double tol, int restart, int maxit,
+                            const sap_field_grads* grads, sap_solver_stats* stats, sap_stream stream);
+
 /* Largest N (degrees of freedom) that sap_step_erk_noalloc accepts. */
 #define SAP_NOALLOC_MAX_DOFS 262144
 
@@ -206,10 +245,15 @@ sap_status sap_adjoint_step_erk(sap_handle h, const double* zeta_prev, double* l
  * fixed array of 24 * SAP_NOALLOC_MAX_DOFS bytes (6 MiB) that every GPU which loads the library
  * holds until the process exits.  The first call on each device looks up that array's device
  * address (cudaGetSymbolAddress) with the device current; make that first call before any stream
- * capture.  Every call shares the one array and it keeps the last call's contents; each step
- * writes every scratch value before reading it, so nothing needs clearing.  Calls that overlap on
- * the GPU (other streams, threads or handles on the same device) race on the array.
- * Errors: SAP_EINVAL (N > SAP_NOALLOC_MAX_DOFS, fields not set, bad arguments), SAP_ECUDA. */
+ * capture.  The address is kept for the life of the process: after cudaDeviceReset (or any other
+ * teardown of the device's primary context) the library must not be used on that device again.
+ * Every call shares the one array and it keeps the last call's contents; each step writes every
+ * scratch value before reading it, so nothing needs clearing.  Calls that overlap on the GPU (other
+ * streams, threads or handles on the same device) race on the array.  Like sap_step_erk, the call
+ * ends the CN initial-guess history of the handle (the next sap_step_cn starts from the plain
+ * previous state).
+ * Errors: SAP_EINVAL (N > SAP_NOALLOC_MAX_DOFS, fields not set, bad arguments), SAP_EUNSUPPORTED
+ * (batch handles: use sap_step_erk), SAP_ECUDA. */
 sap_status sap_step_erk_noalloc(sap_handle h, double* state, double dt, int nsteps, sap_stream stream);
 
 /* Algorithmic cost of one sap_apply_operator call on this context: `flops` = floating-point

@@ -1,34 +1,35 @@
 """Discrete adjoints of Crank--Nicolson and RK4 trajectories as torch.autograd.Functions.
 
-The forward pass runs CN steps in the library (sap_step_cn) and keeps the state every
-`checkpoint` steps.  The backward pass walks the segments from the end: it recomputes a segment's
-states from its checkpoint and runs the library's adjoint step (sap_adjoint_step_cn) through them:
-  A^T mu = lambda_n,   lambda_{n-1} = B^T mu,   dJ/dnu += -dt/2 mu . (dL/dnu)(zeta_{n-1} + zeta_n),
-the last term being exact (nu enters the operator only through the pointwise collision term).  The
-shock speed U1 enters through every field (U, grad U, dU/dt) and the upwind splits; its term
--dt/2 mu . (dL/dU1)(zeta_{n-1} + zeta_n) uses the operator's central difference in U1,
-(L(U1 + e) - L(U1 - e)) / (2e) with e = 1e-6 U1, applied by the library.
+The forward pass runs the steps in the library (sap_step_cn / sap_step_erk) and keeps the state
+every `checkpoint` steps.  The backward pass walks the segments from the end: it recomputes a
+segment's states from its checkpoint and runs the library's adjoint step (sap_adjoint_step) through
+them.  Per CN step (theta = 1/2 of Eq. theta-method) the library solves A^T mu = lambda_n, sets
+lambda_{n-1} = B^T mu and adds the exact gradients of J with respect to every prescribed field at its
+sampling points, -dt/2 mu^T (dL/dfield)(zeta_{n-1} + zeta_n); per RK4 step (Sec. 3.4) it recomputes
+the stage inputs, forms the stage adjoints kb_i and adds -sum_i kb_i^T (dL/dfield) Y_i.  The upwind
+matrices are differentiated by the Daleckii--Krein formula inside the library.
 
-RK4 (ERKTrajectory) follows the same pattern with the library's RK4 adjoint step
-(sap_adjoint_step_erk): per step it recomputes the stage inputs Y_i, forms the stage adjoints kb_i
-and returns lambda_{n-1} = R^T lambda_n (R the RK4 stability polynomial in -dt L) and the exact nu
-term -sum_i kb_i . (dL/dnu) Y_i; the U1 term -sum_i kb_i . (dL/dU1) Y_i uses the same central
-difference in U1 on the stage pairs the library hands back.  RK4 is explicit, so recomputed segments
-reproduce the forward states exactly.
-
-Only argument marshalling and the per-step bookkeeping live here; every operator apply, linear
-solve and gradient accumulation runs in libsapgpu.so.
+The parameters reach the fields by the chain rule, done here once per backward pass:
+  dJ/dnu   is the library's nodal nu-gradient itself (nu is given per phase-space node);
+  dJ/dU1 = sum over the field arrays of <dJ/dfield, dfield/dU1>, with dfield/dU1 evaluated at the
+           library's points from the problem family (for the shock: U, grad U linear in U1, (U.grad)U
+           quadratic).
+Only argument marshalling, the checkpoint bookkeeping and this final chain rule live here; every
+operator apply, linear solve and gradient accumulation runs in libsapgpu.so.
 """
 from __future__ import annotations
 
 import dataclasses
 import time
-from typing import Callable
+from typing import Callable, Optional
 
-import numpy as np
 import torch
 
 from . import sapgpu
+from . import workloads
+
+# field arrays through which the shock speed enters (sap_field_grads members)
+U1_FIELDS = ("U", "gradU", "DUDt", "Uface0", "Uface1", "Uface2")
 
 
 @dataclasses.dataclass
@@ -41,20 +42,29 @@ class CNProblemFamily:
     tol: float = 1e-12
     restart: int = 30
     checkpoint: int = 50
-    u1_rel_eps: float = 1e-6
+    # (nu_nodes_numpy or None, U1) -> Problem whose fields are d(field)/dU1 at any point; None: the
+    # shock family's own (workloads.shock_U1_derivative)
+    make_field_derivative: Optional[Callable] = None
     # filled by the backward pass: wall time of its parts (s) and the adjoint GMRES iterations per step
     last_backward: dict = dataclasses.field(default_factory=dict)
 
     def solver(self, nu_nodes, U1):
         return sapgpu.Solver(self.make_problem(nu_nodes, U1), "fp64")
 
+    def field_derivative(self, nu_nodes, U1):
+        if self.make_field_derivative is not None:
+            return self.make_field_derivative(nu_nodes, U1)
+        return workloads.shock_U1_derivative(self.make_problem(nu_nodes, U1), U1)
 
-def _node_nu_problem(base_make, nu_nodes, U1):
-    prob = base_make(U1)
-    if nu_nodes is not None:
-        vals = np.ascontiguousarray(nu_nodes, dtype=np.float64)
-        prob.nu = lambda xs, p, _v=vals: _v
-    return prob
+
+def _chain_u1(grads, dfields, device):
+    """dJ/dU1 = sum_k <dJ/dfield_k, dfield_k/dU1> (one device reduction per field array)."""
+    total = torch.zeros((), dtype=torch.float64, device=device)
+    for k in U1_FIELDS:
+        g, d = grads.get(k), dfields.get(k)
+        if g is not None and d is not None:
+            total = total + g @ torch.as_tensor(d, dtype=torch.float64, device=device)
+    return total
 
 
 class CNTrajectory(torch.autograd.Function):
@@ -73,7 +83,6 @@ class CNTrajectory(torch.autograd.Function):
             if n % fam.checkpoint == 0 and n < fam.nsteps:
                 ckpts[n] = state.clone()
         ctx.fam, ctx.ckpts, ctx.nu_np, ctx.u1 = fam, ckpts, nu_np, u1
-        ctx.npv = nu_nodes.numel()
         sol.close()
         return state.clone()
 
@@ -82,23 +91,15 @@ class CNTrajectory(torch.autograd.Function):
         fam, ckpts, nu_np, u1 = ctx.fam, ctx.ckpts, ctx.nu_np, ctx.u1
         t_enter = time.perf_counter()
         sol = fam.solver(nu_np, u1)
-        eps = fam.u1_rel_eps * abs(u1)
-        sol_p = fam.solver(nu_np, u1 + eps)
-        sol_m = fam.solver(nu_np, u1 - eps)
         lam = gL.detach().to(torch.float64).contiguous().clone()
-        grad_nu = torch.zeros(ctx.npv, dtype=torch.float64, device=lam.device)
-        mu = torch.empty_like(lam)
-        a = torch.empty_like(lam)
-        b = torch.empty_like(lam)
-        g_u1 = 0.0
-        starts = sorted(ckpts)
+        grads = sol.field_grad_buffers(lam.device, which=U1_FIELDS + ("nu",))
         end = fam.nsteps
         t_rec = t_adj = 0.0
         iters = []
         sync = torch.cuda.synchronize if lam.is_cuda else (lambda: None)  # wall-clock parts only
         sync()
         t_setup = time.perf_counter() - t_enter
-        for s0 in reversed(starts):
+        for s0 in reversed(sorted(ckpts)):
             # recompute the states of [s0, end] from the checkpoint
             t0 = time.perf_counter()
             states = [ckpts[s0].clone()]
@@ -109,23 +110,18 @@ class CNTrajectory(torch.autograd.Function):
             sync()
             t1 = time.perf_counter()
             for k in range(end - s0, 0, -1):
-                zp, zn = states[k - 1], states[k]
-                st = sol.adjoint_step_cn(zp, zn, lam, fam.dt, fam.tol, fam.restart, 20000, mu_out=mu,
-                                         grad_nu=grad_nu)
+                st = sol.adjoint_step("cn", states[k - 1], states[k], lam, fam.dt, grads, fam.tol, fam.restart,
+                                      20000)
                 iters.append(int(st.iterations))
-                w = zp + zn
-                sol_p.apply(w, a)
-                sol_m.apply(w, b)
-                g_u1 += -0.5 * fam.dt * float(mu @ (a - b)) / (2 * eps)
             t_rec += t1 - t0
             t_adj += time.perf_counter() - t1
             end = s0
-        for s in (sol, sol_p, sol_m):
-            s.close()
+        g_u1 = _chain_u1(grads, sol.field_arrays(fam.field_derivative(nu_np, u1)), lam.device)
+        sol.close()
         fam.last_backward = {"total_s": time.perf_counter() - t_enter, "setup_s": t_setup,
                              "recompute_s": t_rec, "adjoint_s": t_adj,
                              "adjoint_iterations_per_step": sum(iters) / max(1, len(iters))}
-        return grad_nu, torch.tensor(g_u1, dtype=torch.float64), None
+        return grads["nu"], g_u1.cpu(), None
 
 
 class ERKTrajectory(torch.autograd.Function):
@@ -144,7 +140,6 @@ class ERKTrajectory(torch.autograd.Function):
             if n % fam.checkpoint == 0 and n < fam.nsteps:
                 ckpts[n] = state.clone()
         ctx.fam, ctx.ckpts, ctx.nu_np, ctx.u1 = fam, ckpts, nu_np, u1
-        ctx.npv = nu_nodes.numel()
         sol.close()
         return state.clone()
 
@@ -152,16 +147,8 @@ class ERKTrajectory(torch.autograd.Function):
     def backward(ctx, gL):
         fam, ckpts, nu_np, u1 = ctx.fam, ctx.ckpts, ctx.nu_np, ctx.u1
         sol = fam.solver(nu_np, u1)
-        eps = fam.u1_rel_eps * abs(u1)
-        sol_p = fam.solver(nu_np, u1 + eps)
-        sol_m = fam.solver(nu_np, u1 - eps)
         lam = gL.detach().to(torch.float64).contiguous().clone()
-        N = lam.numel()
-        grad_nu = torch.zeros(ctx.npv, dtype=torch.float64, device=lam.device)
-        stages = torch.empty(7 * N, dtype=torch.float64, device=lam.device)
-        a = torch.empty_like(lam)
-        b = torch.empty_like(lam)
-        g_u1 = torch.zeros((), dtype=torch.float64, device=lam.device)
+        grads = sol.field_grad_buffers(lam.device, which=U1_FIELDS + ("nu",))
         end = fam.nsteps
         for s0 in reversed(sorted(ckpts)):
             # the states that start the steps of [s0, end)
@@ -171,18 +158,11 @@ class ERKTrajectory(torch.autograd.Function):
                 sol.step_erk(x, fam.dt, 1)
                 states.append(x.clone())
             for k in range(end - s0 - 1, -1, -1):
-                y = states[k]
-                sol.adjoint_step_erk(y, lam, fam.dt, grad_nu=grad_nu, stages_out=stages)
-                Y = [y, stages[:N], stages[N:2 * N], stages[2 * N:3 * N]]
-                for i in range(4):
-                    kb = stages[(3 + i) * N:(4 + i) * N]
-                    sol_p.apply(Y[i], a)
-                    sol_m.apply(Y[i], b)
-                    g_u1 -= kb @ (a - b) / (2 * eps)
+                sol.adjoint_step("erk4", states[k], None, lam, fam.dt, grads)
             end = s0
-        for s in (sol, sol_p, sol_m):
-            s.close()
-        return grad_nu, g_u1.cpu(), None
+        g_u1 = _chain_u1(grads, sol.field_arrays(fam.field_derivative(nu_np, u1)), lam.device)
+        sol.close()
+        return grads["nu"], g_u1.cpu(), None
 
 
 def spectrum_loss(state, prob, target, mask, x_range=(50.0, 150.0)):

@@ -520,7 +520,7 @@ void rows_config_shape(const OpParams<T>& P, int target, int* cells, size_t* sme
 
 template <typename T, int D, int Q>
 cudaError_t launch_rows_shape(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s) {
-  static std::atomic<unsigned long long> opted{0};
+  static DeviceMask opted{};
   if (cudaError_t err = smem_opt_in(rows_kernel<T, D, Q>, (int)kRowsSmemMax, opted); err != cudaSuccess) return err;
   int C;
   size_t smem;
@@ -539,7 +539,7 @@ cudaError_t launch_rows_shape(const OpParams<T>& P, const T* x, const Epi<T>& e,
 template <typename T, int D, int Q>
 cudaError_t launch_rows_batched_shape(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e,
                                       cudaStream_t s) {
-  static std::atomic<unsigned long long> opted{0};
+  static DeviceMask opted{};
   if (cudaError_t err = smem_opt_in(rows_kernel_batched<T, D, Q>, (int)kRowsSmemMax, opted); err != cudaSuccess)
     return err;
   if (B.smem > kRowsSmemMax || B.threads > Shape<T, D, Q>::MAXT) return cudaErrorInvalidConfiguration;

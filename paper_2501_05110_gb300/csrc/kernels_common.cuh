@@ -11,17 +11,28 @@ namespace sap {
 
 void note_launch();  // counts a kernel launch of this host thread (sap_solver_stats.kernel_launches)
 
+// Devices whose kernel attributes the library tracks (ordinals 0 .. kMaxDevices-1).
+constexpr int kMaxDevices = 256;
+
+// One bit per device ordinal: the devices on which a kernel's attribute has been set.
+struct DeviceMask {
+  std::atomic<unsigned long long> w[kMaxDevices / 64];
+};
+
 // Raise `kernel`'s dynamic shared-memory limit to `bytes` on the current device.  The attribute is
-// per device, so `done` (one per call site) records the devices already set, one bit each.
+// per device, so `done` (one per call site) records the devices already set.  Device ordinals
+// beyond kMaxDevices are refused (cudaErrorInvalidDevice) instead of sharing another device's bit.
 template <typename K>
-inline cudaError_t smem_opt_in(K kernel, int bytes, std::atomic<unsigned long long>& done) {
+inline cudaError_t smem_opt_in(K kernel, int bytes, DeviceMask& done) {
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   const unsigned long long bit = 1ull << (dev & 63);
-  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  std::atomic<unsigned long long>& word = done.w[dev >> 6];
+  if (word.load(std::memory_order_acquire) & bit) return cudaSuccess;
   err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (err == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  if (err == cudaSuccess) word.fetch_or(bit, std::memory_order_acq_rel);
   return err;
 }
 

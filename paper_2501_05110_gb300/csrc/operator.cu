@@ -610,7 +610,7 @@ static int cell_stride_elems(const OpParams<T>& P) {
 template <typename T, int DT, int QT>
 static cudaError_t launch_apply_shape(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s, int cpb,
                                       int stride, size_t smem) {
-  static std::atomic<unsigned long long> opted{0};
+  static DeviceMask opted{};
   if (cudaError_t err = smem_opt_in(apply_kernel<T, DT, QT>, 200 * 1024, opted); err != cudaSuccess) return err;
   const int blocks = (P.ncell + cpb - 1) / cpb;
   apply_kernel<T, DT, QT><<<blocks, cpb * P.n * P.nloc, smem, s>>>(P, x, e, cpb, stride);
@@ -639,7 +639,7 @@ static cudaError_t launch_applyT(const OpParams<T>& P, const T* x, const Epi<T>&
   const int cpb = apply_cells_per_block(P.n, P.nloc);
   const int stride = cell_stride_elems(P);
   const size_t smem = (size_t)cpb * stride * sizeof(T);
-  static std::atomic<unsigned long long> opted{0};  // one per instantiation (T)
+  static DeviceMask opted{};  // one per instantiation (T)
   if (cudaError_t err = smem_opt_in(applyT_kernel<T>, 200 * 1024, opted); err != cudaSuccess) return err;
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   const int blocks = (P.ncell + cpb - 1) / cpb;
@@ -1401,7 +1401,7 @@ sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol
 template <typename T, int DT, int QT>
 static cudaError_t launch_apply_batched_shape(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e,
                                               cudaStream_t s) {
-  static std::atomic<unsigned long long> opted{0};
+  static DeviceMask opted{};
   if (cudaError_t err = smem_opt_in(apply_kernel_batched<T, DT, QT>, 200 * 1024, opted); err != cudaSuccess)
     return err;
   apply_kernel_batched<T, DT, QT><<<B.nblocks, B.threads, B.smem, s>>>(B.P, B.doff, B.cpb, B.stride, B.blocks, active, x, e);
@@ -2237,6 +2237,59 @@ cuda_fail:
   c->err = std::string("adjoint erk: ") + cudaGetErrorString(err);
   return SAP_ECUDA;
 #undef CK
+}
+
+// ================================================================================================
+// Adjoint step with field gradients (sap_adjoint_step)
+// ================================================================================================
+// CN: the adjoint solve of adjoint_cn_step leaves mu in the workspace; the fields enter through
+// -dt/2 mu^T L' (zeta_prev + zeta_next) + dt mu^T s'.  RK4: adjoint_erk_step leaves the stage inputs
+// and stage adjoints in the workspace; the fields enter through sum_i kb_i^T (s' - L' Y_i).
+sap_status adjoint_fields_step(sap_ctx* c, int scheme, const double* zp, const double* zn, double* lambda, double dt,
+                               double tol, int m, int maxit, const sap_field_grads& g, sap_solver_stats* st,
+                               cudaStream_t s) {
+  const int64_t N = c->N;
+  const bool spatial = g.U || g.gradU || g.DUDt || g.Bw || g.Uface[0] || g.Uface[1] || g.Uface[2];
+  const int64_t launches0 = g_launches;
+  sap_status rs;
+  cudaError_t err = cudaSuccess;
+  if (scheme == SAP_SCHEME_CN) {
+    rs = adjoint_cn_step(c, zp, zn, lambda, dt, tol, m, maxit, nullptr, g.nu, st, s);
+    if (rs != SAP_OK) return rs;
+    const double* mu = c->ws64 + (size_t)(m + 3) * N;
+    double* w = c->ws64 + (size_t)(m + 2) * N;
+    if (spatial) {
+      if ((err = launch_add2(zp, zn, w, N, s)) != cudaSuccess) goto fail;
+      if ((err = cudaMemsetAsync(c->gpart, 0, sizeof(double) * (size_t)c->ncell * c->gt.ps, s)) != cudaSuccess)
+        goto fail;
+      if ((err = launch_coef_adjoint(c->p64, c->gt, mu, w, c->gpart, s)) != cudaSuccess) goto fail;
+      if ((err = launch_grad_reduce(c->p64, c->gt, c->gpart, c->nscell, c->npc, -0.5 * dt, g, s)) != cudaSuccess)
+        goto fail;
+    }
+    if (g.s000 && (c->desc.terms & SAP_TERM_SRC))
+      if ((err = launch_grad_src(mu, N, 1, c->n, c->nloc, c->npv, dt, g.s000, s)) != cudaSuccess) goto fail;
+  } else {
+    rs = adjoint_erk_step(c, zp, lambda, dt, g.nu, nullptr, st, s);
+    if (rs != SAP_OK) return rs;
+    const double* S = c->ws64;  // Y2, Y3, Y4, kb1, kb2, kb3, kb4
+    if (spatial) {
+      if ((err = cudaMemsetAsync(c->gpart, 0, sizeof(double) * (size_t)c->ncell * c->gt.ps, s)) != cudaSuccess)
+        goto fail;
+      const double* Y[4] = {zp, S, S + N, S + 2 * N};
+      for (int i = 0; i < 4; ++i)
+        if ((err = launch_coef_adjoint(c->p64, c->gt, S + (size_t)(3 + i) * N, Y[i], c->gpart, s)) != cudaSuccess)
+          goto fail;
+      if ((err = launch_grad_reduce(c->p64, c->gt, c->gpart, c->nscell, c->npc, -1.0, g, s)) != cudaSuccess) goto fail;
+    }
+    if (g.s000 && (c->desc.terms & SAP_TERM_SRC))
+      if ((err = launch_grad_src(S + 3 * N, N, 4, c->n, c->nloc, c->npv, 1.0, g.s000, s)) != cudaSuccess) goto fail;
+  }
+  if ((err = cudaStreamSynchronize(s)) != cudaSuccess) goto fail;
+  if (st) st->kernel_launches = g_launches - launches0;
+  return SAP_OK;
+fail:
+  c->err = std::string("adjoint fields: ") + cudaGetErrorString(err);
+  return SAP_ECUDA;
 }
 
 }  // namespace sap

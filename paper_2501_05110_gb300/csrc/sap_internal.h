@@ -115,6 +115,21 @@ struct OpParams {
   unsigned adv_uni[MAXD];
 };
 
+// Tables of the field-gradient kernels of the adjoint (adjoint_fields.cu): the spatial field
+// components that enter some term (compact numbering), the per-cell partial layout, and for the
+// momentum axis the Daleckii--Krein derivatives P_t = d|beta^p|[K_t] of the upwind matrix along each
+// advection term, per (slot, momentum face) in the ELL order of the block pattern.
+struct GradTables {
+  int ncomp;                 // spatial field components with a gradient
+  int comp_sf[SF_NCOMP];     // compact index -> SF component
+  int sf_comp[SF_NCOMP];     // SF component -> compact index or -1
+  int ps;                    // partials per cell: ncomp * qdx (spatial nodes) + 2 dx qsp (face points)
+  int face_off;              // first face partial
+  int qsp;                   // spatial points per spatial face
+  const double* pd[MAXADV];  // [slot][momentum face][pd_w][n] per momentum advection term (or null)
+  int pd_w;                  // ELL width of the block pattern (0: no momentum-face tables)
+};
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -207,6 +222,12 @@ struct sap_ctx {
   };
   std::vector<CnGraph> cn_graphs;
   cudaStream_t cap_stream = nullptr;           // private stream for the captures
+  // field gradients of the adjoint: tables (built on first use for the current fields) and the
+  // per-cell partials
+  sap::GradTables gt{};
+  int gt_version = -1;
+  double* gpart = nullptr;
+  size_t gpart_count = 0;
 };
 
 namespace sap {
@@ -239,6 +260,18 @@ sap_status batch_apply(sap_ctx* c, const void* x, void* y, int mode, cudaStream_
 sap_status batch_cn(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
                     sap_solver_stats* st, cudaStream_t s);
 sap_status batch_erk(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s);
+// field gradients of the adjoint (adjoint_fields.cu)
+int coef_adjoint_smem_doubles(const OpParams<double>& P, const GradTables& G);
+cudaError_t launch_coef_adjoint(const OpParams<double>& P, const GradTables& G, const double* g, const double* w,
+                                double* part, cudaStream_t s);
+cudaError_t launch_grad_reduce(const OpParams<double>& P, const GradTables& G, const double* part, int nscell,
+                               int npc, double sigma, const sap_field_grads& out, cudaStream_t s);
+cudaError_t launch_grad_src(const double* g, int64_t N, int nvec, int n, int nloc, int64_t npv, double coef,
+                            double* grad, cudaStream_t s);
+cudaError_t launch_add2(const double* a, const double* b, double* w, int64_t N, cudaStream_t s);
+sap_status adjoint_fields_step(sap_ctx* c, int scheme, const double* zp, const double* zn, double* lambda, double dt,
+                               double tol, int m, int maxit, const sap_field_grads& g, sap_solver_stats* st,
+                               cudaStream_t s);
 int64_t launch_count();
 void cn_graphs_release(sap_ctx* c);  // destroys the cached CN graphs and the capture stream
 int64_t krylov_scratch_doubles(int64_t N);

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "sap_internal.h"
@@ -121,11 +123,6 @@ template <typename V>
 static std::vector<float> to_f32(const std::vector<V>& v) {
   return std::vector<float>(v.begin(), v.end());
 }
-
-struct FieldStore {  // per-context field-dependent device buffers
-  std::vector<DevBuf> bufs;
-};
-static std::map<sap_ctx*, FieldStore> g_fields;
 
 static void free_bufs(std::vector<DevBuf>& v) {
   for (auto& b : v) cudaFree(b.p);
@@ -528,6 +525,78 @@ static HostCSR to_csr(const Mat& m, double drop = 0.0) {
   return h;
 }
 
+// body(i, scratch) for i = 0 .. count-1 on the host's cores (each i on one thread; `scratch` is a
+// per-thread buffer).  Used for the per-point eigen-decompositions of the momentum-face set-up.
+template <typename F>
+static void parallel_for(int count, F&& body) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nt = (int)std::min<unsigned>(hw ? hw : 1u, 64u);
+  if (nt < 2 || count < 4 * nt) {
+    std::vector<double> scratch;
+    for (int i = 0; i < count; ++i) body(i, scratch);
+    return;
+  }
+  std::atomic<int> next{0};
+  std::atomic<bool> failed{false};
+  auto run = [&]() {
+    std::vector<double> scratch;
+    try {
+      for (;;) {
+        const int i0 = next.fetch_add(8);
+        if (i0 >= count) break;
+        for (int i = i0; i < std::min(count, i0 + 8); ++i) body(i, scratch);
+      }
+    } catch (...) {
+      failed = true;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int k = 1; k < nt; ++k) {
+    try {
+      th.emplace_back(run);
+    } catch (...) {
+      break;  // fewer threads: the remaining work is shared by those that started
+    }
+  }
+  run();
+  for (auto& t : th) t.join();
+  if (failed) throw std::bad_alloc();
+}
+
+// Inputs of the momentum-face upwind data (kept after sap_set_fields for the derivative tables of the
+// adjoint): the block pattern of beta^p, each advection term scattered into it, the fields.
+struct MomFaceSrc {
+  int axis = -1;
+  HostCSR pat;                                                 // dense within each block
+  std::vector<std::vector<int>> blocks;
+  std::vector<std::vector<std::pair<int, double>>> tpos;       // per term: (pattern position, value)
+  int nadv = 0;
+  Term adv[MAXADV];
+  std::vector<double> sf;                                      // [SF_NCOMP][nsv]
+  double V = 1.0;
+  bool has_mom = false;
+  std::vector<int> pslot;
+  int nslot = 0;
+  // beta^p (Eq. beta-p; the ln p form through the term factors) at spatial node sp and momentum p,
+  // on the block pattern
+  void beta_at(int sp, double p, int nsv, std::vector<double>& pv) const {
+    pv.assign(pat.col.size(), 0.0);
+    for (int t = 0; t < nadv; ++t) {
+      const Term& tm = adv[t];
+      const double cf = tm.scale * (tm.sf == SF_ONE ? 1.0 : sf[(size_t)tm.sf * nsv + sp]) *
+                        mom_factor_h(tm.mf, p, has_mom, V);
+      for (const auto& pr : tpos[t]) pv[pr.first] += cf * pr.second;
+    }
+  }
+};
+
+struct FieldStore {  // per-context field-dependent device buffers and host inputs
+  std::vector<DevBuf> bufs;
+  MomFaceSrc mom;
+  std::vector<DevBuf> gbufs;  // derivative tables of the adjoint's field gradients
+};
+static std::map<sap_ctx*, FieldStore> g_fields;
+
 struct BankBuilder {
   std::vector<HostCSR> mats;
   std::map<std::string, int> ids;
@@ -608,6 +677,8 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
       // compute call can read a freed buffer after a failure part-way
       c->fields_set = false;
       free_bufs(fs.bufs);
+      free_bufs(fs.gbufs);
+      fs.mom = MomFaceSrc{};
       const sap_desc& d = c->desc;
       const int n = c->n, nsv = c->nsv;
       const unsigned terms = d.terms;
@@ -742,14 +813,22 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
         if (is_spatial(A.kind)) {
           if (uface_uni[a] && !has_mom) {  // constant beta: |beta| = W |U + lam V| W^T as one matrix
             A.route = ABS_CONST;
+            // entries below 1e-14 of the largest |eigenvalue| are rounding residue of the
+            // back-transformation (they vanish by symmetry); the cut is relative, so a small U or V
+            // keeps every real entry
+            double bmax = 0.0;
+            for (int k = 0; k < n; ++k) bmax = std::max(bmax, std::fabs(uface_u[a] + lam[k] * d.V));
             Mat Ab(n);
             for (int i = 0; i < n; ++i)
               for (int j = 0; j < n; ++j) {
                 double s = 0.0;
                 for (int k = 0; k < n; ++k) s += Wa[a](i, k) * std::fabs(uface_u[a] + lam[k] * d.V) * Wa[a](j, k);
-                Ab(i, j) = std::fabs(s) < 1e-15 ? 0.0 : s;
+                Ab(i, j) = std::fabs(s) <= 1e-14 * bmax ? 0.0 : s;
               }
             A.absmat = B.add("abs" + std::to_string(a), Ab);
+            // eigenvectors also here: the adjoint differentiates |beta| with respect to U_a
+            A.Wmat = B.add("W" + std::to_string(a), Wa[a]);
+            A.WTmat = B.add("WT" + std::to_string(a), transpose(Wa[a]));
           } else {
             A.route = ABS_EIGEN;
             A.Wmat = B.add("W" + std::to_string(a), Wa[a]);
@@ -764,72 +843,71 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
             for (int i = 0; i < n; ++i)
               for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) pat(i, h.col[k]) = 1.0;
           }
-          auto blocks = connected_blocks(pat);
+          MomFaceSrc& M = fs.mom;
+          M = MomFaceSrc{};
+          M.axis = a;
+          M.blocks = connected_blocks(pat);
           Mat full(n);  // block pattern: dense within each block
-          for (auto& b : blocks)
+          for (auto& b : M.blocks)
             for (int i : b)
               for (int j : b) full(i, j) = 1.0;
-          HostCSR pc = to_csr(full);
-          const int nnzp = (int)pc.col.size();
-          A.absmat = B.add_csr("pabs_pattern", pc);
+          M.pat = to_csr(full);
+          A.absmat = B.add_csr("pabs_pattern", M.pat);
           // each term's entries scattered into the block pattern once
-          std::vector<std::vector<std::pair<int, double>>> tpos(A.nadv);
+          M.tpos.assign(A.nadv, {});
           for (int t = 0; t < A.nadv; ++t) {
             const HostCSR& h = B.mats[A.adv[t].mat];
             for (int i = 0; i < n; ++i)
               for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) {
                 const int j = h.col[k];
                 int pos = -1;
-                for (int e = pc.rp[i]; e < pc.rp[i + 1]; ++e)
-                  if (pc.col[e] == j) pos = e;
-                tpos[t].push_back({pos, h.val[k]});
+                for (int e = M.pat.rp[i]; e < M.pat.rp[i + 1]; ++e)
+                  if (M.pat.col[e] == j) pos = e;
+                M.tpos[t].push_back({pos, h.val[k]});
               }
           }
-          std::vector<double> pv(nnzp);
-          auto build_beta = [&](int sp, double p) {  // beta^p at (spatial node, momentum) in the pattern
-            std::fill(pv.begin(), pv.end(), 0.0);
-            for (int t = 0; t < A.nadv; ++t) {
-              const Term& tm = A.adv[t];
-              const double cf = tm.scale * (tm.sf == SF_ONE ? 1.0 : sf[(size_t)tm.sf * nsv + sp]) *
-                                mom_factor_h(tm.mf, p, has_mom, d.V);
-              for (const auto& pr : tpos[t]) pv[pr.first] += cf * pr.second;
-            }
-          };
-          double gmax = 0.0;
-          std::vector<double> pmax(nsv, 0.0);
-          for (int sp = 0; sp < nsv; ++sp)
-            for (int f = 0; f < npface; ++f) {
-              build_beta(sp, c->pface[f]);
-              double mx = 0.0;
-              for (double v : pv) mx = std::max(mx, std::fabs(v));
-              pmax[sp] = std::max(pmax[sp], mx);
-              gmax = std::max(gmax, mx);
-            }
+          M.nadv = A.nadv;
+          for (int t = 0; t < A.nadv; ++t) M.adv[t] = A.adv[t];
+          M.sf = sf;
+          M.V = d.V;
+          M.has_mom = has_mom;
           // points where |beta^p| stays below 1e-15 of its largest value carry no upwinding term
           // beyond FP64 rounding of the largest momentum flux; they are skipped
+          std::vector<double> pmax(nsv, 0.0);
+          parallel_for(nsv, [&](int sp, std::vector<double>& pv) {
+            for (int f = 0; f < npface; ++f) {
+              M.beta_at(sp, c->pface[f], nsv, pv);
+              for (double v : pv) pmax[sp] = std::max(pmax[sp], std::fabs(v));
+            }
+          });
+          double gmax = 0.0;
+          for (double v : pmax) gmax = std::max(gmax, v);
           int nslot = 0;
           for (int sp = 0; sp < nsv; ++sp)
             if (gmax > 0.0 && pmax[sp] > 1e-15 * gmax) pslot[sp] = nslot++;
+          M.pslot = pslot;
+          M.nslot = nslot;
+          const int nnzp = (int)M.pat.col.size();
           pabs.assign((size_t)nslot * npface * nnzp, 0.0);
-          Mat bm(n), Wb;
-          std::vector<double> lb;
-          for (int sp = 0; sp < nsv; ++sp) {
-            if (pslot[sp] < 0) continue;
+          parallel_for(nsv, [&](int sp, std::vector<double>& pv) {
+            if (pslot[sp] < 0) return;
+            Mat bm(n), Wb;
+            std::vector<double> lb;
             for (int f = 0; f < npface; ++f) {
-              build_beta(sp, c->pface[f]);
+              M.beta_at(sp, c->pface[f], nsv, pv);
               for (int i = 0; i < n; ++i)
-                for (int e = pc.rp[i]; e < pc.rp[i + 1]; ++e) bm(i, pc.col[e]) = pv[e];
-              sym_eig_blocks(bm, blocks, Wb, lb);
+                for (int e = M.pat.rp[i]; e < M.pat.rp[i + 1]; ++e) bm(i, M.pat.col[e]) = pv[e];
+              sym_eig_blocks(bm, M.blocks, Wb, lb);
               double* dst = &pabs[((size_t)pslot[sp] * npface + f) * nnzp];
               for (int i = 0; i < n; ++i)
-                for (int k = pc.rp[i]; k < pc.rp[i + 1]; ++k) {
-                  int j = pc.col[k];
+                for (int k = M.pat.rp[i]; k < M.pat.rp[i + 1]; ++k) {
+                  const int j = M.pat.col[k];
                   double s2 = 0.0;
                   for (int e = 0; e < n; ++e) s2 += Wb(i, e) * std::fabs(lb[e]) * Wb(j, e);
                   dst[k] = s2;
                 }
             }
-          }
+          });
         }
       }
       // upload: bank, fields, term lists
@@ -1009,6 +1087,12 @@ extern "C" sap_status sap_step_erk(sap_handle c, double* state, double dt, int n
 extern "C" sap_status sap_step_erk_noalloc(sap_handle c, double* state, double dt, int nsteps, sap_stream stream) {
   return guarded(c, "sap_step_erk_noalloc", [&]() -> sap_status {
     if (!c || !state || nsteps < 0) return SAP_EINVAL;
+    if (!c->sub.empty()) {
+      c->err = "sap_step_erk_noalloc: batch handles are not supported (use sap_step_erk)";
+      return SAP_EUNSUPPORTED;
+    }
+    // as in sap_step_erk: a following CN step starts from the plain previous state
+    c->cn_prev_valid = false;
     if (!c->fields_set) {
       c->err = "fields not set";
       return SAP_EINVAL;
@@ -1152,6 +1236,163 @@ extern "C" sap_status sap_adjoint_step_erk(sap_handle c, const double* zeta_prev
   });
 }
 
+// Gradient tables for the current fields (see GradTables): the compact list of spatial field
+// components, and for the momentum axis the Daleckii--Krein derivatives of |beta^p| along each
+// advection term, P_t = W (Gamma o (W^T K_t W)) W^T per block of the pattern, at every kept
+// (spatial node, momentum face) point.
+static double dk_gamma(double x, double y) {
+  if (x > 0.0 && y > 0.0) return 1.0;
+  if (x < 0.0 && y < 0.0) return -1.0;
+  if (x == y) return 0.0;  // both zero: zero subgradient
+  return (std::fabs(x) - std::fabs(y)) / (x - y);
+}
+
+static void build_grad_tables(sap_ctx* c) {
+  FieldStore& fs = g_fields[c];
+  free_bufs(fs.gbufs);
+  GradTables G;
+  std::memset(&G, 0, sizeof(G));
+  const OpParams<double>& P = c->p64;
+  for (int k = 0; k < SF_NCOMP; ++k) G.sf_comp[k] = -1;
+  auto use = [&](const Term& t) {
+    if (t.sf != SF_ONE && G.sf_comp[t.sf] < 0) {
+      G.sf_comp[t.sf] = G.ncomp;
+      G.comp_sf[G.ncomp++] = t.sf;
+    }
+  };
+  for (int t = 0; t < P.nreact; ++t) use(P.react[t]);
+  for (int a = 0; a < c->D; ++a)
+    for (int t = 0; t < P.ax[a].nadv; ++t) use(P.ax[a].adv[t]);
+  G.qsp = 1;
+  for (int a = 1; a < c->dx; ++a) G.qsp *= c->q;
+  G.face_off = G.ncomp * c->qdx;
+  G.ps = G.face_off + 2 * c->dx * G.qsp;
+  const MomFaceSrc& M = fs.mom;
+  if (M.axis >= 0 && M.nslot > 0) {
+    const AxisInfo& A = P.ax[M.axis];
+    const int n = c->n, nsv = c->nsv, npface = c->npc + 1;
+    const int w = P.bank.ell_w[A.absmat];
+    const int nnzp = (int)M.pat.col.size();
+    std::vector<int> loc(n, 0);
+    for (const auto& b : M.blocks)
+      for (int i = 0; i < (int)b.size(); ++i) loc[b[i]] = i;
+    G.pd_w = w;
+    for (int t = 0; t < A.nadv; ++t) {
+      if (A.adv[t].sf == SF_ONE) continue;
+      std::vector<double> Kp(nnzp, 0.0);  // K_t on the pattern
+      for (const auto& pr : M.tpos[t]) Kp[pr.first] += pr.second;
+      std::vector<double> pe((size_t)M.nslot * npface * w * n, 0.0);
+      parallel_for(nsv, [&](int sp, std::vector<double>& pv) {
+        const int slot = M.pslot[sp];
+        if (slot < 0) return;
+        Mat bm(n), W;
+        std::vector<double> lb, Kb, X, T2;
+        for (int f = 0; f < npface; ++f) {
+          M.beta_at(sp, c->pface[f], nsv, pv);
+          for (int i = 0; i < n; ++i)
+            for (int e = M.pat.rp[i]; e < M.pat.rp[i + 1]; ++e) bm(i, M.pat.col[e]) = pv[e];
+          sym_eig_blocks(bm, M.blocks, W, lb);
+          double* dst = &pe[((size_t)slot * npface + f) * w * n];
+          for (const auto& b : M.blocks) {
+            const int m = (int)b.size();
+            Kb.assign((size_t)m * m, 0.0);
+            for (int i = 0; i < m; ++i)
+              for (int e = M.pat.rp[b[i]]; e < M.pat.rp[b[i] + 1]; ++e) Kb[(size_t)i * m + loc[M.pat.col[e]]] = Kp[e];
+            // X = W_b^T K_b W_b, then Gamma o X, then P_b = W_b X W_b^T
+            T2.assign((size_t)m * m, 0.0);
+            for (int i = 0; i < m; ++i)
+              for (int k = 0; k < m; ++k) {
+                double v = 0.0;
+                for (int j = 0; j < m; ++j) v += Kb[(size_t)i * m + j] * W(b[j], b[k]);
+                T2[(size_t)i * m + k] = v;  // (K_b W_b)[i][k]
+              }
+            X.assign((size_t)m * m, 0.0);
+            for (int k = 0; k < m; ++k)
+              for (int l = 0; l < m; ++l) {
+                double v = 0.0;
+                for (int i = 0; i < m; ++i) v += W(b[i], b[k]) * T2[(size_t)i * m + l];
+                X[(size_t)k * m + l] = v * dk_gamma(lb[b[k]], lb[b[l]]);
+              }
+            for (int i = 0; i < m; ++i)
+              for (int l = 0; l < m; ++l) {
+                double v = 0.0;
+                for (int k = 0; k < m; ++k) v += W(b[i], b[k]) * X[(size_t)k * m + l];
+                T2[(size_t)i * m + l] = v;  // (W_b X)[i][l]
+              }
+            for (int i = 0; i < m; ++i) {
+              const int r = b[i];
+              for (int e = M.pat.rp[r]; e < M.pat.rp[r + 1]; ++e) {
+                const int j = loc[M.pat.col[e]];
+                double v = 0.0;
+                for (int l = 0; l < m; ++l) v += T2[(size_t)i * m + l] * W(b[j], b[l]);
+                dst[(size_t)(e - M.pat.rp[r]) * n + r] = v;  // ELL slot e - rp[r] of row r
+              }
+            }
+          }
+        }
+      });
+      G.pd[t] = (const double*)upload(c, pe, fs.gbufs);
+    }
+  }
+  c->gt = G;
+  c->gt_version = c->fields_version;
+}
+
+extern "C" sap_status sap_adjoint_step(sap_handle c, int scheme, const double* zeta_prev, const double* zeta_next,
+                                       double* lambda, double dt, double tol, int restart, int maxit,
+                                       const sap_field_grads* grads, sap_solver_stats* stats, sap_stream stream) {
+  return guarded(c, "sap_adjoint_step", [&]() -> sap_status {
+    if (!c || !zeta_prev || !lambda || !std::isfinite(dt) || (scheme != SAP_SCHEME_CN && scheme != SAP_SCHEME_ERK4))
+      return SAP_EINVAL;
+    if (scheme == SAP_SCHEME_CN && (!zeta_next || restart < 1 || restart > 31 || maxit < 1 || !(tol > 0)))
+      return SAP_EINVAL;
+    if (!c->sub.empty() || c->prec != SAP_PREC_FP64) {
+      c->err = "adjoint: FP64 single-problem contexts only";
+      return SAP_EUNSUPPORTED;
+    }
+    if (!c->fields_set) {
+      c->err = "fields not set";
+      return SAP_EINVAL;
+    }
+    const int need = scheme == SAP_SCHEME_CN ? restart + 4 : 8;
+    if (!ensure_ws64(c, need)) {
+      c->err = "adjoint: workspace allocation failed";
+      return SAP_ENOMEM;
+    }
+    c->cn_prev_valid = false;  // the adjoint shares the workspace
+    sap_field_grads g{};
+    if (grads) g = *grads;
+    const bool spatial = g.U || g.gradU || g.DUDt || g.Bw || g.Uface[0] || g.Uface[1] || g.Uface[2];
+    if (spatial) {
+      if (c->gt_version != c->fields_version) {
+        try {
+          build_grad_tables(c);
+        } catch (const std::string& e) {
+          c->err = "adjoint: gradient tables: " + e;
+          return SAP_ENOMEM;
+        }
+      }
+      if (coef_adjoint_smem_doubles(c->p64, c->gt) * sizeof(double) > 200 * 1024) {
+        c->err = "adjoint: a cell is too large for the field-gradient kernel";
+        return SAP_EUNSUPPORTED;
+      }
+      const size_t cnt = (size_t)c->ncell * c->gt.ps;
+      if (c->gpart_count < cnt) {
+        if (c->gpart) cudaFree(c->gpart);
+        c->gpart = nullptr;
+        c->gpart_count = 0;
+        if (cudaMalloc(&c->gpart, sizeof(double) * std::max<size_t>(cnt, 1)) != cudaSuccess) {
+          c->err = "adjoint: allocation of the gradient partials failed";
+          return SAP_ENOMEM;
+        }
+        c->gpart_count = cnt;
+      }
+    }
+    return adjoint_fields_step(c, scheme, zeta_prev, zeta_next, lambda, dt, tol, restart, maxit, g, stats,
+                               (cudaStream_t)stream);
+  });
+}
+
 extern "C" sap_status sap_destroy(sap_handle c) {
   if (!c) return SAP_OK;
   if (c->parent) return SAP_EINVAL;  // sub-handles belong to their batch
@@ -1166,8 +1407,10 @@ extern "C" sap_status sap_destroy(sap_handle c) {
   auto it = g_fields.find(c);
   if (it != g_fields.end()) {
     free_bufs(it->second.bufs);
+    free_bufs(it->second.gbufs);
     g_fields.erase(it);
   }
+  if (c->gpart) cudaFree(c->gpart);
   if (c->ws64) cudaFree(c->ws64);
   if (c->ws32) cudaFree(c->ws32);
   if (c->small) cudaFree(c->small);

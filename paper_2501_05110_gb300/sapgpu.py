@@ -22,9 +22,12 @@ PREC = {"fp64": 0, "fp32": 1}
 APPLY_D, APPLY_RHS, APPLY_T = 0, 1, 2
 PTS_SPATIAL, PTS_FACE_X, PTS_FACE_Y, PTS_FACE_Z, PTS_PHASE = range(5)
 
+SCHEME = {"erk4": 0, "cn": 1}
 EXPORTS = ["sap_create", "sap_create_batch", "sap_batch_instance", "sap_field_points", "sap_set_fields", "sap_num_dofs", "sap_apply_operator",
-           "sap_step_erk", "sap_step_erk_noalloc", "sap_step_cn", "sap_adjoint_step_cn", "sap_adjoint_step_erk", "sap_apply_cost", "sap_destroy", "sap_last_error",
-           "sap_coupling_matrix"]
+           "sap_step_erk", "sap_step_erk_noalloc", "sap_step_cn", "sap_adjoint_step_cn", "sap_adjoint_step_erk",
+           "sap_adjoint_step", "sap_apply_cost", "sap_destroy", "sap_last_error", "sap_coupling_matrix"]
+# field arrays of sap_set_fields / gradient arrays of sap_adjoint_step, in struct order
+FIELDS = ("U", "gradU", "DUDt", "Bw", "Uface0", "Uface1", "Uface2", "nu", "s000")
 
 
 class SapError(RuntimeError):
@@ -42,6 +45,11 @@ class Desc(C.Structure):
 class SolverStats(C.Structure):
     _fields_ = [("steps", C.c_int), ("iterations", C.c_int64), ("max_iterations", C.c_int),
                 ("last_rel_residual", C.c_double), ("kernel_launches", C.c_int64)]
+
+
+class FieldGrads(C.Structure):
+    _fields_ = [("U", C.c_void_p), ("gradU", C.c_void_p), ("DUDt", C.c_void_p), ("Bw", C.c_void_p),
+                ("Uface", C.c_void_p * 3), ("nu", C.c_void_p), ("s000", C.c_void_p)]
 
 
 _lib = None
@@ -71,6 +79,8 @@ def load_library(path: str = LIB_PATH):
     lib.sap_adjoint_step_cn.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int, C.c_int, vp, vp,
                                         C.POINTER(SolverStats), vp]
     lib.sap_adjoint_step_erk.argtypes = [vp, vp, vp, C.c_double, vp, vp, C.POINTER(SolverStats), vp]
+    lib.sap_adjoint_step.argtypes = [vp, C.c_int, vp, vp, vp, C.c_double, C.c_double, C.c_int, C.c_int,
+                                     C.POINTER(FieldGrads), C.POINTER(SolverStats), vp]
     lib.sap_destroy.argtypes = [vp]
     lib.sap_last_error.argtypes = [vp]
     lib.sap_last_error.restype = C.c_char_p
@@ -167,26 +177,31 @@ class Solver:
             p = np.exp(col) if prob.momentum == "lnp" else col
         return xs, p
 
-    def set_fields(self, prob):
-        """Evaluate the problem's fields at the library's points and upload them."""
+    def field_arrays(self, prob) -> dict:
+        """The problem's fields at the library's points, in the layouts of sap_set_fields: U (nsv*3),
+        gradU (nsv*9), DUDt (nsv*3), Bw (nsv*3), Uface0..2 (nsf_a, None for absent axes), nu and s000
+        (npv)."""
         xs = self.points(PTS_SPATIAL)
         nsv = xs.shape[0]
-        U = np.ascontiguousarray(prob.U(xs), dtype=np.float64).reshape(nsv, 3)
-        G = np.ascontiguousarray(prob.gradU(xs), dtype=np.float64).reshape(nsv, 9)
-        DU = np.ascontiguousarray(prob.DUDt(xs), dtype=np.float64).reshape(nsv, 3)
-        Bw = prob.B(xs) if prob.momentum is not None else prob.omega(xs)
-        Bw = np.ascontiguousarray(Bw, dtype=np.float64).reshape(nsv, 3)
-        faces = []
+        out = {"U": prob.U(xs), "gradU": prob.gradU(xs), "DUDt": prob.DUDt(xs),
+               "Bw": prob.B(xs) if prob.momentum is not None else prob.omega(xs)}
+        for k, width in (("U", 3), ("gradU", 9), ("DUDt", 3), ("Bw", 3)):
+            out[k] = np.ascontiguousarray(out[k], dtype=np.float64).reshape(nsv * width)
         for a in range(3):
             fp = self.points(PTS_FACE_X + a)
-            faces.append(np.ascontiguousarray(prob.U(fp)[:, a], dtype=np.float64) if fp.shape[0] else None)
-        face_ptrs = (C.POINTER(C.c_double) * 3)(*[_dptr(f) if f is not None else None for f in faces])
+            out[f"Uface{a}"] = np.ascontiguousarray(prob.U(fp)[:, a], dtype=np.float64) if fp.shape[0] else None
         ph = self.points(PTS_PHASE)
         pxs, pp = self._phase_xs_p(ph)
-        nu = np.ascontiguousarray(prob.nu(pxs, pp), dtype=np.float64)
-        s0 = np.ascontiguousarray(prob.s000(pxs, pp), dtype=np.float64)
-        self._check(self.lib.sap_set_fields(self.h, _dptr(U), _dptr(G), _dptr(DU), _dptr(Bw), face_ptrs,
-                                            _dptr(nu), _dptr(s0)))
+        out["nu"] = np.ascontiguousarray(prob.nu(pxs, pp), dtype=np.float64)
+        out["s000"] = np.ascontiguousarray(prob.s000(pxs, pp), dtype=np.float64)
+        return out
+
+    def set_fields(self, prob):
+        """Evaluate the problem's fields at the library's points and upload them."""
+        f = self.field_arrays(prob)
+        face_ptrs = (C.POINTER(C.c_double) * 3)(*[_dptr(f[f"Uface{a}"]) for a in range(3)])
+        self._check(self.lib.sap_set_fields(self.h, _dptr(f["U"]), _dptr(f["gradU"]), _dptr(f["DUDt"]),
+                                            _dptr(f["Bw"]), face_ptrs, _dptr(f["nu"]), _dptr(f["s000"])))
 
     def initial_state(self, device="cuda"):
         """Nodal values of f^0 at the phase-space nodes, canonical layout, FP64 torch tensor."""
@@ -239,6 +254,31 @@ class Solver:
         ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
         self._check(self.lib.sap_adjoint_step_erk(self.h, ptr(zeta_prev), ptr(lam), dt, ptr(grad_nu),
                                                   ptr(stages_out), C.byref(st), _stream_handle(stream)))
+        return st
+
+    def field_grad_buffers(self, device="cuda", which=FIELDS) -> dict:
+        """Zeroed FP64 device accumulators for sap_adjoint_step, one per field array (shapes of
+        field_arrays; absent face axes are None)."""
+        import torch
+        shapes = {k: (None if v is None else v.size) for k, v in self.field_arrays(self.prob).items()}
+        return {k: (None if shapes[k] is None else torch.zeros(shapes[k], dtype=torch.float64, device=device))
+                for k in which}
+
+    def adjoint_step(self, scheme: str, zeta_prev, zeta_next, lam, dt: float, grads: dict = None,
+                     tol: float = 1e-12, restart: int = 30, maxit: int = 4000, stream=None) -> SolverStats:
+        """sap_adjoint_step: lam <- dJ/dzeta_prev (in place) and dJ/d(field) added into the device
+        tensors of ``grads`` (keys of FIELDS; missing keys or None: not formed)."""
+        st = SolverStats()
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        g = FieldGrads()
+        grads = grads or {}
+        for k in ("U", "gradU", "DUDt", "Bw", "nu", "s000"):
+            setattr(g, k, ptr(grads.get(k)))
+        for a in range(3):
+            g.Uface[a] = ptr(grads.get(f"Uface{a}"))
+        self._check(self.lib.sap_adjoint_step(self.h, SCHEME[scheme], ptr(zeta_prev), ptr(zeta_next), ptr(lam),
+                                              dt, tol, restart, maxit, C.byref(g), C.byref(st),
+                                              _stream_handle(stream)))
         return st
 
     def apply_cost(self):

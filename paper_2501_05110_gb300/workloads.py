@@ -137,15 +137,19 @@ def shock_profile(U1, r, Ls):
 
 def shock(nx=256, npc=64, k=1, lmax=3, U1=0.1, r=4.0, Ls=0.5, xr=(-200.0, 200.0), lnpr=(0.0, 10.0),
           nu0=1.0, nu_field=None, Q=0.1, x0=0.0, lnp0=1.0, sig_x=None, sig_lnp=None, B0=1.0,
-          dt=1.0, nsteps=2000, tol=1e-10, restart=30, x_edges=None, name=None):
+          dt=1.0, nsteps=2000, tol=1e-10, restart=30, x_edges=None, name=None, momentum="lnp"):
     """Parallel shock (Sec. 4.4 set-up, with this library's readings of its open points): x upstream
     zero inflow, x downstream continuous, ln p zero inflow at both ends; nu = nu0 p (or a given
     field); B = B0 e_x; Gaussian isotropic source at (x0, ln p0) with rate Q; zero initial state;
-    Crank--Nicolson with GMRES."""
+    Crank--Nicolson with GMRES.  momentum="p" resolves linear p instead of ln p: the momentum axis
+    then has uniform cells in p over [exp(lnpr[0]), exp(lnpr[1])] (the source keeps its ln p shape)."""
     xe = np.linspace(xr[0], xr[1], nx + 1) if x_edges is None else np.asarray(x_edges, float)
-    pe = np.linspace(lnpr[0], lnpr[1], npc + 1)
+    if momentum == "p":
+        pe = np.linspace(math.exp(lnpr[0]), math.exp(lnpr[1]), npc + 1)
+    else:
+        pe = np.linspace(lnpr[0], lnpr[1], npc + 1)
     dx = (xe[-1] - xe[0]) / (len(xe) - 1)
-    dlnp = (pe[-1] - pe[0]) / npc
+    dlnp = (lnpr[1] - lnpr[0]) / npc
     sx = 2 * dx if sig_x is None else sig_x
     sp_ = 2 * dlnp if sig_lnp is None else sig_lnp
     n = (lmax + 1) ** 2
@@ -158,13 +162,25 @@ def shock(nx=256, npc=64, k=1, lmax=3, U1=0.1, r=4.0, Ls=0.5, xr=(-200.0, 200.0)
         return math.sqrt(4 * math.pi) * s
 
     return Problem(
-        name=name or f"shock_x{len(xe)-1}_lnp{npc}_k{k}_l{lmax}",
-        axes=("x", "lnp"), edges=[xe, pe], k=k, lmax=lmax,
+        name=name or f"shock_x{len(xe)-1}_{momentum}{npc}_k{k}_l{lmax}",
+        axes=("x", momentum), edges=[xe, pe], k=k, lmax=lmax,
         bc=[("inflow0", "continuous"), ("inflow0", "inflow0")],
         terms=frozenset({"adv", "mom", "rot", "coll", "src"}),
         U=U, gradU=gradU, DUDt=DUDt, B=_const3([B0, 0, 0]), nu=nu, s000=s000,
         f0=lambda c: np.zeros((c.shape[0], n)),
         dt=dt, nsteps=nsteps, scheme="cn", gmres_tol=tol, gmres_restart=restart)
+
+
+def shock_U1_derivative(prob, U1):
+    """d/dU1 of the shock's prescribed fields, as a Problem with the same points: U and grad U are
+    linear in U1 and (U.grad)U is quadratic (see shock_profile), so dU/dU1 = U/U1,
+    d(grad U)/dU1 = grad U / U1, d(DU/Dt)/dU1 = 2 (DU/Dt) / U1; B, nu and the source do not depend
+    on U1."""
+    U, G, DU = prob.U, prob.gradU, prob.DUDt
+    zero = lambda xs, p=None: np.zeros(xs.shape[0])
+    return dataclasses.replace(
+        prob, U=lambda xs: U(xs) / U1, gradU=lambda xs: G(xs) / U1, DUDt=lambda xs: 2.0 * DU(xs) / U1,
+        B=_const3([0, 0, 0]), omega=_const3([0, 0, 0]), nu=zero, s000=zero)
 
 
 # ------------------------------------------------------------------------------------------------

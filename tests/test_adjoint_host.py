@@ -1,7 +1,8 @@
 """Host logic of the trajectory adjoints (checkpoint segments, recomputation, the pairing of states
-with steps, the U1 central difference) on the CPU: CNTrajectory and ERKTrajectory drive a small
-dense stand-in for the library solver, and their gradients must equal torch autograd through the
-same dense trajectory, for every checkpoint interval."""
+with steps, the accumulation of field gradients and the final chain rule to U1) on the CPU:
+CNTrajectory and ERKTrajectory drive a small dense stand-in for the library solver, and their
+gradients must equal torch autograd through the same dense trajectory, for every checkpoint
+interval."""
 import numpy as np
 import pytest
 import torch
@@ -33,10 +34,14 @@ class _Model:
 
 
 class _FakeSolver:
-    """Dense stand-in for sapgpu.Solver with the library's step and adjoint-step semantics."""
+    """Dense stand-in for sapgpu.Solver with the library's step and adjoint-step semantics.  Its one
+    spatial "field" U (a single value) enters L as U B; its derivative problem has dU/dU1 = 2 U1
+    (the model is evaluated at U = U1^2), which exercises the chain rule's use of the field
+    derivative."""
 
     def __init__(self, model, nu, u1):
-        self.m, self.A = model, model.L(nu, u1)
+        self.m, self.A = model, model.L(nu, u1 ** 2)
+        self.u1 = u1
 
     def initial_state(self):
         return self.m.y0.clone()
@@ -91,6 +96,38 @@ class _FakeSolver:
         lam.copy_(lam - AT @ (kb1 + kb2 + kb3 + kb4))
         return _Stats()
 
+    def field_grad_buffers(self, device="cpu", which=()):
+        out = {k: None for k in which}
+        out["U"] = torch.zeros(1, dtype=torch.float64)
+        out["nu"] = torch.zeros(NPV, dtype=torch.float64)
+        return out
+
+    def field_arrays(self, prob):
+        return {"U": np.array([prob])}  # the fake derivative problem is the number dU/dU1
+
+    def adjoint_step(self, scheme, zp, zn, lam, dt, grads, tol=1e-12, restart=30, maxit=4000):
+        B = self.m.B
+        if scheme == "cn":
+            I = torch.eye(N, dtype=torch.float64)
+            mu = torch.linalg.solve((I + 0.5 * dt * self.A).T, lam)
+            lam.copy_((I - 0.5 * dt * self.A).T @ mu)
+            self._grad_add(grads["nu"], -0.5 * dt, mu, zp + zn)
+            grads["U"] += -0.5 * dt * (mu @ (B @ (zp + zn)))
+        else:
+            AT = self.A.T
+            Y2 = zp + 0.5 * dt * self._F(zp)
+            Y3 = zp + 0.5 * dt * self._F(Y2)
+            Y4 = zp + dt * self._F(Y3)
+            kb4 = dt / 6 * lam
+            kb3 = dt / 3 * lam - dt * (AT @ kb4)
+            kb2 = dt / 3 * lam - 0.5 * dt * (AT @ kb3)
+            kb1 = dt / 6 * lam - 0.5 * dt * (AT @ kb2)
+            for kb, Y in ((kb1, zp), (kb2, Y2), (kb3, Y3), (kb4, Y4)):
+                self._grad_add(grads["nu"], -1.0, kb, Y)
+                grads["U"] += -(kb @ (B @ Y))
+            lam.copy_(lam - AT @ (kb1 + kb2 + kb3 + kb4))
+        return _Stats()
+
     def close(self):
         pass
 
@@ -99,11 +136,14 @@ class _FakeFamily(adjoint.CNProblemFamily):
     def solver(self, nu_nodes, U1):
         return _FakeSolver(self.make_problem, nu_nodes, U1)
 
+    def field_derivative(self, nu_nodes, U1):
+        return 2.0 * U1  # dU/dU1 of the fake's field U = U1^2
+
 
 def _reference(model, scheme, dt, w, nu0, u10):
     nu = torch.tensor(nu0, requires_grad=True)
     u1 = torch.tensor(u10, dtype=torch.float64, requires_grad=True)
-    A = model.L0 + torch.diag(model.c * nu[model.node]) + u1 * model.B
+    A = model.L0 + torch.diag(model.c * nu[model.node]) + u1 ** 2 * model.B
     I = torch.eye(N, dtype=torch.float64)
     F = lambda y: model.s - A @ y
     y = model.y0.clone()
@@ -131,4 +171,4 @@ def test_trajectory_adjoint_matches_autograd(scheme, checkpoint):
     (w @ fn.apply(nu_t, u1_t, fam)).backward()
     g_nu, g_u1 = _reference(model, scheme, dt, w, nu0, 0.3)
     np.testing.assert_allclose(nu_t.grad.numpy(), g_nu, rtol=1e-11, atol=1e-13 * np.abs(g_nu).max())
-    assert abs(float(u1_t.grad) - g_u1) < 1e-7 * abs(g_u1)
+    assert abs(float(u1_t.grad) - g_u1) < 1e-11 * abs(g_u1)

@@ -1,7 +1,8 @@
 """Discrete adjoint of RK4 trajectories (library adjoint step + torch.autograd.Function with
 checkpoints): one step against the oracle's transposed RK4 step, gradients with respect to a per-cell
-nu(x, p) against the oracle's tangent-linear RK4 trajectory, and the U1 gradient against central
-finite differences of GPU trajectories."""
+nu(x, p) against the oracle's tangent-linear RK4 trajectory, and the U1 gradient (library field
+gradients chained to U1) against central finite differences of GPU trajectories and the oracle's
+tangent."""
 import numpy as np
 import pytest
 
@@ -137,6 +138,20 @@ def test_adjoint_erk_U1_gradient_vs_finite_differences(setup):
     e = 1e-5 * 0.1
     fd = (_J_forward(S, None, 0.1 + e) - _J_forward(S, None, 0.1 - e)) / (2 * e)
     assert abs(fd - g_u1) < 1e-5 * abs(fd), (fd, g_u1)
+
+
+def test_adjoint_erk_U1_gradient_vs_oracle_tangent(setup):
+    """dJ/dU1 from the library's field gradients equals the FP64 oracle's tangent-linear RK4
+    trajectory with dD/dU1 from the Richardson difference of its assembled D."""
+    from oracle import dg, steppers
+    S = setup
+    _, g_u1, _ = _adjoint_grads(S, checkpoint=2)
+    make = lambda U1: _base(U1, S["nu_cell_fun"])
+    d0 = dg.Discretisation(make(0.1))
+    dD = dg.parameter_derivative(make, 0.1, 1e-4)
+    _, dz = steppers.rk4_tangent(d0.M, d0.D, d0.h, dD, np.zeros(d0.N), DT, NSTEPS)
+    want = float(S["w"].cpu().numpy() @ d0.to_gauss_nodal(dz))
+    assert abs(g_u1 - want) < 1e-7 * abs(want), (g_u1, want)
 
 
 def test_adjoint_steps_degenerate_inputs(setup):
