@@ -1,23 +1,30 @@
 #!/usr/bin/env python
-"""Throughput benchmark of the GB300 dG-VFP library on the parallel-shock Crank--Nicolson workload.
+"""Throughput benchmark of the GB300 dG-VFP library.
 
-Workload (default, "shock"): reduced phase space (x, ln p), x in [-200, 200] with 256 cells,
-ln p in [0, 10] with 64 cells, dG degree 1, lmax = 3 (n = 16), tanh shock U1 = 0.1, r = 4,
-nu = p, B = e_x, Gaussian source, FP64; one step = one Crank--Nicolson step (dt = 1) solved by
-restarted GMRES(30) to a true relative residual of 1e-10.  N = 1,048,576 DoFs.
+Headline (one step = one Crank--Nicolson step of the parallel shock): reduced phase space (x, ln p),
+x in [-200, 200] with 256 cells, ln p in [0, 10] with 64 cells, dG degree 1, l_max = 3 (n = 16), tanh
+shock U1 = 0.1, r = 4, nu = p, B = e_x, Gaussian source, FP64, dt = 1, restarted GMRES(30) to a true
+relative residual of 1e-10.  N = 1,048,576 DoFs.  `value` = whole-job DoF-updates/s per CN step.
 
-Prints ONE JSON line.  `value` is whole-job DoF-updates/s per CN step (N * steps / time, summed
-over ranks; each rank runs an independent replica: the single-shock solve does not shard).
-Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the stream the
-library runs on, with a 256 MiB L2 flush between timed steps (outside the events).
-`--impl reference` times the FP64 CPU oracle (the only baseline that exists: the paper publishes
-no performance numbers) on the same workload and prints the same line with "impl": "reference".
+The same JSON line carries, under "workloads", the other configurations timed in the same run, each
+with its own value, roofline of its dominant kernel, clocks and end-to-end leg:
+  shock_fp32     the same CN steps in the precision form (FP32 apply, FP64 residual/refinement);
+  box3d_fp64/32  the 48^3 periodic box (k = 2, l_max = 5, N = 107,495,424), DoF-updates/s per RK4
+                 stage (FP64 plain; FP32 stage derivatives with FP64 state);
+  batched_fp32   512 seeded shock instances (l_max in {1,3,5,7}, 64..512 x-cells), one CN step of
+                 the whole batch per step (FP32 apply + FP64 GMRES), beside the same instances run one
+                 at a time on the FP64 plain path;
+  adjoint_fp64   forward + reverse (discrete adjoint with field gradients) of CN steps of the shock
+                 with a per-cell log-normal nu, checkpoints every 50 steps; seconds per step.
+Timing: W untimed warm-up steps, then K steps bracketed by CUDA events on the library's stream; the
+shock state (8 MB) is L2-resident, so a 256 MiB buffer is written between timed steps (outside the
+events); the box and batch states are larger than L2.  `--impl reference` times the FP64 CPU oracle
+(its multi-threaded C driver of the assembled CN step, all host cores) on the headline workload.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -31,83 +38,64 @@ METRIC = "phase-space DoF-updates/s per CN step"
 UNIT = "DoF-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e-3  # SMs x DFMA/clk/SM x 2 flop x max GHz = 1.2586 TFLOP/s (FP64)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3  # SMs x FFMA/clk/SM x 2 flop x max GHz = 80.5 TFLOP/s (FP32)
-# DRAM bytes (read + write) per apply launch from the ncu capture in profiles/rows_kernel_fp64_shock.md,
-# valid only for the kernel source it was taken on (first 16 hex of sha256 of csrc/apply_rows.cu)
-APPLY_TRAFFIC = {"29ab0aa921f8c3aa": 11002112.0}
+HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture, valid only for the
+# kernel source it was taken on (first 16 hex of sha256 of csrc/apply_rows.cu); see profiles/
+APPLY_TRAFFIC = {}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--workload", default="shock", choices=["shock", "box3d", "batched", "adjoint"])
+    ap.add_argument("--workload", default="all", choices=["all", "shock", "box3d", "batched", "adjoint"])
     ap.add_argument("--cells", type=int, default=48, help="box3d: cells per axis")
     ap.add_argument("--instances", type=int, default=512, help="batched: number of shock instances")
+    ap.add_argument("--batched-steps", type=int, default=3, help="batched: timed CN steps (each ~seconds)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-single", type=int, default=16,
                     help="batched: also run this many of the instances one at a time on the FP64 path")
-    ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
-    ap.add_argument("--apply-reps", type=int, default=200)
+    ap.add_argument("--apply-reps", type=int, default=50)
     return ap.parse_args()
 
 
-def workload_problem():
-    from paper_2501_05110_gb300 import workloads as W
-    return W.shock()
-
-
-def workload_config(prob, extra=None):
-    cfg = {"workload": "shock_x256_lnp64_k1_l3_cn_dt1_tol1e-10", "dofs": prob.ndofs,
-           "cells": prob.ncells, "degree": prob.k, "lmax": prob.lmax, "gmres_restart": prob.gmres_restart,
-           "gmres_tol": prob.gmres_tol, "dt": prob.dt, "l2": "flushed between timed steps (256 MiB write)",
-           "parallelism": "replicas"}
-    if extra:
-        cfg.update(extra)
-    return cfg
-
-
 # ------------------------------------------------------------------------------------------------
-# CPU oracle timing (runs in a fresh single-threaded interpreter)
+# peaks
 # ------------------------------------------------------------------------------------------------
-def cpu_worker(nsteps: int):
-    """Time the oracle's CN step (assembled CSR, GMRES(30) with Jacobi, tol 1e-10) on the full
-    workload; assembly is set-up and untimed."""
-    import numpy as np
-    from oracle import dg, steppers
-    prob = workload_problem()
-    d = dg.Discretisation(prob)
-    A = (d.M + 0.5 * prob.dt * d.D).tocsr()
-    B = (d.M - 0.5 * prob.dt * d.D).tocsr()
-    z = np.zeros(d.N)
-    times, its = [], []
-    for _ in range(nsteps):
-        t0 = time.perf_counter()
-        b = B @ z + prob.dt * d.h
-        z, it = steppers.gmres(A, b, z, tol=prob.gmres_tol, restart=prob.gmres_restart)
-        times.append(time.perf_counter() - t0)
-        its.append(it)
-    print(json.dumps({"times": times, "its": its, "N": d.N}))
+def hbm_peak():
+    """(GB/s, provenance) from MEASURED_PEAKS.json, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "of measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "of fallback"
 
 
-def run_cpu_oracle(nsteps: int, skip: int = 0) -> dict:
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    env.pop("CUDA_VISIBLE_DEVICES", None)
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(nsteps)],
-                       capture_output=True, text=True, env=env, cwd=ROOT, timeout=1800)
-    if r.returncode != 0:
-        raise RuntimeError("cpu worker failed: " + r.stderr[-2000:])
-    out = json.loads(r.stdout.strip().splitlines()[-1])
-    times = out["times"][skip:]
-    t = sum(times)
-    return {"value": out["N"] * len(times) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "ms_per_step": 1e3 * t / len(times),
-            "sample": f"{len(times)} timed CN steps of the full workload (N={out['N']}) with the oracle's "
-                      f"assembled CSR + GMRES(30)/Jacobi, tol 1e-10, single thread; assembly untimed; "
-                      f"{statistics.mean(out['its']):.1f} GMRES iterations/step",
-            "seconds": t}
+def roofline_entry(kernel, flops, abytes, t_apply, precision, traffic=None, units=None):
+    """ALU roofline of an operator apply (the operator is above the ridge point in both
+    precisions), with the HBM view of its algorithmic bytes beside it."""
+    peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
+    achieved = flops / t_apply / 1e12
+    hbm, how = hbm_peak()
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": traffic, "kernel": kernel, "apply_us": t_apply * 1e6, "flops_per_apply": flops,
+           "algorithmic_bytes_per_apply": abytes,
+           "hbm_view": {"achieved_gbs": abytes / t_apply / 1e9, "peak_gbs": hbm, "frac": abytes / t_apply / 1e9 / hbm,
+                        "peak_note": how},
+           "peak_note": "nominal from unit counts x max clock (FP64: 2 DFMA/clk/SM; FP32: 128 FFMA/clk/SM); "
+                        "flops from the kernel's cost model (sap_apply_cost)"}
+    if units:
+        out["units_per_launch"] = units
+    return out
+
+
+def apply_sha():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2501_05110_gb300", "csrc", "apply_rows.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
 # ------------------------------------------------------------------------------------------------
@@ -118,11 +106,11 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, tag: str = ""):
         self.gpu = gpu_index
         self.proc = None
         logdir = os.environ.get("SAP_BENCH_LOGDIR", os.path.join(ROOT, "bench_logs"))
-        self.path = os.path.join(logdir, f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(logdir, f"clocks{tag}_rank{gpu_index}.csv")
 
     def start(self):
         try:
@@ -169,7 +157,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------------
-# rank aggregation (replicas: no collective on the data path, only the timing reduction)
+# rank aggregation (replicas / instance shards: no collective on the data path, only the timing)
 # ------------------------------------------------------------------------------------------------
 def max_over_ranks(t: float, world: int, device: str = "cuda") -> float:
     """The job's time: the largest of the ranks' timed regions (all_reduce MAX when world > 1)."""
@@ -182,30 +170,81 @@ def max_over_ranks(t: float, world: int, device: str = "cuda") -> float:
     return float(tt.item())
 
 
+def sum_over_ranks(v: float, world: int, device: str = "cuda") -> float:
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([v], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(tt.item())
+
+
 def job_value(n_per_rank: int, steps: int, world: int, t_max: float) -> float:
     """Whole-job throughput: the DoF-updates of all ranks divided by the slowest rank's time."""
     return n_per_rank * steps * world / t_max
 
 
 # ------------------------------------------------------------------------------------------------
-# GPU arm
+# CPU oracle (multi-threaded C driver of the assembled CN step; assembly untimed)
 # ------------------------------------------------------------------------------------------------
-def run_mine(args):
+def shock_config(prob):
+    """The headline workload's config (identical in both arms)."""
+    return {"workload": "shock_x256_lnp64_k1_l3_cn_dt1_tol1e-10", "dofs": prob.ndofs, "cells": prob.ncells,
+            "degree": prob.k, "lmax": prob.lmax, "gmres_restart": prob.gmres_restart, "gmres_tol": prob.gmres_tol,
+            "dt": prob.dt, "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+
+
+def run_cpu_oracle(nsteps: int, warmup: int = 1) -> dict:
+    import numpy as np
+    from oracle import dg, native
+    from paper_2501_05110_gb300 import workloads as W
+    prob = W.shock()
+    d = dg.Discretisation(prob)
+    drv = native.CNDriver(d, prob.dt)
+    z = np.zeros(d.N)
+    if warmup:
+        drv.steps(z, warmup, tol=prob.gmres_tol, restart=prob.gmres_restart)
+    t0 = time.perf_counter()
+    threads, its = drv.steps(z, nsteps, tol=prob.gmres_tol, restart=prob.gmres_restart)
+    t = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    return {"value": d.N * nsteps / t, "unit": UNIT, "cores": threads, "host_cores": cores, "kind": "oracle",
+            "ms_per_step": 1e3 * t / nsteps, "seconds": t,
+            "sample": f"{nsteps} timed CN steps (after {warmup} warm-up) of the full workload (N={d.N}) by the "
+                      f"oracle's C driver: assembled CSR A = M + dt/2 D, GMRES(30) with right point-Jacobi, "
+                      f"tol 1e-10, OpenMP on {threads} threads; assembly untimed; "
+                      f"{its / nsteps:.1f} GMRES iterations/step"}
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU measurements
+# ------------------------------------------------------------------------------------------------
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def time_apply(torch, sol, x, reps):
+    """Average duration (s) of one operator apply launched alone on the current stream."""
+    y = torch.empty_like(x)
+    for _ in range(3):
+        sol.apply(x, y)
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(reps):
+        sol.apply(x, y)
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e-3 / reps
+
+
+def measure_shock(args, precision, world, rank, local, with_e2e=True):
     import torch
-    import torch.distributed as dist
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    from paper_2501_05110_gb300 import build as sap_build
     from paper_2501_05110_gb300 import sapgpu
-    sap_build.build()
-    prob = workload_problem()
-    sol = sapgpu.Solver(prob, args.precision)
+    from paper_2501_05110_gb300 import workloads as W
+    prob = W.shock()
+    sol = sapgpu.Solver(prob, precision)
     N = sol.N
-    stream = torch.cuda.current_stream()
     state = sol.initial_state()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     tol, restart, maxit = prob.gmres_tol, prob.gmres_restart, 5000
@@ -215,21 +254,21 @@ def run_mine(args):
 
     def barrier():
         if world > 1:
+            import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- device-timed steps --------------------------------------------------------------------
-    start = state.clone()  # the end-to-end leg below replays the same steps from this state
-    clocks = ClockSampler(local)
+    start = state.clone()  # the end-to-end leg replays the same steps from this state
+    clocks = ClockSampler(local, f"_shock_{precision}")
     clocks.start()
     barrier()
     t_steps, its, launches = [], [], 0
     for _ in range(args.steps):
         flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        e0, e1 = _events(torch)
+        e0.record()
         st = sol.step_cn(state, prob.dt, 1, tol, restart, maxit)
-        e1.record(stream)
+        e1.record()
         e1.synchronize()
         t_steps.append(e0.elapsed_time(e1) * 1e-3)
         its.append(st.iterations)
@@ -237,247 +276,197 @@ def run_mine(args):
     barrier()
     clk = clocks.stop()
     t_total = max_over_ranks(sum(t_steps), world)
-    value = job_value(N, args.steps, world, t_total)
-
-    # ---- end to end through the public API with host buffers -------------------------------------
-    host = torch.empty(N, dtype=torch.float64, pin_memory=True)
-    host.copy_(start.cpu())
-    dev = torch.empty_like(state)
-    barrier()
-    t_e2e, its_e2e = 0.0, []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        dev.copy_(host, non_blocking=True)
-        its_e2e.append(sol.step_cn(dev, prob.dt, 1, tol, restart, maxit).iterations)
-        host.copy_(dev, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        t_e2e += e0.elapsed_time(e1) * 1e-3
-    barrier()
-    t_e2e = max_over_ranks(t_e2e, world)
-    e2e = {"value": job_value(N, args.steps, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": N * 8,
-           "d2h_bytes_per_step": N * 8, "gmres_iterations_per_step": statistics.mean(its_e2e),
-           "trajectory": "the device-timed steps replayed from the same starting state"}
-
-    # ---- dominant kernel: the operator apply, timed alone on the same stream ----------------------
+    out = {"value": job_value(N, args.steps, world, t_total), "unit": UNIT,
+           "ms_per_step": 1e3 * t_total / args.steps, "steps": args.steps, "warmup": args.warmup,
+           "gmres_iterations_per_step": statistics.mean(its), "gpu_launches": int(launches), "clocks": clk,
+           "dofs": N}
+    if with_e2e:
+        host = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        host.copy_(start.cpu())
+        dev = torch.empty_like(state)
+        barrier()
+        t_e2e, its_e2e = 0.0, []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = _events(torch)
+            e0.record()
+            dev.copy_(host, non_blocking=True)
+            its_e2e.append(sol.step_cn(dev, prob.dt, 1, tol, restart, maxit).iterations)
+            host.copy_(dev, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            t_e2e += e0.elapsed_time(e1) * 1e-3
+        barrier()
+        t_e2e = max_over_ranks(t_e2e, world)
+        out["e2e"] = {"value": job_value(N, args.steps, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": N * 8,
+                      "d2h_bytes_per_step": N * 8, "gmres_iterations_per_step": statistics.mean(its_e2e),
+                      "trajectory": "the device-timed steps replayed from the same starting state"}
     flops, abytes = sol.apply_cost()
-    x = state.clone() if args.precision == "fp64" else state.float()
-    y = torch.empty_like(x)
-    for _ in range(10):
-        sol.apply(x, y)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.apply_reps):
-        sol.apply(x, y)
-    e1.record(stream)
-    e1.synchronize()
-    t_apply = e0.elapsed_time(e1) * 1e-3 / args.apply_reps
-    achieved = flops / t_apply / 1e12
-    peak_alu = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
-    import hashlib
-    src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2501_05110_gb300", "csrc", "apply_rows.cu"), "rb").read()).hexdigest()[:16]
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                "frac": achieved / peak_alu,
-                "traffic": APPLY_TRAFFIC.get(src_sha) if args.precision == "fp64" else None,
-                "kernel": "rows_kernel<double,2,2>" if args.precision == "fp64" else "rows_kernel<float,2,2>",
-                "apply_us": t_apply * 1e6, "flops_per_apply": flops, "algorithmic_bytes_per_apply": abytes,
-                "hbm_view": {"achieved_gbs": abytes / t_apply / 1e9, "peak_gbs": 6746.3,
-                             "frac": abytes / t_apply / 1e9 / 6746.3},
-                "peak_note": "nominal from unit counts x max clock (FP64: 2 DFMA/clk/SM; FP32: 128 FFMA/clk/SM)"}
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if args.precision == "fp64" else "f32 apply + f64 residual/refinement",
-           "data": "synthetic",
-           "config": workload_config(prob, {"gmres_iterations_per_step": statistics.mean(its),
-                                            "precision": args.precision}),
-           "roofline": roofline, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches)}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        try:
-            out["cpu_baseline"] = run_cpu_oracle(2)
-        except Exception as exc:  # reported, not hidden
-            out["cpu_baseline"] = {"value": None, "error": str(exc)[:300]}
-    if rank == 0:
-        print(json.dumps(out))
+    x = state.clone() if precision == "fp64" else state.float()
+    t_apply = time_apply(torch, sol, x, args.apply_reps * 4)
+    traffic = APPLY_TRAFFIC.get(("shock", precision, apply_sha()))
+    out["roofline"] = roofline_entry(f"rows_kernel<{'double' if precision == 'fp64' else 'float'},2,2>", flops,
+                                     abytes, t_apply, precision, traffic, units=f"{N} DoFs (one apply)")
     sol.close()
-    if world > 1:
-        dist.destroy_process_group()
+    return out
 
 
-def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    res = run_cpu_oracle_steps(args.warmup, args.steps)
-    prob = workload_problem()
-    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
-            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": workload_config(prob),
-            "cpu_baseline": {"value": res["value"], "unit": UNIT, "kind": "oracle", "cores": 1,
-                             "sample": res["sample"]},
-            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
-
-
-ORACLE_MAX_STEPS = 30  # about 40 s of single-thread oracle time: the reference arm stays within minutes
-
-
-def run_cpu_oracle_steps(warmup: int, steps: int) -> dict:
-    timed = min(steps, ORACLE_MAX_STEPS)
-    res = run_cpu_oracle(min(warmup, 1) + timed, skip=min(warmup, 1))
-    if timed < steps:
-        res["sample"] += f" (first {timed} of the {steps} requested steps)"
-    return res
-
-
-def run_box3d(args):
-    """RK4 on the 48^3 periodic box (k = 2, lmax = 5, N = 107,495,424): DoF-updates/s per RK4
-    stage; the state (0.86 GB FP64) is larger than L2, so no flush is needed between steps."""
+def measure_box3d(args, precision):
+    """RK4 on the 48^3 periodic box: DoF-updates/s per RK4 stage (4 per step); the state (0.86 GB
+    FP64) is larger than L2."""
     import torch
-    from paper_2501_05110_gb300 import build as sap_build
     from paper_2501_05110_gb300 import sapgpu
     from paper_2501_05110_gb300 import workloads as W
-    sap_build.build()
     prob = W.box3d(ncells=args.cells)
-    sol = sapgpu.Solver(prob, args.precision)
+    sol = sapgpu.Solver(prob, precision)
     N = sol.N
-    stream = torch.cuda.current_stream()
     y = sol.initial_state()
+    start = y.clone()
     for _ in range(args.warmup):
         sol.step_erk(y, prob.dt, 1)
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(0, f"_box3d_{precision}")
     clocks.start()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    e0, e1 = _events(torch)
+    e0.record()
     sol.step_erk(y, prob.dt, args.steps)
-    e1.record(stream)
+    e1.record()
     e1.synchronize()
     clk = clocks.stop()
     t = e0.elapsed_time(e1) * 1e-3
-    flops, abytes = sol.apply_cost()
-    x = (y if args.precision == "fp64" else y.float()).clone()
-    out = torch.empty_like(x)
-    for _ in range(3):
-        sol.apply(x, out)
-    e0.record(stream)
-    for _ in range(args.apply_reps):
-        sol.apply(x, out)
-    e1.record(stream)
+    # end to end: the state comes from and returns to pinned host memory every step
+    host = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    host.copy_(start.cpu())
+    dev = torch.empty_like(y)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        dev.copy_(host, non_blocking=True)
+        sol.step_erk(dev, prob.dt, 1)
+        host.copy_(dev, non_blocking=True)
+    e1.record()
     e1.synchronize()
-    t_apply = e0.elapsed_time(e1) * 1e-3 / args.apply_reps
-    w = 8 if args.precision == "fp64" else 4
-    stage_bytes = N * 5 * 8 if args.precision == "fp64" else N * (2 * 4 + 3 * 8)
-    print(json.dumps({"metric": "phase-space DoF-updates/s per ERK stage", "value": N * 4 * args.steps / t,
-                      "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
-                      "dtype": "f64" if args.precision == "fp64" else "f32 apply, f64 state",
-                      "data": "synthetic", "config": {"workload": f"box3d_{args.cells}c_k2_l5_erk4_dt0.01", "dofs": N,
-                                                      "l2": "state larger than L2"},
-                      "apply": {"us": t_apply * 1e6, "flops": flops, "tflops": flops / t_apply / 1e12,
-                                "algorithmic_bytes": abytes, "gbs": abytes / t_apply / 1e9,
-                                "hbm_frac": abytes / t_apply / 1e9 / 6746.3},
-                      "stage_algorithmic_bytes_per_dof": stage_bytes / N,
-                      "stage_gbs": stage_bytes * 4 * args.steps / t / 1e9, "clocks": clk}))
+    t_e2e = e0.elapsed_time(e1) * 1e-3
+    flops, abytes = sol.apply_cost()
+    x = (y if precision == "fp64" else y.float()).clone()
+    del host, dev
+    t_apply = time_apply(torch, sol, x, max(5, args.apply_reps // 5))
+    stage_bytes = N * 5 * 8 if precision == "fp64" else N * (2 * 4 + 3 * 8)
+    traffic = APPLY_TRAFFIC.get(("box3d", precision, apply_sha()))
+    out = {"metric": "phase-space DoF-updates/s per ERK stage", "value": N * 4 * args.steps / t, "unit": UNIT,
+           "ms_per_step": 1e3 * t / args.steps, "steps": args.steps, "warmup": args.warmup,
+           "dtype": "f64" if precision == "fp64" else "f32 stage derivatives, f64 state",
+           "config": {"workload": f"box3d_{args.cells}c_k2_l5_erk4_dt0.01", "dofs": N, "l2": "state larger than L2"},
+           "stage_algorithmic_bytes_per_dof": stage_bytes / N,
+           "stage_gbs": stage_bytes * 4 * args.steps / t / 1e9,
+           "e2e": {"value": N * 4 * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": N * 8,
+                   "d2h_bytes_per_step": N * 8},
+           "roofline": roofline_entry(f"rows_kernel<{'double' if precision == 'fp64' else 'float'},3,3>", flops, abytes,
+                                      t_apply, precision, traffic, units=f"{N} DoFs (one apply)"),
+           "clocks": clk, "gpu_launches": 4 * args.steps + (args.steps if precision == "fp32" else 0)}
+    sol.close()
+    return out
 
 
-def run_batched(args):
-    """CN steps on a batch of independent seeded shock instances (r, nu0, lmax, x-cell count drawn
-    per instance), one batched apply launch per operator application, per-instance GMRES."""
+def measure_batched(args, world=1, rank=0, local=0):
+    """CN steps on a batch of independent seeded shock instances (r, nu0, l_max, x-cell count drawn
+    per instance), FP32 apply + FP64 GMRES.  With several ranks the instances are sharded across them
+    (instance i on rank i mod world): no exchange, only the timing reduction."""
     import torch
-    from paper_2501_05110_gb300 import build as sap_build
-    from paper_2501_05110_gb300 import sapgpu
+    from paper_2501_05110_gb300 import sapgpu, sharding
     from paper_2501_05110_gb300 import workloads as W
-    sap_build.build()
-    probs = W.batched_shocks(count=args.instances)
+    probs_all = W.batched_shocks(count=args.instances)
+    mine = sharding.shard_instances(len(probs_all), rank, world)
+    probs = [probs_all[i] for i in mine]
     t0 = time.perf_counter()
-    batch = sapgpu.Batch(probs, args.precision)
+    batch = sapgpu.Batch(probs, "fp32")
     t_setup = time.perf_counter() - t0
     N = batch.N
     y = batch.initial_state()
-    stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    start = y.clone()
+    for _ in range(1):
         batch.step_cn(y, 1.0, 1, 1e-10, 30, 20000)
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(local, "_batched")
     clocks.start()
     torch.cuda.synchronize()
     times, its, launches = [], [], 0
-    for _ in range(args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+    for _ in range(args.batched_steps):
+        e0, e1 = _events(torch)
+        e0.record()
         st = batch.step_cn(y, 1.0, 1, 1e-10, 30, 20000)
-        e1.record(stream)
+        e1.record()
         e1.synchronize()
         times.append(e0.elapsed_time(e1) * 1e-3)
         its.append(st.max_iterations)
         launches += st.kernel_launches
     clk = clocks.stop()
-    x = (y if args.precision == "fp64" else y.float()).clone()
-    out = torch.empty_like(x)
-    for _ in range(2):
-        batch.apply(x, out)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(5):
-        batch.apply(x, out)
-    e1.record(stream)
+    t = max_over_ranks(sum(times), world)
+    n_all = int(sum_over_ranks(N, world))
+    # end to end: the whole batch state from / to pinned host memory each step
+    host = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    host.copy_(start.cpu())
+    dev = torch.empty_like(y)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(args.batched_steps):
+        dev.copy_(host, non_blocking=True)
+        batch.step_cn(dev, 1.0, 1, 1e-10, 30, 20000)
+        host.copy_(dev, non_blocking=True)
+    e1.record()
     e1.synchronize()
-    t_apply = e0.elapsed_time(e1) * 1e-3 / 5
+    t_e2e = max_over_ranks(e0.elapsed_time(e1) * 1e-3, world)
+    del host, dev
+    x = y.float()
+    t_apply = time_apply(torch, batch, x, 3)
     flops, abytes = batch.apply_cost()
-    t = sum(times)
     batch.close()
-    # the same instances run one at a time on the plain FP64 path (equal tolerance, same steps): every
-    # (count/K)-th instance, each from its own initial state with the same warm-up
     single = None
-    if args.compare_single > 0:
+    if args.compare_single > 0 and rank == 0:
+        # the same kind of instances one at a time on the plain FP64 path (equal tolerance)
         idx = list(range(0, len(probs), max(1, len(probs) // args.compare_single)))[:args.compare_single]
         dofs, t_single, its_single = 0, 0.0, []
         for i in idx:
             sol = sapgpu.Solver(probs[i], "fp64")
             ys = sol.initial_state()
-            for _ in range(args.warmup):
-                sol.step_cn(ys, 1.0, 1, 1e-10, 30, 20000)
+            sol.step_cn(ys, 1.0, 1, 1e-10, 30, 20000)
             torch.cuda.synchronize()
-            for _ in range(args.steps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
+            for _ in range(args.batched_steps):
+                e0, e1 = _events(torch)
+                e0.record()
                 st = sol.step_cn(ys, 1.0, 1, 1e-10, 30, 20000)
-                e1.record(stream)
+                e1.record()
                 e1.synchronize()
                 t_single += e0.elapsed_time(e1) * 1e-3
                 its_single.append(st.iterations)
             dofs += sol.N
             sol.close()
-        single = {"path": "one instance at a time, FP64 plain, tol 1e-10", "instances": len(idx),
-                  "instance_index_step": max(1, len(probs) // args.compare_single), "dofs": dofs,
-                  "value": dofs * args.steps / t_single, "unit": UNIT,
+        single = {"path": "one instance at a time, FP64 plain, tol 1e-10", "instances": len(idx), "dofs": dofs,
+                  "value": dofs * args.batched_steps / t_single, "unit": UNIT,
                   "gmres_iterations_per_step": statistics.mean(its_single)}
-    print(json.dumps({"metric": "phase-space DoF-updates/s per CN step (batched)", "value": N * args.steps / t,
-                      "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
-                      "dtype": "f64" if args.precision == "fp64" else "f32 apply + f64 residual/refinement",
-                      "data": "synthetic",
-                      "config": {"workload": f"batched_shocks_{args.instances}_seed4", "dofs": N,
-                                 "instances": args.instances, "setup_s": t_setup,
-                                 "max_gmres_iterations_per_step": statistics.mean(its),
-                                 "lmax_counts": {str(l): sum(p.lmax == l for p in probs) for l in (1, 3, 5, 7)}},
-                      "apply": {"us": t_apply * 1e6, "gbs": abytes / t_apply / 1e9,
-                                "hbm_frac": abytes / t_apply / 1e9 / 6746.3, "tflops": flops / t_apply / 1e12},
-                      "gpu_launches": int(launches), "clocks": clk, "single_instances": single}))
+    return {"metric": "phase-space DoF-updates/s per CN step (batched)", "value": n_all * args.batched_steps / t,
+            "unit": UNIT, "ms_per_step": 1e3 * t / args.batched_steps, "steps": args.batched_steps, "warmup": 1,
+            "dtype": "f32 apply + f64 residual/refinement",
+            "config": {"workload": f"batched_shocks_{args.instances}_seed4", "dofs": n_all,
+                       "instances": args.instances, "instances_per_rank": len(probs), "setup_s": t_setup,
+                       "l2": "state larger than L2",
+                       "lmax_counts": {str(l): sum(p.lmax == l for p in probs_all) for l in (1, 3, 5, 7)}},
+            "max_gmres_iterations_per_step": statistics.mean(its),
+            "e2e": {"value": n_all * args.batched_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": N * 8,
+                    "d2h_bytes_per_step": N * 8},
+            "roofline": roofline_entry("rows_kernel_batched<float,2,2>", flops, abytes, t_apply, "fp32",
+                                       APPLY_TRAFFIC.get(("batched", "fp32", apply_sha())),
+                                       units=f"{N} DoFs (one batched apply)"),
+            "clocks": clk, "gpu_launches": int(launches), "single_instances": single}
 
 
-def run_adjoint(args):
-    """Forward + reverse (discrete adjoint) of CN steps on the full shock workload with a per-cell
-    log-normal nu field, checkpoints every 50 steps; reports wall time per forward+reverse step."""
+def measure_adjoint(args):
+    """Forward + reverse (discrete adjoint with field gradients) of CN steps on the full shock with a
+    per-cell log-normal nu field, checkpoints every 50 steps; wall time per forward+reverse step."""
     import numpy as np
     import torch
     from paper_2501_05110_gb300 import adjoint, sapgpu
-    from paper_2501_05110_gb300 import build as sap_build
     from paper_2501_05110_gb300 import workloads as W
-    sap_build.build()
     base = W.shock()
     xe, pe = base.edges
     nu_fun, _ = W.lognormal_cell_nu(xe, pe, seed=6)
@@ -495,7 +484,6 @@ def run_adjoint(args):
     target = torch.from_numpy(np.random.default_rng(5).normal(0.0, 1e-3, 64)).cuda()
 
     def run(nsteps):
-        """One forward + reverse pass over nsteps CN steps; returns timings (s) and the gradients."""
         fam = adjoint.CNProblemFamily(make_problem=make, nsteps=nsteps, dt=1.0, tol=1e-10, checkpoint=50)
         nu_t = torch.tensor(nu_nodes, dtype=torch.float64, device="cuda", requires_grad=True)
         u1_t = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
@@ -504,8 +492,6 @@ def run_adjoint(args):
         zN = adjoint.CNTrajectory.apply(nu_t, u1_t, fam)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        # spectrum misfit near the shock: S_j = mean over the x-cells within 20 of the shock of the
-        # cell-averaged f_000 at momentum cell j; L = sum_j (S_j - T_j)^2 with a seeded target
         S = zN.view(64, 256, 16, 4)[:, :, 0, :].mean(dim=2)[:, sel].mean(dim=1)
         L = ((S - target) ** 2).sum()
         L.backward()
@@ -513,40 +499,114 @@ def run_adjoint(args):
         t2 = time.perf_counter()
         return t0, t1, t2, fam, nu_t, u1_t
 
-    # warm-up passes: the first use of each torch kernel of the loss (and of its backward) can cost
-    # seconds on a fresh machine (module loading); they are not part of the method
-    for _ in range(max(1, args.warmup)):
-        run(2)
-    nsteps = args.steps
-    t0, t1, t2, fam, nu_t, u1_t = run(nsteps)
-    print(json.dumps({"metric": "forward + reverse wall time per CN step (adjoint, FP64)",
-                      "value": (t2 - t0) / nsteps, "unit": "s/step", "steps": nsteps, "warmup": max(1, args.warmup),
-                      "forward_s": t1 - t0, "reverse_s": t2 - t1, "higher_is_better": False,
-                      "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": "adjoint_shock_x256_lnp64_k1_l3_cn_lognormal_nu",
-                                 "checkpoint": 50, "dofs": base.ndofs, "gmres_tol": 1e-10},
-                      "grad_norm_nu": float(nu_t.grad.norm()), "grad_U1": float(u1_t.grad),
-                      "reverse_parts": {k: v for k, v in fam.last_backward.items() if k != "entered_at"}}))
+    run(2)  # first use of the torch kernels of the loss and its backward
+    t0, t1, t2, fam, nu_t, u1_t = run(args.steps)
+    return {"metric": "forward + reverse wall time per CN step (adjoint, FP64)", "value": (t2 - t0) / args.steps,
+            "unit": "s/step", "higher_is_better": False, "steps": args.steps, "warmup": 1,
+            "forward_s": t1 - t0, "reverse_s": t2 - t1, "dtype": "f64",
+            "config": {"workload": "adjoint_shock_x256_lnp64_k1_l3_cn_lognormal_nu", "checkpoint": 50,
+                       "dofs": base.ndofs, "gmres_tol": 1e-10},
+            "grad_norm_nu": float(nu_t.grad.norm()), "grad_U1": float(u1_t.grad),
+            "reverse_parts": dict(fam.last_backward)}
+
+
+def run_mine(args):
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2501_05110_gb300 import build as sap_build
+    sap_build.build()
+    head = measure_shock(args, args.precision, world, rank, local)
+    from paper_2501_05110_gb300 import workloads as W
+    prob = W.shock()
+    out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32 apply + f64 residual/refinement",
+           "data": "synthetic", "config": shock_config(prob), "precision": args.precision,
+           "gmres_iterations_per_step": head["gmres_iterations_per_step"],
+           "roofline": head["roofline"], "e2e": head["e2e"], "clocks": head["clocks"],
+           "gpu_launches": head["gpu_launches"]}
+    workloads = {}
+    if args.workload == "all":
+        plan = [("shock_fp32", lambda: measure_shock(args, "fp32", world, rank, local)),
+                ("batched_fp32", lambda: measure_batched(args, world, rank, local))]
+        if world == 1:
+            plan[1:1] = [("box3d_fp64", lambda: measure_box3d(args, "fp64")),
+                         ("box3d_fp32", lambda: measure_box3d(args, "fp32"))]
+            plan.append(("adjoint_fp64", lambda: measure_adjoint(args)))
+        for name, fn in plan:
+            try:
+                workloads[name] = fn()
+            except Exception as exc:  # reported in the line, not hidden
+                workloads[name] = {"error": f"{type(exc).__name__}: {str(exc)[:300]}"}
+            torch.cuda.empty_cache()
+        out["workloads"] = workloads
+        out["gpu_launches"] += sum(int(w.get("gpu_launches", 0)) for w in workloads.values())
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = run_cpu_oracle(min(args.steps, 10))
+        except Exception as exc:  # reported, not hidden
+            out["cpu_baseline"] = {"value": None, "error": str(exc)[:300]}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_single_workload(args):
+    """--workload box3d | batched | adjoint | shock: one configuration on its own line."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2501_05110_gb300 import build as sap_build
+    sap_build.build()
+    if args.workload == "box3d":
+        res = measure_box3d(args, args.precision)
+    elif args.workload == "batched":
+        res = measure_batched(args)
+    elif args.workload == "adjoint":
+        res = measure_adjoint(args)
+    else:
+        res = measure_shock(args, args.precision, 1, 0, 0)
+    res.setdefault("n_gpus", 1)
+    print(json.dumps(res))
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle (its multi-threaded C driver, all host cores) on the
+    headline workload; each timed step is one full CN step of the 1,048,576-DoF shock."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2501_05110_gb300 import workloads as W
+    timed = min(args.steps, 30)
+    res = run_cpu_oracle(timed, warmup=min(args.warmup, 1))
+    if timed < args.steps:
+        res["sample"] += f" (first {timed} of the {args.steps} requested steps)"
+    prob = W.shock()
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": shock_config(prob),
+            "cpu_baseline": {"value": res["value"], "unit": UNIT, "kind": "oracle", "cores": res["cores"],
+                             "sample": res["sample"]},
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
 
 
 def main():
     args = parse()
-    if args.workload == "box3d" and not args.cpu_worker:
-        run_box3d(args)
-        return
-    if args.workload == "batched" and not args.cpu_worker:
-        run_batched(args)
-        return
-    if args.workload == "adjoint" and not args.cpu_worker:
-        run_adjoint(args)
-        return
-    if args.cpu_worker:
-        cpu_worker(args.cpu_worker)
-        return
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "all":
         run_mine(args)
+    else:
+        run_single_workload(args)
 
 
 if __name__ == "__main__":
