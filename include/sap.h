@@ -80,7 +80,7 @@ typedef struct {
   const double* edges[3];   /* host, ncells[a]+1 strictly increasing edges (graded meshes allowed) */
   int bc_lo[3], bc_hi[3];   /* SAP_BC_*; periodic must be set on both ends                         */
   int lmax;                 /* expansion order, 0..11; n = (lmax+1)^2 (Sec. 2.1)                  */
-  int degree;               /* dG degree k >= 0 (Sec. 3.1), k <= 4                                 */
+  int degree;               /* dG degree k >= 0 (Sec. 3.1), k <= 5                                 */
   double V;                 /* particle speed, used only without a momentum axis                  */
   unsigned terms;           /* OR of SAP_TERM_*                                                    */
 } sap_desc;
@@ -134,6 +134,16 @@ sap_status sap_set_fields(sap_handle h, const double* U, const double* gradU, co
                           const double* Bw, const double* const Uface[3], const double* nu,
                           const double* s000);
 
+/* sap_set_fields with the field arrays in device memory (same shapes and layouts; any pointer may be
+ * NULL): the arrays are read on `stream`, after the work already queued there (for instance the
+ * kernels that produced them), with one synchronisation of that stream; then the term tables and the
+ * momentum-face eigen data are built as in sap_set_fields.  The device arrays may be reused or freed
+ * once the call returns.  Errors: SAP_EINVAL (also for a batch handle: set the fields of its
+ * instances), SAP_ENOMEM, SAP_ECUDA. */
+sap_status sap_set_fields_device(sap_handle h, const double* U, const double* gradU, const double* DUDt,
+                                 const double* Bw, const double* const Uface[3], const double* nu,
+                                 const double* s000, sap_stream stream);
+
 /* Number of degrees of freedom N = ncells * n * (k+1)^D (Sec. 3.1). */
 sap_status sap_num_dofs(sap_handle h, int64_t* n);
 
@@ -163,6 +173,15 @@ sap_status sap_step_erk(sap_handle h, double* state, double dt, int nsteps, sap_
  * Errors: SAP_EINVAL, SAP_ENOCONV (state holds the last iterate), SAP_ECUDA. */
 sap_status sap_step_cn(sap_handle h, double* state, double dt, int nsteps, double tol, int restart,
                        int maxit, sap_solver_stats* stats, sap_stream stream);
+
+/* Advance the FP64 device state by `nsteps` steps of the theta-method (Eq. theta-method):
+ * (1 + theta dt M^-1 D) zeta^n = (1 - (1 - theta) dt M^-1 D) zeta^(n-1) + dt M^-1 h, theta in [0, 1]
+ * (0: forward Euler, 1: backward Euler, 1/2: Crank--Nicolson, the same as sap_step_cn), solved as in
+ * sap_step_cn (for theta = 0 the system matrix is the identity and GMRES ends after one iteration).
+ * Synchronous.  Errors: SAP_EINVAL (theta outside [0, 1], bad arguments), SAP_ENOCONV, SAP_ECUDA,
+ * SAP_EUNSUPPORTED (batch handles with theta != 1/2). */
+sap_status sap_step_theta(sap_handle h, double* state, double dt, double theta, int nsteps, double tol, int restart,
+                          int maxit, sap_solver_stats* stats, sap_stream stream);
 
 /* One step of the discrete adjoint of the Crank--Nicolson step (Eq. theta-method, theta = 1/2).
  * The forward step maps zeta_prev to zeta_next through A zeta_next = B zeta_prev + dt M^-1 h with

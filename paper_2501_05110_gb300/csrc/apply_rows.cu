@@ -309,8 +309,10 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
   const T* Fc = Fs + lc * n * NLP;
   const T* CVc = CV + lc * nvt * NLP;
   if (valid) {
-    for (int t = 0; t < P.nreact; ++t)
+    for (int t = 0; t < P.nreact; ++t) {
+      if ((P.react_zero >> t) & 1u) continue;  // identically zero coefficient
       term_apply<T, NL, NLP>(P.bank, P.react[t].mat, (P.react_uni >> t) & 1u, CVc + t * NLP, r, n, Fc, acc);
+    }
     static_for<0, D>([&](auto ac) {
       constexpr int a = decltype(ac)::value;
       const AxisInfo& A = P.ax[a];
@@ -318,9 +320,11 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
       T g[NL];
 #pragma unroll
       for (int i = 0; i < NL; ++i) g[i] = T(0);
-      for (int t = 0; t < A.nadv; ++t)
+      for (int t = 0; t < A.nadv; ++t) {
+        if ((P.adv_zero[a] >> t) & 1u) continue;
         term_apply<T, NL, NLP>(P.bank, A.adv[t].mat, (P.adv_uni[a] >> t) & 1u, CVc + (adv_off[a] + t) * NLP, r, n,
                                Fc, g);
+      }
       const T invh = __ldg(P.cell_invh + cell * D + a);
       constexpr int qa = ipow(Q, a);
 #pragma unroll
@@ -414,6 +418,7 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
 #pragma unroll
         for (int fp = 0; fp < NF; ++fp) J[fp] = T(0);
         for (int t = 0; t < A.nadv; ++t) {
+          if ((P.adv_zero[a] >> t) & 1u) continue;
           T tmp[NF];
 #pragma unroll
           for (int fp = 0; fp < NF; ++fp) tmp[fp] = T(0);

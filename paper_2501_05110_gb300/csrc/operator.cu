@@ -1173,12 +1173,12 @@ static cudaError_t enqueue_arnoldi(sap_ctx* c, const OpParams<TV>& PV, TV* V, do
 // private stream for this operator (forward or transposed), dt, field set and workspace; nullptr
 // (direct launches) if capture fails.
 template <typename TV, bool TRANS>
-static cudaGraphExec_t arnoldi_graph(sap_ctx* c, const OpParams<TV>& PV, TV* V, double dt, int j0, int cnt) {
+static cudaGraphExec_t arnoldi_graph(sap_ctx* c, const OpParams<TV>& PV, TV* V, double alpha, int j0, int cnt) {
   const int kind = TRANS ? 1 : 0;
   const void* ws = static_cast<const void*>(V);
   if (!c->cn_graphs.empty()) {
     const auto& g0 = c->cn_graphs.front();
-    if (g0.dt != dt || g0.fields_version != c->fields_version || g0.ws != ws) cn_graphs_release(c);
+    if (g0.alpha != alpha || g0.fields_version != c->fields_version || g0.ws != ws) cn_graphs_release(c);
   }
   for (const auto& gg : c->cn_graphs)
     if (gg.kind == kind && gg.j0 == j0 && gg.cnt == cnt) return gg.exec;
@@ -1193,7 +1193,7 @@ static cudaGraphExec_t arnoldi_graph(sap_ctx* c, const OpParams<TV>& PV, TV* V, 
     cudaGetLastError();
     return nullptr;
   }
-  const cudaError_t e1 = enqueue_arnoldi<TV, TRANS>(c, PV, V, 0.5 * dt, j0, cnt, c->cap_stream);
+  const cudaError_t e1 = enqueue_arnoldi<TV, TRANS>(c, PV, V, alpha, j0, cnt, c->cap_stream);
   const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
   g_launches = l0;
   cudaGraphExec_t ex = nullptr;
@@ -1204,7 +1204,7 @@ static cudaGraphExec_t arnoldi_graph(sap_ctx* c, const OpParams<TV>& PV, TV* V, 
   }
   cudaGraphDestroy(graph);
   sap_ctx::CnGraph gg;
-  gg.exec = ex; gg.kind = kind; gg.j0 = j0; gg.cnt = cnt; gg.fields_version = c->fields_version; gg.dt = dt;
+  gg.exec = ex; gg.kind = kind; gg.j0 = j0; gg.cnt = cnt; gg.fields_version = c->fields_version; gg.alpha = alpha;
   gg.ws = ws;
   c->cn_graphs.push_back(gg);
   return ex;
@@ -1215,7 +1215,7 @@ static cudaGraphExec_t arnoldi_graph(sap_ctx* c, const OpParams<TV>& PV, TV* V, 
 // or the cycle length mlen, then y = R^-1 g by back substitution on the host and x += V y.
 // *jd = the cycle's iterations.
 template <typename TV, bool TRANS>
-static cudaError_t gmres_cycle(sap_ctx* c, const OpParams<TV>& PV, TV* V, double dt, double beta, double target,
+static cudaError_t gmres_cycle(sap_ctx* c, const OpParams<TV>& PV, TV* V, double alpha, double beta, double target,
                                int mlen, double* x, cudaStream_t s, int* jd) {
   const int64_t N = c->N;
   GmresDev* G = reinterpret_cast<GmresDev*>(c->gdev);
@@ -1241,12 +1241,12 @@ static cudaError_t gmres_cycle(sap_ctx* c, const OpParams<TV>& PV, TV* V, double
   ++g_launches;
   for (int j0 = 0; j0 < mlen; j0 += group) {
     const int cnt = std::min(group, mlen - j0);
-    cudaGraphExec_t ex = arnoldi_graph<TV, TRANS>(c, PV, V, dt, j0, cnt);
+    cudaGraphExec_t ex = arnoldi_graph<TV, TRANS>(c, PV, V, alpha, j0, cnt);
     if (ex) {
       err = cudaGraphLaunch(ex, s);
       g_launches += 6 * cnt;
     } else {
-      err = enqueue_arnoldi<TV, TRANS>(c, PV, V, 0.5 * dt, j0, cnt, s);
+      err = enqueue_arnoldi<TV, TRANS>(c, PV, V, alpha, j0, cnt, s);
     }
     if (err != cudaSuccess) return err;
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
@@ -1276,8 +1276,8 @@ static cudaError_t gmres_cycle(sap_ctx* c, const OpParams<TV>& PV, TV* V, double
 // updates) inside the FP64 residual / refinement loop, each cycle asking for no more than the FP32
 // operator can deliver (1e-6).
 template <typename TV>
-static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
-                             sap_solver_stats* st, cudaStream_t s) {
+static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, double theta, int nsteps, double tol, int restart,
+                             int maxit, sap_solver_stats* st, cudaStream_t s) {
   const int64_t N = c->N;
   const int m = restart;
   constexpr bool f64 = sizeof(TV) == 8;
@@ -1288,7 +1288,8 @@ static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, d
   const OpParams<TV>& PV = *reinterpret_cast<const OpParams<TV>*>(f64 ? (const void*)&c->p64 : (const void*)&c->p32);
   GmresDev* Gh = reinterpret_cast<GmresDev*>(c->gdev_host);
   const OpParams<double>& P = c->p64;
-  const double half = 0.5 * dt;
+  // theta-method: A = 1 + alpha L, B = 1 - brhs L (alpha = theta dt, brhs = (1 - theta) dt)
+  const double alpha = theta * dt, brhs = (1.0 - theta) * dt;
   int64_t total_its = 0;
   const int64_t launches0 = g_launches;
   int max_its = 0;
@@ -1297,7 +1298,7 @@ static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, d
   auto jcopy = [&](Epi<double>& e) {  // Jacobi-scaled copy of the residual into V_0
     if constexpr (f64) e.outj = reinterpret_cast<double*>(V);
     else e.out32 = reinterpret_cast<float*>(V);
-    e.cj = half;
+    e.cj = alpha;
   };
 #define CK(x)                               \
   do {                                      \
@@ -1307,10 +1308,10 @@ static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, d
   for (int step = 0; step < nsteps; ++step) {
     // one apply gives b = zeta - dt/2 L zeta + dt s (Eq. system-matrix-rhs), the residual of the
     // initial guess zeta, r = b - A zeta = dt (s - L zeta), and its Jacobi-scaled copy in V_0
-    const bool extrap = c->cn_prev_valid && c->cn_prev_ptr == state && c->cn_prev_dt == dt;
+    const bool extrap = c->cn_prev_valid && c->cn_prev_ptr == state && c->cn_prev_dt == dt && c->cn_prev_theta == theta;
     if (!extrap) {
       Epi<double> e{};
-      e.out = b; e.ax = 1.0; e.bl = -half; e.gs = dt;
+      e.out = b; e.ax = 1.0; e.bl = -brhs; e.gs = dt;
       e.out2 = tmp; e.ax2 = 0.0; e.bl2 = -dt; e.gs2 = dt;
       jcopy(e);
       CK(launch_apply<double>(P, state, e, s));
@@ -1319,18 +1320,19 @@ static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, d
       // initial guess 2 zeta^(n-1) - zeta^(n-2) (linear extrapolation; only the iteration count
       // depends on it), then r = b - A x0 and its Jacobi-scaled copy
       Epi<double> e{};
-      e.out = b; e.ax = 1.0; e.bl = -half; e.gs = dt;
+      e.out = b; e.ax = 1.0; e.bl = -brhs; e.gs = dt;
       CK(launch_apply<double>(P, state, e, s));
       extrapolate_kernel<<<1024, KRY_THREADS, 0, s>>>(state, prev, N);
       ++g_launches;
       Epi<double> e2{};
-      e2.out = tmp; e2.bvec = b; e2.wb = 1.0; e2.ax = -1.0; e2.bl = -half;
+      e2.out = tmp; e2.bvec = b; e2.wb = 1.0; e2.ax = -1.0; e2.bl = -alpha;
       jcopy(e2);
       CK(launch_apply<double>(P, state, e2, s));
     }
     c->cn_prev_valid = true;
     c->cn_prev_ptr = state;
     c->cn_prev_dt = dt;
+    c->cn_prev_theta = theta;
     norm2_dev<double>(c, b, 0, s);
     norm2_dev<double>(c, tmp, 1, s);
     norm2_dev<TV>(c, V, 2, s);
@@ -1347,12 +1349,12 @@ static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, int nsteps, d
     while (!(rel <= tol) && its < maxit && std::isfinite(rel)) {
       const double target = f64 ? 0.5 * beta * (tol / rel) : beta * std::max(0.5 * tol / rel, 1e-6);
       int jd = 0;
-      CK((gmres_cycle<TV, false>(c, PV, V, dt, beta, target, std::min(m, maxit - its), state, s, &jd)));
+      CK((gmres_cycle<TV, false>(c, PV, V, alpha, beta, target, std::min(m, maxit - its), state, s, &jd)));
       its += jd;
       // true residual r = b - A zeta and its Jacobi-scaled copy (start of a further cycle)
       {
         Epi<double> e{};
-        e.out = tmp; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half;
+        e.out = tmp; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -alpha;
         jcopy(e);
         CK(launch_apply<double>(P, state, e, s));
       }
@@ -1386,10 +1388,10 @@ cuda_fail:
 #undef CK
 }
 
-sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
-                    sap_solver_stats* st, cudaStream_t s) {
-  return c->prec == SAP_PREC_FP64 ? cn_steps_t<double>(c, state, dt, nsteps, tol, restart, maxit, st, s)
-                                  : cn_steps_t<float>(c, state, dt, nsteps, tol, restart, maxit, st, s);
+sap_status cn_steps(sap_ctx* c, double* state, double dt, double theta, int nsteps, double tol, int restart,
+                    int maxit, sap_solver_stats* st, cudaStream_t s) {
+  return c->prec == SAP_PREC_FP64 ? cn_steps_t<double>(c, state, dt, theta, nsteps, tol, restart, maxit, st, s)
+                                  : cn_steps_t<float>(c, state, dt, theta, nsteps, tol, restart, maxit, st, s);
 }
 
 
@@ -1792,6 +1794,8 @@ static sap_status batch_cn_impl(sap_ctx* c, double* state, double dt, int nsteps
   double* b = c->ws64;
   double* r = b + N;
   TV* V = (sizeof(TV) == 8) ? reinterpret_cast<TV*>(c->ws64 + 2 * N) : reinterpret_cast<TV*>(c->ws32);
+  // the state before the last step (initial-guess history), after the Krylov basis / b and r
+  double* prev = (sizeof(TV) == 8) ? c->ws64 + (size_t)(m + 3) * N : c->ws64 + 2 * N;
   const BatchChunks& C = c->chunks;
   double* partial = c->small;
   const int SS = 4 * KRY_MAXV;                     // per-instance scalar stride
@@ -1846,6 +1850,19 @@ static sap_status batch_cn_impl(sap_ctx* c, double* state, double dt, int nsteps
       e.out = b; e.ax = 1.0; e.bl = -half; e.gs = dt;
       CK(apply64(state, e));
     }
+    // initial guess: the linear extrapolation 2 zeta^(n-1) - zeta^(n-2) when the previous step ran on
+    // the same buffer with the same dt (as in the single-problem path; only the iteration count
+    // depends on it), else zeta^(n-1)
+    if (c->cn_prev_valid && c->cn_prev_ptr == state && c->cn_prev_dt == dt && c->cn_prev_theta == 0.5) {
+      extrapolate_kernel<<<1024, KRY_THREADS, 0, s>>>(state, prev, N);
+      ++g_launches;
+    } else {
+      CK(cudaMemcpyAsync(prev, state, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    }
+    c->cn_prev_valid = true;
+    c->cn_prev_ptr = state;
+    c->cn_prev_dt = dt;
+    c->cn_prev_theta = 0.5;
     dots64(b, 1);
     CK(fetch_all());
     for (int i = 0; i < ni; ++i) {
@@ -2091,7 +2108,7 @@ sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, doubl
         const double beta = std::sqrt(Gh->misc[2]);
         if (rel <= tol || its >= maxit || !std::isfinite(rel)) break;
         int jd = 0;
-        CK((gmres_cycle<double, true>(c, P, V, dt, beta, 0.5 * beta * (tol / rel), std::min(m, maxit - its), mu, s,
+        CK((gmres_cycle<double, true>(c, P, V, half, beta, 0.5 * beta * (tol / rel), std::min(m, maxit - its), mu, s,
                                       &jd)));
         its += jd;
         if (jd == 0) break;

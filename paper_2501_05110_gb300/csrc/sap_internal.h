@@ -12,7 +12,7 @@
 namespace sap {
 
 constexpr int MAXD = 3;
-constexpr int MAXQ = 5;          // dG degree <= 4
+constexpr int MAXQ = 6;          // dG degree <= 5
 constexpr int MAXTERMS = 28;     // reaction terms
 constexpr int MAXADV = 12;       // advection terms per axis
 constexpr int MAT_I = -1;        // identity "matrix"
@@ -113,6 +113,10 @@ struct OpParams {
   // every node of every cell
   unsigned react_uni;
   unsigned adv_uni[MAXD];
+  // bit t set: the coefficient of the term is identically zero (a uniform field component that is
+  // zero, such as U = 0): the apply kernels skip it
+  unsigned react_zero;
+  unsigned adv_zero[MAXD];
 };
 
 // Tables of the field-gradient kernels of the adjoint (adjoint_fields.cu): the spatial field
@@ -194,7 +198,7 @@ struct sap_ctx {
   // CN initial-guess history: the state before the last step, valid for the buffer and dt it was
   // taken with (any other call starts from the plain previous state)
   const double* cn_prev_ptr = nullptr;
-  double cn_prev_dt = 0.0;
+  double cn_prev_dt = 0.0, cn_prev_theta = 0.5;
   bool cn_prev_valid = false;
   std::vector<double> bank_nnz;                // nnz per bank matrix (cost model)
   int64_t launches = 0;                        // kernels launched by the current call
@@ -213,11 +217,11 @@ struct sap_ctx {
   std::vector<int> h_active;
   sap_ctx* parent = nullptr;                   // set on the sub-contexts of a batch
   // CUDA graphs of the GMRES iteration groups of sap_step_cn (kind 0) and of the adjoint step (kind 1),
-  // replayed while the configuration they were captured for (dt, fields, workspace, group) holds
+  // replayed while the configuration they were captured for (alpha, fields, workspace, group) holds
   struct CnGraph {
     cudaGraphExec_t exec = nullptr;
     int kind = 0, j0 = -1, cnt = 0, fields_version = -1;
-    double dt = 0.0;
+    double alpha = 0.0;  // the captured operator A = 1 + alpha L
     const void* ws = nullptr;
   };
   std::vector<CnGraph> cn_graphs;
@@ -236,8 +240,8 @@ cudaError_t launch_apply64(const OpParams<double>& p, const double* x, double* y
 cudaError_t launch_apply32(const OpParams<float>& p, const float* x, float* y, int mode, cudaStream_t s);
 sap_status erk_steps(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s);
 sap_status erk_steps_noalloc(sap_ctx* c, double* state, double dt, int nsteps, cudaStream_t s);
-sap_status cn_steps(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
-                    sap_solver_stats* st, cudaStream_t s);
+sap_status cn_steps(sap_ctx* c, double* state, double dt, double theta, int nsteps, double tol, int restart,
+                    int maxit, sap_solver_stats* st, cudaStream_t s);
 sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, double* lambda, double dt, double tol,
                            int m, int maxit, double* mu_out, double* grad_nu, sap_solver_stats* st, cudaStream_t s);
 sap_status adjoint_erk_step(sap_ctx* c, const double* y, double* lambda, double dt, double* grad_nu, double* stages,

@@ -162,7 +162,7 @@ static std::string validate(const sap_desc* d) {
   bool mom = !is_spatial(d->axis_kind[d->ndim - 1]);
   if ((d->terms & SAP_TERM_MOM) && !mom) return "momentum terms need a momentum axis";
   if (d->lmax < 0 || d->lmax > 11) return "lmax must be 0..11";
-  if (d->degree < 0 || d->degree > MAXQ - 1) return "degree must be 0..4";
+  if (d->degree < 0 || d->degree > MAXQ - 1) return "degree must be 0..5";
   if (!mom && !(d->V > 0)) return "particle speed V must be > 0 without a momentum axis";
   return "";
 }
@@ -991,6 +991,22 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
           for (int t = 0; t < P.ax[a].nadv; ++t)
             if (term_uni(P.ax[a].adv[t])) P.adv_uni[a] |= 1u << t;
         }
+        // terms whose coefficient is zero everywhere (the spatial advection U_a I with U_a = 0)
+        auto term_zero = [&](const Term& tm) {
+          return (tm.sf != SF_ONE && uni[tm.sf] && uval[tm.sf] == 0.0) || (tm.nu && nu_uni && nu_u == 0.0);
+        };
+        P.react_zero = 0u;
+        for (int t = 0; t < P.nreact; ++t)
+          if (term_zero(P.react[t])) P.react_zero |= 1u << t;
+        for (int a = 0; a < MAXD; ++a) {
+          P.adv_zero[a] = 0u;
+          for (int t = 0; t < P.ax[a].nadv; ++t) {
+            const Term& tm = P.ax[a].adv[t];
+            // a spatial face coefficient of U_a uses the face values, so both must vanish
+            const bool face_ok = !(tm.sf == SF_U + a && a < c->dx) || (uface_uni[a] && uface_u[a] == 0.0);
+            if (term_zero(tm) && face_ok) P.adv_zero[a] |= 1u << t;
+          }
+        }
       };
       fill(c->p64, double{});
       fill(c->p32, float{});
@@ -1002,6 +1018,45 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
       return SAP_ENOMEM;
     }
     return SAP_OK;
+  });
+}
+
+extern "C" sap_status sap_set_fields_device(sap_handle c, const double* U, const double* gradU, const double* DUDt,
+                                            const double* Bw, const double* const Uface[3], const double* nu,
+                                            const double* s000, sap_stream stream) {
+  return guarded(c, "sap_set_fields_device", [&]() -> sap_status {
+    if (!c) return SAP_EINVAL;
+    if (!c->sub.empty()) {
+      c->err = "sap_set_fields_device: set the fields of a batch through its instance handles";
+      return SAP_EINVAL;
+    }
+    const cudaStream_t s = (cudaStream_t)stream;
+    // the term tables and the momentum-face eigen data are built on the host: read the fields back
+    // on the caller's stream (ordered after whatever produced them), then build as sap_set_fields
+    std::vector<double> hU, hG, hDU, hB, hF[3], hnu, hs;
+    cudaError_t err = cudaSuccess;
+    auto fetch = [&](const double* d, size_t count, std::vector<double>& h) -> const double* {
+      if (!d) return nullptr;
+      h.resize(std::max<size_t>(count, 1));
+      if (count && err == cudaSuccess) err = cudaMemcpyAsync(h.data(), d, sizeof(double) * count, cudaMemcpyDeviceToHost, s);
+      return h.data();
+    };
+    const size_t nsv = (size_t)c->nsv, npv = (size_t)c->npv;
+    const double* pU = fetch(U, nsv * 3, hU);
+    const double* pG = fetch(gradU, nsv * 9, hG);
+    const double* pDU = fetch(DUDt, nsv * 3, hDU);
+    const double* pB = fetch(Bw, nsv * 3, hB);
+    const double* pF[3] = {nullptr, nullptr, nullptr};
+    for (int a = 0; a < 3; ++a)
+      if (Uface && a < c->dx) pF[a] = fetch(Uface[a], (size_t)c->nsf[a], hF[a]);
+    const double* pnu = fetch(nu, npv, hnu);
+    const double* ps = fetch(s000, npv, hs);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) {
+      c->err = std::string("sap_set_fields_device: copy of the fields: ") + cudaGetErrorString(err);
+      return SAP_ECUDA;
+    }
+    return sap_set_fields(c, pU, pG, pDU, pB, pF, pnu, ps);
   });
 }
 
@@ -1101,36 +1156,57 @@ extern "C" sap_status sap_step_erk_noalloc(sap_handle c, double* state, double d
   });
 }
 
-extern "C" sap_status sap_step_cn(sap_handle c, double* state, double dt, int nsteps, double tol, int restart,
-                                  int maxit, sap_solver_stats* stats, sap_stream stream) {
-  return guarded(c, "sap_step_cn", [&]() -> sap_status {
-    if (!c || !state || nsteps < 0 || restart < 1 || restart > 31 || maxit < 1 || !(tol > 0)) return SAP_EINVAL;
-    if (!c->sub.empty()) {
-      const bool ok = c->prec == SAP_PREC_FP64 ? ensure_ws64(c, restart + 3) : (ensure_ws32(c, restart + 1) && ensure_ws64(c, 2));
-      if (!ok) {
-        c->err = "cn: workspace allocation failed";
-        return SAP_ENOMEM;
-      }
-      return batch_cn(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
+static sap_status step_theta(sap_handle c, double* state, double dt, double theta, int nsteps, double tol, int restart,
+                             int maxit, sap_solver_stats* stats, sap_stream stream) {
+  if (!c || !state || nsteps < 0 || restart < 1 || restart > 31 || maxit < 1 || !(tol > 0) || !(theta >= 0.0) ||
+      !(theta <= 1.0) || !std::isfinite(dt))
+    return SAP_EINVAL;
+  if (!c->sub.empty()) {
+    if (theta != 0.5) {
+      c->err = "batch: Crank--Nicolson (theta = 1/2) only";
+      return SAP_EUNSUPPORTED;
     }
-    if (!c->fields_set) {
-      c->err = "fields not set";
-      return SAP_EINVAL;
-    }
-    if (c->prec == SAP_PREC_FP32) {
-      if (c->ws64_count < 3) c->cn_prev_valid = false;
-      if (!ensure_ws32(c, restart + 1) || !ensure_ws64(c, 3)) {
-        c->err = "cn: workspace allocation failed";
-        return SAP_ENOMEM;
-      }
-      return cn_steps(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
-    }
-    if (c->ws64_count < restart + 4) c->cn_prev_valid = false;  // the history lives in the workspace
-    if (!ensure_ws64(c, restart + 4)) {
+    // FP64: b, r, the Krylov basis and the initial-guess history; FP32: FP32 basis, FP64 b, r, history
+    const int need64 = c->prec == SAP_PREC_FP64 ? restart + 4 : 3;
+    if (c->ws64_count < need64) c->cn_prev_valid = false;  // the history lives in the workspace
+    const bool ok = c->prec == SAP_PREC_FP64 ? ensure_ws64(c, need64) : (ensure_ws32(c, restart + 1) && ensure_ws64(c, need64));
+    if (!ok) {
       c->err = "cn: workspace allocation failed";
       return SAP_ENOMEM;
     }
-    return cn_steps(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
+    return batch_cn(c, state, dt, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
+  }
+  if (!c->fields_set) {
+    c->err = "fields not set";
+    return SAP_EINVAL;
+  }
+  if (c->prec == SAP_PREC_FP32) {
+    if (c->ws64_count < 3) c->cn_prev_valid = false;
+    if (!ensure_ws32(c, restart + 1) || !ensure_ws64(c, 3)) {
+      c->err = "cn: workspace allocation failed";
+      return SAP_ENOMEM;
+    }
+    return cn_steps(c, state, dt, theta, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
+  }
+  if (c->ws64_count < restart + 4) c->cn_prev_valid = false;  // the history lives in the workspace
+  if (!ensure_ws64(c, restart + 4)) {
+    c->err = "cn: workspace allocation failed";
+    return SAP_ENOMEM;
+  }
+  return cn_steps(c, state, dt, theta, nsteps, tol, restart, maxit, stats, (cudaStream_t)stream);
+}
+
+extern "C" sap_status sap_step_cn(sap_handle c, double* state, double dt, int nsteps, double tol, int restart,
+                                  int maxit, sap_solver_stats* stats, sap_stream stream) {
+  return guarded(c, "sap_step_cn", [&]() -> sap_status {
+    return step_theta(c, state, dt, 0.5, nsteps, tol, restart, maxit, stats, stream);
+  });
+}
+
+extern "C" sap_status sap_step_theta(sap_handle c, double* state, double dt, double theta, int nsteps, double tol,
+                                     int restart, int maxit, sap_solver_stats* stats, sap_stream stream) {
+  return guarded(c, "sap_step_theta", [&]() -> sap_status {
+    return step_theta(c, state, dt, theta, nsteps, tol, restart, maxit, stats, stream);
   });
 }
 

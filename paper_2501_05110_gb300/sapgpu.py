@@ -25,7 +25,7 @@ PTS_SPATIAL, PTS_FACE_X, PTS_FACE_Y, PTS_FACE_Z, PTS_PHASE = range(5)
 SCHEME = {"erk4": 0, "cn": 1}
 EXPORTS = ["sap_create", "sap_create_batch", "sap_batch_instance", "sap_field_points", "sap_set_fields", "sap_num_dofs", "sap_apply_operator",
            "sap_step_erk", "sap_step_erk_noalloc", "sap_step_cn", "sap_adjoint_step_cn", "sap_adjoint_step_erk",
-           "sap_adjoint_step", "sap_apply_cost", "sap_destroy", "sap_last_error", "sap_coupling_matrix"]
+           "sap_adjoint_step", "sap_step_theta", "sap_set_fields_device", "sap_apply_cost", "sap_destroy", "sap_last_error", "sap_coupling_matrix"]
 # field arrays of sap_set_fields / gradient arrays of sap_adjoint_step, in struct order
 FIELDS = ("U", "gradU", "DUDt", "Bw", "Uface0", "Uface1", "Uface2", "nu", "s000")
 
@@ -69,12 +69,15 @@ def load_library(path: str = LIB_PATH):
     lib.sap_batch_instance.argtypes = [vp, C.c_int, C.POINTER(C.c_void_p), i64p]
     lib.sap_field_points.argtypes = [vp, C.c_int, dp, i64p]
     lib.sap_set_fields.argtypes = [vp, dp, dp, dp, dp, C.POINTER(dp), dp, dp]
+    lib.sap_set_fields_device.argtypes = [vp, vp, vp, vp, vp, C.POINTER(vp), vp, vp, vp]
     lib.sap_num_dofs.argtypes = [vp, i64p]
     lib.sap_apply_operator.argtypes = [vp, vp, vp, C.c_int, vp]
     lib.sap_step_erk.argtypes = [vp, vp, C.c_double, C.c_int, vp]
     lib.sap_step_erk_noalloc.argtypes = [vp, vp, C.c_double, C.c_int, vp]
     lib.sap_step_cn.argtypes = [vp, vp, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
                                 C.POINTER(SolverStats), vp]
+    lib.sap_step_theta.argtypes = [vp, vp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
+                                   C.POINTER(SolverStats), vp]
     lib.sap_apply_cost.argtypes = [vp, dp, dp]
     lib.sap_adjoint_step_cn.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int, C.c_int, vp, vp,
                                         C.POINTER(SolverStats), vp]
@@ -203,6 +206,15 @@ class Solver:
         self._check(self.lib.sap_set_fields(self.h, _dptr(f["U"]), _dptr(f["gradU"]), _dptr(f["DUDt"]),
                                             _dptr(f["Bw"]), face_ptrs, _dptr(f["nu"]), _dptr(f["s000"])))
 
+    def set_fields_device(self, fields: dict, stream=None):
+        """sap_set_fields_device from device tensors (keys of FIELDS; missing or None: not given)."""
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        faces = (C.c_void_p * 3)(*[ptr(fields.get(f"Uface{a}")) for a in range(3)])
+        self._check(self.lib.sap_set_fields_device(self.h, ptr(fields.get("U")), ptr(fields.get("gradU")),
+                                                   ptr(fields.get("DUDt")), ptr(fields.get("Bw")), faces,
+                                                   ptr(fields.get("nu")), ptr(fields.get("s000")),
+                                                   _stream_handle(stream)))
+
     def initial_state(self, device="cuda"):
         """Nodal values of f^0 at the phase-space nodes, canonical layout, FP64 torch tensor."""
         import torch
@@ -234,6 +246,14 @@ class Solver:
         st = SolverStats()
         self._check(self.lib.sap_step_cn(self.h, C.c_void_p(state.data_ptr()), dt, nsteps, tol, restart, maxit,
                                          C.byref(st), _stream_handle(stream)))
+        return st
+
+    def step_theta(self, state, dt: float, theta: float, nsteps: int, tol: float = 1e-10, restart: int = 30,
+                   maxit: int = 2000, stream=None) -> SolverStats:
+        """theta-method steps (0 forward Euler, 1 backward Euler, 1/2 Crank--Nicolson)."""
+        st = SolverStats()
+        self._check(self.lib.sap_step_theta(self.h, C.c_void_p(state.data_ptr()), dt, theta, nsteps, tol, restart,
+                                            maxit, C.byref(st), _stream_handle(stream)))
         return st
 
     def adjoint_step_cn(self, zeta_prev, zeta_next, lam, dt: float, tol: float = 1e-12, restart: int = 30,

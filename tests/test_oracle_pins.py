@@ -254,18 +254,32 @@ def _rel_l2_000(disc, z, exact, t, k, nc, Lbox=20.0):
     return math.sqrt(np.sum(w * (y - exact(t, x)) ** 2)) / math.sqrt(np.sum(w * y ** 2))
 
 
-@pytest.mark.parametrize("k", [1, 2, 3])
+# meshes and RK4 steps of the space-order study per degree: the time error stays below the space
+# error (dt = 0.001 for k = 5, whose finest error is ~3e-12)
+CONV_SPACE = {1: ((8, 16, 32), 0.005), 2: ((8, 16, 32), 0.005), 3: ((8, 16, 32), 0.005),
+              4: ((4, 8, 16, 32), 0.005), 5: ((4, 8, 16, 32), 0.001)}
+CONV_FINEST = {1: 5e-4, 2: 2e-5, 3: 1e-6, 4: 2e-9, 5: 1e-11}
+
+
+def convergence_order(ncs, errs):
+    """Least-squares slope of log(err) against log(1/nc)."""
+    return -np.polyfit(np.log(np.asarray(ncs, float)), np.log(np.asarray(errs)), 1)[0]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 def test_convergence_study_space(k):
-    """ERK4, Delta t small: the error against the closed form falls as Delta x^(k+1) (Sec. 4.1)."""
+    """ERK4, Delta t small: the error against the closed form falls as Delta x^(k+1) (Sec. 4.1; the
+    paper runs k = 1..5).  For k >= 4 the mesh-to-mesh orders oscillate about k+1 (6.1, 5.4, 6.9 for
+    k = 5), so the least-squares slope over the meshes is checked."""
+    ncs, dt = CONV_SPACE[k]
     errs = []
-    for nc in (8, 16, 32):
+    for nc in ncs:
         prob, ex = _convergence_problem(nc, k)
         disc = dg.Discretisation(prob)
-        z = steppers.rk4(disc.M, disc.D, disc.h, dg.project_initial(disc, prob.f0), 0.005, 200)
+        z = steppers.rk4(disc.M, disc.D, disc.h, dg.project_initial(disc, prob.f0), dt, int(round(1.0 / dt)))
         errs.append(_rel_l2_000(disc, z, ex, 1.0, k, nc))
-    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
-    assert min(orders) > k + 1 - 0.45, (errs, orders)
-    assert errs[-1] < [5e-4, 2e-5, 1e-6][k - 1]
+    assert convergence_order(ncs, errs) > k + 1 - 0.3, errs
+    assert errs[-1] < CONV_FINEST[k], errs
 
 
 @pytest.mark.parametrize("theta,order", [(0.5, 2), (1.0, 1), (0.0, 1)])
