@@ -41,7 +41,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3  # SMs x FFMA/clk/SM x 2 flop x max 
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture, valid only for the
 # kernel source it was taken on (first 16 hex of sha256 of csrc/apply_rows.cu); see profiles/
-APPLY_TRAFFIC = {}
+APPLY_TRAFFIC = {("shock", "fp64", "025719a36b5601f4"): 11002624.0}
 
 
 def parse():
