@@ -74,9 +74,13 @@ def hbm_peak():
         return HBM_FALLBACK_GBS, "of fallback"
 
 
+ALU_PROBE = {}  # measured FMA roofs of this run (sap_probe_fma), TFLOP/s per precision
+
+
 def roofline_entry(kernel, flops, abytes, t_apply, precision, traffic=None, units=None):
     """ALU roofline of an operator apply (the operator is above the ridge point in both
-    precisions), with the HBM view of its algorithmic bytes beside it."""
+    precisions), with the HBM view of its algorithmic bytes beside it.  `peak` is the nominal one
+    from unit counts and the maximum clock; the FMA roof measured in this run is given beside it."""
     peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
     achieved = flops / t_apply / 1e12
     hbm, how = hbm_peak()
@@ -89,7 +93,28 @@ def roofline_entry(kernel, flops, abytes, t_apply, precision, traffic=None, unit
                         "flops from the kernel's cost model (sap_apply_cost)"}
     if units:
         out["units_per_launch"] = units
+    if precision in ALU_PROBE:
+        out["measured_fma_roof_tflops"] = ALU_PROBE[precision]
+        out["frac_of_measured_fma_roof"] = achieved / ALU_PROBE[precision]
     return out
+
+
+def probe_alu(local):
+    """FMA roofs of the device in both precisions (library probe), with the clocks seen."""
+    from paper_2501_05110_gb300 import sapgpu
+    clocks = ClockSampler(local, "_alu_probe")
+    clocks.start()
+    res = {}
+    for prec in ("fp64", "fp32"):
+        best = 0.0
+        for _ in range(3):
+            best = max(best, sapgpu.probe_fma(prec) / 1e12)
+        res[prec] = best
+        ALU_PROBE[prec] = best
+    res["clocks"] = clocks.stop()
+    res["unit"] = "TFLOP/s"
+    res["how"] = "sap_probe_fma: 8 independent FMA chains per thread, 16 blocks of 256 threads per SM, best of 3"
+    return res
 
 
 def apply_sha():
@@ -521,6 +546,7 @@ def run_mine(args):
     torch.cuda.set_device(local)
     from paper_2501_05110_gb300 import build as sap_build
     sap_build.build()
+    alu = probe_alu(local)
     head = measure_shock(args, args.precision, world, rank, local)
     from paper_2501_05110_gb300 import workloads as W
     prob = W.shock()
@@ -531,7 +557,7 @@ def run_mine(args):
            "data": "synthetic", "config": shock_config(prob), "precision": args.precision,
            "gmres_iterations_per_step": head["gmres_iterations_per_step"],
            "roofline": head["roofline"], "e2e": head["e2e"], "clocks": head["clocks"],
-           "gpu_launches": head["gpu_launches"]}
+           "gpu_launches": head["gpu_launches"], "alu_probe": alu}
     workloads = {}
     if args.workload == "all":
         plan = [("shock_fp32", lambda: measure_shock(args, "fp32", world, rank, local)),
@@ -565,6 +591,7 @@ def run_single_workload(args):
     torch.cuda.set_device(0)
     from paper_2501_05110_gb300 import build as sap_build
     sap_build.build()
+    probe_alu(0)
     if args.workload == "box3d":
         res = measure_box3d(args, args.precision)
     elif args.workload == "batched":

@@ -103,12 +103,15 @@ sap_status sap_create(const sap_desc* desc, int prec, sap_handle* out);
 
 /* Create a batch of `ninst` independent problems (one descriptor each; different lmax, degree,
  * meshes and fields allowed) that run together: every operator apply is one kernel launch over all
- * instances, and sap_step_cn runs one restarted GMRES per instance in lock-step (own Krylov space,
- * Hessenberg matrix and convergence test; finished instances are masked out).  The batch state is
- * the concatenation of the instances' canonical states (offsets from sap_batch_instance).  The
- * thread-block size is autotuned on the first compute call by timing the batched apply.
- * sap_apply_operator, sap_step_erk and sap_step_cn accept the batch handle.  Fields are set per
- * instance through the sub-handles of sap_batch_instance.  Errors as sap_create. */
+ * instances.  sap_step_cn runs one restarted GMRES per instance (own Krylov space, Hessenberg matrix,
+ * Givens rotations and convergence test) with the control on the device: a CN step is one CUDA-graph
+ * launch (captured on first use for the state buffer, dt, tolerances and fields), finished instances
+ * cost nothing in later launches, and the host reads the per-instance status once per step.  The
+ * batch state is the concatenation of the instances' canonical states (offsets from
+ * sap_batch_instance).  The tile shape (cells per thread block) is autotuned per expansion order on
+ * the first compute call by timing the batched apply of each l_max class.  sap_apply_operator,
+ * sap_step_erk and sap_step_cn accept the batch handle.  Fields are set per instance through the
+ * sub-handles of sap_batch_instance.  Errors as sap_create. */
 sap_status sap_create_batch(int ninst, const sap_desc* descs, int prec, sap_handle* out);
 
 /* Sub-handle of instance `inst` of a batch (for sap_field_points, sap_set_fields, sap_num_dofs; owned
@@ -280,6 +283,13 @@ sap_status sap_step_erk_noalloc(sap_handle h, double* state, double dt, int nste
  * upwind fluxes, volume terms, lifts); `bytes` = 2 N w (read x, write y; w = word size of the
  * context's precision).  Host-only.  Errors: SAP_EINVAL (fields not set). */
 sap_status sap_apply_cost(sap_handle h, double* flops, double* bytes);
+
+/* Measured fused-multiply-add throughput of the current device in precision `prec` (SAP_PREC_FP64 or
+ * SAP_PREC_FP32), in flop/s (an FMA counts 2): eight independent FMA chains per thread on every SM,
+ * timed with CUDA events over five launches after a warm-up.  The arithmetic roof of the operator
+ * apply, which is above the ridge point in both precisions.  The paper has no counterpart
+ * (measurement).  Synchronous; allocates a small output buffer.  Errors: SAP_EINVAL, SAP_ECUDA. */
+sap_status sap_probe_fma(int prec, double* flops_per_s);
 
 /* Destroy a context and free its device memory.  NULL is accepted. */
 sap_status sap_destroy(sap_handle h);

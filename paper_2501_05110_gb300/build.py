@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libsapgpu.so")
-SOURCES = ["operator.cu", "apply_rows.cu", "adjoint_fields.cu", "setup.cpp", "sh_tables.cpp"]
+SOURCES = ["operator.cu", "apply_rows.cu", "adjoint_fields.cu", "probe.cu", "setup.cpp", "sh_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

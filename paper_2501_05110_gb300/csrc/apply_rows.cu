@@ -542,11 +542,15 @@ cudaError_t launch_rows_shape(const OpParams<T>& P, const T* x, const Epi<T>& e,
 }
 
 template <typename T, int D, int Q>
+cudaError_t opt_in_rows_batched_shape() {
+  static DeviceMask opted{};
+  return smem_opt_in(rows_kernel_batched<T, D, Q>, (int)kRowsSmemMax, opted);
+}
+
+template <typename T, int D, int Q>
 cudaError_t launch_rows_batched_shape(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e,
                                       cudaStream_t s) {
-  static DeviceMask opted{};
-  if (cudaError_t err = smem_opt_in(rows_kernel_batched<T, D, Q>, (int)kRowsSmemMax, opted); err != cudaSuccess)
-    return err;
+  if (cudaError_t err = opt_in_rows_batched_shape<T, D, Q>(); err != cudaSuccess) return err;
   if (B.smem > kRowsSmemMax || B.threads > Shape<T, D, Q>::MAXT) return cudaErrorInvalidConfiguration;
   rows_kernel_batched<T, D, Q><<<B.nblocks, B.threads, B.smem, s>>>(B.P, B.doff, B.cpb, B.blocks, active, x, e);
   note_launch();
@@ -582,6 +586,16 @@ cudaError_t launch_rows_batched(const BatchDev<T>& B, const int* active, const T
   return cudaErrorInvalidConfiguration;
 }
 
+template <typename T>
+cudaError_t prepare_rows_batched(const BatchDev<T>& B) {
+  if (B.shape_d == 1 && B.shape_q == 3) return opt_in_rows_batched_shape<T, 1, 3>();
+  if (B.shape_d == 2 && B.shape_q == 2) return opt_in_rows_batched_shape<T, 2, 2>();
+  if (B.shape_d == 3 && B.shape_q == 3) return opt_in_rows_batched_shape<T, 3, 3>();
+  return cudaErrorInvalidConfiguration;
+}
+
+template cudaError_t prepare_rows_batched<double>(const BatchDev<double>&);
+template cudaError_t prepare_rows_batched<float>(const BatchDev<float>&);
 template void rows_config<double>(const OpParams<double>&, int, int*, size_t*);
 template void rows_config<float>(const OpParams<float>&, int, int*, size_t*);
 template cudaError_t launch_rows<double>(const OpParams<double>&, const double*, const Epi<double>&, cudaStream_t);

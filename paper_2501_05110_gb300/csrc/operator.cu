@@ -1411,6 +1411,35 @@ static cudaError_t launch_apply_batched_shape(const BatchDev<T>& B, const int* a
   return cudaGetLastError();
 }
 
+// dynamic shared-memory limit of the batched apply kernel that runs B, set once per device
+template <typename T>
+static cudaError_t prepare_batched(const BatchDev<T>& B) {
+  if (B.rows) return prepare_rows_batched<T>(B);
+  static DeviceMask opted{};
+  return smem_opt_in(apply_kernel_batched<T, 0, 0>, 200 * 1024, opted);
+}
+template <typename T>
+static cudaError_t prepare_batched(const std::vector<BatchDev<T>>& Bs) {
+  for (const auto& B : Bs)
+    if (cudaError_t err = prepare_batched<T>(B); err != cudaSuccess) return err;
+  return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t launch_apply_batched(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e,
+                                        cudaStream_t s);
+
+// one launch per group of instances with the same expansion order (each with its own tile shape)
+template <typename T>
+static cudaError_t launch_apply_batched(const std::vector<BatchDev<T>>& Bs, const int* active, const T* x,
+                                        const Epi<T>& e, cudaStream_t s) {
+  for (const auto& B : Bs) {
+    if (B.nblocks == 0) continue;
+    if (cudaError_t err = launch_apply_batched<T>(B, active, x, e, s); err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
 template <typename T>
 static cudaError_t launch_apply_batched(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e,
                                         cudaStream_t s) {
@@ -1579,7 +1608,9 @@ static void* dev_upload(sap_ctx* c, const std::vector<V>& h) {
   return p;
 }
 
-static void batch_tables(sap_ctx* c, int target) {
+// Tables of a batch for the thread-block targets target[i] of every instance (the row kernel picks
+// an instance's cells per block from its target and its n).
+static void batch_tables(sap_ctx* c, const std::vector<int>& target) {
   for (auto& b : c->batch_bufs) cudaFree(b.p);
   c->batch_bufs.clear();
   const int ni = (int)c->sub.size();
@@ -1595,37 +1626,47 @@ static void batch_tables(sap_ctx* c, int target) {
     P32[i] = c->sub[i]->p32;
     doff[i] = c->inst_off[i];
   }
-  // cells per block, block list, block size and shared memory for one precision
+  // instances are grouped by expansion order: each group is one launch with its own block size
+  c->batch_class.assign(ni, 0);
+  std::vector<int> lclass;
+  for (int i = 0; i < ni; ++i) {
+    const int l = c->sub[i]->desc.lmax;
+    auto it = std::find(lclass.begin(), lclass.end(), l);
+    c->batch_class[i] = (int)(it - lclass.begin());
+    if (it == lclass.end()) lclass.push_back(l);
+  }
+  const int ncls = (int)lclass.size();
+  // cells per block, block lists (per group), block sizes and shared memory for one precision
   auto plan = [&](auto tag, const auto& Pv, std::vector<int>& cpb, std::vector<int>& stride,
-                  std::vector<int2>& blocks, int& threads, size_t& smem) {
+                  std::vector<std::vector<int2>>& blocks, std::vector<int>& threads, std::vector<size_t>& smem) {
     using T = decltype(tag);
     cpb.assign(ni, 1);
     stride.assign(ni, 0);
-    blocks.clear();
-    threads = 1;
-    smem = 0;
+    blocks.assign(ncls, {});
+    threads.assign(ncls, 1);
+    smem.assign(ncls, 0);
     for (int i = 0; i < ni; ++i) {
       sap_ctx* sc = c->sub[i];
+      const int g = c->batch_class[i];
       size_t sm = 0;
       if (rows) {
-        rows_config<T>(Pv[i], target, &cpb[i], &sm);
-        threads = std::max(threads, cpb[i] * sc->n);
+        rows_config<T>(Pv[i], target[i], &cpb[i], &sm);
+        threads[g] = std::max(threads[g], cpb[i] * sc->n);
       } else {
         const int per = sc->n * sc->nloc;
         if (per > 1024) throw std::string("an instance has n (k+1)^D > 1024");
-        cpb[i] = std::max(1, std::min(target, 1024) / per);
+        cpb[i] = std::max(1, std::min(target[i], 1024) / per);
         stride[i] = cell_stride_elems(sc->p64);
-        threads = std::max(threads, cpb[i] * per);
+        threads[g] = std::max(threads[g], cpb[i] * per);
         sm = (size_t)cpb[i] * stride[i] * sizeof(T);
       }
-      smem = std::max(smem, sm);
-      for (int c0 = 0; c0 < sc->ncell; c0 += cpb[i]) blocks.push_back(make_int2(i, c0));
+      smem[g] = std::max(smem[g], sm);
+      for (int c0 = 0; c0 < sc->ncell; c0 += cpb[i]) blocks[g].push_back(make_int2(i, c0));
     }
   };
-  std::vector<int> cpb64, cpb32, st64, st32;
-  std::vector<int2> bl64, bl32;
-  int th64, th32;
-  size_t sm64, sm32;
+  std::vector<int> cpb64, cpb32, st64, st32, th64, th32;
+  std::vector<std::vector<int2>> bl64, bl32;
+  std::vector<size_t> sm64, sm32;
   plan(double{}, P64, cpb64, st64, bl64, th64, sm64);
   plan(float{}, P32, cpb32, st32, bl32, th32, sm32);
   std::vector<int> cinst, clen, cfirst(ni), ccount(ni);
@@ -1641,12 +1682,20 @@ static void batch_tables(sap_ctx* c, int target) {
     ccount[i] = (int)cinst.size() - cfirst[i];
   }
   const int64_t* d_doff = (const int64_t*)dev_upload(c, doff);
-  c->b64 = BatchDev<double>{(const OpParams<double>*)dev_upload(c, P64), d_doff, (const int*)dev_upload(c, cpb64),
-                            (const int*)dev_upload(c, st64), (const int2*)dev_upload(c, bl64), (int)bl64.size(),
-                            th64, sm64, sd, sq, rows ? 1 : 0};
-  c->b32 = BatchDev<float>{(const OpParams<float>*)dev_upload(c, P32), d_doff, (const int*)dev_upload(c, cpb32),
-                           (const int*)dev_upload(c, st32), (const int2*)dev_upload(c, bl32), (int)bl32.size(),
-                           th32, sm32, sd, sq, rows ? 1 : 0};
+  const auto* dP64 = (const OpParams<double>*)dev_upload(c, P64);
+  const auto* dP32 = (const OpParams<float>*)dev_upload(c, P32);
+  const int* dcpb64 = (const int*)dev_upload(c, cpb64);
+  const int* dcpb32 = (const int*)dev_upload(c, cpb32);
+  const int* dst64 = (const int*)dev_upload(c, st64);
+  const int* dst32 = (const int*)dev_upload(c, st32);
+  c->b64.clear();
+  c->b32.clear();
+  for (int g = 0; g < ncls; ++g) {
+    c->b64.push_back(BatchDev<double>{dP64, d_doff, dcpb64, dst64, (const int2*)dev_upload(c, bl64[g]),
+                                      (int)bl64[g].size(), th64[g], sm64[g], sd, sq, rows ? 1 : 0});
+    c->b32.push_back(BatchDev<float>{dP32, d_doff, dcpb32, dst32, (const int2*)dev_upload(c, bl32[g]),
+                                     (int)bl32[g].size(), th32[g], sm32[g], sd, sq, rows ? 1 : 0});
+  }
   c->chunks = BatchChunks{(const int*)dev_upload(c, cinst), (const int64_t*)dev_upload(c, ck0),
                           (const int*)dev_upload(c, clen), (const int*)dev_upload(c, cfirst),
                           (const int*)dev_upload(c, ccount), (int)cinst.size()};
@@ -1654,8 +1703,10 @@ static void batch_tables(sap_ctx* c, int target) {
   c->d_active = (int*)dev_upload(c, c->h_active);
 }
 
-// Builds the batch tables; on the first call the thread-block size is autotuned by timing the
-// batched apply for several targets (cells per block are picked per instance from the target).
+// Builds the batch tables.  On the first call the tile shape is autotuned per expansion order: for
+// every candidate thread-block target the batched apply is timed with only the instances of one
+// l_max active (the others' blocks return at once), and each l_max keeps its fastest target, i.e. its
+// own cells per block.
 sap_status batch_prepare(sap_ctx* c, cudaStream_t s) {
   int version = 0;
   for (auto* sc : c->sub) {
@@ -1666,9 +1717,9 @@ sap_status batch_prepare(sap_ctx* c, cudaStream_t s) {
     version += sc->fields_version;
   }
   if (version == c->batch_built_version) return SAP_OK;
+  const int ni = (int)c->sub.size();
   try {
     if (!c->batch_tuned) {
-      // autotune on scratch vectors of the context's precision
       const size_t w = c->prec == SAP_PREC_FP64 ? 8 : 4;
       void *x = nullptr, *y = nullptr;
       if (cudaMalloc(&x, w * c->N) != cudaSuccess || cudaMalloc(&y, w * c->N) != cudaSuccess) {
@@ -1677,41 +1728,55 @@ sap_status batch_prepare(sap_ctx* c, cudaStream_t s) {
         return SAP_ENOMEM;
       }
       cudaMemsetAsync(x, 0, w * c->N, s);
-      float best = 1e30f;
-      int best_t = 256;
+      std::vector<int> lclass;  // distinct expansion orders
+      for (auto* sc : c->sub)
+        if (std::find(lclass.begin(), lclass.end(), sc->desc.lmax) == lclass.end()) lclass.push_back(sc->desc.lmax);
+      const int cand[4] = {64, 128, 256, 512};
+      std::vector<float> best(lclass.size(), 1e30f);
+      std::vector<int> best_t(lclass.size(), 256);
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
-      for (int target : {64, 128, 256, 512}) {
-        batch_tables(c, target);
-        const int64_t l0 = g_launches;
-        for (int rep = 0; rep < 4; ++rep) {
-          if (rep == 1) cudaEventRecord(e0, s);
-          cudaError_t err = c->prec == SAP_PREC_FP64
-                                ? launch_apply_batched<double>(c->b64, c->d_active, (const double*)x,
-                                                               Epi<double>{(double*)y, nullptr, 0, 0, 1, 0}, s)
-                                : launch_apply_batched<float>(c->b32, c->d_active, (const float*)x,
-                                                              Epi<float>{(float*)y, nullptr, 0, 0, 1, 0}, s);
-          if (err != cudaSuccess) break;
-        }
-        g_launches = l0;
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 1e30f;
-        if (cudaGetLastError() == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-          best = ms;
-          best_t = target;
+      for (int target : cand) {
+        batch_tables(c, std::vector<int>(ni, target));
+        // the groups are launched one by one, so each is timed on its own launch
+        for (size_t L = 0; L < lclass.size(); ++L) {
+          const int g = c->batch_class[std::find_if(c->sub.begin(), c->sub.end(),
+                                                    [&](sap_ctx* sc) { return sc->desc.lmax == lclass[L]; }) -
+                                       c->sub.begin()];
+          const int64_t l0 = g_launches;
+          for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, s);
+            cudaError_t err = c->prec == SAP_PREC_FP64
+                                  ? launch_apply_batched<double>(c->b64[g], c->d_active, (const double*)x,
+                                                                 Epi<double>{(double*)y, nullptr, 0, 0, 1, 0}, s)
+                                  : launch_apply_batched<float>(c->b32[g], c->d_active, (const float*)x,
+                                                                Epi<float>{(float*)y, nullptr, 0, 0, 1, 0}, s);
+            if (err != cudaSuccess) break;
+          }
+          g_launches = l0;
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 1e30f;
+          if (cudaGetLastError() == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best[L]) {
+            best[L] = ms;
+            best_t[L] = target;
+          }
         }
       }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
+      cudaStreamSynchronize(s);
       cudaFree(x);
       cudaFree(y);
-      c->batch_target_threads = best_t;
+      c->batch_targets.assign(ni, 256);
+      for (int i = 0; i < ni; ++i)
+        for (size_t L = 0; L < lclass.size(); ++L)
+          if (c->sub[i]->desc.lmax == lclass[L]) c->batch_targets[i] = best_t[L];
       c->batch_tuned = true;
     }
-    batch_tables(c, c->batch_target_threads);
+    batch_tables(c, c->batch_targets);
   } catch (const std::string& e) {
     c->err = "batch: " + e;
     return SAP_ENOMEM;
@@ -1782,241 +1847,424 @@ sap_status batch_erk(sap_ctx* c, double* state, double dt, int nsteps, cudaStrea
   return SAP_OK;
 }
 
-// Crank--Nicolson on a batch: every instance runs its own restarted GMRES (own Krylov space,
-// Hessenberg matrix and convergence test); the instances advance in lock-step and finished ones are
-// masked out of every kernel.  TV = double: FP64 operator and vectors; TV = float: FP32 inner
-// GMRES inside the FP64 residual/refinement loop.
+// ------------------------------------------------------------------------------------------------
+// Batched CN with per-instance GMRES control on the device, one CUDA-graph launch per step
+// ------------------------------------------------------------------------------------------------
+// Every instance runs its own restarted GMRES (own Krylov space, Hessenberg matrix, Givens rotations,
+// convergence test).  The decisions the host used to take between launches (re-orthogonalisation,
+// column finalisation, convergence, restart targets, back substitution) are taken by control kernels
+// with one thread per instance, which write the per-instance masks that the batched kernels read, so
+// a whole CN step is a fixed sequence of launches: it is captured once as a CUDA graph (per state
+// buffer, dt, fields, workspace, initial-guess variant) and replayed with one launch per step.
+// Launches that find every instance finished return at once.  The host reads the per-instance
+// status once after the graph; instances that need more refinement cycles (rare) get one-cycle
+// continuation graphs.
+enum { BS_SOLVING = 0, BS_DONE = 1, BS_ZERO = 2, BS_STOPPED = 3 };
+
+struct BCtl {
+  double H[KRY_MAXV * (KRY_MAXV + 1)];  // H[i * KRY_MAXV + j]
+  double g[KRY_MAXV + 1], cs[KRY_MAXV], sn[KRY_MAXV];
+  double bnorm, rel, target;
+  int its, status, jdone, pad;
+};
+
+struct BStat {  // per-instance status copied to the host after each graph
+  double rel;
+  int its, status;
+};
+
+struct BMasks {  // device masks read by the batched kernels, written by the control kernels
+  int* act;      // instance still solving this step
+  int* inner;    // instance active in the current Arnoldi iteration
+  int* reo;      // instance needs the second Gram--Schmidt pass in this iteration
+  int* mi;       // basis vectors to combine into the solution (0: none)
+  int* zero;     // right side is zero: the state is set to zero
+};
+
+__global__ void bctl_init(BCtl* ctl, BMasks M, int ni) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    ctl[i].its = 0;
+    ctl[i].status = BS_SOLVING;
+    ctl[i].rel = 0.0;
+    M.act[i] = 1;
+    M.inner[i] = 0;
+    M.reo[i] = 0;
+    M.mi[i] = 0;
+    M.zero[i] = 0;
+  }
+}
+
+// ||b|| from the dots (region 1, index 0); a zero right side finishes the instance at zero
+__global__ void bctl_bnorm(BCtl* ctl, BMasks M, const double* dsc, int SS, int ni) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    const double bn = sqrt(dsc[(size_t)i * SS + KRY_MAXV]);
+    ctl[i].bnorm = bn;
+    const bool z = bn == 0.0;
+    M.zero[i] = z;
+    M.act[i] = !z && isfinite(bn);
+    if (z) ctl[i].status = BS_ZERO;
+    if (!isfinite(bn)) {  // reported as not converged
+      ctl[i].status = BS_STOPPED;
+      ctl[i].rel = bn;
+    }
+  }
+}
+
+// true relative residual from the dots of r (region 1, index 0): converged, stopped or go on
+__global__ void bctl_residual(BCtl* ctl, BMasks M, const double* dsc, int SS, int ni, double tol, int maxit) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    if (!M.act[i]) continue;
+    const double rel = sqrt(dsc[(size_t)i * SS + KRY_MAXV]) / ctl[i].bnorm;
+    ctl[i].rel = rel;
+    if (rel <= tol) {
+      ctl[i].status = BS_DONE;
+      M.act[i] = 0;
+    } else if (ctl[i].its >= maxit || !isfinite(rel)) {
+      ctl[i].status = BS_STOPPED;
+      M.act[i] = 0;
+    }
+  }
+}
+
+// start of an Arnoldi cycle: beta = |P^-1 r| (region 1), g = beta e_1, the cycle's target
+__global__ void bctl_beta(BCtl* ctl, BMasks M, const double* dsc, int SS, int ni, double tol, double floor_rel) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    M.inner[i] = M.act[i];
+    M.mi[i] = 0;
+    if (!M.act[i]) continue;
+    BCtl& C = ctl[i];
+    const double beta = sqrt(dsc[(size_t)i * SS + KRY_MAXV]);
+    for (int k = 0; k <= KRY_MAXV; ++k) C.g[k] = 0.0;
+    C.g[0] = beta;
+    C.jdone = 0;
+    C.target = beta * fmax(0.5 * tol / C.rel, floor_rel);
+    if (!(beta > 0.0)) M.inner[i] = 0;
+  }
+}
+
+// after the first Gram--Schmidt pass of column j: h (region 0, j+1 values) into H; second pass when
+// |w'| < |w| / sqrt(2) (|w|^2 at region 0 index j+1, |w'|^2 at region 1 index 0)
+__global__ void bctl_reo(BCtl* ctl, BMasks M, const double* dsc, int SS, int ni, int j) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    M.reo[i] = 0;
+    if (!M.inner[i]) continue;
+    const double* h = dsc + (size_t)i * SS;
+    for (int k = 0; k <= j; ++k) ctl[i].H[k * KRY_MAXV + j] = h[k];
+    M.reo[i] = h[KRY_MAXV] < 0.5 * h[j + 1];
+  }
+}
+
+// after the second pass: its coefficients (region 2) added to column j
+__global__ void bctl_addh2(BCtl* ctl, BMasks M, const double* dsc, int SS, int ni, int j) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    if (!M.reo[i]) continue;
+    const double* h2 = dsc + (size_t)i * SS + 2 * KRY_MAXV;
+    for (int k = 0; k <= j; ++k) ctl[i].H[k * KRY_MAXV + j] += h2[k];
+  }
+}
+
+// column j finalised: subdiagonal |w| (region 1), previous rotations, new rotation, residual
+// estimate |g_{j+1}|; the instance leaves the cycle when it meets its target or maxit
+__global__ void bctl_finalize(BCtl* ctl, BMasks M, const double* dsc, int SS, int ni, int j, int maxit) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    if (!M.inner[i]) continue;
+    BCtl& C = ctl[i];
+    const int MM = KRY_MAXV;
+    const double hn = sqrt(dsc[(size_t)i * SS + KRY_MAXV]);
+    C.H[(j + 1) * MM + j] = hn;
+    for (int k = 0; k < j; ++k) {
+      const double a0 = C.H[k * MM + j], a1 = C.H[(k + 1) * MM + j];
+      C.H[k * MM + j] = C.cs[k] * a0 + C.sn[k] * a1;
+      C.H[(k + 1) * MM + j] = -C.sn[k] * a0 + C.cs[k] * a1;
+    }
+    const double a0 = C.H[j * MM + j], a1 = C.H[(j + 1) * MM + j];
+    const double den = hypot(a0, a1);
+    C.cs[j] = den > 0 ? a0 / den : 1.0;
+    C.sn[j] = den > 0 ? a1 / den : 0.0;
+    C.H[j * MM + j] = den;
+    C.H[(j + 1) * MM + j] = 0.0;
+    C.g[j + 1] = -C.sn[j] * C.g[j];
+    C.g[j] = C.cs[j] * C.g[j];
+    C.its += 1;
+    C.jdone = j + 1;
+    if (fabs(C.g[j + 1]) <= C.target || hn == 0.0 || C.its >= maxit) M.inner[i] = 0;
+  }
+}
+
+// end of a cycle: y = R^-1 g (region 3) and the number of basis vectors to combine
+__global__ void bctl_solve(BCtl* ctl, BMasks M, double* dsc, int SS, int ni) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    M.mi[i] = 0;
+    if (!M.act[i]) continue;
+    BCtl& C = ctl[i];
+    const int jd = C.jdone;
+    double* y = dsc + (size_t)i * SS + 3 * KRY_MAXV;
+    for (int k = jd - 1; k >= 0; --k) {
+      double v = C.g[k];
+      for (int l = k + 1; l < jd; ++l) v -= C.H[k * KRY_MAXV + l] * y[l];
+      y[k] = v / C.H[k * KRY_MAXV + k];
+    }
+    M.mi[i] = jd;
+  }
+}
+
+__global__ void bctl_status(const BCtl* ctl, BStat* out, int ni) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    out[i].rel = ctl[i].rel;
+    out[i].its = ctl[i].its;
+    out[i].status = ctl[i].status;
+  }
+}
+
 template <typename TV>
-static sap_status batch_cn_impl(sap_ctx* c, double* state, double dt, int nsteps, double tol, int m, int maxit,
-                                sap_solver_stats* st, cudaStream_t s) {
+struct BatchGraphArgs {
+  double* state;
+  double *b, *r, *prev;
+  TV* V;
+  double dt;
+  double tol;
+  int m, maxit;
+};
+
+// the launches of one refinement cycle (Arnoldi from the prepared V_0, solution update, new
+// residual and decision), or of the start of a step (right side, initial guess, first residual)
+template <typename TV>
+static cudaError_t batch_enqueue(sap_ctx* c, const BatchGraphArgs<TV>& A, int what, int extrap, cudaStream_t s) {
   const int64_t N = c->N;
   const int ni = (int)c->sub.size();
-  double* b = c->ws64;
-  double* r = b + N;
-  TV* V = (sizeof(TV) == 8) ? reinterpret_cast<TV*>(c->ws64 + 2 * N) : reinterpret_cast<TV*>(c->ws32);
-  // the state before the last step (initial-guess history), after the Krylov basis / b and r
-  double* prev = (sizeof(TV) == 8) ? c->ws64 + (size_t)(m + 3) * N : c->ws64 + 2 * N;
   const BatchChunks& C = c->chunks;
   double* partial = c->small;
-  const int SS = 4 * KRY_MAXV;                     // per-instance scalar stride
+  const int SS = 4 * KRY_MAXV;
   double* dsc = c->small + (size_t)(KRY_MAXV + 1) * C.nchunks;
-  double* hsc = c->small_host;
-  int* d_act = c->d_active;
-  int* d_mi = d_act + ni;                           // [ni] combine lengths
-  int* d_zero = d_mi + ni;                          // [ni] zero masks
-  const double half = 0.5 * dt;
-  std::vector<double> H((size_t)ni * (m + 1) * m), g((size_t)ni * (m + 1)), cs((size_t)ni * m), sn((size_t)ni * m);
-  std::vector<double> bnorm(ni), rel(ni), target(ni), beta(ni);
-  std::vector<int> act(ni), inner(ni), jdone(ni), its(ni), zero(ni);
+  BCtl* ctl = reinterpret_cast<BCtl*>(c->bctl);
+  BMasks M{c->bmask, c->bmask + ni, c->bmask + 2 * ni, c->bmask + 3 * ni, c->bmask + 4 * ni};
+  const double half = 0.5 * A.dt;
+  const int cb = (ni + 127) / 128;
+  cudaError_t err = cudaSuccess;
+  auto dots = [&](const TV* Vb, int mm, const TV* w, int ww, int region, const int* mask) {
+    multidot_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(Vb, N, mm, w, ww, C, mask, partial);
+    reduce_b_kernel<<<ni, 32 * (mm + ww), 0, s>>>(partial, C, mask, mm + ww, dsc + region * KRY_MAXV, SS);
+    g_launches += 2;
+  };
+  auto dots64 = [&](const double* w, const int* mask) {
+    multidot_b_kernel<double><<<C.nchunks, KRY_THREADS, 0, s>>>(nullptr, N, 0, w, 1, C, mask, partial);
+    reduce_b_kernel<<<ni, 32, 0, s>>>(partial, C, mask, 1, dsc + KRY_MAXV, SS);
+    g_launches += 2;
+  };
+  auto update = [&](int mm, int hregion, TV* w, const int* mask) {
+    update_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(A.V, N, mm, dsc + hregion * KRY_MAXV, SS, w, C, mask, partial);
+    reduce_b_kernel<<<ni, 32, 0, s>>>(partial, C, mask, 1, dsc + KRY_MAXV, SS);
+    g_launches += 2;
+  };
+  auto residual = [&]() -> cudaError_t {
+    // r = b - A zeta in FP64 and the inner right side V_0 = P^-1 r
+    Epi<double> e{};
+    e.out = A.r; e.bvec = A.b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.cj = half;
+    if (sizeof(TV) == 4) e.out32 = reinterpret_cast<float*>(A.V);
+    else e.outj = reinterpret_cast<double*>(A.V);
+    cudaError_t e1 = launch_apply_batched<double>(c->b64, M.act, A.state, e, s);
+    if (e1 != cudaSuccess) return e1;
+    dots64(A.r, M.act);
+    bctl_residual<<<cb, 128, 0, s>>>(ctl, M, dsc, SS, ni, A.tol, A.maxit);
+    ++g_launches;
+    return cudaGetLastError();
+  };
+  if (what == 0) {  // start of a step
+    bctl_init<<<cb, 128, 0, s>>>(ctl, M, ni);
+    ++g_launches;
+    Epi<double> e{};
+    e.out = A.b; e.ax = 1.0; e.bl = -half; e.gs = A.dt;
+    if ((err = launch_apply_batched<double>(c->b64, M.act, A.state, e, s)) != cudaSuccess) return err;
+    if (extrap) {
+      extrapolate_kernel<<<1024, KRY_THREADS, 0, s>>>(A.state, A.prev, N);
+    } else {
+      if ((err = cudaMemcpyAsync(A.prev, A.state, sizeof(double) * N, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return err;
+    }
+    dots64(A.b, M.act);
+    bctl_bnorm<<<cb, 128, 0, s>>>(ctl, M, dsc, SS, ni);
+    zero_b_kernel<<<C.nchunks, KRY_THREADS, 0, s>>>(A.state, C, M.zero);
+    g_launches += 3;
+    return residual();
+  }
+  // one refinement cycle
+  dots(nullptr, 0, A.V, 1, 1, M.act);
+  bctl_beta<<<cb, 128, 0, s>>>(ctl, M, dsc, SS, ni, A.tol, sizeof(TV) == 8 ? 0.0 : 1e-6);
+  scale_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(A.V, A.V, dsc + KRY_MAXV, SS, C, M.inner);
+  g_launches += 2;
+  for (int j = 0; j < A.m; ++j) {
+    TV* w = A.V + (size_t)(j + 1) * N;
+    Epi<TV> e{};
+    e.out = w; e.ax = TV(1); e.bl = TV(half); e.jacobi = 1; e.cj = TV(half);
+    if constexpr (sizeof(TV) == 8) err = launch_apply_batched<double>(c->b64, M.inner, A.V + (size_t)j * N, e, s);
+    else err = launch_apply_batched<float>(c->b32, M.inner, A.V + (size_t)j * N, e, s);
+    if (err != cudaSuccess) return err;
+    dots(A.V, j + 1, w, 1, 0, M.inner);
+    update(j + 1, 0, w, M.inner);
+    bctl_reo<<<cb, 128, 0, s>>>(ctl, M, dsc, SS, ni, j);
+    ++g_launches;
+    dots(A.V, j + 1, w, 0, 2, M.reo);
+    update(j + 1, 2, w, M.reo);
+    bctl_addh2<<<cb, 128, 0, s>>>(ctl, M, dsc, SS, ni, j);
+    scale_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(w, w, dsc + KRY_MAXV, SS, C, M.inner);
+    bctl_finalize<<<cb, 128, 0, s>>>(ctl, M, dsc, SS, ni, j, A.maxit);
+    g_launches += 3;
+  }
+  bctl_solve<<<cb, 128, 0, s>>>(ctl, M, dsc, SS, ni);
+  combine_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(A.V, N, M.mi, dsc + 3 * KRY_MAXV, SS, A.state, C);
+  g_launches += 2;
+  return residual();
+}
+
+// refinement cycles in the graph that starts a step (two cover the FP32 form at 1e-10: each cycle
+// asks the FP32 solve for at most a 1e-6 reduction)
+constexpr int kBatchStartCycles = 2;
+
+template <typename TV>
+static sap_status batch_cn_graph(sap_ctx* c, double* state, double dt, int nsteps, double tol, int m, int maxit,
+                                 sap_solver_stats* st, cudaStream_t s) {
+  // kernel attributes (dynamic shared-memory limits) are set before any capture
+  if (cudaError_t e0 = prepare_batched<double>(c->b64); e0 != cudaSuccess) {
+    c->err = std::string("batch cn: ") + cudaGetErrorString(e0);
+    return SAP_ECUDA;
+  }
+  if (cudaError_t e0 = prepare_batched<TV>(*reinterpret_cast<const std::vector<BatchDev<TV>>*>(
+          sizeof(TV) == 8 ? (const void*)&c->b64 : (const void*)&c->b32));
+      e0 != cudaSuccess) {
+    c->err = std::string("batch cn: ") + cudaGetErrorString(e0);
+    return SAP_ECUDA;
+  }
+  const int64_t N = c->N;
+  const int ni = (int)c->sub.size();
+  BatchGraphArgs<TV> A{};
+  A.state = state;
+  A.b = c->ws64;
+  A.r = c->ws64 + N;
+  A.V = (sizeof(TV) == 8) ? reinterpret_cast<TV*>(c->ws64 + 2 * N) : reinterpret_cast<TV*>(c->ws32);
+  A.prev = (sizeof(TV) == 8) ? c->ws64 + (size_t)(m + 3) * N : c->ws64 + 2 * N;
+  A.dt = dt;
+  A.tol = tol;
+  A.m = m;
+  A.maxit = maxit;
+  cudaError_t err = cudaSuccess;
+  if (!c->bctl) {
+    if (cudaMalloc(&c->bctl, sizeof(BCtl) * ni) != cudaSuccess ||
+        cudaMalloc(&c->bmask, sizeof(int) * 5 * ni) != cudaSuccess ||
+        cudaMalloc(&c->bstat, sizeof(BStat) * ni) != cudaSuccess ||
+        cudaMallocHost(&c->bstat_host, sizeof(BStat) * ni) != cudaSuccess) {
+      c->err = "batch cn: allocation of the control blocks failed";
+      return SAP_ENOMEM;
+    }
+  }
+  BStat* hst = reinterpret_cast<BStat*>(c->bstat_host);
+  // graphs are kept per (kind, extrapolation) for the current state buffer, dt, tolerances, fields and
+  // workspace
+  const void* ws = static_cast<const void*>(A.V);
+  auto key_ok = [&](const sap_ctx::BGraph& g) {
+    return g.state == state && g.dt == dt && g.tol == tol && g.m == m && g.maxit == maxit && g.ws == ws &&
+           g.version == c->batch_built_version;
+  };
+  if (!c->bgraphs.empty() && !key_ok(c->bgraphs.front())) {
+    for (auto& g : c->bgraphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    c->bgraphs.clear();
+  }
+  auto get_graph = [&](int kind, int extrap, int64_t* nl) -> cudaGraphExec_t {
+    for (const auto& g : c->bgraphs)
+      if (g.kind == kind && g.extrap == extrap) {
+        *nl = g.launches;
+        return g.exec;
+      }
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      c->cap_stream = nullptr;
+      cudaGetLastError();
+      return nullptr;
+    }
+    const int64_t l0 = g_launches;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    cudaError_t e1 = cudaSuccess;
+    if (kind == 0) {
+      e1 = batch_enqueue<TV>(c, A, 0, extrap, c->cap_stream);
+      for (int k = 0; k < kBatchStartCycles && e1 == cudaSuccess; ++k) e1 = batch_enqueue<TV>(c, A, 1, 0, c->cap_stream);
+    } else {
+      e1 = batch_enqueue<TV>(c, A, 1, 0, c->cap_stream);
+    }
+    if (e1 == cudaSuccess) {
+      bctl_status<<<(ni + 127) / 128, 128, 0, c->cap_stream>>>(reinterpret_cast<BCtl*>(c->bctl),
+                                                               reinterpret_cast<BStat*>(c->bstat), ni);
+      ++g_launches;
+      e1 = cudaMemcpyAsync(c->bstat_host, c->bstat, sizeof(BStat) * ni, cudaMemcpyDeviceToHost, c->cap_stream);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+    const int64_t launched = g_launches - l0;
+    g_launches = l0;
+    cudaGraphExec_t ex = nullptr;
+    if (e1 != cudaSuccess || e2 != cudaSuccess || !graph || cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return nullptr;
+    }
+    cudaGraphDestroy(graph);
+    sap_ctx::BGraph g;
+    g.exec = ex; g.kind = kind; g.extrap = extrap; g.state = state; g.dt = dt; g.tol = tol; g.m = m;
+    g.maxit = maxit; g.ws = ws; g.version = c->batch_built_version; g.launches = launched;
+    c->bgraphs.push_back(g);
+    *nl = launched;
+    return ex;
+  };
   int64_t total_its = 0;
   int max_its = 0;
   double worst_rel = 0.0;
   const int64_t launches0 = g_launches;
-  cudaError_t err = cudaSuccess;
-  auto put_mask = [&](const std::vector<int>& v, int* d) {
-    cudaMemcpyAsync(d, v.data(), sizeof(int) * ni, cudaMemcpyHostToDevice, s);
-    return cudaStreamSynchronize(s);  // v is pageable host memory reused right after
-  };
-  auto dots = [&](const TV* Vb, int mm, const TV* w, int ww, int region) {
-    multidot_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(Vb, N, mm, w, ww, C, d_act, partial);
-    reduce_b_kernel<<<ni, 32 * (mm + ww), 0, s>>>(partial, C, d_act, mm + ww, dsc + region * KRY_MAXV, SS);
-    g_launches += 2;
-  };
-  auto dots64 = [&](const double* w, int region) {
-    multidot_b_kernel<double><<<C.nchunks, KRY_THREADS, 0, s>>>(nullptr, N, 0, w, 1, C, d_act, partial);
-    reduce_b_kernel<<<ni, 32, 0, s>>>(partial, C, d_act, 1, dsc + region * KRY_MAXV, SS);
-    g_launches += 2;
-  };
-  auto update = [&](const TV* Vb, int mm, int hregion, TV* w) {
-    update_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(Vb, N, mm, dsc + hregion * KRY_MAXV, SS, w, C, d_act, partial);
-    reduce_b_kernel<<<ni, 32, 0, s>>>(partial, C, d_act, 1, dsc + 1 * KRY_MAXV, SS);  // |w|^2 -> region 1 [0]
-    g_launches += 2;
-  };
-  auto fetch_all = [&]() {
-    cudaMemcpyAsync(hsc, dsc, sizeof(double) * ni * SS, cudaMemcpyDeviceToHost, s);
-    return cudaStreamSynchronize(s);
-  };
-  auto apply64 = [&](const double* x, const Epi<double>& e) { return launch_apply_batched<double>(c->b64, d_act, x, e, s); };
-#define CK(x)                               \
-  do {                                      \
-    err = (x);                              \
-    if (err != cudaSuccess) goto cuda_fail; \
-  } while (0)
   for (int step = 0; step < nsteps; ++step) {
-    std::fill(act.begin(), act.end(), 1);
-    CK(put_mask(act, d_act));
-    {
-      Epi<double> e{};
-      e.out = b; e.ax = 1.0; e.bl = -half; e.gs = dt;
-      CK(apply64(state, e));
+    const int extrap = c->cn_prev_valid && c->cn_prev_ptr == state && c->cn_prev_dt == dt && c->cn_prev_theta == 0.5;
+    int64_t nl = 0;
+    cudaGraphExec_t ex = get_graph(0, extrap, &nl);
+    if (!ex) {
+      c->err = "batch cn: CUDA graph capture of the step failed";
+      return SAP_ECUDA;
     }
-    // initial guess: the linear extrapolation 2 zeta^(n-1) - zeta^(n-2) when the previous step ran on
-    // the same buffer with the same dt (as in the single-problem path; only the iteration count
-    // depends on it), else zeta^(n-1)
-    if (c->cn_prev_valid && c->cn_prev_ptr == state && c->cn_prev_dt == dt && c->cn_prev_theta == 0.5) {
-      extrapolate_kernel<<<1024, KRY_THREADS, 0, s>>>(state, prev, N);
-      ++g_launches;
-    } else {
-      CK(cudaMemcpyAsync(prev, state, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-    }
+    if ((err = cudaGraphLaunch(ex, s)) != cudaSuccess) goto cuda_fail;
+    g_launches += nl;
     c->cn_prev_valid = true;
     c->cn_prev_ptr = state;
     c->cn_prev_dt = dt;
     c->cn_prev_theta = 0.5;
-    dots64(b, 1);
-    CK(fetch_all());
-    for (int i = 0; i < ni; ++i) {
-      bnorm[i] = std::sqrt(hsc[(size_t)i * SS + KRY_MAXV]);
-      zero[i] = bnorm[i] == 0.0;
-      act[i] = !zero[i];
-      its[i] = 0;
-    }
-    CK(put_mask(zero, d_zero));
-    zero_b_kernel<<<C.nchunks, KRY_THREADS, 0, s>>>(state, C, d_zero);
-    ++g_launches;
-    for (;;) {
-      CK(put_mask(act, d_act));
-      // FP64 residual; inner right side v0 = P^-1 r
-      {
-        Epi<double> e{};
-        e.out = r; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half;
-        if (sizeof(TV) == 4) { e.out32 = reinterpret_cast<float*>(V); e.cj = half; }
-        CK(apply64(state, e));
+    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) goto cuda_fail;
+    for (;;) {  // continuation cycles for instances still solving under maxit
+      bool more = false;
+      for (int i = 0; i < ni; ++i) more = more || hst[i].status == BS_SOLVING;
+      if (!more) break;
+      cudaGraphExec_t exc = get_graph(1, 0, &nl);
+      if (!exc) {
+        c->err = "batch cn: CUDA graph capture of a refinement cycle failed";
+        return SAP_ECUDA;
       }
-      if (sizeof(TV) == 8) {
-        Epi<double> e{};
-        e.out = reinterpret_cast<double*>(V); e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.jacobi = 1;
-        e.cj = half;
-        CK(apply64(state, e));
-      }
-      dots64(r, 1);
-      CK(fetch_all());
-      bool any = false;
-      for (int i = 0; i < ni; ++i) {
-        if (!act[i]) continue;
-        rel[i] = std::sqrt(hsc[(size_t)i * SS + KRY_MAXV]) / bnorm[i];
-        if (rel[i] <= tol || its[i] >= maxit || !std::isfinite(rel[i])) act[i] = 0;
-        any = any || act[i];
-      }
-      if (!any) break;
-      CK(put_mask(act, d_act));
-      dots(nullptr, 0, V, 1, 1);
-      scale_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(V, V, dsc + KRY_MAXV, SS, C, d_act);
-      ++g_launches;
-      CK(fetch_all());
-      for (int i = 0; i < ni; ++i) {
-        inner[i] = act[i];
-        jdone[i] = 0;
-        if (!act[i]) continue;
-        beta[i] = std::sqrt(hsc[(size_t)i * SS + KRY_MAXV]);
-        std::fill(g.begin() + (size_t)i * (m + 1), g.begin() + (size_t)(i + 1) * (m + 1), 0.0);
-        g[(size_t)i * (m + 1)] = beta[i];
-        target[i] = beta[i] * (sizeof(TV) == 8 ? 0.5 * tol / rel[i] : std::max(0.5 * tol / rel[i], 1e-6));
-      }
-      for (int j = 0; j < m; ++j) {
-        bool anyin = false;
-        for (int i = 0; i < ni; ++i) anyin = anyin || inner[i];
-        if (!anyin) break;
-        CK(put_mask(inner, d_act));
-        TV* w = V + (size_t)(j + 1) * N;
-        {
-          Epi<TV> e{};
-          e.out = w; e.ax = TV(1); e.bl = TV(half); e.jacobi = 1; e.cj = TV(half);
-          if constexpr (sizeof(TV) == 8) CK(launch_apply_batched<double>(c->b64, d_act, V + (size_t)j * N, e, s));
-          else CK(launch_apply_batched<float>(c->b32, d_act, V + (size_t)j * N, e, s));
-        }
-        dots(V, j + 1, w, 1, 0);
-        update(V, j + 1, 0, w);
-        CK(fetch_all());
-        std::vector<int> reo(ni, 0);
-        bool anyre = false;
-        for (int i = 0; i < ni; ++i) {
-          if (!inner[i]) continue;
-          const double* hs = hsc + (size_t)i * SS;
-          double* Hi = &H[(size_t)i * (m + 1) * m];
-          for (int i2 = 0; i2 <= j; ++i2) Hi[(size_t)i2 * m + j] = hs[i2];
-          if (std::sqrt(hs[KRY_MAXV]) < 0.7071067811865476 * std::sqrt(hs[j + 1])) {
-            reo[i] = 1;
-            anyre = true;
-          }
-        }
-        if (anyre) {
-          CK(put_mask(reo, d_act));
-          dots(V, j + 1, w, 0, 2);
-          update(V, j + 1, 2, w);
-          CK(fetch_all());
-          for (int i = 0; i < ni; ++i) {
-            if (!reo[i]) continue;
-            double* Hi = &H[(size_t)i * (m + 1) * m];
-            for (int i2 = 0; i2 <= j; ++i2) Hi[(size_t)i2 * m + j] += hsc[(size_t)i * SS + 2 * KRY_MAXV + i2];
-          }
-          CK(put_mask(inner, d_act));
-        }
-        scale_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(w, w, dsc + KRY_MAXV, SS, C, d_act);
-        ++g_launches;
-        for (int i = 0; i < ni; ++i) {
-          if (!inner[i]) continue;
-          double* Hi = &H[(size_t)i * (m + 1) * m];
-          double* gi = &g[(size_t)i * (m + 1)];
-          double* csi = &cs[(size_t)i * m];
-          double* sni = &sn[(size_t)i * m];
-          const double wn = std::sqrt(hsc[(size_t)i * SS + KRY_MAXV]);
-          Hi[(size_t)(j + 1) * m + j] = wn;
-          for (int i2 = 0; i2 < j; ++i2) {
-            const double a0 = Hi[(size_t)i2 * m + j], a1 = Hi[(size_t)(i2 + 1) * m + j];
-            Hi[(size_t)i2 * m + j] = csi[i2] * a0 + sni[i2] * a1;
-            Hi[(size_t)(i2 + 1) * m + j] = -sni[i2] * a0 + csi[i2] * a1;
-          }
-          const double a0 = Hi[(size_t)j * m + j], a1 = Hi[(size_t)(j + 1) * m + j];
-          const double den = std::hypot(a0, a1);
-          csi[j] = den > 0 ? a0 / den : 1.0;
-          sni[j] = den > 0 ? a1 / den : 0.0;
-          Hi[(size_t)j * m + j] = den;
-          Hi[(size_t)(j + 1) * m + j] = 0.0;
-          gi[j + 1] = -sni[j] * gi[j];
-          gi[j] = csi[j] * gi[j];
-          ++its[i];
-          jdone[i] = j + 1;
-          if (std::fabs(gi[j + 1]) <= target[i] || wn == 0.0 || its[i] >= maxit) inner[i] = 0;
-        }
-      }
-      // y = H^-1 g per instance ; zeta += V y
-      for (int i = 0; i < ni; ++i) {
-        const int jd = act[i] ? jdone[i] : 0;
-        const double* Hi = &H[(size_t)i * (m + 1) * m];
-        const double* gi = &g[(size_t)i * (m + 1)];
-        double* yi = hsc + (size_t)i * SS + 3 * KRY_MAXV;
-        for (int i2 = jd - 1; i2 >= 0; --i2) {
-          double v = gi[i2];
-          for (int k2 = i2 + 1; k2 < jd; ++k2) v -= Hi[(size_t)i2 * m + k2] * yi[k2];
-          yi[i2] = v / Hi[(size_t)i2 * m + i2];
-        }
-        jdone[i] = jd;
-      }
-      CK(cudaMemcpyAsync(dsc, hsc, sizeof(double) * ni * SS, cudaMemcpyHostToDevice, s));
-      CK(put_mask(jdone, d_mi));
-      combine_b_kernel<TV><<<C.nchunks, KRY_THREADS, 0, s>>>(V, N, d_mi, dsc + 3 * KRY_MAXV, SS, state, C);
-      ++g_launches;
-      CK(cudaGetLastError());
+      if ((err = cudaGraphLaunch(exc, s)) != cudaSuccess) goto cuda_fail;
+      g_launches += nl;
+      if ((err = cudaStreamSynchronize(s)) != cudaSuccess) goto cuda_fail;
     }
     for (int i = 0; i < ni; ++i) {
-      total_its += its[i];
-      max_its = std::max(max_its, its[i]);
-      if (!zero[i]) worst_rel = std::max(worst_rel, rel[i]);
-      if (!zero[i] && !(rel[i] <= tol)) {
+      total_its += hst[i].its;
+      max_its = std::max(max_its, hst[i].its);
+      if (hst[i].status != BS_ZERO) worst_rel = std::max(worst_rel, hst[i].rel);
+    }
+    for (int i = 0; i < ni; ++i) {
+      if (hst[i].status == BS_STOPPED) {
         c->err = "batch cn: GMRES did not reach the tolerance within maxit on instance " + std::to_string(i);
         if (st) {
           st->steps = step + 1; st->iterations = total_its; st->max_iterations = max_its;
           st->last_rel_residual = worst_rel; st->kernel_launches = g_launches - launches0;
         }
-        std::fill(act.begin(), act.end(), 1);
-        put_mask(act, d_act);
+        c->cn_prev_valid = false;
         return SAP_ENOCONV;
       }
     }
   }
-  std::fill(act.begin(), act.end(), 1);
-  CK(put_mask(act, d_act));
   if (st) {
     st->steps = nsteps; st->iterations = total_its; st->max_iterations = max_its;
     st->last_rel_residual = worst_rel; st->kernel_launches = g_launches - launches0;
@@ -2025,15 +2273,14 @@ static sap_status batch_cn_impl(sap_ctx* c, double* state, double dt, int nsteps
 cuda_fail:
   c->err = std::string("batch cn: ") + cudaGetErrorString(err);
   return SAP_ECUDA;
-#undef CK
 }
 
 sap_status batch_cn(sap_ctx* c, double* state, double dt, int nsteps, double tol, int restart, int maxit,
                     sap_solver_stats* st, cudaStream_t s) {
   sap_status ps = batch_prepare(c, s);
   if (ps != SAP_OK) return ps;
-  return c->prec == SAP_PREC_FP64 ? batch_cn_impl<double>(c, state, dt, nsteps, tol, restart, maxit, st, s)
-                                  : batch_cn_impl<float>(c, state, dt, nsteps, tol, restart, maxit, st, s);
+  return c->prec == SAP_PREC_FP64 ? batch_cn_graph<double>(c, state, dt, nsteps, tol, restart, maxit, st, s)
+                                  : batch_cn_graph<float>(c, state, dt, nsteps, tol, restart, maxit, st, s);
 }
 
 

@@ -191,7 +191,6 @@ struct sap_ctx {
   float* ws32 = nullptr;
   int ws32_count = 0;
   double* small = nullptr;                     // block partial sums of the Krylov reductions (+ batch scalars)
-  double* small_host = nullptr;                // pinned mirror of the batch scalars (batch handles only)
   void* gdev = nullptr;                        // device Arnoldi control block
   void* gdev_host = nullptr;                   // pinned mirror
   int krylov_restart = 0;
@@ -207,11 +206,12 @@ struct sap_ctx {
   std::vector<int64_t> inst_off;
   int fields_version = 0;                      // bumped by sap_set_fields
   int batch_built_version = -1;                // sum of the sub versions the batch tables were built for
-  int batch_target_threads = 256;              // autotuned thread-block size target
+  std::vector<int> batch_targets;              // autotuned thread-block target of every instance (per l_max)
   bool batch_tuned = false;
   std::vector<sap::DevBuf> batch_bufs;
-  sap::BatchDev<double> b64;
-  sap::BatchDev<float> b32;
+  std::vector<sap::BatchDev<double>> b64;      // one launch per group of instances with the same l_max
+  std::vector<sap::BatchDev<float>> b32;
+  std::vector<int> batch_class;                // group of every instance
   sap::BatchChunks chunks;
   int* d_active = nullptr;                     // [ninst] device activity mask
   std::vector<int> h_active;
@@ -226,6 +226,21 @@ struct sap_ctx {
   };
   std::vector<CnGraph> cn_graphs;
   cudaStream_t cap_stream = nullptr;           // private stream for the captures
+  // batched CN: per-instance GMRES control blocks, masks and status (device, pinned mirror) and the
+  // CUDA graphs of a step and of a continuation cycle
+  void* bctl = nullptr;
+  int* bmask = nullptr;
+  void* bstat = nullptr;
+  void* bstat_host = nullptr;
+  struct BGraph {
+    cudaGraphExec_t exec = nullptr;
+    int kind = 0, extrap = 0, m = 0, maxit = 0, version = -1;
+    const double* state = nullptr;
+    double dt = 0.0, tol = 0.0;
+    const void* ws = nullptr;
+    int64_t launches = 0;
+  };
+  std::vector<BGraph> bgraphs;
   // field gradients of the adjoint: tables (built on first use for the current fields) and the
   // per-cell partials
   sap::GradTables gt{};
@@ -258,6 +273,8 @@ template <typename T>
 void rows_config(const OpParams<T>& P, int target_threads, int* cells, size_t* smem);
 template <typename T>
 cudaError_t launch_rows_batched(const BatchDev<T>& B, const int* active, const T* x, const Epi<T>& e, cudaStream_t s);
+template <typename T>
+cudaError_t prepare_rows_batched(const BatchDev<T>& B);  // shared-memory limit of the batched row kernel
 int apply_cell_stride(const OpParams<double>& P);
 sap_status batch_prepare(sap_ctx* c, cudaStream_t s);
 sap_status batch_apply(sap_ctx* c, const void* x, void* y, int mode, cudaStream_t s);

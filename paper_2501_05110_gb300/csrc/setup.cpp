@@ -394,8 +394,7 @@ extern "C" sap_status sap_create_batch(int ninst, const sap_desc* descs, int pre
       Ns.push_back(sub->N);
       c->sub.push_back(sub);
     }
-    if (cudaMalloc(&c->small, sizeof(double) * krylov_batch_scratch_doubles(Ns)) != cudaSuccess ||
-        cudaMallocHost(&c->small_host, sizeof(double) * 4 * 32 * (size_t)ninst) != cudaSuccess) {
+    if (cudaMalloc(&c->small, sizeof(double) * krylov_batch_scratch_doubles(Ns)) != cudaSuccess) {
       g_create_error = "sap_create_batch: allocation failed";
       sap_destroy(c);
       return SAP_ENOMEM;
@@ -1455,6 +1454,12 @@ extern "C" sap_status sap_adjoint_step(sap_handle c, int scheme, const double* z
       const size_t cnt = (size_t)c->ncell * c->gt.ps;
       if (c->gpart_count < cnt) {
         if (c->gpart) cudaFree(c->gpart);
+  for (auto& g : c->bgraphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (c->bctl) cudaFree(c->bctl);
+  if (c->bmask) cudaFree(c->bmask);
+  if (c->bstat) cudaFree(c->bstat);
+  if (c->bstat_host) cudaFreeHost(c->bstat_host);
         c->gpart = nullptr;
         c->gpart_count = 0;
         if (cudaMalloc(&c->gpart, sizeof(double) * std::max<size_t>(cnt, 1)) != cudaSuccess) {
@@ -1490,7 +1495,6 @@ extern "C" sap_status sap_destroy(sap_handle c) {
   if (c->ws64) cudaFree(c->ws64);
   if (c->ws32) cudaFree(c->ws32);
   if (c->small) cudaFree(c->small);
-  if (c->small_host) cudaFreeHost(c->small_host);
   if (c->gdev) cudaFree(c->gdev);
   if (c->gdev_host) cudaFreeHost(c->gdev_host);
   cn_graphs_release(c);

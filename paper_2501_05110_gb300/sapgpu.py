@@ -25,7 +25,7 @@ PTS_SPATIAL, PTS_FACE_X, PTS_FACE_Y, PTS_FACE_Z, PTS_PHASE = range(5)
 SCHEME = {"erk4": 0, "cn": 1}
 EXPORTS = ["sap_create", "sap_create_batch", "sap_batch_instance", "sap_field_points", "sap_set_fields", "sap_num_dofs", "sap_apply_operator",
            "sap_step_erk", "sap_step_erk_noalloc", "sap_step_cn", "sap_adjoint_step_cn", "sap_adjoint_step_erk",
-           "sap_adjoint_step", "sap_step_theta", "sap_set_fields_device", "sap_apply_cost", "sap_destroy", "sap_last_error", "sap_coupling_matrix"]
+           "sap_adjoint_step", "sap_step_theta", "sap_set_fields_device", "sap_probe_fma", "sap_apply_cost", "sap_destroy", "sap_last_error", "sap_coupling_matrix"]
 # field arrays of sap_set_fields / gradient arrays of sap_adjoint_step, in struct order
 FIELDS = ("U", "gradU", "DUDt", "Bw", "Uface0", "Uface1", "Uface2", "nu", "s000")
 
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
     lib.sap_step_theta.argtypes = [vp, vp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
                                    C.POINTER(SolverStats), vp]
     lib.sap_apply_cost.argtypes = [vp, dp, dp]
+    lib.sap_probe_fma.argtypes = [C.c_int, dp]
     lib.sap_adjoint_step_cn.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int, C.c_int, vp, vp,
                                         C.POINTER(SolverStats), vp]
     lib.sap_adjoint_step_erk.argtypes = [vp, vp, vp, C.c_double, vp, vp, C.POINTER(SolverStats), vp]
@@ -103,6 +104,16 @@ def coupling_matrix(lmax: int, which: int, a: int = 0, b: int = 0) -> np.ndarray
     if st != SAP_OK:
         raise SapError(st, "sap_coupling_matrix")
     return out.reshape(n, n)
+
+
+def probe_fma(precision: str = "fp64") -> float:
+    """Measured FMA throughput (flop/s) of the current device (sap_probe_fma)."""
+    lib = load_library()
+    v = C.c_double()
+    st = lib.sap_probe_fma(PREC[precision], C.byref(v))
+    if st != SAP_OK:
+        raise SapError(st, "sap_probe_fma")
+    return v.value
 
 
 def _dptr(a):
