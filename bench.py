@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -50,7 +51,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--workload", default="all", choices=["all", "shock", "box3d", "batched", "adjoint"])
+    ap.add_argument("--workload", default="all", choices=["all", "shock", "box3d", "batched", "adjoint", "dsa"])
+    ap.add_argument("--dsa-steps", type=int, default=500000, help="dsa: CN steps (dt = 1) of the run")
     ap.add_argument("--cells", type=int, default=48, help="box3d: cells per axis")
     ap.add_argument("--instances", type=int, default=512, help="batched: number of shock instances")
     ap.add_argument("--batched-steps", type=int, default=3, help="batched: timed CN steps (each ~seconds)")
@@ -535,6 +537,60 @@ def measure_adjoint(args):
             "reverse_parts": dict(fam.last_backward)}
 
 
+def measure_dsa(args):
+    """The paper's diffusive-shock-acceleration run (Sec. 4.4): l_max = 1 parallel shock on the graded
+    mesh, CN with dt = 1 from an empty domain; reports the spectrum at the shock (slope, normalisation
+    N_num) at the end and the time dependence phi(t) at p = 59.9 against the paper's formula."""
+    import numpy as np
+    import torch
+    from paper_2501_05110_gb300 import sapgpu
+    from paper_2501_05110_gb300 import workloads as W
+    prob = W.dsa_shock(nsteps=args.dsa_steps)
+    sol = sapgpu.Solver(prob, args.precision)
+    xe, pe = prob.edges
+    nx, npc = len(xe) - 1, len(pe) - 1
+    i0 = int(np.searchsorted(xe, 0.0)) - 1  # the x-cells on both sides of x = 0
+    lpc = 0.5 * (pe[1:] + pe[:-1])
+    j1 = int(np.searchsorted(pe, math.log(59.9)) - 1)
+    y = sol.initial_state()
+    p0, U1, r = 2.0, 1.0 / 60.0, 4.0
+    N = 0.1 / (p0 * U1) * 3 * r / (r - 1)  # 12
+
+    def spectrum(v):
+        f = v.view(npc, nx, prob.n, 4)[:, i0:i0 + 2, 0, :].mean(dim=(1, 2)) / math.sqrt(4 * math.pi)
+        return f.cpu().numpy()
+
+    chunk = 1000
+    done, series, its = 0, [], 0
+    clocks = ClockSampler(0, "_dsa")
+    clocks.start()
+    t0 = time.perf_counter()
+    while done < args.dsa_steps:
+        nst = min(chunk, args.dsa_steps - done)
+        st = sol.step_cn(y, prob.dt, nst, 1e-10, 30, 5000)
+        its += st.iterations
+        done += nst
+        F = spectrum(y)
+        series.append((done, float(F[j1] / (N * (math.exp(lpc[j1]) / p0) ** -4))))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    F = spectrum(y)
+    sel = (lpc > math.log(4.0)) & (lpc < math.log(40.0))
+    slope, icpt = np.polyfit(lpc[sel], np.log(F[sel]), 1)
+    Nnum = float(np.mean(F[sel] * (np.exp(lpc[sel]) / p0) ** 4))
+    phi = [{"t": t, "numerical": v, "paper_formula": W.dsa_phi(t)} for (t, v) in series
+           if t in (10000, 20000, 50000, 100000, 200000, 300000, 500000) or t == done]
+    return {"metric": "diffusive shock acceleration run (Sec. 4.4)", "steps": done, "dt": prob.dt,
+            "dofs": prob.ndofs, "cells": prob.ncells, "precision": args.precision,
+            "wall_s": wall, "ms_per_step": 1e3 * wall / done, "gmres_iterations_per_step": its / done,
+            "slope": float(slope), "slope_error": float(abs(slope + 4.0)), "paper_slope_error": 1.5e-3,
+            "fit": "ln p in (ln 4, ln 40), f_000 / sqrt(4 pi) averaged over the two x-cells at the shock",
+            "N_num": Nnum, "paper_N_num": 12.14, "N_analytic": N,
+            "N_analytic_gaussian_source": N * math.exp(8 * (0.125 / p0) ** 2),
+            "phi_p59.9": phi, "clocks": clk}
+
+
 def run_mine(args):
     import torch
     import torch.distributed as dist
@@ -598,6 +654,8 @@ def run_single_workload(args):
         res = measure_batched(args)
     elif args.workload == "adjoint":
         res = measure_adjoint(args)
+    elif args.workload == "dsa":
+        res = measure_dsa(args)
     else:
         res = measure_shock(args, args.precision, 1, 0, 0)
     res.setdefault("n_gpus", 1)

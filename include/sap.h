@@ -66,6 +66,10 @@ enum { SAP_PREC_FP64 = 0, SAP_PREC_FP32 = 1 };
 enum { SAP_APPLY_D = 0,        /* y = M^-1 D x                       */
        SAP_APPLY_RHS = 1,      /* y = M^-1 (h - D x)  (ERK right side) */
        SAP_APPLY_T = 2 };      /* y = (M^-1 D)^T x: transpose of the nodal operator (discrete adjoint) */
+/* numerical flux on the faces (sap_set_flux) */
+enum { SAP_FLUX_UPWIND = 0,    /* J = W (L+ W^T f_lo + L- W^T f_hi)  (Eq. definition-upwind-flux)        */
+       SAP_FLUX_LLF = 1 };     /* local Lax--Friedrichs: J = 1/2 beta (f_lo + f_hi) + 1/2 alpha (f_lo - f_hi),
+                                  alpha = largest |eigenvalue| of n.beta at the face point                */
 /* point sets reported by sap_field_points */
 enum { SAP_PTS_SPATIAL = 0,    /* spatial volume points (nsv x dim_x), fields U, gradU, DUDt, B   */
        SAP_PTS_FACE_X = 1,     /* spatial face points normal to x (nsf x dim_x), field U_x         */
@@ -146,6 +150,15 @@ sap_status sap_set_fields(sap_handle h, const double* U, const double* gradU, co
 sap_status sap_set_fields_device(sap_handle h, const double* U, const double* gradU, const double* DUDt,
                                  const double* Bw, const double* const Uface[3], const double* nu,
                                  const double* s000, sap_stream stream);
+
+/* Choose the numerical flux of the faces (SAP_FLUX_*; the default is the upwind flux of Eq.
+ * definition-upwind-flux; the paper names the local Lax--Friedrichs flux as the alternative, Sec. 3.2).
+ * Boundaries keep their definitions with the flux's split: zero inflow takes the outgoing half
+ * 1/2 (beta +- alpha) of the chosen flux, continuous takes beta.  Takes effect at the next
+ * sap_set_fields; changing it clears the fields, which must be set again.  sap_adjoint_step does not
+ * differentiate the LLF flux (alpha is a maximum over eigenvalues) and returns SAP_EUNSUPPORTED for it.
+ * Errors: SAP_EINVAL. */
+sap_status sap_set_flux(sap_handle h, int flux);
 
 /* Number of degrees of freedom N = ncells * n * (k+1)^D (Sec. 3.1). */
 sap_status sap_num_dofs(sap_handle h, int64_t* n);

@@ -7,6 +7,8 @@ code with the CUDA library and the product path never imports it.
 Follows the paper (arXiv:2501.05110) step by step:
 
 * advection matrices beta^alpha, reaction matrix R (Sec. 2.2, Eq. definitions-advection-reaction-eq);
+* the local Lax--Friedrichs flux J = 1/2 beta (f_lo + f_hi) + 1/2 alpha (f_lo - f_hi) as the
+  alternative the paper names (Sec. 3.2), selected by a problem's ``flux``;
 * broken tensor-product Lagrange space Q^k, equidistant nodes for k <= 2 and Gauss--Lobatto nodes
   for k > 2 (Sec. 3.1);
 * weak form after integration by parts (Eq. advection-term-by-parts, Eq.
@@ -207,9 +209,16 @@ def reaction_minus_div(prob, T, st, terms):
     return R - div
 
 
-def upwind_split(beta):
-    """beta_+ = W L+ W^T and beta_- = W L- W^T for stacked symmetric matrices (P, n, n)."""
+def upwind_split(beta, flux="upwind"):
+    """The face flux J = K_+ f_lo + K_- f_hi for stacked symmetric matrices beta (P, n, n):
+    upwind (Eq. definition-upwind-flux): K_+- = W L+- W^T, the positive / negative eigen-parts;
+    local Lax--Friedrichs (Sec. 3.2): K_+- = (beta +- alpha 1) / 2 with alpha the largest |eigenvalue|
+    at the point, i.e. J = 1/2 beta (f_lo + f_hi) + 1/2 alpha (f_lo - f_hi)."""
     lam, W = np.linalg.eigh(beta)
+    if flux == "llf":
+        alpha = np.abs(lam).max(axis=1)
+        eye = np.eye(beta.shape[1])[None]
+        return 0.5 * (beta + alpha[:, None, None] * eye), 0.5 * (beta - alpha[:, None, None] * eye)
     lp = np.where(lam > 0, lam, 0.0)
     lm = np.where(lam < 0, lam, 0.0)
     bp = np.einsum("pij,pj,pkj->pik", W, lp, W)
@@ -390,7 +399,7 @@ class Discretisation:
             Wf = np.prod(self.wg[fidx], axis=1)[None, :] * np.prod(h[:, tang], axis=1)[:, None] if tang else np.ones((nt, 1))
             st = _point_state(prob, coords.reshape(-1, D))
             beta = advection_matrix(prob, T, m.axes[ax], st, self.terms)
-            bp, bm = upwind_split(beta)
+            bp, bm = upwind_split(beta, getattr(prob, "flux", "upwind"))
             beta = beta.reshape(nt, nfq, n, n)
             bp = bp.reshape(beta.shape)
             bm = bm.reshape(beta.shape)

@@ -402,7 +402,14 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
           const T* c1 = c0 + NFP;
           T* Ys = (s ? Y1 : Y0) + roff + r * NFP;
 #pragma unroll
-          for (int fp = 0; fp < NF; ++fp) Ys[fp] = fabs(c0[fp] + lr * c1[fp]) * tmp[fp];
+          if (A.llf) {  // alpha = max over the eigenvalues of |c0 + lam c1|, at an extreme eigenvalue
+#pragma unroll
+            for (int fp = 0; fp < NF; ++fp)
+              Ys[fp] = fmax(fabs(c0[fp] + T(A.lam_lo) * c1[fp]), fabs(c0[fp] + T(A.lam_hi) * c1[fp])) * tmp[fp];
+          } else {
+#pragma unroll
+            for (int fp = 0; fp < NF; ++fp) Ys[fp] = fabs(c0[fp] + lr * c1[fp]) * tmp[fp];
+          }
         }
       }
       __syncthreads();

@@ -259,7 +259,8 @@ __device__ __forceinline__ void apply_body(const OpParams<T>& P, const T* __rest
         Jf[w] = T(0.5) * acc;
         const T c0 = CF[(f * MAXADV + 0) * nfp + fp];
         const T c1 = CF[(f * MAXADV + 1) * nfp + fp];
-        W1[w] = fabs(c0 + P.lam[rr] * c1) * csr_row(P.bank, A.WTmat, rr, Db, nfp);
+        const T ab = A.llf ? fmax(fabs(c0 + T(A.lam_lo) * c1), fabs(c0 + T(A.lam_hi) * c1)) : fabs(c0 + P.lam[rr] * c1);
+        W1[w] = ab * csr_row(P.bank, A.WTmat, rr, Db, nfp);
       }
     }
   }
@@ -485,7 +486,8 @@ __device__ __forceinline__ void applyT_body(const OpParams<T>& P, const T* __res
         Jf[w] = T(0.5) * acc;
         const T c0 = CF[(f * MAXADV + 0) * nfp + fp];
         const T c1 = CF[(f * MAXADV + 1) * nfp + fp];
-        W1[w] = sgn * fabs(c0 + P.lam[rr] * c1) * csr_row(P.bank, A.WTmat, rr, Gb, nfp);
+        const T ab = A.llf ? fmax(fabs(c0 + T(A.lam_lo) * c1), fabs(c0 + T(A.lam_hi) * c1)) : fabs(c0 + P.lam[rr] * c1);
+        W1[w] = sgn * ab * csr_row(P.bank, A.WTmat, rr, Gb, nfp);
       }
     }
   }

@@ -42,6 +42,8 @@ struct AxisInfo {
   int absmat;                 // ABS_CONST: |beta| matrix id; ABS_POINT: pattern matrix id
   int Wmat, WTmat;            // ABS_EIGEN: eigenvectors W and W^T (bank ids)
   // ABS_EIGEN: beta = c0 I + c1 A with c0 = adv[0] coefficient, c1 = adv[1] coefficient at the face
+  int llf;                    // local Lax--Friedrichs flux: |beta| replaced by alpha I, alpha = max |eig|
+  double lam_lo, lam_hi;      // smallest and largest eigenvalue of A^a (alpha of the eigen route)
 };
 
 // Device-side CSR bank of n x n matrices (rowptr per matrix: n+1 entries at rp_off[m]).
@@ -226,6 +228,7 @@ struct sap_ctx {
   };
   std::vector<CnGraph> cn_graphs;
   cudaStream_t cap_stream = nullptr;           // private stream for the captures
+  int flux = SAP_FLUX_UPWIND;                  // numerical flux of the faces (sap_set_flux)
   // batched CN: per-instance GMRES control blocks, masks and status (device, pinned mirror) and the
   // CUDA graphs of a step and of a continuation cycle
   void* bctl = nullptr;

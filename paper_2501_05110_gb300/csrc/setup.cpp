@@ -785,6 +785,11 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
       Mat Wx;
       std::vector<double> lam;
       sym_eig_blocks(Tb.A[0], c->Ablocks, Wx, lam);
+      for (int a = 0; a < c->D; ++a) {
+        ax[a].llf = c->flux == SAP_FLUX_LLF;
+        ax[a].lam_lo = *std::min_element(lam.begin(), lam.end());
+        ax[a].lam_hi = *std::max_element(lam.begin(), lam.end());
+      }
       Mat Wa[3];
       Wa[0] = Wx;
       Wa[1] = matmul(transpose(Tb.Uz), Wx);
@@ -818,12 +823,16 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
             double bmax = 0.0;
             for (int k = 0; k < n; ++k) bmax = std::max(bmax, std::fabs(uface_u[a] + lam[k] * d.V));
             Mat Ab(n);
-            for (int i = 0; i < n; ++i)
-              for (int j = 0; j < n; ++j) {
-                double s = 0.0;
-                for (int k = 0; k < n; ++k) s += Wa[a](i, k) * std::fabs(uface_u[a] + lam[k] * d.V) * Wa[a](j, k);
-                Ab(i, j) = std::fabs(s) <= 1e-14 * bmax ? 0.0 : s;
-              }
+            if (c->flux == SAP_FLUX_LLF) {  // alpha I with alpha = the largest |eigenvalue|
+              for (int i = 0; i < n; ++i) Ab(i, i) = bmax;
+            } else {
+              for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                  double s = 0.0;
+                  for (int k = 0; k < n; ++k) s += Wa[a](i, k) * std::fabs(uface_u[a] + lam[k] * d.V) * Wa[a](j, k);
+                  Ab(i, j) = std::fabs(s) <= 1e-14 * bmax ? 0.0 : s;
+                }
+            }
             A.absmat = B.add("abs" + std::to_string(a), Ab);
             // eigenvectors also here: the adjoint differentiates |beta| with respect to U_a
             A.Wmat = B.add("W" + std::to_string(a), Wa[a]);
@@ -887,6 +896,7 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
           M.pslot = pslot;
           M.nslot = nslot;
           const int nnzp = (int)M.pat.col.size();
+          const bool llf = c->flux == SAP_FLUX_LLF;
           pabs.assign((size_t)nslot * npface * nnzp, 0.0);
           parallel_for(nsv, [&](int sp, std::vector<double>& pv) {
             if (pslot[sp] < 0) return;
@@ -898,6 +908,13 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
                 for (int e = M.pat.rp[i]; e < M.pat.rp[i + 1]; ++e) bm(i, M.pat.col[e]) = pv[e];
               sym_eig_blocks(bm, M.blocks, Wb, lb);
               double* dst = &pabs[((size_t)pslot[sp] * npface + f) * nnzp];
+              if (llf) {  // alpha I on the pattern, alpha = the largest |eigenvalue| at the point
+                double alpha = 0.0;
+                for (int e = 0; e < n; ++e) alpha = std::max(alpha, std::fabs(lb[e]));
+                for (int i = 0; i < n; ++i)
+                  for (int k = M.pat.rp[i]; k < M.pat.rp[i + 1]; ++k) dst[k] = M.pat.col[k] == i ? alpha : 0.0;
+                continue;
+              }
               for (int i = 0; i < n; ++i)
                 for (int k = M.pat.rp[i]; k < M.pat.rp[i + 1]; ++k) {
                   const int j = M.pat.col[k];
@@ -1018,6 +1035,19 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
     }
     return SAP_OK;
   });
+}
+
+extern "C" sap_status sap_set_flux(sap_handle c, int flux) {
+  if (!c || (flux != SAP_FLUX_UPWIND && flux != SAP_FLUX_LLF)) return SAP_EINVAL;
+  if (!c->sub.empty()) {
+    c->err = "sap_set_flux: set the flux of a batch through its instance handles";
+    return SAP_EINVAL;
+  }
+  if (flux != c->flux) {
+    c->flux = flux;
+    c->fields_set = false;  // the face tables depend on the flux: the fields must be set again
+  }
+  return SAP_OK;
 }
 
 extern "C" sap_status sap_set_fields_device(sap_handle c, const double* U, const double* gradU, const double* DUDt,
@@ -1428,6 +1458,11 @@ extern "C" sap_status sap_adjoint_step(sap_handle c, int scheme, const double* z
     if (!c->fields_set) {
       c->err = "fields not set";
       return SAP_EINVAL;
+    }
+    if (c->flux != SAP_FLUX_UPWIND && grads &&
+        (grads->U || grads->gradU || grads->DUDt || grads->Bw || grads->Uface[0] || grads->Uface[1] || grads->Uface[2])) {
+      c->err = "adjoint: field gradients of the local Lax--Friedrichs flux are not formed";
+      return SAP_EUNSUPPORTED;
     }
     const int need = scheme == SAP_SCHEME_CN ? restart + 4 : 8;
     if (!ensure_ws64(c, need)) {

@@ -19,13 +19,14 @@ AXIS = {"x": 0, "y": 1, "z": 2, "p": 3, "lnp": 4}
 BC = {"periodic": 0, "inflow0": 1, "continuous": 2}
 TERM = {"adv": 1, "mom": 2, "rot": 4, "coll": 8, "src": 16}
 PREC = {"fp64": 0, "fp32": 1}
+FLUX = {"upwind": 0, "llf": 1}
 APPLY_D, APPLY_RHS, APPLY_T = 0, 1, 2
 PTS_SPATIAL, PTS_FACE_X, PTS_FACE_Y, PTS_FACE_Z, PTS_PHASE = range(5)
 
 SCHEME = {"erk4": 0, "cn": 1}
 EXPORTS = ["sap_create", "sap_create_batch", "sap_batch_instance", "sap_field_points", "sap_set_fields", "sap_num_dofs", "sap_apply_operator",
            "sap_step_erk", "sap_step_erk_noalloc", "sap_step_cn", "sap_adjoint_step_cn", "sap_adjoint_step_erk",
-           "sap_adjoint_step", "sap_step_theta", "sap_set_fields_device", "sap_probe_fma", "sap_apply_cost", "sap_destroy", "sap_last_error", "sap_coupling_matrix"]
+           "sap_adjoint_step", "sap_step_theta", "sap_set_fields_device", "sap_set_flux", "sap_probe_fma", "sap_apply_cost", "sap_destroy", "sap_last_error", "sap_coupling_matrix"]
 # field arrays of sap_set_fields / gradient arrays of sap_adjoint_step, in struct order
 FIELDS = ("U", "gradU", "DUDt", "Bw", "Uface0", "Uface1", "Uface2", "nu", "s000")
 
@@ -70,6 +71,7 @@ def load_library(path: str = LIB_PATH):
     lib.sap_field_points.argtypes = [vp, C.c_int, dp, i64p]
     lib.sap_set_fields.argtypes = [vp, dp, dp, dp, dp, C.POINTER(dp), dp, dp]
     lib.sap_set_fields_device.argtypes = [vp, vp, vp, vp, vp, C.POINTER(vp), vp, vp, vp]
+    lib.sap_set_flux.argtypes = [vp, C.c_int]
     lib.sap_num_dofs.argtypes = [vp, i64p]
     lib.sap_apply_operator.argtypes = [vp, vp, vp, C.c_int, vp]
     lib.sap_step_erk.argtypes = [vp, vp, C.c_double, C.c_int, vp]
@@ -164,6 +166,8 @@ class Solver:
         n = C.c_int64()
         self._check(self.lib.sap_num_dofs(self.h, C.byref(n)))
         self.N = n.value
+        if getattr(prob, "flux", "upwind") != "upwind":
+            self._check(self.lib.sap_set_flux(self.h, FLUX[prob.flux]))
         self.set_fields(prob)
 
     # -- helpers -------------------------------------------------------------------------------

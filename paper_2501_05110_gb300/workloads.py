@@ -48,6 +48,7 @@ class Problem:
     scheme: str = "erk4"                 # "erk4" | "cn"
     gmres_tol: float = 1e-10
     gmres_restart: int = 30
+    flux: str = "upwind"                 # "upwind" (Eq. definition-upwind-flux) | "llf" (local Lax--Friedrichs)
 
     @property
     def n(self) -> int:
@@ -212,6 +213,92 @@ def box3d(ncells=48, k=2, lmax=5, nu=0.5, L=20.0, V=1.0, dt=0.01, nsteps=200, se
         U=_const3([0, 0, 0]), gradU=_zero33, DUDt=_const3([0, 0, 0]),
         omega=_const3([c45, c45, 0.0]), V=V, nu=_scalar(nu), s000=_scalar(0.0),
         f0=_iso_f0(f000, n), dt=dt, nsteps=nsteps, scheme="erk4")
+
+
+# ------------------------------------------------------------------------------------------------
+# advection in a constant magnetic field (gyration), ERK4
+# ------------------------------------------------------------------------------------------------
+def gyro_advection(ncells=64, k=3, lmax=3, U0=0.1, L=20.0, gamma=2.0, B0=2.0 * math.pi, sigma=1.5, dt=0.02,
+                   nsteps=10000):
+    """Monoenergetic particles in a constant field B = B0 e_z without scattering, in a periodic
+    (x, y) box of side L moving with U = (U0, U0, 0) (U0 = 0: static plasma); f_000 = Gaussian of
+    width sigma, other coefficients zero (Sec. 4.2 set-up).  omega = B0 / gamma, V = sqrt(1 - 1/gamma^2);
+    the distribution returns to its initial state after N gyro-periods when L = N U0 T_g."""
+    n = (lmax + 1) ** 2
+    omega = B0 / gamma
+    V = math.sqrt(1.0 - 1.0 / gamma ** 2)
+    e = np.linspace(-L / 2, L / 2, ncells + 1)
+    return Problem(
+        name=f"gyro_{ncells}c_k{k}_l{lmax}_U{U0}",
+        axes=("x", "y"), edges=[e, e.copy()], k=k, lmax=lmax,
+        bc=[("periodic", "periodic")] * 2, terms=frozenset({"adv", "rot"}),
+        U=_const3([U0, U0, 0]), gradU=_zero33, DUDt=_const3([0, 0, 0]),
+        omega=_const3([0, 0, omega]), V=V, nu=_scalar(0.0), s000=_scalar(0.0),
+        f0=_iso_f0(lambda c: np.exp(-(c[:, 0] ** 2 + c[:, 1] ** 2) / (2 * sigma ** 2)), n),
+        dt=dt, nsteps=nsteps, scheme="erk4")
+
+
+# ------------------------------------------------------------------------------------------------
+# closure: free streaming of an initially isotropic Gaussian, ERK4
+# ------------------------------------------------------------------------------------------------
+def closure(ncells=256, k=2, lmax=11, nu=0.0, gamma=2.0, sigma=1.0, xr=(-15.0, 15.0), dt=None, nsteps=None):
+    """Monoenergetic particles streaming along x with scattering rate nu (Sec. 4.3 set-up): 1-D,
+    terms spatial advection and collision, f_000(x, 0) = sqrt(2)/sigma exp(-x^2/(2 sigma^2)) (the
+    Y_000 projection of an isotropic Gaussian of unit mass), zero-inflow boundaries far from the
+    particles; dt = 1/(100 sqrt(3)) and t_F = 12/sqrt(3) by default."""
+    n = (lmax + 1) ** 2
+    V = math.sqrt(1.0 - 1.0 / gamma ** 2)
+    dt = 1.0 / (100.0 * math.sqrt(3.0)) if dt is None else dt
+    nsteps = int(round((12.0 / math.sqrt(3.0)) / dt)) if nsteps is None else nsteps
+    return Problem(
+        name=f"closure_{ncells}c_k{k}_l{lmax}_nu{nu}",
+        axes=("x",), edges=[np.linspace(xr[0], xr[1], ncells + 1)], k=k, lmax=lmax,
+        bc=[("inflow0", "inflow0")], terms=frozenset({"adv", "coll"}),
+        U=_const3([0, 0, 0]), gradU=_zero33, DUDt=_const3([0, 0, 0]),
+        omega=_const3([0, 0, 0]), V=V, nu=_scalar(nu), s000=_scalar(0.0),
+        f0=_iso_f0(lambda c: math.sqrt(2.0) / sigma * np.exp(-c[:, 0] ** 2 / (2 * sigma ** 2)), n),
+        dt=dt, nsteps=nsteps, scheme="erk4")
+
+
+# ------------------------------------------------------------------------------------------------
+# diffusive shock acceleration at a parallel shock (the paper's production set-up)
+# ------------------------------------------------------------------------------------------------
+def dsa_x_edges(Ls=1.0 / 25.0, dx_shock=0.01, growth=0.01, xmax=280.0):
+    """Cells of width dx_shock across the shock region [-Ls, Ls], then widths sinh(growth i),
+    i = 1, 2, ..., on both sides until |x| = xmax (the last cell ends at xmax)."""
+    inner = np.linspace(-Ls, Ls, int(round(2 * Ls / dx_shock)) + 1)
+    right = [Ls]
+    i = 1
+    while right[-1] < xmax:
+        right.append(min(right[-1] + math.sinh(growth * i), xmax))
+        i += 1
+    if right[-1] - right[-2] < 0.5 * math.sinh(growth * (i - 2)):  # merge a sliver into its neighbour
+        del right[-2]
+    right = np.array(right[1:])
+    return np.concatenate([-right[::-1], inner, right])
+
+
+def dsa_shock(npc=256, k=1, p0=2.0, Q=0.1, dt=1.0, nsteps=500000):
+    """Diffusive shock acceleration (Sec. 4.4, Tab. of simulation parameters): l_max = 1, U1 = 1/60,
+    r = 4, L_s = 1/25, nu = 1, B0 = 1, injection at x0 = 0 and p0 = 2 with widths 1/8 in x and in p,
+    domain [-280, 280] x [ln 0.1, ln 100] with 256 ln p cells, graded x-cells (dsa_x_edges), CN with
+    dt = 1.  The paper injects Q particles per unit time at p0 (per unit p); the shock workload's
+    source is a Gaussian per unit ln p, so it carries Q / p0 with width (1/8) / p0 in ln p."""
+    return shock(x_edges=dsa_x_edges(), npc=npc, k=k, lmax=1, U1=1.0 / 60.0, r=4.0, Ls=1.0 / 25.0,
+                 lnpr=(math.log(0.1), math.log(100.0)), nu_field=lambda xs, p: np.ones(xs.shape[0]),
+                 Q=Q / p0, x0=0.0, lnp0=math.log(p0), sig_x=0.125, sig_lnp=0.125 / p0, B0=1.0, dt=dt,
+                 nsteps=nsteps, name="dsa_shock")
+
+
+def dsa_phi(t, c1=78909.74, sd=48859.1):
+    """Approximate time dependence of the spectrum at the shock, phi(t) = int_0^t zeta (Sec. 4.4,
+    Eq. cumulative-temporal-distribution), with the mean c1 and standard deviation of the
+    acceleration time the paper gives for p = 59.9."""
+    from math import erfc, exp, sqrt
+    c2 = sd * sd
+    a = sqrt(c1 ** 3 / (2.0 * t * c2))
+    b = sqrt(c1 * t / (2.0 * c2))
+    return 0.5 * (exp(2.0 * c1 * c1 / c2) * erfc(a + b) + erfc(a - b))
 
 
 # ------------------------------------------------------------------------------------------------

@@ -613,3 +613,55 @@ def test_c_driver_cn_matches_lu():
         zp, k = steppers.gmres(A, B @ zp + d.h, zp, tol=1e-12)
         its_py += k
     assert abs(its - its_py) <= 4, (its, its_py)
+
+
+# ----------------------------------------------------------------------------------------------
+# local Lax--Friedrichs flux (the alternative numerical flux of Sec. 3.2)
+# ----------------------------------------------------------------------------------------------
+def _with_flux(prob, flux):
+    import dataclasses
+    return dataclasses.replace(prob, flux=flux)
+
+
+def test_llf_equals_upwind_for_scalar_advection():
+    """l_max = 0: beta = U is a scalar, alpha = |U|, so the two fluxes coincide."""
+    for prob in (W.periodic_1d(ncells=6, k=2, lmax=0, U=0.3), W.shock(nx=5, npc=3, lmax=0, xr=(-2.0, 2.0), lnpr=(0.0, 2.0))):
+        Du = dg.Discretisation(prob).D
+        Dl = dg.Discretisation(_with_flux(prob, "llf")).D
+        assert abs(Du - Dl).max() < 1e-14 * abs(Du).max()
+
+
+def test_llf_adds_dissipation_and_conserves():
+    """alpha 1 - |beta| is positive semi-definite at every face point, so x^T (D_llf - D_up) x >= 0
+    (LLF is at least as dissipative); both fluxes telescope, so particle number is conserved on a
+    periodic mesh; and the two operators differ for l_max >= 1."""
+    prob = W.periodic_1d(ncells=8, k=2, lmax=3)
+    du, dl = dg.Discretisation(prob), dg.Discretisation(_with_flux(prob, "llf"))
+    rng = np.random.default_rng(12)
+    diff = (dl.D - du.D).toarray()
+    for _ in range(20):
+        x = rng.standard_normal(du.N)
+        assert x @ diff @ x >= -1e-12 * np.abs(diff).max() * (x @ x)
+    assert np.abs(diff).max() > 1e-3
+    w = np.zeros(dl.N)
+    n, nloc = dl.n, dl.mesh.nloc
+    for c in range(dl.mesh.ncell):
+        w[dl.dof(c, 0, 0): dl.dof(c, 0, 0) + nloc] = 1.0
+    Mw = dl.M.T @ w
+    colsum = dl.D.T @ w  # sum over the f_000 test functions of every column
+    assert np.abs(colsum).max() < 1e-12 * np.abs(dl.D).max(), np.abs(colsum).max()
+    assert Mw.any()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_llf_convergence_study_space(k):
+    """With the LLF flux the error of the Sec. 4.1 problem against its closed form still falls as
+    Delta x^(k+1)."""
+    errs = []
+    ncs = (8, 16, 32)
+    for nc in ncs:
+        prob, ex = _convergence_problem(nc, k)
+        disc = dg.Discretisation(_with_flux(prob, "llf"))
+        z = steppers.rk4(disc.M, disc.D, disc.h, dg.project_initial(disc, prob.f0), 0.005, 200)
+        errs.append(_rel_l2_000(disc, z, ex, 1.0, k, nc))
+    assert convergence_order(ncs, errs) > k + 1 - 0.3, errs
