@@ -199,7 +199,11 @@ __host__ __device__ inline int rows_smem_elems(const OpParams<T>& P, int C) {
   return C * n * S::NLP + freg + C * nvt * S::NLP + C * 2 * D * nadvmax * S::NFP;
 }
 
-template <typename T, int D, int Q>
+// TRANS = false: y = L x.  TRANS = true: y = L^T x, the transpose of the nodal operator, term by term:
+// transposed couplings; volume -(1/h) beta^a (S^T x along the axis); faces g = (lift-weighted traces
+// of x from both cells, each with its own 1/h), then beta+ g distributed to the lower cell (its upper
+// face) and beta- g to the upper cell, beta+- = (beta +- |beta|)/2 (beta at a continuous boundary).
+template <typename T, int D, int Q, bool TRANS>
 __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restrict__ x, const Epi<T>& E, int C,
                                           int cell0, int64_t doff, unsigned char* smem_raw) {
   using S = Shape<T, D, Q>;
@@ -311,8 +315,49 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
   if (valid) {
     for (int t = 0; t < P.nreact; ++t) {
       if ((P.react_zero >> t) & 1u) continue;  // identically zero coefficient
-      term_apply<T, NL, NLP>(P.bank, P.react[t].mat, (P.react_uni >> t) & 1u, CVc + t * NLP, r, n, Fc, acc);
+      term_apply<T, NL, NLP>(P.bank, TRANS ? P.react[t].matT : P.react[t].mat, (P.react_uni >> t) & 1u, CVc + t * NLP,
+                             r, n, Fc, acc);
     }
+  }
+  if constexpr (TRANS) {
+    // volume: z = S^T x along the axis for every row (shared memory), then -(1/h) sum_t c_t K_t^T z
+    static_for<0, D>([&](auto ac) {
+      constexpr int a = decltype(ac)::value;
+      const AxisInfo& A = P.ax[a];
+      if (!A.active) return;  // uniform over the block
+      constexpr int qa = ipow(Q, a);
+      T* Z = FR;  // [C][n][NLP], free until the faces
+      if (valid) {
+        T z[NLP];
+#pragma unroll
+        for (int i = 0; i < NLP; ++i) z[i] = T(0);
+#pragma unroll
+        for (int i = 0; i < NL; ++i) {
+          const int ia = (i / qa) % Q;
+          const int b = i - ia * qa;
+#pragma unroll
+          for (int qq = 0; qq < Q; ++qq) z[i] += P.S[qq][ia] * Fc[r * NLP + b + qq * qa];
+        }
+#pragma unroll
+        for (int i = 0; i < NLP; ++i) Z[(lc * n + r) * NLP + i] = z[i];
+      }
+      __syncthreads();
+      if (valid) {
+        T g[NL];
+#pragma unroll
+        for (int i = 0; i < NL; ++i) g[i] = T(0);
+        for (int t = 0; t < A.nadv; ++t) {
+          if ((P.adv_zero[a] >> t) & 1u) continue;
+          term_apply<T, NL, NLP>(P.bank, A.adv[t].matT, (P.adv_uni[a] >> t) & 1u, CVc + (adv_off[a] + t) * NLP, r, n,
+                                 Z + lc * n * NLP, g);
+        }
+        const T invh = __ldg(P.cell_invh + cell * D + a);
+#pragma unroll
+        for (int i = 0; i < NL; ++i) acc[i] -= invh * g[i];
+      }
+      __syncthreads();  // Z is reused by the next axis and the faces
+    });
+  } else if (valid) {
     static_for<0, D>([&](auto ac) {
       constexpr int a = decltype(ac)::value;
       const AxisInfo& A = P.ax[a];
@@ -372,19 +417,40 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
         // a missing neighbour (boundary) reads the own cell and the value is replaced below
         const T* xl = x + (size_t)(nbl >= 0 ? nbl : c2) * per_cell + c * NL;
         const T* xh = x + (size_t)(nbh >= 0 ? nbh : c2) * per_cell + c * NL;
-        T tl = T(0), th = T(0);
+        if constexpr (TRANS) {
+          // g = lift-weighted traces of both cells at the face, each with its own 1/h:
+          // lower face g = (1/h_lo) L1^T x_lo - (1/h) L0^T x, upper face g = (1/h) L1^T x - (1/h_hi) L0^T x_hi
+          T ol = T(0), oh = T(0), gl = T(0), gh = T(0);
 #pragma unroll
-        for (int j = 0; j < Q; ++j) {
-          tl += P.B1[j] * __ldg(xl + node_of<Q>(fp, j, a));
-          th += P.B0[j] * __ldg(xh + node_of<Q>(fp, j, a));
+          for (int j = 0; j < Q; ++j) {
+            const T v = own[node_of<Q>(fp, j, a)];
+            ol += P.L0[j] * v;
+            oh += P.L1[j] * v;
+            gl += P.L1[j] * __ldg(xl + node_of<Q>(fp, j, a));
+            gh += P.L0[j] * __ldg(xh + node_of<Q>(fp, j, a));
+          }
+          const T ih = __ldg(P.cell_invh + c2 * D + a);
+          const T ihl = nbl >= 0 ? __ldg(P.cell_invh + nbl * D + a) : T(0);  // a missing side adds nothing
+          const T ihh = nbh >= 0 ? __ldg(P.cell_invh + nbh * D + a) : T(0);
+          S0[R * NFP + fp] = ihl * gl - ih * ol;
+          S1[R * NFP + fp] = ih * oh - ihh * gh;
+          (void)tr0;
+          (void)tr1;
+        } else {
+          T tl = T(0), th = T(0);
+#pragma unroll
+          for (int j = 0; j < Q; ++j) {
+            tl += P.B1[j] * __ldg(xl + node_of<Q>(fp, j, a));
+            th += P.B0[j] * __ldg(xh + node_of<Q>(fp, j, a));
+          }
+          if (nbl < 0) tl = A.bc_lo == SAP_BC_CONTINUOUS ? tr0 : T(0);
+          if (nbh < 0) th = A.bc_hi == SAP_BC_CONTINUOUS ? tr1 : T(0);
+          // lower face: f_lo = lower neighbour, f_hi = own; upper face: f_lo = own, f_hi = upper neighbour
+          S0[R * NFP + fp] = tl + tr0;
+          D0[R * NFP + fp] = tl - tr0;
+          S1[R * NFP + fp] = tr1 + th;
+          D1[R * NFP + fp] = tr1 - th;
         }
-        if (nbl < 0) tl = A.bc_lo == SAP_BC_CONTINUOUS ? tr0 : T(0);
-        if (nbh < 0) th = A.bc_hi == SAP_BC_CONTINUOUS ? tr1 : T(0);
-        // lower face: f_lo = lower neighbour, f_hi = own; upper face: f_lo = own, f_hi = upper neighbour
-        S0[R * NFP + fp] = tl + tr0;
-        D0[R * NFP + fp] = tl - tr0;
-        S1[R * NFP + fp] = tr1 + th;
-        D1[R * NFP + fp] = tr1 - th;
       }
     }
     __syncthreads();
@@ -397,11 +463,10 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
           T tmp[NF];
 #pragma unroll
           for (int fp = 0; fp < NF; ++fp) tmp[fp] = T(0);
-          ell_apply<T, NF, NFP>(P.bank, A.WTmat, r, n, (s ? D1 : D0) + roff, tmp);
+          ell_apply<T, NF, NFP>(P.bank, A.WTmat, r, n, (TRANS ? (s ? S1 : S0) : (s ? D1 : D0)) + roff, tmp);
           const T* c0 = CF + ((lc * NFACE + 2 * a + s) * nadvmax) * NFP;
           const T* c1 = c0 + NFP;
           T* Ys = (s ? Y1 : Y0) + roff + r * NFP;
-#pragma unroll
           if (A.llf) {  // alpha = max over the eigenvalues of |c0 + lam c1|, at an extreme eigenvalue
 #pragma unroll
             for (int fp = 0; fp < NF; ++fp)
@@ -420,7 +485,7 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
       for (int s = 0; s < 2; ++s) {
         const int f = 2 * a + s;
         const T* Ss = (s ? S1 : S0) + roff;
-        const T* Ds = (s ? D1 : D0) + roff;
+        const T* Ds = TRANS ? Ss : (s ? D1 : D0) + roff;  // the transpose applies |beta| to g as well
         T J[NF];
 #pragma unroll
         for (int fp = 0; fp < NF; ++fp) J[fp] = T(0);
@@ -429,11 +494,19 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
           T tmp[NF];
 #pragma unroll
           for (int fp = 0; fp < NF; ++fp) tmp[fp] = T(0);
-          ell_apply<T, NF, NFP>(P.bank, A.adv[t].mat, r, n, Ss, tmp);
+          ell_apply<T, NF, NFP>(P.bank, TRANS ? A.adv[t].matT : A.adv[t].mat, r, n, Ss, tmp);
           T cv[NFP];
           ldv<NFP>(CF + ((lc * NFACE + f) * nadvmax + t) * NFP, cv);
 #pragma unroll
           for (int fp = 0; fp < NF; ++fp) J[fp] += cv[fp] * tmp[fp];
+        }
+        T Jc[NF];  // the central part alone (the transpose at a continuous boundary uses all of beta)
+        if constexpr (TRANS) {
+#pragma unroll
+          for (int fp = 0; fp < NF; ++fp) {
+            Jc[fp] = J[fp];
+            J[fp] = T(0);
+          }
         }
         if (A.route == ABS_CONST) {
           ell_apply<T, NF, NFP>(P.bank, A.absmat, r, n, Ds, J);
@@ -462,11 +535,26 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
             }
           }
         }
-        // lift: lower face -L0[j] J, upper face +L1[j] J, times 1/h (the 1/2 of the flux folded in)
+        if constexpr (TRANS) {
+          // J = beta+ g (upper face) or beta- g (lower face), beta at a continuous boundary; the
+          // traces B distribute it into the nodes (the 1/h are inside g)
+          const int nb = __ldg(P.cell_nb + cell * NFACE + f);
+          const bool cont = nb < 0 && (s ? A.bc_hi : A.bc_lo) == SAP_BC_CONTINUOUS;
+          const T sg = s ? T(0.5) : T(-0.5);
 #pragma unroll
-        for (int fp = 0; fp < NF; ++fp)
+          for (int fp = 0; fp < NF; ++fp) {
+            const T jt = cont ? Jc[fp] : T(0.5) * Jc[fp] + sg * J[fp];
 #pragma unroll
-          for (int j = 0; j < Q; ++j) acc[node_of<Q>(fp, j, a)] += h2 * (s ? P.L1[j] : -P.L0[j]) * J[fp];
+            for (int j = 0; j < Q; ++j) acc[node_of<Q>(fp, j, a)] += (s ? P.B1[j] : P.B0[j]) * jt;
+          }
+        } else {
+          (void)Jc;
+          // lift: lower face -L0[j] J, upper face +L1[j] J, times 1/h (the 1/2 of the flux folded in)
+#pragma unroll
+          for (int fp = 0; fp < NF; ++fp)
+#pragma unroll
+            for (int j = 0; j < Q; ++j) acc[node_of<Q>(fp, j, a)] += h2 * (s ? P.L1[j] : -P.L0[j]) * J[fp];
+        }
       }
     }
     __syncthreads();  // the next axis (or P3) reuses the face buffers
@@ -494,11 +582,11 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
   }
 }
 
-template <typename T, int D, int Q>
+template <typename T, int D, int Q, bool TRANS>
 __global__ void __launch_bounds__(Shape<T, D, Q>::MAXT) rows_kernel(const __grid_constant__ OpParams<T> P,
                                                                    const T* __restrict__ x, const Epi<T> E, int C) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  rows_body<T, D, Q>(P, x, E, C, blockIdx.x * C, 0, smem_raw);
+  rows_body<T, D, Q, TRANS>(P, x, E, C, blockIdx.x * C, 0, smem_raw);
 }
 
 // Batched: block b works on instance blocks[b].x, cells [blocks[b].y, + cpb[inst]); the instance's
@@ -515,7 +603,7 @@ __global__ void __launch_bounds__(Shape<T, D, Q>::MAXT) rows_kernel_batched(
   int* dst = reinterpret_cast<int*>(pbuf);
   for (int k = threadIdx.x; k < (int)(sizeof(OpParams<T>) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
   __syncthreads();
-  rows_body<T, D, Q>(*reinterpret_cast<const OpParams<T>*>(pbuf), x, E, cpbs[bb.x], bb.y, doffs[bb.x], smem_raw);
+  rows_body<T, D, Q, false>(*reinterpret_cast<const OpParams<T>*>(pbuf), x, E, cpbs[bb.x], bb.y, doffs[bb.x], smem_raw);
 }
 
 constexpr size_t kRowsSmemMax = 160 * 1024;
@@ -530,10 +618,11 @@ void rows_config_shape(const OpParams<T>& P, int target, int* cells, size_t* sme
   *smem = (size_t)rows_smem_elems<T, D, Q>(P, C) * sizeof(T);
 }
 
-template <typename T, int D, int Q>
+template <typename T, int D, int Q, bool TRANS>
 cudaError_t launch_rows_shape(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s) {
   static DeviceMask opted{};
-  if (cudaError_t err = smem_opt_in(rows_kernel<T, D, Q>, (int)kRowsSmemMax, opted); err != cudaSuccess) return err;
+  if (cudaError_t err = smem_opt_in(rows_kernel<T, D, Q, TRANS>, (int)kRowsSmemMax, opted); err != cudaSuccess)
+    return err;
   int C;
   size_t smem;
   // threads per block measured best on GB300: FP64 rows need many registers (3-D: ~190), so
@@ -543,7 +632,7 @@ cudaError_t launch_rows_shape(const OpParams<T>& P, const T* x, const Epi<T>& e,
   rows_config_shape<T, D, Q>(P, target, &C, &smem);
   if (smem > kRowsSmemMax || C * P.n > Shape<T, D, Q>::MAXT) return cudaErrorInvalidConfiguration;
   const int blocks = (P.ncell + C - 1) / C;
-  rows_kernel<T, D, Q><<<blocks, C * P.n, smem, s>>>(P, x, e, C);
+  rows_kernel<T, D, Q, TRANS><<<blocks, C * P.n, smem, s>>>(P, x, e, C);
   note_launch();
   return cudaGetLastError();
 }
@@ -579,9 +668,17 @@ void rows_config(const OpParams<T>& P, int target, int* cells, size_t* smem) {
 
 template <typename T>
 cudaError_t launch_rows(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s) {
-  if (P.D == 1 && P.q == 3) return launch_rows_shape<T, 1, 3>(P, x, e, s);
-  if (P.D == 2 && P.q == 2) return launch_rows_shape<T, 2, 2>(P, x, e, s);
-  if (P.D == 3 && P.q == 3) return launch_rows_shape<T, 3, 3>(P, x, e, s);
+  if (P.D == 1 && P.q == 3) return launch_rows_shape<T, 1, 3, false>(P, x, e, s);
+  if (P.D == 2 && P.q == 2) return launch_rows_shape<T, 2, 2, false>(P, x, e, s);
+  if (P.D == 3 && P.q == 3) return launch_rows_shape<T, 3, 3, false>(P, x, e, s);
+  return cudaErrorInvalidConfiguration;
+}
+
+template <typename T>
+cudaError_t launch_rows_transposed(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s) {
+  if (P.D == 1 && P.q == 3) return launch_rows_shape<T, 1, 3, true>(P, x, e, s);
+  if (P.D == 2 && P.q == 2) return launch_rows_shape<T, 2, 2, true>(P, x, e, s);
+  if (P.D == 3 && P.q == 3) return launch_rows_shape<T, 3, 3, true>(P, x, e, s);
   return cudaErrorInvalidConfiguration;
 }
 
@@ -607,6 +704,10 @@ template void rows_config<double>(const OpParams<double>&, int, int*, size_t*);
 template void rows_config<float>(const OpParams<float>&, int, int*, size_t*);
 template cudaError_t launch_rows<double>(const OpParams<double>&, const double*, const Epi<double>&, cudaStream_t);
 template cudaError_t launch_rows<float>(const OpParams<float>&, const float*, const Epi<float>&, cudaStream_t);
+template cudaError_t launch_rows_transposed<double>(const OpParams<double>&, const double*, const Epi<double>&,
+                                                    cudaStream_t);
+template cudaError_t launch_rows_transposed<float>(const OpParams<float>&, const float*, const Epi<float>&,
+                                                   cudaStream_t);
 template cudaError_t launch_rows_batched<double>(const BatchDev<double>&, const int*, const double*,
                                                  const Epi<double>&, cudaStream_t);
 template cudaError_t launch_rows_batched<float>(const BatchDev<float>&, const int*, const float*, const Epi<float>&,

@@ -636,6 +636,7 @@ static cudaError_t launch_apply(const OpParams<T>& P, const T* x, const Epi<T>& 
 
 template <typename T>
 static cudaError_t launch_applyT(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s) {
+  if (rows_supported(P.D, P.q)) return launch_rows_transposed<T>(P, x, e, s);
   const int per = P.n * P.nloc;
   if (per > 1024) return cudaErrorInvalidConfiguration;
   const int cpb = apply_cells_per_block(P.n, P.nloc);

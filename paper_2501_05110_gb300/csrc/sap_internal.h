@@ -271,6 +271,8 @@ template <typename T>
 struct Epi;
 template <typename T>
 cudaError_t launch_rows(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rows_transposed(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s);
 // cells per block and dynamic shared memory (bytes) of the row kernel for a problem
 template <typename T>
 void rows_config(const OpParams<T>& P, int target_threads, int* cells, size_t* smem);
