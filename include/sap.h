@@ -70,6 +70,9 @@ enum { SAP_APPLY_D = 0,        /* y = M^-1 D x                       */
 enum { SAP_FLUX_UPWIND = 0,    /* J = W (L+ W^T f_lo + L- W^T f_hi)  (Eq. definition-upwind-flux)        */
        SAP_FLUX_LLF = 1 };     /* local Lax--Friedrichs: J = 1/2 beta (f_lo + f_hi) + 1/2 alpha (f_lo - f_hi),
                                   alpha = largest |eigenvalue| of n.beta at the face point                */
+/* operator-apply kernel choice (sap_set_apply_kernel) */
+enum { SAP_KERNEL_AUTO = 0,    /* the node kernel for uniform-coefficient 3-D k = 2 problems, else the row kernel */
+       SAP_KERNEL_ROWS = 1 };  /* always the row kernel (or the cell-node kernel for shapes it lacks)        */
 /* point sets reported by sap_field_points */
 enum { SAP_PTS_SPATIAL = 0,    /* spatial volume points (nsv x dim_x), fields U, gradU, DUDt, B   */
        SAP_PTS_FACE_X = 1,     /* spatial face points normal to x (nsf x dim_x), field U_x         */
@@ -159,6 +162,22 @@ sap_status sap_set_fields_device(sap_handle h, const double* U, const double* gr
  * differentiate the LLF flux (alpha is a maximum over eigenvalues) and returns SAP_EUNSUPPORTED for it.
  * Errors: SAP_EINVAL. */
 sap_status sap_set_flux(sap_handle h, int flux);
+
+/* Choose the kernel of the forward operator apply (y = M^-1 D x and the fused RK4 / CN forms; the
+ * transposed apply always runs the row kernel).  SAP_KERNEL_AUTO (the default) runs, for a spatial
+ * 3-D problem with k = 2 and l_max <= 5 whose every term coefficient is one number (uniform U, B and
+ * nu; constant upwind matrices), the node kernel: one thread per node with the combined coupling
+ * matrices R = sum_t c_t K_t, beta_a and |beta_a| applied as compiled sparse patterns (the operator of
+ * Eq. definition-mass-and-dg-matrix written as sums of Kronecker products).  Other problems run the
+ * row kernel.  SAP_KERNEL_ROWS forces the row kernel.  cells_per_block > 0 sets the node kernel's
+ * cells per block (clamped to 8 in FP32, 4 in FP64); 0 keeps the default (the largest).  Both kernels
+ * compute the same operator; results differ by the order of the sums.  Takes effect at the next apply
+ * or step (CUDA graphs captured before the call are captured again).  Errors: SAP_EINVAL (null
+ * handle, unknown kernel, negative cells, a batch handle). */
+sap_status sap_set_apply_kernel(sap_handle h, int kernel, int cells_per_block);
+/* The kernel the forward apply runs now: 1 the node kernel (uniform coefficients), 0 the row kernel
+ * or the cell-node kernel.  Errors: SAP_EINVAL (null handle or pointer, fields not set). */
+sap_status sap_apply_kernel_in_use(sap_handle h, int* uniform);
 
 /* Number of degrees of freedom N = ncells * n * (k+1)^D (Sec. 3.1). */
 sap_status sap_num_dofs(sap_handle h, int64_t* n);

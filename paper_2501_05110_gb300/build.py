@@ -15,7 +15,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libsapgpu.so")
-SOURCES = ["operator.cu", "apply_rows.cu", "adjoint_fields.cu", "probe.cu", "setup.cpp", "sh_tables.cpp"]
+SOURCES = ["operator.cu", "apply_rows.cu", "uniform.cu", "adjoint_fields.cu", "probe.cu", "setup.cpp", "sh_tables.cpp"]
+# l_max values the uniform-coefficient kernel is compiled for (patterns generated by gen_uniform)
+UNIFORM_LMAX = [1, 2, 3, 4, 5]
+PATTERNS = os.path.join(OUT, "uniform_patterns.inc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -28,7 +31,7 @@ def _nvcc():
 
 def _compile(src: str) -> str:
     obj = os.path.join(OUT, os.path.basename(src) + ".o")
-    cmd = [_nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+    cmd = [_nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I", OUT,
            "-x", "cu" if src.endswith(".cu") else "c++", "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ["--expt-relaxed-constexpr"]
@@ -38,16 +41,32 @@ def _compile(src: str) -> str:
     return obj
 
 
+def _generate_patterns() -> None:
+    """Compile and run the host generator of the uniform kernel's sparsity patterns."""
+    exe = os.path.join(OUT, "gen_uniform")
+    cmd = [_nvcc(), "-O2", "-std=c++17", "-x", "c++", os.path.join(CSRC, "gen_uniform.cpp"),
+           os.path.join(CSRC, "sh_tables.cpp"), "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"gen_uniform build failed:\n{r.stdout}\n{r.stderr}")
+    r = subprocess.run([exe, PATTERNS + ".tmp", *map(str, UNIFORM_LMAX)], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"gen_uniform failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(PATTERNS + ".tmp", PATTERNS)
+
+
 def build(force: bool = False) -> str:
     """Compile and link; returns the path of the shared library."""
     os.makedirs(OUT, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     deps = srcs + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))] + \
+        [os.path.join(CSRC, "gen_uniform.cpp")] + \
         [os.path.join(HERE, "..", "include", "sap.h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in deps):
             return LIB
+    _generate_patterns()
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(_compile, SOURCES))
     cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", LIB + ".tmp", *objs]

@@ -624,6 +624,7 @@ static cudaError_t launch_apply_shape(const OpParams<T>& P, const T* x, const Ep
 // shape runs the generic cell-node kernel.
 template <typename T>
 static cudaError_t launch_apply(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s) {
+  if (P.uni_L >= 0) return launch_uniform<T>(P, x, e, s);
   if (rows_supported(P.D, P.q)) return launch_rows<T>(P, x, e, s);
   const int per = P.n * P.nloc;
   if (per > 1024) return cudaErrorInvalidConfiguration;  // n (k+1)^D must fit one thread block

@@ -119,6 +119,12 @@ struct OpParams {
   // zero, such as U = 0): the apply kernels skip it
   unsigned react_zero;
   unsigned adv_zero[MAXD];
+  // uniform-coefficient kernel (uniform.cu): l_max of the compiled patterns it runs with, or -1;
+  // the packed values of R, beta_a, |beta_a| (host memory owned by the context); cells per block
+  // (0: the default)
+  int uni_L = -1;
+  const void* uni = nullptr;
+  int uni_cells = 0;
 };
 
 // Tables of the field-gradient kernels of the adjoint (adjoint_fields.cu): the spatial field
@@ -181,6 +187,11 @@ struct sap_ctx {
   std::vector<double> xg, wg;                  // Gauss rule on [0,1]
   std::vector<double> pnode, pface;            // momentum values
   std::vector<int> scell_face_h;               // [nscell][2dx]
+  int uni_avail = -1;                          // l_max of the node kernel's patterns if the problem fits, else -1
+  int apply_kernel = SAP_KERNEL_AUTO;          // sap_set_apply_kernel
+  int uni_cells = 0;
+  std::vector<double> uni_v64;                 // packed values of the uniform-coefficient kernel
+  std::vector<float> uni_v32;
   sap::OpParams<double> p64{};
   sap::OpParams<float> p32{};
   std::vector<sap::DevBuf> owned;              // device allocations
@@ -267,8 +278,23 @@ sap_status adjoint_erk_step(sap_ctx* c, const double* y, double* lambda, double 
 int apply_cells_per_block(int n, int nloc);
 // row-per-thread apply (apply_rows.cu) for the compiled shapes (D, q) = (1, 3), (2, 2), (3, 3)
 bool rows_supported(int D, int q);
+
+// Combined dense matrices (n x n, row major, FP64) of a problem whose term coefficients are all
+// uniform: R = sum of the reaction terms, B[a] = sum of the advection terms of axis a, A[a] = the
+// upwind matrix |beta_a| of axis a.
+struct UniDense {
+  int lmax = 0, n = 0;
+  std::vector<double> R, B[3], A[3];
+};
+bool uni_supported(int lmax);
+// the values at the compiled patterns' positions (R, B0..2, A0..2 in turn); false if l_max is not
+// compiled or a matrix has a nonzero outside its pattern
+bool uni_pack(const UniDense& u, std::vector<double>& vals);
+
 template <typename T>
 struct Epi;
+template <typename T>
+cudaError_t launch_uniform(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s);
 template <typename T>
 cudaError_t launch_rows(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s);
 template <typename T>

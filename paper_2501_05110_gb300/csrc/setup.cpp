@@ -124,6 +124,16 @@ static std::vector<float> to_f32(const std::vector<V>& v) {
   return std::vector<float>(v.begin(), v.end());
 }
 
+// The forward apply's kernel (sap_set_apply_kernel): the node kernel where the problem fits it and
+// it is not switched off, else the row kernel.
+static void apply_kernel_choice(sap_ctx* c) {
+  const bool uni = c->apply_kernel == SAP_KERNEL_AUTO && c->uni_avail >= 0;
+  c->p64.uni_L = c->p32.uni_L = uni ? c->uni_avail : -1;
+  c->p64.uni = uni ? static_cast<const void*>(c->uni_v64.data()) : nullptr;
+  c->p32.uni = uni ? static_cast<const void*>(c->uni_v32.data()) : nullptr;
+  c->p64.uni_cells = c->p32.uni_cells = c->uni_cells;
+}
+
 static void free_bufs(std::vector<DevBuf>& v) {
   for (auto& b : v) cudaFree(b.p);
   v.clear();
@@ -1026,6 +1036,61 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
       };
       fill(c->p64, double{});
       fill(c->p32, float{});
+      // the uniform-coefficient kernel: a spatial 3-D problem with k = 2 whose every term coefficient
+      // is one number and whose faces use the constant upwind matrix
+      c->uni_avail = -1;
+      c->uni_v64.clear();
+      c->uni_v32.clear();
+      if (c->D == 3 && c->dx == 3 && !has_mom && c->q == 3 && uni_supported(c->T.lmax)) {
+        const double p0 = c->pnode.empty() ? 1.0 : c->pnode[0];
+        auto coef = [&](const Term& tm) {
+          return tm.scale * (tm.sf == SF_ONE ? 1.0 : uval[tm.sf]) * mom_factor_h(tm.mf, p0, false, d.V) *
+                 (tm.nu ? nu_u : 1.0);
+        };
+        auto add_dense = [&](std::vector<double>& m, int mat, double cv) {
+          if (mat == MAT_I) {
+            for (int i = 0; i < n; ++i) m[(size_t)i * n + i] += cv;
+            return;
+          }
+          const HostCSR& h = B.mats[mat];
+          for (int i = 0; i < n; ++i)
+            for (int k = h.rp[i]; k < h.rp[i + 1]; ++k) m[(size_t)i * n + h.col[k]] += cv * h.val[k];
+        };
+        UniDense u;
+        u.lmax = c->T.lmax;
+        u.n = n;
+        u.R.assign((size_t)n * n, 0.0);
+        bool ok = nu_uni;
+        const OpParams<double>& P = c->p64;
+        for (int t = 0; t < P.nreact && ok; ++t) {
+          if ((P.react_zero >> t) & 1u) continue;
+          if (!((P.react_uni >> t) & 1u)) ok = false;
+          else add_dense(u.R, P.react[t].mat, coef(P.react[t]));
+        }
+        for (int a = 0; a < 3 && ok; ++a) {
+          u.B[a].assign((size_t)n * n, 0.0);
+          u.A[a].assign((size_t)n * n, 0.0);
+          const AxisInfo& A = P.ax[a];
+          if (!A.active) continue;
+          if (A.route != ABS_CONST || !uface_uni[a]) ok = false;
+          for (int t = 0; t < A.nadv && ok; ++t) {
+            const Term& tm = A.adv[t];
+            if ((P.adv_zero[a] >> t) & 1u) continue;
+            if (!((P.adv_uni[a] >> t) & 1u)) { ok = false; break; }
+            // the face coefficient of U_a is the face value: it must equal the node value
+            if (tm.sf == SF_U + a && uface_u[a] != uval[tm.sf]) { ok = false; break; }
+            add_dense(u.B[a], tm.mat, coef(tm));
+          }
+          if (ok) add_dense(u.A[a], A.absmat, 1.0);
+        }
+        std::vector<double> vals;
+        if (ok && uni_pack(u, vals)) {
+          c->uni_v64 = vals;
+          c->uni_v32 = to_f32(vals);
+          c->uni_avail = u.lmax;
+        }
+      }
+      apply_kernel_choice(c);
       c->fields_set = true;
       c->fields_version += 1;
       c->cn_prev_valid = false;
@@ -1047,6 +1112,29 @@ extern "C" sap_status sap_set_flux(sap_handle c, int flux) {
     c->flux = flux;
     c->fields_set = false;  // the face tables depend on the flux: the fields must be set again
   }
+  return SAP_OK;
+}
+
+extern "C" sap_status sap_set_apply_kernel(sap_handle c, int kernel, int cells_per_block) {
+  if (!c || (kernel != SAP_KERNEL_AUTO && kernel != SAP_KERNEL_ROWS) || cells_per_block < 0) return SAP_EINVAL;
+  if (!c->sub.empty()) {
+    c->err = "sap_set_apply_kernel: a batch runs the row kernel";
+    return SAP_EINVAL;
+  }
+  c->apply_kernel = kernel;
+  c->uni_cells = cells_per_block;
+  apply_kernel_choice(c);
+  c->fields_version += 1;  // graphs captured with the previous kernel are captured again
+  return SAP_OK;
+}
+
+extern "C" sap_status sap_apply_kernel_in_use(sap_handle c, int* uniform) {
+  if (!c || !uniform) return SAP_EINVAL;
+  if (!c->fields_set) {
+    c->err = "sap_apply_kernel_in_use: fields not set";
+    return SAP_EINVAL;
+  }
+  *uniform = c->p64.uni_L >= 0 ? 1 : 0;
   return SAP_OK;
 }
 

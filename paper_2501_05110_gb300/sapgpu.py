@@ -24,9 +24,11 @@ APPLY_D, APPLY_RHS, APPLY_T = 0, 1, 2
 PTS_SPATIAL, PTS_FACE_X, PTS_FACE_Y, PTS_FACE_Z, PTS_PHASE = range(5)
 
 SCHEME = {"erk4": 0, "cn": 1}
+KERNEL = {"auto": 0, "rows": 1}
 EXPORTS = ["sap_create", "sap_create_batch", "sap_batch_instance", "sap_field_points", "sap_set_fields", "sap_num_dofs", "sap_apply_operator",
            "sap_step_erk", "sap_step_erk_noalloc", "sap_step_cn", "sap_adjoint_step_cn", "sap_adjoint_step_erk",
-           "sap_adjoint_step", "sap_step_theta", "sap_set_fields_device", "sap_set_flux", "sap_probe_fma", "sap_apply_cost", "sap_destroy", "sap_last_error", "sap_coupling_matrix"]
+           "sap_adjoint_step", "sap_step_theta", "sap_set_fields_device", "sap_set_flux", "sap_probe_fma", "sap_apply_cost", "sap_destroy", "sap_last_error", "sap_coupling_matrix",
+           "sap_set_apply_kernel", "sap_apply_kernel_in_use"]
 # field arrays of sap_set_fields / gradient arrays of sap_adjoint_step, in struct order
 FIELDS = ("U", "gradU", "DUDt", "Bw", "Uface0", "Uface1", "Uface2", "nu", "s000")
 
@@ -72,6 +74,8 @@ def load_library(path: str = LIB_PATH):
     lib.sap_set_fields.argtypes = [vp, dp, dp, dp, dp, C.POINTER(dp), dp, dp]
     lib.sap_set_fields_device.argtypes = [vp, vp, vp, vp, vp, C.POINTER(vp), vp, vp, vp]
     lib.sap_set_flux.argtypes = [vp, C.c_int]
+    lib.sap_set_apply_kernel.argtypes = [vp, C.c_int, C.c_int]
+    lib.sap_apply_kernel_in_use.argtypes = [vp, C.POINTER(C.c_int)]
     lib.sap_num_dofs.argtypes = [vp, i64p]
     lib.sap_apply_operator.argtypes = [vp, vp, vp, C.c_int, vp]
     lib.sap_step_erk.argtypes = [vp, vp, C.c_double, C.c_int, vp]
@@ -315,6 +319,17 @@ class Solver:
                                               dt, tol, restart, maxit, C.byref(g), C.byref(st),
                                               _stream_handle(stream)))
         return st
+
+    def set_apply_kernel(self, kernel="auto", cells_per_block=0):
+        """Choose the forward apply's kernel: "auto" (the node kernel where the problem has uniform
+        coefficients, 3-D, k = 2, l_max <= 5) or "rows"."""
+        self._check(self.lib.sap_set_apply_kernel(self.h, KERNEL[kernel], int(cells_per_block)))
+
+    def apply_kernel_in_use(self):
+        """"node" or "rows" (the kernel the forward apply runs now)."""
+        u = C.c_int()
+        self._check(self.lib.sap_apply_kernel_in_use(self.h, C.byref(u)))
+        return "node" if u.value else "rows"
 
     def apply_cost(self):
         """(flops, bytes) of one operator apply, from the library's cost model."""
