@@ -121,9 +121,10 @@ def probe_alu(local):
     return res
 
 
-def apply_sha():
+def apply_sha(source="apply_rows.cu"):
+    """First 16 hex digits of the sha256 of the kernel source an ncu traffic figure was taken from."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2501_05110_gb300", "csrc", "apply_rows.cu"), "rb") as fh:
+    with open(os.path.join(ROOT, "paper_2501_05110_gb300", "csrc", source), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
@@ -333,7 +334,7 @@ def measure_shock(args, precision, world, rank, local, with_e2e=True):
     flops, abytes = sol.apply_cost()
     x = state.clone() if precision == "fp64" else state.float()
     t_apply = time_apply(torch, sol, x, args.apply_reps * 4)
-    traffic = APPLY_TRAFFIC.get(("shock", precision, apply_sha()))
+    traffic = APPLY_TRAFFIC.get(("shock", precision, apply_sha("apply_rows.cu")))
     out["roofline"] = roofline_entry(f"rows_kernel<{'double' if precision == 'fp64' else 'float'},2,2>", flops,
                                      abytes, t_apply, precision, traffic, units=f"{N} DoFs (one apply)")
     sol.close()
@@ -380,8 +381,15 @@ def measure_box3d(args, precision):
     x = (y if precision == "fp64" else y.float()).clone()
     del host, dev
     t_apply = time_apply(torch, sol, x, max(5, args.apply_reps // 5))
+    tname = "double" if precision == "fp64" else "float"
+    node = sol.apply_kernel_in_use() == "node"
+    kernel = f"uniform_kernel<{tname},5>" if node else f"rows_kernel<{tname},3,3>"
+    # the row kernel on the same state, for comparison
+    sol.set_apply_kernel("rows")
+    t_rows = time_apply(torch, sol, x, max(5, args.apply_reps // 5))
+    sol.set_apply_kernel("auto")
     stage_bytes = N * 5 * 8 if precision == "fp64" else N * (2 * 4 + 3 * 8)
-    traffic = APPLY_TRAFFIC.get(("box3d", precision, apply_sha()))
+    traffic = APPLY_TRAFFIC.get(("box3d", precision, apply_sha("uniform.cu" if node else "apply_rows.cu")))
     out = {"metric": "phase-space DoF-updates/s per ERK stage", "value": N * 4 * args.steps / t, "unit": UNIT,
            "ms_per_step": 1e3 * t / args.steps, "steps": args.steps, "warmup": args.warmup,
            "dtype": "f64" if precision == "fp64" else "f32 stage derivatives, f64 state",
@@ -390,8 +398,9 @@ def measure_box3d(args, precision):
            "stage_gbs": stage_bytes * 4 * args.steps / t / 1e9,
            "e2e": {"value": N * 4 * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": N * 8,
                    "d2h_bytes_per_step": N * 8},
-           "roofline": roofline_entry(f"rows_kernel<{'double' if precision == 'fp64' else 'float'},3,3>", flops, abytes,
-                                      t_apply, precision, traffic, units=f"{N} DoFs (one apply)"),
+           "roofline": roofline_entry(kernel, flops, abytes, t_apply, precision, traffic,
+                                      units=f"{N} DoFs (one apply)"),
+           "row_kernel_apply_us": 1e6 * t_rows,
            "clocks": clk, "gpu_launches": 4 * args.steps + (args.steps if precision == "fp32" else 0)}
     sol.close()
     return out

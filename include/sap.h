@@ -312,7 +312,9 @@ sap_status sap_step_erk_noalloc(sap_handle h, double* state, double dt, int nste
 
 /* Algorithmic cost of one sap_apply_operator call on this context: `flops` = floating-point
  * operations (an FMA counts 2) summed from the kernel's term tables (coefficient set-up, traces,
- * upwind fluxes, volume terms, lifts); `bytes` = 2 N w (read x, write y; w = word size of the
+ * upwind fluxes, volume terms, lifts; for the node kernel its own count from the compiled patterns:
+ * reaction, derivative along each axis, beta_a, lifts, traces, beta_a and |beta_a| at the faces) of the
+ * kernel the forward apply runs now (sap_apply_kernel_in_use); `bytes` = 2 N w (read x, write y; w = word size of the
  * context's precision).  Host-only.  Errors: SAP_EINVAL (fields not set). */
 sap_status sap_apply_cost(sap_handle h, double* flops, double* bytes);
 

@@ -8,7 +8,7 @@
 // own coupling tables (sh_tables.cpp, the same code the set-up runs) and writes, for every l_max
 // the kernel is built for, straight-line device functions in which every nonzero is one fused
 // multiply-add with register operands at compile-time indices and the value read from the kernel's
-// parameter block; plus host tables of the (row, column) pairs in the same order, which the set-up
+// parameter block, visiting the columns in turn (one input value live at a time); plus host tables of the (row, column) pairs in the same order, which the set-up
 // uses to pack the values and to check that a problem's matrices fit the patterns.
 //
 // Patterns: R = Om^x u Om^y u Om^z u diagonal; beta_a = A^a u diagonal; |beta_a| = the pattern of
@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sh_tables.h"
@@ -74,31 +75,46 @@ void emit_host_table(FILE* f, const char* name, const Pat& p) {
   std::fprintf(f, "};\n");
 }
 
-// acc[r] += v[k] * x[c] for every nonzero k (row-major order)
+// Column-major emission: the values v[k] keep the row-major order of the pattern (the packing
+// order), the code visits the columns in turn so that one column value is live at a time besides the
+// accumulators.  col(c) is a callable the kernel passes (it forms the column value from shared memory).
+std::vector<std::vector<std::pair<int, size_t>>> by_column(const Pat& p, int n) {
+  std::vector<std::vector<std::pair<int, size_t>>> cols(n);
+  for (size_t k = 0; k < p.r.size(); ++k) cols[p.c[k]].push_back({p.r[k], k});
+  return cols;
+}
+
+// acc[r] += v[k] * col(c) for every nonzero k
 void emit_matvec(FILE* f, const std::string& fname, const Pat& p, int n) {
   std::fprintf(f,
-               "  template <typename T>\n  static __device__ __forceinline__ void %s(const T* __restrict__ v, const T (&x)[%d], "
-               "T (&acc)[%d]) {\n",
-               fname.c_str(), n, n);
-  for (size_t k = 0; k < p.r.size(); ++k)
-    std::fprintf(f, "    acc[%d] = fma(v[%zu], x[%d], acc[%d]);\n", p.r[k], k, p.c[k], p.r[k]);
+               "  template <typename T, typename Col>\n  static __device__ __forceinline__ void %s(const T* __restrict__ v, "
+               "Col&& col, T (&acc)[%d]) {\n",
+               fname.c_str(), n);
+  const auto cols = by_column(p, n);
+  for (int c = 0; c < n; ++c) {
+    if (cols[c].empty()) continue;
+    std::fprintf(f, "    { const T xc = col(%d);", c);
+    for (auto& e : cols[c]) std::fprintf(f, " acc[%d] = fma(v[%zu], xc, acc[%d]);", e.first, e.second, e.first);
+    std::fprintf(f, " }\n");
+  }
   std::fprintf(f, "  }\n");
 }
 
-// out[r] = sum_k vb[k] S[c] + sum_k va[k] D[c], row by row
+// out[r] = sum_k vb[k] S[c] + sum_k va[k] D[c] with sd(c, S_c, D_c) forming column c's pair
 void emit_flux(FILE* f, const std::string& fname, const Pat& pb, const Pat& pa, int n) {
   std::fprintf(f,
-               "  template <typename T>\n  static __device__ __forceinline__ void %s(const T* __restrict__ vb, "
-               "const T* __restrict__ va, const T (&S)[%d], const T (&D)[%d], T* __restrict__ out) {\n",
-               fname.c_str(), n, n);
-  size_t kb = 0, ka = 0;
-  for (int r = 0; r < n; ++r) {
-    std::fprintf(f, "    { T j = T(0);");
-    for (; kb < pb.r.size() && pb.r[kb] == r; ++kb) std::fprintf(f, " j = fma(vb[%zu], S[%d], j);", kb, pb.c[kb]);
-    for (; ka < pa.r.size() && pa.r[ka] == r; ++ka) std::fprintf(f, " j = fma(va[%zu], D[%d], j);", ka, pa.c[ka]);
-    std::fprintf(f, " out[%d] = j; }\n", r);
+               "  template <typename T, typename SD>\n  static __device__ __forceinline__ void %s(const T* __restrict__ vb, "
+               "const T* __restrict__ va, SD&& sd, T* __restrict__ out) {\n    T J[%d];\n",
+               fname.c_str(), n);
+  std::fprintf(f, "#pragma unroll\n    for (int r = 0; r < %d; ++r) J[r] = T(0);\n", n);
+  const auto cb = by_column(pb, n), ca = by_column(pa, n);
+  for (int c = 0; c < n; ++c) {
+    std::fprintf(f, "    { T sc, dc; sd(%d, sc, dc);", c);
+    for (auto& e : cb[c]) std::fprintf(f, " J[%d] = fma(vb[%zu], sc, J[%d]);", e.first, e.second, e.first);
+    for (auto& e : ca[c]) std::fprintf(f, " J[%d] = fma(va[%zu], dc, J[%d]);", e.first, e.second, e.first);
+    std::fprintf(f, " }\n");
   }
-  std::fprintf(f, "  }\n");
+  std::fprintf(f, "#pragma unroll\n    for (int r = 0; r < %d; ++r) out[r] = J[r];\n  }\n", n);
 }
 
 }  // namespace

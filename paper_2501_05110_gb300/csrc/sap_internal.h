@@ -287,6 +287,8 @@ struct UniDense {
   std::vector<double> R, B[3], A[3];
 };
 bool uni_supported(int lmax);
+// floating-point operations of the node kernel per cell (axes with active[a] != 0)
+double uni_flops_per_cell(int lmax, const int* active);
 // the values at the compiled patterns' positions (R, B0..2, A0..2 in turn); false if l_max is not
 // compiled or a matrix has a nonzero outside its pattern
 bool uni_pack(const UniDense& u, std::vector<double>& vals);

@@ -1345,6 +1345,12 @@ extern "C" sap_status sap_apply_cost(sap_handle c, double* flops, double* bytes)
     }
     if (!c->fields_set) return SAP_EINVAL;
     const OpParams<double>& P = c->p64;
+    *bytes = 2.0 * (double)c->N * (c->prec == SAP_PREC_FP64 ? 8.0 : 4.0);
+    if (P.uni_L >= 0) {  // the node kernel: its own count
+      const int active[3] = {P.ax[0].active, P.ax[1].active, P.ax[2].active};
+      *flops = uni_flops_per_cell(P.uni_L, active) * c->ncell;
+      return SAP_OK;
+    }
     const int n = c->n, nloc = c->nloc, nfp = c->nfp, q = c->q, D = c->D;
     auto nnz_row_avg = [&](int mat) -> double {
       if (mat == MAT_I) return 1.0;
@@ -1377,7 +1383,6 @@ extern "C" sap_status sap_apply_cost(sap_handle c, double* flops, double* bytes)
     for (int t = 0; t < P.nreact; ++t) rx += 2.0 * nnz_row_avg(P.react[t].mat) + 2.0;
     per_cell += (rx + 4.0) * n * nloc;
     *flops = per_cell * c->ncell;
-    *bytes = 2.0 * (double)c->N * (c->prec == SAP_PREC_FP64 ? 8.0 : 4.0);
     return SAP_OK;
   });
 }

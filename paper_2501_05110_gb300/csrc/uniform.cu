@@ -10,9 +10,10 @@
 // nonzero of R, beta_a, |beta_a| is one FMA whose value comes from the parameter block (the
 // sparsity patterns are compiled in, see gen_uniform.cpp).  Phases of one block (C cells):
 //   1. stage the block's cells in shared memory (coalesced);
-//   2. upwind fluxes: 54 tasks per cell (3 axes x 2 faces x 9 face points), two per thread, each
-//      forming the traces of all n rows from its own cell (shared memory) and the neighbour (global),
-//      then J = beta_a (f_lo + f_hi) + |beta_a| (f_lo - f_hi) into shared memory;
+//   2. upwind fluxes: 54 tasks per cell (3 axes x 2 faces x 9 face points), one per axis for 18 of
+//      each cell's 27 threads, each forming the traces of the n rows from its own cell (shared memory)
+//      and the neighbour (global), then J = beta_a (f_lo + f_hi) + |beta_a| (f_lo - f_hi) into
+//      shared memory;
 //   3. per node: reaction R x; per axis the volume term -(1/h) beta_a (S x along the axis) and the
 //      lift of both faces' J; the fused epilogue (mass inverse is the nodal scaling already in L and S).
 // The result equals the row kernel's (apply_rows.cu) up to the order of the sums.
@@ -33,11 +34,11 @@ struct UniK;
 namespace {
 
 // threads per block at most (27 per cell) and blocks per SM the registers are sized for: FP32
-// 8 cells, FP64 4 cells, two blocks per SM
+// 8 cells, three blocks per SM; FP64 4 cells, four blocks per SM
 template <typename T>
 struct UniLaunch {
   static constexpr int max_threads = sizeof(T) == 8 ? 108 : 216;
-  static constexpr int min_blocks = 2;
+  static constexpr int min_blocks = sizeof(T) == 8 ? 4 : 3;
 };
 
 template <typename T, int L>
@@ -46,6 +47,7 @@ struct UniParams {
   T vR[K::nR];
   T vB0[K::nB0], vB1[K::nB1], vB2[K::nB2];
   T vA0[K::nA0], vA1[K::nA1], vA2[K::nA2];
+  T dR[K::n];  // diagonal of R (the point-Jacobi diagonal of the reaction part)
   T S[3][3], B0[3], B1[3], L0[3], L1[3];
   const int* cell_nb;  // [ncell][6]
   const T* cell_invh;  // [ncell][3]
@@ -97,9 +99,8 @@ __device__ __forceinline__ void flux_task(const UniParams<T, L>& P, const T* __r
   int nd[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) nd[q] = unode(fp, q, A);
-  T Sv[n], Dv[n];
-#pragma unroll
-  for (int c = 0; c < n; ++c) {
+  // column c of the flux: the traces of row c on both sides of the face
+  auto sd = [&](int c, T& sc, T& dc) {
     T uo = T(0), un = T(0);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -108,13 +109,13 @@ __device__ __forceinline__ void flux_task(const UniParams<T, L>& P, const T* __r
     }
     if (nb < 0) un = cont ? uo : T(0);
     const T flo = s ? uo : un, fhi = s ? un : uo;
-    Sv[c] = flo + fhi;
-    Dv[c] = flo - fhi;
-  }
+    sc = flo + fhi;
+    dc = flo - fhi;
+  };
   T* out = F + ((lc2 * 6 + 2 * A + s) * 9 + fp) * n;
-  if constexpr (A == 0) K::flux0(P.vB0, P.vA0, Sv, Dv, out);
-  else if constexpr (A == 1) K::flux1(P.vB1, P.vA1, Sv, Dv, out);
-  else K::flux2(P.vB2, P.vA2, Sv, Dv, out);
+  if constexpr (A == 0) K::flux0(P.vB0, P.vA0, sd, out);
+  else if constexpr (A == 1) K::flux1(P.vB1, P.vA1, sd, out);
+  else K::flux2(P.vB2, P.vA2, sd, out);
 }
 
 // volume term and lift of axis A at node i of local cell lc
@@ -138,18 +139,16 @@ __device__ __forceinline__ void node_axis(const UniParams<T, L>& P, const T* __r
   int nd[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) nd[q] = unode(fp, q, A);
-  // z = -(1/h) (S x)(node i) along the axis, then acc += beta_a z
-  T z[n];
-#pragma unroll
-  for (int c = 0; c < n; ++c) {
+  // acc += beta_a z with z = -(1/h) (S x)(node i) along the axis, one column at a time
+  auto zf = [&](int c) {
     T v = T(0);
 #pragma unroll
     for (int q = 0; q < 3; ++q) v = fma(sw[q], Xc[c * NL + nd[q]], v);
-    z[c] = v;
-  }
-  if constexpr (A == 0) K::B0(P.vB0, z, acc);
-  else if constexpr (A == 1) K::B1(P.vB1, z, acc);
-  else K::B2(P.vB2, z, acc);
+    return v;
+  };
+  if constexpr (A == 0) K::B0(P.vB0, zf, acc);
+  else if constexpr (A == 1) K::B1(P.vB1, zf, acc);
+  else K::B2(P.vB2, zf, acc);
   // lift: lower face -L0[ia] J/2h, upper face +L1[ia] J/2h
   const T wl = -T(0.5) * invh * sel3(P.L0, ia), wu = T(0.5) * invh * sel3(P.L1, ia);
   const T* J0 = Fc + ((2 * A) * 9 + fp) * n;
@@ -179,44 +178,37 @@ __global__ void __launch_bounds__(UniLaunch<T>::max_threads, UniLaunch<T>::min_b
     for (int e = tid; e < Cv * per_cell; e += blockDim.x) X[e] = __ldg(xb + e);
   }
   __syncthreads();
-  // upwind fluxes: task t = (axis, local cell, side, face point), two per thread; a warp sees one
-  // axis except where the range of an axis ends
-  if (valid) {
-    const int per_axis = 18 * Cv;
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      const int t = tid + h * NL * Cv;
-      const int a = t / per_axis, rem = t - a * per_axis;
-      const int lc2 = rem / 18, sp = rem - lc2 * 18, s = sp / 9, fp = sp - s * 9;
-      if (!P.active[a]) continue;
-      if (a == 0) flux_task<T, L, 0>(P, x, X, F, cell0, lc2, s, fp);
-      else if (a == 1) flux_task<T, L, 1>(P, x, X, F, cell0, lc2, s, fp);
-      else flux_task<T, L, 2>(P, x, X, F, cell0, lc2, s, fp);
-    }
+  // upwind fluxes: thread t < 18 Cv takes (local cell, side, face point) = t and does that task for the
+  // three axes in turn, so all warps run the same axis's code at a time
+  if (tid < 18 * Cv) {
+    const int lc2 = tid / 18, sp = tid - lc2 * 18, s = sp / 9, fp = sp - s * 9;
+    if (P.active[0]) flux_task<T, L, 0>(P, x, X, F, cell0, lc2, s, fp);
+    if (P.active[1]) flux_task<T, L, 1>(P, x, X, F, cell0, lc2, s, fp);
+    if (P.active[2]) flux_task<T, L, 2>(P, x, X, F, cell0, lc2, s, fp);
   }
   __syncthreads();
-  if (!valid) return;  // no barrier follows
   const T* Xc = X + lc * per_cell;
-  const T* Fc = F + lc * 6 * 9 * n;
+  T* Fc = F + lc * 6 * 9 * n;
   T acc[n];
-  {
-    T xi[n];
+  if (valid) {
 #pragma unroll
-    for (int c = 0; c < n; ++c) {
-      xi[c] = Xc[c * NL + i];
-      acc[c] = T(0);
-    }
-    K::R(P.vR, xi, acc);
+    for (int r = 0; r < n; ++r) acc[r] = T(0);
+    K::R(P.vR, [&](int c) { return Xc[c * NL + i]; }, acc);
+    node_axis<T, L, 0>(P, Xc, Fc, cell, i, acc);
+    node_axis<T, L, 1>(P, Xc, Fc, cell, i, acc);
+    node_axis<T, L, 2>(P, Xc, Fc, cell, i, acc);
   }
-  node_axis<T, L, 0>(P, Xc, Fc, cell, i, acc);
-  node_axis<T, L, 1>(P, Xc, Fc, cell, i, acc);
-  node_axis<T, L, 2>(P, Xc, Fc, cell, i, acc);
-  T rd[n];
-  K::Rdiag(P.vR, rd);
+  __syncthreads();  // every thread has read the fluxes: the cell's flux area takes the results
+  if (!valid) return;  // no barrier follows
+  // epilogue through shared memory (each thread reads back only what it wrote) in a loop over the
+  // rows: one copy of the epilogue's code instead of n
+#pragma unroll
+  for (int r = 0; r < n; ++r) Fc[r * NL + i] = acc[r];
   const T src = P.s000 ? __ldg(P.s000 + (size_t)cell * NL + i) : P.s_uni;
   const size_t dof = (size_t)cell * per_cell + i;
-#pragma unroll
-  for (int r = 0; r < n; ++r) epi_write(E, dof + (size_t)r * NL, Xc[r * NL + i], acc[r], r == 0 ? src : T(0), rd[r]);
+#pragma unroll 1
+  for (int r = 0; r < n; ++r)
+    epi_write(E, dof + (size_t)r * NL, Xc[r * NL + i], Fc[r * NL + i], r == 0 ? src : T(0), P.dR[r]);
 }
 
 }  // namespace
@@ -270,6 +262,8 @@ UniParams<T, L> make_params(const OpParams<T>& P) {
   take(U.vA0, K::nA0);
   take(U.vA1, K::nA1);
   take(U.vA2, K::nA2);
+  for (int k = 0; k < K::nR; ++k)
+    if (K::patR[k][0] == K::patR[k][1]) U.dR[K::patR[k][0]] = U.vR[k];
   for (int j = 0; j < 3; ++j) {
     for (int q = 0; q < 3; ++q) U.S[j][q] = P.S[j][q];
     U.B0[j] = P.B0[j];
@@ -294,8 +288,10 @@ UniParams<T, L> make_params(const OpParams<T>& P) {
 template <typename T, int L>
 void uni_config(const OpParams<T>& P, int* cells, size_t* smem) {
   constexpr int n = UniK<L>::n;
+  // default from a sweep on the 48^3 box at l_max = 5 (FP32: 1.35 ms at 6 cells, 1.38 at 8 and at 3,
+  // 1.51 at 1; FP64: 16.0 ms at 3 cells, 16.8 at 4): three blocks per SM fit the shared memory
   const int cmax = UniLaunch<T>::max_threads / 27;
-  const int C = P.uni_cells > 0 ? std::min(P.uni_cells, cmax) : cmax;
+  const int C = P.uni_cells > 0 ? std::min(P.uni_cells, cmax) : (sizeof(T) == 8 ? 3 : 6);
   *cells = C;
   *smem = (size_t)C * (n * 27 + 54 * n) * sizeof(T);
 }
@@ -320,6 +316,36 @@ cudaError_t launch_l(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStre
 }  // namespace
 
 bool uni_supported(int lmax) { return lmax >= 1 && lmax <= 5; }
+
+namespace {
+// floating-point operations of one cell (an FMA counts 2): reaction, per axis the derivative along
+// the axis, beta_a, the lifts and the 18 face tasks (traces of both sides, sum and difference,
+// beta_a and |beta_a|)
+template <int L>
+double flops_l(const int* active) {
+  using K = UniK<L>;
+  constexpr int n = K::n;
+  const int nb[3] = {K::nB0, K::nB1, K::nB2}, na[3] = {K::nA0, K::nA1, K::nA2};
+  double f = 2.0 * 27 * K::nR;
+  for (int a = 0; a < 3; ++a) {
+    if (!active[a]) continue;
+    f += 27.0 * (2.0 * 3 * n + 2.0 * nb[a] + 2.0 * 2 * n);
+    f += 18.0 * (2.0 * 6 * n + 2.0 * n + 2.0 * (nb[a] + na[a]));
+  }
+  return f;
+}
+}  // namespace
+
+double uni_flops_per_cell(int lmax, const int* active) {
+  switch (lmax) {
+    case 1: return flops_l<1>(active);
+    case 2: return flops_l<2>(active);
+    case 3: return flops_l<3>(active);
+    case 4: return flops_l<4>(active);
+    case 5: return flops_l<5>(active);
+    default: return 0.0;
+  }
+}
 
 bool uni_pack(const UniDense& u, std::vector<double>& vals) {
   switch (u.lmax) {
