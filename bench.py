@@ -42,7 +42,13 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3  # SMs x FFMA/clk/SM x 2 flop x max 
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture, valid only for the
 # kernel source it was taken on (first 16 hex of sha256 of csrc/apply_rows.cu); see profiles/
-APPLY_TRAFFIC = {("shock", "fp64", "025719a36b5601f4"): 11002624.0}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one apply launch, keyed by (workload, precision,
+# sha256 prefix of the kernel source at capture): the shock at full size; the 48^3 box from a 32^3
+# capture scaled by the cell ratio 3.375 (traffic grows with the cells; the rule on capture sizes keeps
+# the 48^3 case out of ncu)
+APPLY_TRAFFIC = {("shock", "fp64", "a2df80b18bbf2840"): 11006208.0,
+                 ("box3d", "fp32", "db2d1b994e781804"): 225560832.0 * 3.375,
+                 ("box3d", "fp64", "db2d1b994e781804"): 493351168.0 * 3.375}
 
 
 def parse():
