@@ -70,6 +70,14 @@ __device__ __forceinline__ int ufp(int i, int a) {
   if (a == 1) return (i % 3) + 3 * (i / 9);
   return i % 9;
 }
+// L2 prefetch of [p, p + bytes) by one bulk copy-engine request, trimmed to 16-byte boundaries (the
+// rule of cp.async.bulk); a hint only: nothing is read into the SM
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15);
+  const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + bytes) & ~uintptr_t(15);
+  if (e > a) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(unsigned(e - a)) : "memory");
+}
+
 // w[j] selected by a runtime j in {0,1,2} without indexing the parameter block
 template <typename T>
 __device__ __forceinline__ T sel3(const T (&w)[3], int j) {
@@ -173,6 +181,11 @@ __global__ void __launch_bounds__(UniLaunch<T>::max_threads, UniLaunch<T>::min_b
   const int lc = tid / NL, i = tid - lc * NL;
   const bool valid = lc < Cv;
   const int cell = cell0 + (valid ? lc : 0);
+  if (E.erk && E.y0 && tid == 0) {  // the RK4 epilogue reads the FP64 state and accumulator of these cells
+    const size_t off = (size_t)cell0 * per_cell, bytes = (size_t)Cv * per_cell * sizeof(double);
+    prefetch_l2(E.y0 + off, bytes);
+    if (E.erk >= 2) prefetch_l2(E.acc + off, bytes);
+  }
   {
     const T* xb = x + (size_t)cell0 * per_cell;
     for (int e = tid; e < Cv * per_cell; e += blockDim.x) X[e] = __ldg(xb + e);
