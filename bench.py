@@ -47,8 +47,8 @@ HBM_FALLBACK_GBS = 6800.0
 # capture scaled by the cell ratio 3.375 (traffic grows with the cells; the rule on capture sizes keeps
 # the 48^3 case out of ncu)
 APPLY_TRAFFIC = {("shock", "fp64", "a2df80b18bbf2840"): 11006208.0,
-                 ("box3d", "fp32", "db2d1b994e781804"): 225560832.0 * 3.375,
-                 ("box3d", "fp64", "db2d1b994e781804"): 493351168.0 * 3.375}
+                 ("box3d", "fp32", "52ea1b9e15bf6d4a"): 225562112.0 * 3.375,
+                 ("box3d", "fp64", "52ea1b9e15bf6d4a"): 492249856.0 * 3.375}
 
 
 def parse():
