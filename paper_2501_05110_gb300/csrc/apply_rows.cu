@@ -514,10 +514,16 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
           ell_apply<T, NF, NFP>(P.bank, A.Wmat, r, n, (s ? Y1 : Y0) + roff, J);
         } else if (P.pabs_ell) {  // ABS_POINT: |beta^p| tabulated per (spatial node, momentum face)
           const int scell = __ldg(P.cell_scell + cell), pcell = __ldg(P.cell_pcell + cell);
-          const int w = P.bank.ell_w[A.absmat];
           int slot[NF];
+          bool any_slot = false;
 #pragma unroll
-          for (int fp = 0; fp < NF; ++fp) slot[fp] = __ldg(P.pslot + scell * qdx + fp);
+          for (int fp = 0; fp < NF; ++fp) {
+            slot[fp] = __ldg(P.pslot + scell * qdx + fp);
+            any_slot |= slot[fp] >= 0;
+          }
+          // a cell none of whose points has a slot (|beta^p| negligible there) adds nothing: skip
+          // the loop (most cells of a shock lie away from the velocity gradient)
+          const int w = any_slot ? P.bank.ell_w[A.absmat] : 0;
           int idx = P.bank.ell_off[A.absmat] + r;
           const int pf = pcell + s;
           for (int k = 0; k < w; ++k, idx += n) {
