@@ -196,7 +196,10 @@ __host__ __device__ inline int rows_smem_elems(const OpParams<T>& P, int C) {
   const int fsz = C * n * S::NFP;
   const int acc = (C * n * S::NL + S::VEC - 1) / S::VEC * S::VEC;
   const int freg = (eigen ? 6 : 4) * fsz > acc ? (eigen ? 6 : 4) * fsz : acc;
-  return C * n * S::NLP + freg + C * nvt * S::NLP + C * 2 * D * nadvmax * S::NFP;
+  // + per cell: a 64-bit mask of the volume / reaction terms and one mask per face of the advection
+  // terms whose coefficient is nonzero somewhere in the cell
+  const int masks = (C * (2 + 2 * D) * 4 + (int)sizeof(T) - 1) / (int)sizeof(T);
+  return C * n * S::NLP + freg + C * nvt * S::NLP + C * 2 * D * nadvmax * S::NFP + masks;
 }
 
 // TRANS = false: y = L x.  TRANS = true: y = L^T x, the transpose of the nodal operator, term by term:
@@ -242,6 +245,18 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
   T* FR = Fs + C * n * NLP;        // face buffers S0 D0 S1 D1 (Y0 Y1), later the row results
   T* CV = FR + freg;               // [C][nvt][NLP] node coefficients of every term
   T* CF = CV + C * nvt * NLP;      // [C][2D][nadvmax][NFP] face coefficients of the advection terms
+  // [C][2 + 2D]: bit tt of words 0-1: term tt (reaction, then advection by axis) has a nonzero node
+  // coefficient in the cell; bit t of word 2 + f: advection term t has a nonzero coefficient on face f.
+  // A term that is zero on the whole cell adds nothing and is skipped (shock cells away from the
+  // velocity gradient, where the momentum terms' FP32 coefficients underflow to zero).  FP32 only:
+  // FP64 coefficients of these terms stay nonzero and the bookkeeping would cost more than it saves.
+  constexpr bool kMask = sizeof(T) == 4;
+  constexpr int MKS = 2 + NFACE;
+  unsigned* MK = reinterpret_cast<unsigned*>(CF + C * NFACE * nadvmax * NFP);
+  if constexpr (kMask) {
+    for (int k = tid; k < C * MKS; k += blockDim.x) MK[k] = 0u;
+    __syncthreads();
+  }
   const int qdx = has_mom ? NF : NL;           // spatial nodes per cell
   const int qsp = has_mom ? NF / Q : NF;       // spatial points per spatial face
 
@@ -271,6 +286,11 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
       T c = T(tm->scale) * spatial_factor(P, tm->sf, sp) * mom_node(P, tm->mf, pn);
       if (tm->nu) c *= P.nu ? P.nu[(size_t)c2 * NL + ii] : P.nu_uni;
       CV[q1 * NLP + ii] = c;
+      if (kMask && c != T(0)) {
+        unsigned* m = MK + lc2 * MKS + (tt >> 5);
+        const unsigned bit = 1u << (tt & 31);
+        if (!(*m & bit)) atomicOr(m, bit);
+      }
     }
     if (nadvmax > 0) {
       const FastDiv diva(nadvmax);
@@ -301,6 +321,10 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
           c *= mom_face(P, tm.mf, pcell + side);
         }
         CF[q1 * NFP + fp] = c;
+        if (kMask && c != T(0)) {
+          unsigned* m = MK + lc2 * MKS + 2 + f;
+          if (!(*m & (1u << tt))) atomicOr(m, 1u << tt);
+        }
       }
     }
   }
@@ -312,9 +336,11 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
   for (int i = 0; i < NL; ++i) acc[i] = T(0);
   const T* Fc = Fs + lc * n * NLP;
   const T* CVc = CV + lc * nvt * NLP;
+  const unsigned mlo = kMask ? MK[lc * MKS] : ~0u, mhi = kMask ? MK[lc * MKS + 1] : ~0u;
+  auto live = [&](int tt) { return ((tt < 32 ? mlo >> tt : mhi >> (tt - 32)) & 1u) != 0u; };
   if (valid) {
     for (int t = 0; t < P.nreact; ++t) {
-      if ((P.react_zero >> t) & 1u) continue;  // identically zero coefficient
+      if (((P.react_zero >> t) & 1u) || !live(t)) continue;  // zero coefficient (everywhere, or in the cell)
       term_apply<T, NL, NLP>(P.bank, TRANS ? P.react[t].matT : P.react[t].mat, (P.react_uni >> t) & 1u, CVc + t * NLP,
                              r, n, Fc, acc);
     }
@@ -347,7 +373,7 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
 #pragma unroll
         for (int i = 0; i < NL; ++i) g[i] = T(0);
         for (int t = 0; t < A.nadv; ++t) {
-          if ((P.adv_zero[a] >> t) & 1u) continue;
+          if (((P.adv_zero[a] >> t) & 1u) || !live(adv_off[a] + t)) continue;
           term_apply<T, NL, NLP>(P.bank, A.adv[t].matT, (P.adv_uni[a] >> t) & 1u, CVc + (adv_off[a] + t) * NLP, r, n,
                                  Z + lc * n * NLP, g);
         }
@@ -366,7 +392,7 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
 #pragma unroll
       for (int i = 0; i < NL; ++i) g[i] = T(0);
       for (int t = 0; t < A.nadv; ++t) {
-        if ((P.adv_zero[a] >> t) & 1u) continue;
+        if (((P.adv_zero[a] >> t) & 1u) || !live(adv_off[a] + t)) continue;
         term_apply<T, NL, NLP>(P.bank, A.adv[t].mat, (P.adv_uni[a] >> t) & 1u, CVc + (adv_off[a] + t) * NLP, r, n,
                                Fc, g);
       }
@@ -489,8 +515,9 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
         T J[NF];
 #pragma unroll
         for (int fp = 0; fp < NF; ++fp) J[fp] = T(0);
+        const unsigned fmask = kMask ? MK[lc * MKS + 2 + f] : ~0u;
         for (int t = 0; t < A.nadv; ++t) {
-          if ((P.adv_zero[a] >> t) & 1u) continue;
+          if (((P.adv_zero[a] >> t) & 1u) || !((fmask >> t) & 1u)) continue;
           T tmp[NF];
 #pragma unroll
           for (int fp = 0; fp < NF; ++fp) tmp[fp] = T(0);

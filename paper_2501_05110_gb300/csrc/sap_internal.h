@@ -213,6 +213,8 @@ struct sap_ctx {
   double cn_prev_dt = 0.0, cn_prev_theta = 0.5;
   bool cn_prev_valid = false;
   std::vector<double> bank_nnz;                // nnz per bank matrix (cost model)
+  double pslot_cell_frac = 1.0;                // spatial cells with a tabulated |beta^p| point (cost model)
+  double sf_zero_frac32[sap::SF_NCOMP] = {};        // spatial cells where a field component is 0 in FP32 (cost model)
   int64_t launches = 0;                        // kernels launched by the current call
   // batches: a batch handle owns one sub-context per instance and runs them with batched launches
   std::vector<sap_ctx*> sub;

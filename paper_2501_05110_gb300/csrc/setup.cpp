@@ -714,6 +714,17 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
           if (v != uval[k]) uni[k] = false;
         }
       }
+      // the FP32 row kernel skips, per cell, terms whose coefficient is zero at all its nodes: the
+      // fraction of spatial cells where each component's FP32 value vanishes (cost model)
+      for (int k = 0; k < SF_NCOMP; ++k) {
+        int z = 0;
+        for (int sc = 0; sc < c->nscell; ++sc) {
+          bool all0 = true;
+          for (int j2 = 0; j2 < c->qdx && all0; ++j2) all0 = float(sf[(size_t)k * nsv + (size_t)sc * c->qdx + j2]) == 0.0f;
+          z += all0 ? 1 : 0;
+        }
+        c->sf_zero_frac32[k] = c->nscell ? double(z) / c->nscell : 0.0;
+      }
       const bool has_mom = c->has_mom;
       const bool lnp = has_mom && d.axis_kind[c->D - 1] == SAP_AXIS_LNP;
       BankBuilder B;
@@ -904,6 +915,15 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
           for (int sp = 0; sp < nsv; ++sp)
             if (gmax > 0.0 && pmax[sp] > 1e-15 * gmax) pslot[sp] = nslot++;
           M.pslot = pslot;
+          {  // the row kernel skips the |beta^p| loop in cells without a tabulated point
+            int with = 0;
+            for (int sc = 0; sc < c->nscell; ++sc) {
+              bool any = false;
+              for (int j = 0; j < c->qdx; ++j) any = any || pslot[(size_t)sc * c->qdx + j] >= 0;
+              with += any ? 1 : 0;
+            }
+            c->pslot_cell_frac = c->nscell ? double(with) / c->nscell : 1.0;
+          }
           M.nslot = nslot;
           const int nnzp = (int)M.pat.col.size();
           const bool llf = c->flux == SAP_FLUX_LLF;
@@ -1365,22 +1385,33 @@ extern "C" sap_status sap_apply_cost(sap_handle c, double* flops, double* bytes)
     const double faces = 2.0 * D * n * nfp;            // face entries per cell
     per_cell += 2.0 * faces * 2.0 * q;                  // own + neighbour traces
     per_cell += 2.0 * faces;                            // sum / difference
+    // share of the cells in which a term is applied: none for a term that is zero everywhere; in FP32,
+    // not in cells where its spatial field component is zero at every node
+    auto share = [&](const Term& tm, bool zero) -> double {
+      if (zero) return 0.0;
+      if (c->prec == SAP_PREC_FP32 && tm.sf != SF_ONE) return 1.0 - c->sf_zero_frac32[tm.sf];
+      return 1.0;
+    };
     for (int a = 0; a < D; ++a) {
       const AxisInfo& A = P.ax[a];
       if (!A.active) continue;
       const double fe = 2.0 * n * nfp;  // this axis' face entries per cell
       double f = 1.0;
-      for (int t = 0; t < A.nadv; ++t) f += 2.0 * nnz_row_avg(A.adv[t].mat) + 2.0;
+      for (int t = 0; t < A.nadv; ++t)
+        f += share(A.adv[t], (P.adv_zero[a] >> t) & 1u) * (2.0 * nnz_row_avg(A.adv[t].mat) + 2.0);
       if (A.route == ABS_EIGEN) f += 2.0 * nnz_row_avg(A.WTmat) + 3.0 + 2.0 * nnz_row_avg(A.Wmat) + 2.0;
+      else if (A.route == ABS_POINT) f += c->pslot_cell_frac * (2.0 * nnz_row_avg(A.absmat)) + 1.0;
       else f += 2.0 * nnz_row_avg(A.absmat) + 1.0;
       per_cell += fe * f;
       double v = 0.0;  // volume advection per DoF
-      for (int t = 0; t < A.nadv; ++t) v += 2.0 * nnz_row_avg(A.adv[t].mat) + 2.0;
+      for (int t = 0; t < A.nadv; ++t)
+        v += share(A.adv[t], (P.adv_zero[a] >> t) & 1u) * (2.0 * nnz_row_avg(A.adv[t].mat) + 2.0);
       v += 2.0 * q + 6.0;  // derivative and lifts
       per_cell += v * n * nloc;
     }
     double rx = 0.0;
-    for (int t = 0; t < P.nreact; ++t) rx += 2.0 * nnz_row_avg(P.react[t].mat) + 2.0;
+    for (int t = 0; t < P.nreact; ++t)
+      rx += share(P.react[t], (P.react_zero >> t) & 1u) * (2.0 * nnz_row_avg(P.react[t].mat) + 2.0);
     per_cell += (rx + 4.0) * n * nloc;
     *flops = per_cell * c->ncell;
     return SAP_OK;
