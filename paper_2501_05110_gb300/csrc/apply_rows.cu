@@ -202,6 +202,64 @@ __host__ __device__ inline int rows_smem_elems(const OpParams<T>& P, int C) {
   return C * n * S::NLP + freg + C * nvt * S::NLP + C * 2 * D * nadvmax * S::NFP + masks;
 }
 
+// Coefficient of term tt (reaction terms first, then the advection terms axis by axis) at node ii of
+// cell c2: scale x spatial field at the node's spatial point x momentum factor at its momentum node
+// (x nu for the collision term).
+template <typename T, int D, int Q>
+__device__ __forceinline__ T node_coef(const OpParams<T>& P, int c2, int tt, int ii) {
+  using S = Shape<T, D, Q>;
+  constexpr int NL = S::NL, NF = S::NF;
+  const int has_mom = P.has_mom;
+  const int qdx = has_mom ? NF : NL;
+  const Term* tm;
+  if (tt < P.nreact) {
+    tm = &P.react[tt];
+  } else {
+    int a = 0, off = P.nreact;
+    while (a + 1 < D && tt >= off + P.ax[a].nadv) off += P.ax[a++].nadv;
+    tm = &P.ax[a].adv[tt - off];
+  }
+  const int scell = __ldg(P.cell_scell + c2), pcell = __ldg(P.cell_pcell + c2);
+  const int sp = scell * qdx + (has_mom ? ii % NF : ii);
+  const int pn = has_mom ? pcell * Q + ii / NF : 0;
+  T c = T(tm->scale) * spatial_factor(P, tm->sf, sp) * mom_node(P, tm->mf, pn);
+  if (tm->nu) c *= P.nu ? P.nu[(size_t)c2 * NL + ii] : P.nu_uni;
+  return c;
+}
+
+// Coefficient of advection term tt of axis f / 2 on face f of cell c2 at face point fp (0 for an
+// inactive axis or a term index beyond the axis's terms).
+template <typename T, int D, int Q>
+__device__ __forceinline__ T face_coef(const OpParams<T>& P, int c2, int f, int tt, int fp) {
+  using S = Shape<T, D, Q>;
+  constexpr int NL = S::NL, NF = S::NF;
+  const int has_mom = P.has_mom;
+  const int qdx = has_mom ? NF : NL;
+  const int qsp = has_mom ? NF / Q : NF;
+  const int a = f >> 1, side = f & 1;
+  const AxisInfo& A = P.ax[a];
+  if (!A.active || tt >= A.nadv) return T(0);
+  const int scell = __ldg(P.cell_scell + c2), pcell = __ldg(P.cell_pcell + c2);
+  const Term& tm = A.adv[tt];
+  T c = T(tm.scale);
+  if (A.kind <= SAP_AXIS_Z) {
+    // spatial face: U_a at the spatial face point, momentum factor at the point's p
+    const int fsp = has_mom ? fp % qsp : fp;
+    if (tm.sf == SF_U + a) {
+      const int fb = __ldg(P.scell_face + scell * 2 * P.dx + 2 * a + side);
+      c *= P.uface_is_uni[a] ? P.uface_uni[a] : P.uface[a][fb + fsp];
+    } else {
+      c *= spatial_factor(P, tm.sf, scell * qdx);  // only SF_ONE occurs here
+    }
+    c *= mom_node(P, tm.mf, has_mom ? pcell * Q + fp / qsp : 0);
+  } else {
+    // momentum face: spatial factor at the spatial node (fp), momentum at the face
+    c *= spatial_factor(P, tm.sf, scell * qdx + fp);
+    c *= mom_face(P, tm.mf, pcell + side);
+  }
+  return c;
+}
+
 // TRANS = false: y = L x.  TRANS = true: y = L^T x, the transpose of the nodal operator, term by term:
 // transposed couplings; volume -(1/h) beta^a (S^T x along the axis); faces g = (lift-weighted traces
 // of x from both cells, each with its own 1/h), then beta+ g distributed to the lower cell (its upper
@@ -253,12 +311,13 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
   constexpr bool kMask = sizeof(T) == 4;
   constexpr int MKS = 2 + NFACE;
   unsigned* MK = reinterpret_cast<unsigned*>(CF + C * NFACE * nadvmax * NFP);
-  if constexpr (kMask) {
+  // P0 reads the coefficients from the per-cell tables built at sap_set_fields when they exist
+  const bool tab = P.cvtab != nullptr;  // uniform over the grid
+  if (kMask && !tab) {
     for (int k = tid; k < C * MKS; k += blockDim.x) MK[k] = 0u;
     __syncthreads();
   }
   const int qdx = has_mom ? NF : NL;           // spatial nodes per cell
-  const int qsp = has_mom ? NF / Q : NF;       // spatial points per spatial face
 
   // ---- P0 ---------------------------------------------------------------------------------------
   {
@@ -267,63 +326,46 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
       const int R = e / NL;
       Fs[R * NLP + (e - R * NL)] = x[base + e];
     }
-    const FastDiv divt(nvt);
-    for (int w = tid; w < Cv * nvt * NL; w += blockDim.x) {
-      const int q1 = w / NL, ii = w - q1 * NL;  // q1 = lc2 nvt + tt
-      const int lc2 = divt(q1), tt = q1 - lc2 * nvt;
-      const int c2 = cell0 + lc2;
-      const Term* tm;
-      if (tt < P.nreact) {
-        tm = &P.react[tt];
-      } else {
-        int a = 0, off = P.nreact;
-        while (a + 1 < D && tt >= off + P.ax[a].nadv) off += P.ax[a++].nadv;
-        tm = &P.ax[a].adv[tt - off];
+    if (tab) {
+      const T* cvt = P.cvtab + (size_t)cell0 * nvt * NL;
+      for (int w = tid; w < Cv * nvt * NL; w += blockDim.x) {
+        const int q1 = w / NL;
+        CV[q1 * NLP + (w - q1 * NL)] = __ldg(cvt + w);
       }
-      const int scell = __ldg(P.cell_scell + c2), pcell = __ldg(P.cell_pcell + c2);
-      const int sp = scell * qdx + (has_mom ? ii % NF : ii);
-      const int pn = has_mom ? pcell * Q + ii / NF : 0;
-      T c = T(tm->scale) * spatial_factor(P, tm->sf, sp) * mom_node(P, tm->mf, pn);
-      if (tm->nu) c *= P.nu ? P.nu[(size_t)c2 * NL + ii] : P.nu_uni;
-      CV[q1 * NLP + ii] = c;
-      if (kMask && c != T(0)) {
-        unsigned* m = MK + lc2 * MKS + (tt >> 5);
-        const unsigned bit = 1u << (tt & 31);
-        if (!(*m & bit)) atomicOr(m, bit);
-      }
-    }
-    if (nadvmax > 0) {
-      const FastDiv diva(nadvmax);
+      const T* cft = P.cftab + (size_t)cell0 * NFACE * nadvmax * NF;
       for (int w = tid; w < Cv * NFACE * nadvmax * NF; w += blockDim.x) {
-        const int q1 = w / NF, fp = w - q1 * NF;  // q1 = (lc2 NFACE + f) nadvmax + tt
-        const int q2 = diva(q1), tt = q1 - q2 * nadvmax;
-        const int lc2 = q2 / NFACE, f = q2 - lc2 * NFACE;
-        const int a = f >> 1, side = f & 1;
-        const AxisInfo& A = P.ax[a];
-        if (!A.active || tt >= A.nadv) continue;
-        const int c2 = cell0 + lc2;
-        const int scell = __ldg(P.cell_scell + c2), pcell = __ldg(P.cell_pcell + c2);
-        const Term& tm = A.adv[tt];
-        T c = T(tm.scale);
-        if (A.kind <= SAP_AXIS_Z) {
-          // spatial face: U_a at the spatial face point, momentum factor at the point's p
-          const int fsp = has_mom ? fp % qsp : fp;
-          if (tm.sf == SF_U + a) {
-            const int fb = __ldg(P.scell_face + scell * 2 * P.dx + 2 * a + side);
-            c *= P.uface_is_uni[a] ? P.uface_uni[a] : P.uface[a][fb + fsp];
-          } else {
-            c *= spatial_factor(P, tm.sf, scell * qdx);  // only SF_ONE occurs here
-          }
-          c *= mom_node(P, tm.mf, has_mom ? pcell * Q + fp / qsp : 0);
-        } else {
-          // momentum face: spatial factor at the spatial node (fp), momentum at the face
-          c *= spatial_factor(P, tm.sf, scell * qdx + fp);
-          c *= mom_face(P, tm.mf, pcell + side);
-        }
-        CF[q1 * NFP + fp] = c;
+        const int q1 = w / NF;
+        CF[q1 * NFP + (w - q1 * NF)] = __ldg(cft + w);
+      }
+      if constexpr (kMask)
+        for (int k = tid; k < C * MKS; k += blockDim.x) MK[k] = k < Cv * MKS ? __ldg(P.mktab + (size_t)cell0 * MKS + k) : 0u;
+    } else {
+      const FastDiv divt(nvt);
+      for (int w = tid; w < Cv * nvt * NL; w += blockDim.x) {
+        const int q1 = w / NL, ii = w - q1 * NL;  // q1 = lc2 nvt + tt
+        const int lc2 = divt(q1), tt = q1 - lc2 * nvt;
+        const T c = node_coef<T, D, Q>(P, cell0 + lc2, tt, ii);
+        CV[q1 * NLP + ii] = c;
         if (kMask && c != T(0)) {
-          unsigned* m = MK + lc2 * MKS + 2 + f;
-          if (!(*m & (1u << tt))) atomicOr(m, 1u << tt);
+          unsigned* m = MK + lc2 * MKS + (tt >> 5);
+          const unsigned bit = 1u << (tt & 31);
+          if (!(*m & bit)) atomicOr(m, bit);
+        }
+      }
+      if (nadvmax > 0) {
+        const FastDiv diva(nadvmax);
+        for (int w = tid; w < Cv * NFACE * nadvmax * NF; w += blockDim.x) {
+          const int q1 = w / NF, fp = w - q1 * NF;  // q1 = (lc2 NFACE + f) nadvmax + tt
+          const int q2 = diva(q1), tt = q1 - q2 * nadvmax;
+          const int lc2 = q2 / NFACE, f = q2 - lc2 * NFACE;
+          const AxisInfo& A = P.ax[f >> 1];
+          if (!A.active || tt >= A.nadv) continue;
+          const T c = face_coef<T, D, Q>(P, cell0 + lc2, f, tt, fp);
+          CF[q1 * NFP + fp] = c;
+          if (kMask && c != T(0)) {
+            unsigned* m = MK + lc2 * MKS + 2 + f;
+            if (!(*m & (1u << tt))) atomicOr(m, 1u << tt);
+          }
         }
       }
     }
@@ -639,6 +681,66 @@ __global__ void __launch_bounds__(Shape<T, D, Q>::MAXT) rows_kernel_batched(
   rows_body<T, D, Q, false>(*reinterpret_cast<const OpParams<T>*>(pbuf), x, E, cpbs[bb.x], bb.y, doffs[bb.x], smem_raw);
 }
 
+// Per-cell coefficient tables of the row kernel (built once per sap_set_fields): the node
+// coefficients [cell][term][node], the face coefficients [cell][face][term][point] and the masks of
+// the terms that are nonzero somewhere in the cell (FP32 contexts; mktab zeroed by the caller).
+template <typename T, int D, int Q>
+__global__ void coef_tables_kernel(const __grid_constant__ OpParams<T> P, T* __restrict__ cvtab, T* __restrict__ cftab,
+                                   unsigned* __restrict__ mktab, int nvt, int nadvmax) {
+  using S = Shape<T, D, Q>;
+  constexpr int NL = S::NL, NF = S::NF, NFACE = 2 * D, MKS = 2 + NFACE;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t ncv = (int64_t)P.ncell * nvt * NL;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < ncv; w += stride) {
+    const int64_t q1 = w / NL;
+    const int ii = (int)(w - q1 * NL);
+    const int c2 = (int)(q1 / nvt), tt = (int)(q1 - (int64_t)c2 * nvt);
+    const T c = node_coef<T, D, Q>(P, c2, tt, ii);
+    cvtab[w] = c;
+    if (mktab && c != T(0)) atomicOr(mktab + (size_t)c2 * MKS + (tt >> 5), 1u << (tt & 31));
+  }
+  const int64_t ncf = (int64_t)P.ncell * NFACE * nadvmax * NF;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < ncf; w += stride) {
+    const int64_t q1 = w / NF;
+    const int fp = (int)(w - q1 * NF);
+    const int64_t q2 = q1 / nadvmax;
+    const int tt = (int)(q1 - q2 * nadvmax);
+    const int c2 = (int)(q2 / NFACE), f = (int)(q2 - (int64_t)c2 * NFACE);
+    const T c = face_coef<T, D, Q>(P, c2, f, tt, fp);
+    cftab[w] = c;
+    if (mktab && c != T(0)) atomicOr(mktab + (size_t)c2 * MKS + 2 + f, 1u << tt);
+  }
+}
+
+template <typename T, int D, int Q>
+cudaError_t coef_tables_shape(OpParams<T>& P, std::vector<DevBuf>& owner) {
+  int nvt, nadvmax;
+  bool eigen;
+  term_counts(P, &nvt, &nadvmax, &eigen);
+  using S = Shape<T, D, Q>;
+  const size_t ncv = (size_t)P.ncell * nvt * S::NL, ncf = (size_t)P.ncell * 2 * D * nadvmax * S::NF;
+  const size_t nmk = sizeof(T) == 4 ? (size_t)P.ncell * (2 + 2 * D) : 0;
+  void* pv = nullptr;
+  void* pf = nullptr;
+  void* pm = nullptr;
+  cudaError_t err = cudaMalloc(&pv, sizeof(T) * std::max<size_t>(ncv, 1));
+  if (err == cudaSuccess) err = cudaMalloc(&pf, sizeof(T) * std::max<size_t>(ncf, 1));
+  if (err == cudaSuccess && nmk) err = cudaMalloc(&pm, sizeof(unsigned) * nmk);
+  if (pv) owner.push_back(DevBuf{pv, sizeof(T) * std::max<size_t>(ncv, 1)});
+  if (pf) owner.push_back(DevBuf{pf, sizeof(T) * std::max<size_t>(ncf, 1)});
+  if (pm) owner.push_back(DevBuf{pm, sizeof(unsigned) * nmk});
+  if (err != cudaSuccess) return err;
+  if (nmk && (err = cudaMemset(pm, 0, sizeof(unsigned) * nmk)) != cudaSuccess) return err;
+  coef_tables_kernel<T, D, Q><<<1024, 256>>>(P, static_cast<T*>(pv), static_cast<T*>(pf), static_cast<unsigned*>(pm),
+                                             nvt, nadvmax);
+  note_launch();
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  P.cvtab = static_cast<const T*>(pv);
+  P.cftab = static_cast<const T*>(pf);
+  P.mktab = static_cast<const unsigned*>(pm);
+  return cudaSuccess;
+}
+
 constexpr size_t kRowsSmemMax = 160 * 1024;
 
 template <typename T, int D, int Q>
@@ -708,6 +810,17 @@ cudaError_t launch_rows(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaS
 }
 
 template <typename T>
+cudaError_t build_coef_tables(OpParams<T>& P, std::vector<DevBuf>& owner) {
+  P.cvtab = nullptr;
+  P.cftab = nullptr;
+  P.mktab = nullptr;
+  if (P.D == 1 && P.q == 3) return coef_tables_shape<T, 1, 3>(P, owner);
+  if (P.D == 2 && P.q == 2) return coef_tables_shape<T, 2, 2>(P, owner);
+  if (P.D == 3 && P.q == 3) return coef_tables_shape<T, 3, 3>(P, owner);
+  return cudaSuccess;  // other shapes run the cell-node kernel, which computes its coefficients
+}
+
+template <typename T>
 cudaError_t launch_rows_transposed(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s) {
   if (P.D == 1 && P.q == 3) return launch_rows_shape<T, 1, 3, true>(P, x, e, s);
   if (P.D == 2 && P.q == 2) return launch_rows_shape<T, 2, 2, true>(P, x, e, s);
@@ -737,6 +850,8 @@ template void rows_config<double>(const OpParams<double>&, int, int*, size_t*);
 template void rows_config<float>(const OpParams<float>&, int, int*, size_t*);
 template cudaError_t launch_rows<double>(const OpParams<double>&, const double*, const Epi<double>&, cudaStream_t);
 template cudaError_t launch_rows<float>(const OpParams<float>&, const float*, const Epi<float>&, cudaStream_t);
+template cudaError_t build_coef_tables<double>(OpParams<double>&, std::vector<DevBuf>&);
+template cudaError_t build_coef_tables<float>(OpParams<float>&, std::vector<DevBuf>&);
 template cudaError_t launch_rows_transposed<double>(const OpParams<double>&, const double*, const Epi<double>&,
                                                     cudaStream_t);
 template cudaError_t launch_rows_transposed<float>(const OpParams<float>&, const float*, const Epi<float>&,

@@ -125,6 +125,12 @@ struct OpParams {
   int uni_L = -1;
   const void* uni = nullptr;
   int uni_cells = 0;
+  // row kernel: per-cell coefficient tables built at sap_set_fields (null: computed in the kernel):
+  // node coefficients [cell][term][node], face coefficients [cell][face][term][point], and (FP32)
+  // masks [cell][2 + 2D] of the terms nonzero somewhere in the cell
+  const T* cvtab = nullptr;
+  const T* cftab = nullptr;
+  const unsigned* mktab = nullptr;
 };
 
 // Tables of the field-gradient kernels of the adjoint (adjoint_fields.cu): the spatial field
@@ -301,6 +307,9 @@ template <typename T>
 cudaError_t launch_uniform(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s);
 template <typename T>
 cudaError_t launch_rows(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s);
+// build the row kernel's coefficient tables of P (device buffers appended to `owner`)
+template <typename T>
+cudaError_t build_coef_tables(OpParams<T>& P, std::vector<DevBuf>& owner);
 template <typename T>
 cudaError_t launch_rows_transposed(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s);
 // cells per block and dynamic shared memory (bytes) of the row kernel for a problem

@@ -686,6 +686,9 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
       // compute call can read a freed buffer after a failure part-way
       c->fields_set = false;
       free_bufs(fs.bufs);
+      // tables that lived in those buffers
+      c->p64.cvtab = nullptr; c->p64.cftab = nullptr; c->p64.mktab = nullptr;
+      c->p32.cvtab = nullptr; c->p32.cftab = nullptr; c->p32.mktab = nullptr;
       free_bufs(fs.gbufs);
       fs.mom = MomFaceSrc{};
       const sap_desc& d = c->desc;
@@ -1111,6 +1114,14 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
         }
       }
       apply_kernel_choice(c);
+      // the row kernel's per-cell coefficient tables (not for problems the node kernel runs: their
+      // transposed applies compute the coefficients in the kernel)
+      if (c->uni_avail < 0) {
+        cudaError_t te = build_coef_tables<double>(c->p64, fs.bufs);
+        if (te == cudaSuccess) te = build_coef_tables<float>(c->p32, fs.bufs);
+        if (te == cudaSuccess) te = cudaDeviceSynchronize();
+        if (te != cudaSuccess) throw std::string("coefficient tables: ") + cudaGetErrorString(te);
+      }
       c->fields_set = true;
       c->fields_version += 1;
       c->cn_prev_valid = false;
