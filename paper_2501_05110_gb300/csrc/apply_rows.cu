@@ -650,9 +650,14 @@ __device__ __forceinline__ void rows_body(const OpParams<T>& P, const T* __restr
     T s = T(0);
     if (c == 0) s = P.s000 ? P.s000[(size_t)(cell0 + lc2) * NL + i] : P.s_uni;
     T rd = T(0);
-    if (need_rd)
-      for (int t = 0; t < P.nreact; ++t)
-        rd += CV[(lc2 * nvt + t) * NLP + i] * csr_diag(P.bank, P.react[t].mat, c, n);
+    if (need_rd) {
+      if (P.rdtab) {
+        rd = __ldg(P.rdtab + (size_t)cell0 * per_cell + e);
+      } else {
+        for (int t = 0; t < P.nreact; ++t)
+          rd += CV[(lc2 * nvt + t) * NLP + i] * csr_diag(P.bank, P.react[t].mat, c, n);
+      }
+    }
     epi_write(E, dbase + e, Fs[R * NLP + i], Ab[e], s, rd);
   }
 }
@@ -686,7 +691,7 @@ __global__ void __launch_bounds__(Shape<T, D, Q>::MAXT) rows_kernel_batched(
 // the terms that are nonzero somewhere in the cell (FP32 contexts; mktab zeroed by the caller).
 template <typename T, int D, int Q>
 __global__ void coef_tables_kernel(const __grid_constant__ OpParams<T> P, T* __restrict__ cvtab, T* __restrict__ cftab,
-                                   unsigned* __restrict__ mktab, int nvt, int nadvmax) {
+                                   unsigned* __restrict__ mktab, T* __restrict__ rdtab, int nvt, int nadvmax) {
   using S = Shape<T, D, Q>;
   constexpr int NL = S::NL, NF = S::NF, NFACE = 2 * D, MKS = 2 + NFACE;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -710,10 +715,23 @@ __global__ void coef_tables_kernel(const __grid_constant__ OpParams<T> P, T* __r
     cftab[w] = c;
     if (mktab && c != T(0)) atomicOr(mktab + (size_t)c2 * MKS + 2 + f, 1u << tt);
   }
+  // the reaction diagonal at every DoF (the point-Jacobi diagonal): sum_t c_t(node) K_t[r][r]
+  if (rdtab) {
+    const int n = P.n;
+    const int64_t N = (int64_t)P.ncell * n * NL;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < N; w += stride) {
+      const int64_t R = w / NL;
+      const int ii = (int)(w - R * NL);
+      const int c2 = (int)(R / n), r = (int)(R - (int64_t)c2 * n);
+      T d = T(0);
+      for (int t = 0; t < P.nreact; ++t) d += node_coef<T, D, Q>(P, c2, t, ii) * csr_diag(P.bank, P.react[t].mat, r, n);
+      rdtab[w] = d;
+    }
+  }
 }
 
 template <typename T, int D, int Q>
-cudaError_t coef_tables_shape(OpParams<T>& P, std::vector<DevBuf>& owner) {
+cudaError_t coef_tables_shape(OpParams<T>& P, std::vector<DevBuf>& owner, bool with_diag) {
   int nvt, nadvmax;
   bool eigen;
   term_counts(P, &nvt, &nadvmax, &eigen);
@@ -723,21 +741,26 @@ cudaError_t coef_tables_shape(OpParams<T>& P, std::vector<DevBuf>& owner) {
   void* pv = nullptr;
   void* pf = nullptr;
   void* pm = nullptr;
+  void* pd = nullptr;
+  const size_t nd = with_diag ? (size_t)P.ncell * P.n * S::NL : 0;
   cudaError_t err = cudaMalloc(&pv, sizeof(T) * std::max<size_t>(ncv, 1));
   if (err == cudaSuccess) err = cudaMalloc(&pf, sizeof(T) * std::max<size_t>(ncf, 1));
   if (err == cudaSuccess && nmk) err = cudaMalloc(&pm, sizeof(unsigned) * nmk);
+  if (err == cudaSuccess && nd) err = cudaMalloc(&pd, sizeof(T) * nd);
   if (pv) owner.push_back(DevBuf{pv, sizeof(T) * std::max<size_t>(ncv, 1)});
   if (pf) owner.push_back(DevBuf{pf, sizeof(T) * std::max<size_t>(ncf, 1)});
   if (pm) owner.push_back(DevBuf{pm, sizeof(unsigned) * nmk});
+  if (pd) owner.push_back(DevBuf{pd, sizeof(T) * nd});
   if (err != cudaSuccess) return err;
   if (nmk && (err = cudaMemset(pm, 0, sizeof(unsigned) * nmk)) != cudaSuccess) return err;
   coef_tables_kernel<T, D, Q><<<1024, 256>>>(P, static_cast<T*>(pv), static_cast<T*>(pf), static_cast<unsigned*>(pm),
-                                             nvt, nadvmax);
+                                             static_cast<T*>(pd), nvt, nadvmax);
   note_launch();
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   P.cvtab = static_cast<const T*>(pv);
   P.cftab = static_cast<const T*>(pf);
   P.mktab = static_cast<const unsigned*>(pm);
+  P.rdtab = static_cast<const T*>(pd);
   return cudaSuccess;
 }
 
@@ -810,13 +833,14 @@ cudaError_t launch_rows(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaS
 }
 
 template <typename T>
-cudaError_t build_coef_tables(OpParams<T>& P, std::vector<DevBuf>& owner) {
+cudaError_t build_coef_tables(OpParams<T>& P, std::vector<DevBuf>& owner, bool with_diag) {
   P.cvtab = nullptr;
   P.cftab = nullptr;
   P.mktab = nullptr;
-  if (P.D == 1 && P.q == 3) return coef_tables_shape<T, 1, 3>(P, owner);
-  if (P.D == 2 && P.q == 2) return coef_tables_shape<T, 2, 2>(P, owner);
-  if (P.D == 3 && P.q == 3) return coef_tables_shape<T, 3, 3>(P, owner);
+  P.rdtab = nullptr;
+  if (P.D == 1 && P.q == 3) return coef_tables_shape<T, 1, 3>(P, owner, with_diag);
+  if (P.D == 2 && P.q == 2) return coef_tables_shape<T, 2, 2>(P, owner, with_diag);
+  if (P.D == 3 && P.q == 3) return coef_tables_shape<T, 3, 3>(P, owner, with_diag);
   return cudaSuccess;  // other shapes run the cell-node kernel, which computes its coefficients
 }
 
@@ -850,8 +874,8 @@ template void rows_config<double>(const OpParams<double>&, int, int*, size_t*);
 template void rows_config<float>(const OpParams<float>&, int, int*, size_t*);
 template cudaError_t launch_rows<double>(const OpParams<double>&, const double*, const Epi<double>&, cudaStream_t);
 template cudaError_t launch_rows<float>(const OpParams<float>&, const float*, const Epi<float>&, cudaStream_t);
-template cudaError_t build_coef_tables<double>(OpParams<double>&, std::vector<DevBuf>&);
-template cudaError_t build_coef_tables<float>(OpParams<float>&, std::vector<DevBuf>&);
+template cudaError_t build_coef_tables<double>(OpParams<double>&, std::vector<DevBuf>&, bool);
+template cudaError_t build_coef_tables<float>(OpParams<float>&, std::vector<DevBuf>&, bool);
 template cudaError_t launch_rows_transposed<double>(const OpParams<double>&, const double*, const Epi<double>&,
                                                     cudaStream_t);
 template cudaError_t launch_rows_transposed<float>(const OpParams<float>&, const float*, const Epi<float>&,

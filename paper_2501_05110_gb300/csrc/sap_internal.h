@@ -131,6 +131,7 @@ struct OpParams {
   const T* cvtab = nullptr;
   const T* cftab = nullptr;
   const unsigned* mktab = nullptr;
+  const T* rdtab = nullptr;  // reaction diagonal per DoF (the point-Jacobi diagonal), or null
 };
 
 // Tables of the field-gradient kernels of the adjoint (adjoint_fields.cu): the spatial field
@@ -307,9 +308,10 @@ template <typename T>
 cudaError_t launch_uniform(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s);
 template <typename T>
 cudaError_t launch_rows(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s);
-// build the row kernel's coefficient tables of P (device buffers appended to `owner`)
+// build the row kernel's coefficient tables of P (device buffers appended to `owner`); with_diag: also
+// the per-DoF reaction diagonal the Jacobi epilogues read
 template <typename T>
-cudaError_t build_coef_tables(OpParams<T>& P, std::vector<DevBuf>& owner);
+cudaError_t build_coef_tables(OpParams<T>& P, std::vector<DevBuf>& owner, bool with_diag);
 template <typename T>
 cudaError_t launch_rows_transposed(const OpParams<T>& P, const T* x, const Epi<T>& e, cudaStream_t s);
 // cells per block and dynamic shared memory (bytes) of the row kernel for a problem

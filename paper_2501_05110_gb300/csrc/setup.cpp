@@ -687,8 +687,8 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
       c->fields_set = false;
       free_bufs(fs.bufs);
       // tables that lived in those buffers
-      c->p64.cvtab = nullptr; c->p64.cftab = nullptr; c->p64.mktab = nullptr;
-      c->p32.cvtab = nullptr; c->p32.cftab = nullptr; c->p32.mktab = nullptr;
+      c->p64.cvtab = nullptr; c->p64.cftab = nullptr; c->p64.mktab = nullptr; c->p64.rdtab = nullptr;
+      c->p32.cvtab = nullptr; c->p32.cftab = nullptr; c->p32.mktab = nullptr; c->p32.rdtab = nullptr;
       free_bufs(fs.gbufs);
       fs.mom = MomFaceSrc{};
       const sap_desc& d = c->desc;
@@ -1117,8 +1117,9 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
       // the row kernel's per-cell coefficient tables (not for problems the node kernel runs: their
       // transposed applies compute the coefficients in the kernel)
       if (c->uni_avail < 0) {
-        cudaError_t te = build_coef_tables<double>(c->p64, fs.bufs);
-        if (te == cudaSuccess) te = build_coef_tables<float>(c->p32, fs.bufs);
+        // the Jacobi diagonal per DoF for the precision whose applies the Krylov solves run
+        cudaError_t te = build_coef_tables<double>(c->p64, fs.bufs, c->prec == SAP_PREC_FP64);
+        if (te == cudaSuccess) te = build_coef_tables<float>(c->p32, fs.bufs, c->prec == SAP_PREC_FP32);
         if (te == cudaSuccess) te = cudaDeviceSynchronize();
         if (te != cudaSuccess) throw std::string("coefficient tables: ") + cudaGetErrorString(te);
       }
