@@ -46,8 +46,8 @@ HBM_FALLBACK_GBS = 6800.0
 # sha256 prefix of the kernel source at capture): the shock at full size; the 48^3 box from a 32^3
 # capture scaled by the cell ratio 3.375 (traffic grows with the cells; the rule on capture sizes keeps
 # the 48^3 case out of ncu)
-APPLY_TRAFFIC = {("shock", "fp64", "bf69b25ada471fab"): 11007232.0,
-                 ("shock", "fp32", "bf69b25ada471fab"): 5734400.0,
+APPLY_TRAFFIC = {("shock", "fp64", "db4fdc5e07bd34b9"): 26137856.0,
+                 ("shock", "fp32", "db4fdc5e07bd34b9"): 13666560.0,
                  ("box3d", "fp32", "52ea1b9e15bf6d4a"): 225562112.0 * 3.375,
                  ("box3d", "fp64", "52ea1b9e15bf6d4a"): 492249856.0 * 3.375}
 
