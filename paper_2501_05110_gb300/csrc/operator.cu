@@ -934,6 +934,18 @@ __device__ __forceinline__ double dot_chunk(const TV* __restrict__ a, const doub
     const TV2* a2 = reinterpret_cast<const TV2*>(a);
     const int np = len >> 1;
     int p = lane;
+    // four pairs per lane and step: eight loads in flight per warp (the loop is latency-bound)
+    for (; p + 96 < np; p += 128) {
+      const TV2 u = __ldg(a2 + p), v = __ldg(a2 + p + 32), u2 = __ldg(a2 + p + 64), v2 = __ldg(a2 + p + 96);
+      acc0 += double(u.x) * ws[2 * p];
+      acc1 += double(u.y) * ws[2 * p + 1];
+      acc2 += double(v.x) * ws[2 * p + 64];
+      acc3 += double(v.y) * ws[2 * p + 65];
+      acc0 += double(u2.x) * ws[2 * p + 128];
+      acc1 += double(u2.y) * ws[2 * p + 129];
+      acc2 += double(v2.x) * ws[2 * p + 192];
+      acc3 += double(v2.y) * ws[2 * p + 193];
+    }
     for (; p + 32 < np; p += 64) {
       const TV2 u = __ldg(a2 + p), v = __ldg(a2 + p + 32);
       acc0 += double(u.x) * ws[2 * p];
@@ -1045,7 +1057,30 @@ __global__ void __launch_bounds__(LB_THREADS) update_lb_kernel(const TV* __restr
     }
     nrm = double(ns) + double(nc);
   } else {
-    for (int k = threadIdx.x; k < len; k += LB_THREADS) {
+    // four elements per thread at a time, the basis vectors outermost: four independent loads per
+    // vector in flight (the loop is latency-bound)
+    int k = threadIdx.x;
+    for (; k + 3 * LB_THREADS < len; k += 4 * LB_THREADS) {
+      double v0 = double(w[k0 + k]), v1 = double(w[k0 + k + LB_THREADS]);
+      double v2 = double(w[k0 + k + 2 * LB_THREADS]), v3 = double(w[k0 + k + 3 * LB_THREADS]);
+      const TV* vp = V + k0 + k;
+#pragma unroll 2
+      for (int i = 0; i < m; ++i) {
+        const TV* vi = vp + i * ldv;
+        const double hi = hs[i];
+        v0 -= hi * double(__ldg(vi));
+        v1 -= hi * double(__ldg(vi + LB_THREADS));
+        v2 -= hi * double(__ldg(vi + 2 * LB_THREADS));
+        v3 -= hi * double(__ldg(vi + 3 * LB_THREADS));
+      }
+      const TV s0 = TV(v0), s1 = TV(v1), s2 = TV(v2), s3 = TV(v3);
+      w[k0 + k] = s0;
+      w[k0 + k + LB_THREADS] = s1;
+      w[k0 + k + 2 * LB_THREADS] = s2;
+      w[k0 + k + 3 * LB_THREADS] = s3;
+      nrm += double(s0) * double(s0) + double(s1) * double(s1) + double(s2) * double(s2) + double(s3) * double(s3);
+    }
+    for (; k < len; k += LB_THREADS) {
       double v = double(w[k0 + k]);
       const TV* vp = V + k0 + k;
 #pragma unroll 4
