@@ -19,8 +19,9 @@
 // The result equals the row kernel's (apply_rows.cu) up to the order of the sums.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstdint>
 #include <cstring>
-#include <mutex>
 
 #include "kernels_common.cuh"
 #include "sap_internal.h"
