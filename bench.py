@@ -254,6 +254,30 @@ def run_cpu_oracle(nsteps: int, warmup: int = 1) -> dict:
                       f"{its / nsteps:.1f} GMRES iterations/step"}
 
 
+def run_cpu_oracle_rk4(nsteps: int = 40, warmup: int = 1, cells: int = 4) -> dict:
+    """The oracle's RK4 step on a small box with the 3-D workload's k, l_max and fields (the full
+    48^3 box cannot be assembled by the oracle): C driver, all host cores; DoF-updates/s per stage."""
+    import numpy as np
+    from oracle import dg, native
+    from paper_2501_05110_gb300 import workloads as W
+    prob = W.box3d(ncells=cells)
+    d = dg.Discretisation(prob)
+    drv = native.RK4Driver(d)
+    z = np.random.default_rng(0).standard_normal(d.N)
+    if warmup:
+        drv.steps(z, prob.dt, warmup)
+    t0 = time.perf_counter()
+    threads = drv.steps(z, prob.dt, nsteps)
+    t = time.perf_counter() - t0
+    return {"value": d.N * 4 * nsteps / t, "unit": UNIT, "cores": threads,
+            "host_cores": len(os.sched_getaffinity(0)), "kind": "oracle", "ms_per_step": 1e3 * t / nsteps,
+            "seconds": t,
+            "sample": f"{nsteps} timed RK4 steps (after {warmup} warm-up) of a {cells}^3 box with the workload's "
+                      f"k = 2, l_max = 5 and fields (N = {d.N}) by the oracle's C driver: assembled CSR D "
+                      f"({d.D.nnz} nonzeros) and inverted mass blocks, OpenMP on {threads} threads; assembly "
+                      f"untimed; DoF-updates per RK4 stage"}
+
+
 # ------------------------------------------------------------------------------------------------
 # GPU measurements
 # ------------------------------------------------------------------------------------------------
@@ -410,6 +434,11 @@ def measure_box3d(args, precision):
            "row_kernel_apply_us": 1e6 * t_rows,
            "clocks": clk, "gpu_launches": 4 * args.steps + (args.steps if precision == "fp32" else 0)}
     sol.close()
+    if precision == "fp64" and not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = run_cpu_oracle_rk4()
+        except Exception as exc:  # reported, never fatal for the GPU measurement
+            out["cpu_baseline"] = {"value": None, "error": f"{type(exc).__name__}: {str(exc)[:200]}"}
     return out
 
 

@@ -1,6 +1,7 @@
 /*
- * TEST INFRASTRUCTURE ONLY (part of the FP64 CPU oracle): a multi-threaded driver of the oracle's
- * assembled Crank--Nicolson step, used as the CPU baseline that is timed beside the GPU library.
+ * TEST INFRASTRUCTURE ONLY (part of the FP64 CPU oracle): multi-threaded drivers of the oracle's
+ * assembled Crank--Nicolson step and RK4 step, used as the CPU baselines that are timed beside the
+ * GPU library.
  *
  * Each step forms b = B z + dt h and solves A z' = b (Eq. theta-method with theta = 1/2,
  * A = M + dt/2 D, B = M - dt/2 D, Eq. system-matrix-rhs) by restarted GMRES(restart) with modified
@@ -137,5 +138,51 @@ int oracle_cn_gmres_steps(int64_t n, const int64_t* arp, const int32_t* aci, con
   }
   *iterations = its;
   free(dinv); free(b); free(r); free(w); free(V); free(H); free(g); free(cs); free(sn); free(y);
+  return omp_get_max_threads();
+}
+
+/* Classical RK4 (Sec. 3.4) on zeta' = M^-1 (h - D zeta), the algorithm of oracle/steppers.py rk4(),
+ * with the oracle's assembled D (CSR) and the inverses of its block-diagonal mass matrix: minv holds,
+ * per cell, the inverse of the nloc x nloc mass block that every one of the cell's n coefficient
+ * rows shares (degree of freedom (cell n + r) nloc + a).  OpenMP loops over all host cores (or
+ * `threads`).  Returns the number of threads, -1 on allocation failure; z (in/out) holds the state. */
+int oracle_rk4_steps(int64_t ncell, int n, int nloc, const int64_t* rp, const int32_t* ci, const double* v,
+                     const double* minv, const double* h, double* z, int nsteps, double dt, int threads) {
+  if (threads > 0) omp_set_num_threads(threads);
+  const int64_t N = ncell * (int64_t)n * nloc;
+  double* t = malloc(sizeof(double) * N);
+  double* y = malloc(sizeof(double) * N);
+  double* k = malloc(sizeof(double) * N);
+  double* acc = malloc(sizeof(double) * N);
+  if (!t || !y || !k || !acc) {
+    free(t); free(y); free(k); free(acc);
+    return -1;
+  }
+  const double a[4] = {0.5, 0.5, 1.0, 0.0};          /* stage input Y_{s+1} = z + a_s dt k_s */
+  const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  for (int step = 0; step < nsteps; ++step) {
+    memcpy(y, z, sizeof(double) * N);
+    memcpy(acc, z, sizeof(double) * N);
+    for (int st = 0; st < 4; ++st) {
+      spmv(N, rp, ci, v, y, t); /* t = D Y */
+#pragma omp parallel for schedule(static)
+      for (int64_t blk = 0; blk < ncell * (int64_t)n; ++blk) { /* k = M^-1 (h - D Y) */
+        const double* mi = minv + (size_t)(blk / n) * nloc * nloc;
+        const int64_t o = blk * nloc;
+        for (int i = 0; i < nloc; ++i) {
+          double s = 0.0;
+          for (int j = 0; j < nloc; ++j) s += mi[i * nloc + j] * (h[o + j] - t[o + j]);
+          k[o + i] = s;
+        }
+      }
+#pragma omp parallel for schedule(static)
+      for (int64_t i = 0; i < N; ++i) {
+        acc[i] += dt * b[st] * k[i];
+        y[i] = z[i] + a[st] * dt * k[i];
+      }
+    }
+    memcpy(z, acc, sizeof(double) * N);
+  }
+  free(t); free(y); free(k); free(acc);
   return omp_get_max_threads();
 }

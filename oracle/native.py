@@ -1,8 +1,8 @@
 """Build and call the oracle's multi-threaded C driver (csr_driver.c).
 
 TEST INFRASTRUCTURE ONLY: part of the FP64 CPU oracle.  It times the oracle's assembled
-Crank--Nicolson step on all host cores for the CPU baseline (bench.py) and is checked against the
-oracle's sparse-LU step in tests/.  The library never uses it.
+Crank--Nicolson and RK4 steps on all host cores for the CPU baselines (bench.py) and is checked
+against the oracle's Python steppers in tests/.  The library never uses it.
 """
 from __future__ import annotations
 
@@ -41,6 +41,8 @@ def _load():
         lib.oracle_cn_gmres_steps.argtypes = [C.c_int64, p, p, p, p, p, p, p, p, C.c_int, C.c_double, C.c_int,
                                               C.c_int, C.c_int, C.POINTER(C.c_int64)]
         lib.oracle_cn_gmres_steps.restype = C.c_int
+        lib.oracle_rk4_steps.argtypes = [C.c_int64, C.c_int, C.c_int, p, p, p, p, p, p, C.c_int, C.c_double, C.c_int]
+        lib.oracle_rk4_steps.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -78,3 +80,29 @@ class CNDriver:
         if nt < 0:
             raise MemoryError("oracle C driver: allocation failed")
         return nt, its.value
+
+
+class RK4Driver:
+    """The oracle's RK4 step on zeta' = M^-1 (h - D zeta) for one fully assembled discretisation,
+    with the inverses of the mass blocks (one per cell, shared by the cell's coefficient rows)."""
+
+    def __init__(self, disc):
+        m = disc.D.tocsr()
+        m.sort_indices()
+        self.rp = np.ascontiguousarray(m.indptr, dtype=np.int64)
+        self.ci = np.ascontiguousarray(m.indices, dtype=np.int32)
+        self.v = np.ascontiguousarray(m.data, dtype=np.float64)
+        self.minv = np.ascontiguousarray(np.linalg.inv(disc.mass_blocks), dtype=np.float64)
+        self.h = np.ascontiguousarray(disc.h, dtype=np.float64)
+        self.ncell, self.n, self.nloc = disc.mass_blocks.shape[0], disc.n, disc.mesh.nloc
+        self.N = disc.N
+
+    def steps(self, z, dt: float, nsteps: int, threads=0):
+        """Advances z (float64, in place); returns the number of OpenMP threads used."""
+        lib = _load()
+        ptr = lambda a: C.c_void_p(a.ctypes.data)
+        nt = lib.oracle_rk4_steps(self.ncell, self.n, self.nloc, ptr(self.rp), ptr(self.ci), ptr(self.v),
+                                  ptr(self.minv), ptr(self.h), ptr(z), nsteps, dt, threads)
+        if nt < 0:
+            raise MemoryError("oracle C driver: allocation failed")
+        return nt

@@ -615,6 +615,19 @@ def test_c_driver_cn_matches_lu():
     assert abs(its - its_py) <= 4, (its, its_py)
 
 
+def test_c_driver_rk4_matches_python():
+    """The C driver's RK4 step (D in CSR, inverted mass blocks, OpenMP) equals the oracle's Python RK4
+    (sparse LU of M) on a 3-D box and a graded shock, to rounding."""
+    from oracle import native
+    for prob, dt in ((W.box3d(ncells=2, k=2, lmax=2), 0.01), (W.shock(nx=6, npc=4, lmax=3), 0.05)):
+        d = dg.Discretisation(prob)
+        z0 = np.random.default_rng(3).standard_normal(d.N)
+        want = steppers.rk4(d.M, d.D, d.h, z0, dt, 3)
+        z = z0.copy()
+        assert native.RK4Driver(d).steps(z, dt, 3, threads=2) == 2
+        assert np.linalg.norm(z - want) < 1e-12 * np.linalg.norm(want)
+
+
 # ----------------------------------------------------------------------------------------------
 # local Lax--Friedrichs flux (the alternative numerical flux of Sec. 3.2)
 # ----------------------------------------------------------------------------------------------
