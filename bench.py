@@ -48,8 +48,8 @@ HBM_FALLBACK_GBS = 6800.0
 # the 48^3 case out of ncu)
 APPLY_TRAFFIC = {("shock", "fp64", "db4fdc5e07bd34b9"): 26137856.0,
                  ("shock", "fp32", "db4fdc5e07bd34b9"): 13666560.0,
-                 ("box3d", "fp32", "52ea1b9e15bf6d4a"): 225562112.0 * 3.375,
-                 ("box3d", "fp64", "52ea1b9e15bf6d4a"): 492249856.0 * 3.375}
+                 ("box3d", "fp32", "a7df1f11032ab442"): 225672704.0 * 3.375,
+                 ("box3d", "fp64", "a7df1f11032ab442"): 492894208.0 * 3.375}
 
 
 def parse():
