@@ -66,7 +66,7 @@ def _adjoint_grads(S, checkpoint):
     return np.bincount(S["cell_of_node"], weights=g_node), float(u1_t.grad), float(J.detach())
 
 
-@pytest.mark.parametrize("name", ["shock_small", "box_tiny", "periodic1d_tiny"])
+@pytest.mark.parametrize("name", ["shock_small", "box_tiny", "box_k2_node", "periodic1d_tiny"])
 def test_adjoint_erk_step_vs_oracle_transpose(setup, name):
     """One library RK4 adjoint step equals the oracle's transposed RK4 step (stability polynomial
     in the transposed nodal operator, built column by column from the oracle), element by element."""
@@ -74,6 +74,8 @@ def test_adjoint_erk_step_vs_oracle_transpose(setup, name):
     sapgpu = setup["sapgpu"]
     prob = {"shock_small": lambda: W.shock(nx=4, npc=3, lmax=2, xr=(-4.0, 4.0), lnpr=(0.0, 2.0)),
             "box_tiny": lambda: W.box3d(ncells=2, k=1, lmax=2),
+            # k = 2: the forward stages run the node kernel, the transposed ones the row kernel
+            "box_k2_node": lambda: W.box3d(ncells=2, k=2, lmax=2),
             "periodic1d_tiny": lambda: W.periodic_1d(ncells=5, k=2, lmax=2)}[name]()
     from oracle import steppers
     orc = NodalOracle(prob)
