@@ -889,12 +889,21 @@ __device__ __forceinline__ void df_fma(float& s, float& c, float a, float b) {
 // V_i . w over one chunk by one warp, FP32 vectors, double-float sums (ws: the chunk of w in FP32)
 __device__ __forceinline__ double dot_chunk_df(const float* __restrict__ a, const float* ws, int len, int lane,
                                                bool pairs) {
-  float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
+  // four compensated sums: the dependent chain of each is a quarter as long
+  float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f, s2 = 0.0f, c2 = 0.0f, s3 = 0.0f, c3 = 0.0f;
   int k = lane;
   if (pairs) {
     const float2* a2 = reinterpret_cast<const float2*>(a);
     const int np = len >> 1;
-    for (int p = lane; p < np; p += 32) {
+    int p = lane;
+    for (; p + 32 < np; p += 64) {
+      const float2 x = __ldg(a2 + p), y = __ldg(a2 + p + 32);
+      df_fma(s0, c0, x.x, ws[2 * p]);
+      df_fma(s1, c1, x.y, ws[2 * p + 1]);
+      df_fma(s2, c2, y.x, ws[2 * p + 64]);
+      df_fma(s3, c3, y.y, ws[2 * p + 65]);
+    }
+    for (; p < np; p += 32) {
       const float2 x = __ldg(a2 + p);
       df_fma(s0, c0, x.x, ws[2 * p]);
       df_fma(s1, c1, x.y, ws[2 * p + 1]);
@@ -902,7 +911,7 @@ __device__ __forceinline__ double dot_chunk_df(const float* __restrict__ a, cons
     k = 2 * np + lane;
   }
   for (; k < len; k += 32) df_fma(s0, c0, __ldg(a + k), ws[k]);
-  return (double(s0) + double(c0)) + (double(s1) + double(c1));
+  return ((double(s0) + double(c0)) + (double(s1) + double(c1))) + ((double(s2) + double(c2)) + (double(s3) + double(c3)));
 }
 
 // w . w over one chunk by one warp, double-float sums
@@ -923,6 +932,46 @@ __device__ __forceinline__ float update_df(float wk, const float* __restrict__ v
     c = fmaf(-hl[i], v, c);
   }
   return s + c;
+}
+
+// w_k -= sum_i h_i V_i[k] for the chunk's elements k, four elements per thread at a time with the
+// basis vectors outermost (four independent loads per vector in flight); each element's arithmetic is
+// that of update_df.  Adds |w'|^2 to (ns, nc).
+__device__ __forceinline__ void update_chunk_df(float* __restrict__ w, const float* __restrict__ V, int64_t k0,
+                                                int len, int64_t ldv, int m, const float* hh, const float* hl,
+                                                int nthreads, float& ns, float& nc) {
+  int k = threadIdx.x;
+  for (; k + 3 * nthreads < len; k += 4 * nthreads) {
+    float s[4], c[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      s[q] = w[k0 + k + q * nthreads];
+      c[q] = 0.0f;
+    }
+    const float* vp = V + k0 + k;
+#pragma unroll 2
+    for (int i = 0; i < m; ++i) {
+      float v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = __ldg(vp + i * ldv + q * nthreads);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        df_fma(s[q], c[q], -hh[i], v[q]);
+        c[q] = fmaf(-hl[i], v[q], c[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float vs = s[q] + c[q];
+      w[k0 + k + q * nthreads] = vs;
+      df_fma(ns, nc, vs, vs);
+    }
+  }
+  for (; k < len; k += nthreads) {
+    const float vs = update_df(w[k0 + k], V + k0 + k, ldv, m, hh, hl);
+    w[k0 + k] = vs;
+    df_fma(ns, nc, vs, vs);
+  }
 }
 
 template <typename TV>
@@ -1050,11 +1099,8 @@ __global__ void __launch_bounds__(LB_THREADS) update_lb_kernel(const TV* __restr
     }
     __syncthreads();
     float ns = 0.0f, nc = 0.0f;
-    for (int k = threadIdx.x; k < len; k += LB_THREADS) {
-      const float vs = update_df(w[k0 + k], V + k0 + k, ldv, m, hh, hl);
-      w[k0 + k] = vs;
-      df_fma(ns, nc, vs, vs);
-    }
+    update_chunk_df(reinterpret_cast<float*>(w), reinterpret_cast<const float*>(V), k0, len, ldv, m, hh, hl,
+                    LB_THREADS, ns, nc);
     nrm = double(ns) + double(nc);
   } else {
     // four elements per thread at a time, the basis vectors outermost: four independent loads per
@@ -1564,11 +1610,8 @@ __global__ void __launch_bounds__(KRY_THREADS) update_b_kernel(const TV* __restr
     }
     __syncthreads();
     float ns = 0.0f, nc = 0.0f;
-    for (int k = threadIdx.x; k < len; k += KRY_THREADS) {
-      const float vs = update_df(w[k0 + k], V + k0 + k, ldv, m, hh, hl);
-      w[k0 + k] = vs;
-      df_fma(ns, nc, vs, vs);
-    }
+    update_chunk_df(reinterpret_cast<float*>(w), reinterpret_cast<const float*>(V), k0, len, ldv, m, hh, hl,
+                    KRY_THREADS, ns, nc);
     nrm = double(ns) + double(nc);
   } else {
     for (int k = threadIdx.x; k < len; k += KRY_THREADS) {
