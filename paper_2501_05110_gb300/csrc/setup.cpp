@@ -1117,8 +1117,9 @@ extern "C" sap_status sap_set_fields(sap_handle c, const double* U, const double
       // the row kernel's per-cell coefficient tables (not for problems the node kernel runs: their
       // transposed applies compute the coefficients in the kernel)
       if (c->uni_avail < 0) {
-        // the Jacobi diagonal per DoF for the precision whose applies the Krylov solves run
-        cudaError_t te = build_coef_tables<double>(c->p64, fs.bufs, c->prec == SAP_PREC_FP64);
+        // the Jacobi diagonal per DoF: FP64 always (the Krylov matvecs of FP64 contexts, the
+        // Jacobi-scaled FP32 copy of the FP64 residual in FP32 contexts), FP32 for FP32 contexts
+        cudaError_t te = build_coef_tables<double>(c->p64, fs.bufs, true);
         if (te == cudaSuccess) te = build_coef_tables<float>(c->p32, fs.bufs, c->prec == SAP_PREC_FP32);
         if (te == cudaSuccess) te = cudaDeviceSynchronize();
         if (te != cudaSuccess) throw std::string("coefficient tables: ") + cudaGetErrorString(te);
