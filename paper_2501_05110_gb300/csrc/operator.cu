@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <atomic>
 #include <mutex>
 #include <type_traits>
 #include <string>
@@ -921,6 +922,30 @@ __device__ __forceinline__ double dot_self_df(const float* ws, int len, int lane
   return double(s) + double(c);
 }
 
+// x (FP64) += sum_{i<m} y[i] V_i for FP32 basis vectors: the sum in double-float on the FP32 units
+// (y split into FP32 hi + lo parts, exact products, compensated sums), then one FP64 add per entry.
+// The FP64 form of this loop (combine_kernel) is bound by the FP64 pipe.
+__global__ void combine_df_kernel(const float* __restrict__ V, int64_t ldv, int m, const double* __restrict__ y,
+                                  double* __restrict__ x, int64_t N) {
+  __shared__ float yh[KRY_MAXV], yl[KRY_MAXV];
+  if (threadIdx.x < m) {
+    const double v = y[threadIdx.x];
+    yh[threadIdx.x] = float(v);
+    yl[threadIdx.x] = float(v - double(float(v)));
+  }
+  __syncthreads();
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.0f, c = 0.0f;
+#pragma unroll 4
+    for (int i = 0; i < m; ++i) {
+      const float v = __ldg(V + i * ldv + k);
+      df_fma(s, c, yh[i], v);
+      c = fmaf(yl[i], v, c);
+    }
+    x[k] += double(s) + double(c);
+  }
+}
+
 // w_k - sum_{i<m} h_i V_i[k] in double-float (h split into FP32 hi + lo parts), rounded to FP32
 __device__ __forceinline__ float update_df(float wk, const float* __restrict__ vp, int64_t ldv, int m,
                                            const float* hh, const float* hl) {
@@ -1015,58 +1040,151 @@ __device__ __forceinline__ double dot_chunk(const TV* __restrict__ a, const doub
   return (acc0 + acc1) + (acc2 + acc3);
 }
 
+// Launch shape of the single-problem Krylov kernels: one wave of blocks (the kernel's occupancy
+// times the SM count), block b on the contiguous range [b per, (b+1) per) of `unit`-entry units.  A
+// grid of fixed-size chunks left a partial second wave (512 chunks of a 2^20-entry vector on 456
+// resident blocks).  The grid never exceeds the chunk count the partial-sum scratch is sized for.
+struct KryShape {
+  int grid;
+  int64_t per;
+};
+
+static KryShape kry_shape(int64_t N, int unit, int wave) {
+  const int64_t nchunks = std::max<int64_t>(1, (N + KRY_CHUNK - 1) / KRY_CHUNK);
+  const int64_t nu = std::max<int64_t>(1, (N + unit - 1) / unit);
+  int64_t g = std::min<int64_t>(nchunks, wave > 0 ? wave : nchunks);
+  const int64_t per = (nu + g - 1) / g;
+  g = (nu + per - 1) / per;  // every block has units
+  return {(int)g, per};
+}
+
+// blocks of LB_THREADS threads of `kernel` resident at once on the current device, cached per
+// device ordinal and kernel slot (0 when the query fails: kry_shape then uses one block per chunk)
+constexpr int KRY_WAVE_SLOTS = 4;  // multidot FP64, FP32; update FP64, FP32
+template <typename K>
+static int kry_wave(K kernel, int slot) {
+  static std::atomic<int> cache[KRY_WAVE_SLOTS][128];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const bool cached = dev >= 0 && dev < 128 && slot >= 0 && slot < KRY_WAVE_SLOTS;
+  if (cached) {
+    const int v = cache[slot][dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int nsm = 0, bps = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, LB_THREADS, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int v = std::max(1, nsm) * std::max(1, bps);
+  if (cached) cache[slot][dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+// dots of w with V_0..V_{m-1} (+ w.w): block b takes the range [b per, (b+1) per) (per a multiple of 64,
+// so V_i + k0 stays 16-byte aligned when ldv is even), staged through shared memory in equal
+// sub-chunks of at most KRY_CHUNK entries.  One basis vector per warp, streamed with four paired loads
+// per lane in flight, its partial sum kept per lane across the sub-chunks; w.w is summed by every
+// thread while it stages w.  The last block sums the blocks' partials in block order.  out[i] for
+// i < m is the dot with V_i, out[m] (with_ww) is w.w.  (Measured on 2^20 entries against a variant
+// that keeps all basis vectors' sums per lane over 16-byte units: as fast up to 8 vectors, faster
+// beyond, in FP64 and FP32.)
 template <typename TV>
 __global__ void __launch_bounds__(LB_THREADS) multidot_lb_kernel(const TV* __restrict__ V, int64_t ldv, int m,
-                                                                 const TV* __restrict__ w, int64_t N, int with_ww,
-                                                                 double* __restrict__ partial, int nchunks,
+                                                                 const TV* __restrict__ w, int64_t N, int64_t per,
+                                                                 int with_ww, double* __restrict__ partial,
                                                                  unsigned int* counter, double* out,
                                                                  const int* done, const int* need) {
   if (kry_skip(done, need)) return;
+  constexpr int NW = LB_THREADS / 32;
+  constexpr int NQ = (KRY_MAXV + NW - 1) / NW;  // basis vectors per warp
   __shared__ unsigned int ticket;
-  const int64_t k0 = (int64_t)blockIdx.x * KRY_CHUNK;
-  const int len = (int)((N - k0) < KRY_CHUNK ? (N - k0) : KRY_CHUNK);
+  __shared__ double red[NW];
+  const int nb = gridDim.x;
+  const int64_t beg = (int64_t)blockIdx.x * per;
+  const int64_t end = beg + per < N ? beg + per : N;
+  const int64_t nsub = (per + KRY_CHUNK - 1) / KRY_CHUNK;
+  const int64_t sub = ((per + nsub - 1) / nsub + 63) / 64 * 64;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int mt = m + (with_ww ? 1 : 0);
-  const bool pairs = ((ldv & 1) == 0);  // V_i + k0 stays 2-element aligned
+  const bool pairs = ((ldv & 1) == 0);
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  double ww = 0.0;
   if constexpr (sizeof(TV) == 4) {
     __shared__ float wsf[KRY_CHUNK];
-    for (int k = threadIdx.x; k < len; k += LB_THREADS) wsf[k] = w[k0 + k];
-    __syncthreads();
-    for (int i = warp; i < mt; i += LB_THREADS / 32) {
-      double acc = i < m ? dot_chunk_df(V + i * ldv + k0, wsf, len, lane, pairs) : dot_self_df(wsf, len, lane);
-      acc = warp_sum(acc);
-      if (lane == 0) partial[(size_t)i * nchunks + blockIdx.x] = acc;
+    float ss = 0.0f, sc = 0.0f;
+    for (int64_t k0 = beg; k0 < end; k0 += sub) {
+      const int len = (int)(end - k0 < sub ? end - k0 : sub);
+      __syncthreads();  // the previous sub-chunk's reads of wsf are done
+      for (int k = threadIdx.x; k < len; k += LB_THREADS) {
+        const float wv = w[k0 + k];
+        wsf[k] = wv;
+        df_fma(ss, sc, wv, wv);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int i = warp + q * NW;
+        if (i < m) acc[q] += dot_chunk_df(V + i * ldv + k0, wsf, len, lane, pairs);
+      }
     }
+    ww = double(ss) + double(sc);
   } else {
     __shared__ double ws[KRY_CHUNK];
-    for (int k = threadIdx.x; k < len; k += LB_THREADS) ws[k] = double(w[k0 + k]);
-    __syncthreads();
-    for (int i = warp; i < mt; i += LB_THREADS / 32) {
-      double acc;
-      if (i < m) {
-        acc = dot_chunk<TV>(V + i * ldv + k0, ws, len, lane, pairs);
-      } else {
-        acc = 0.0;
-        for (int k = lane; k < len; k += 32) acc += ws[k] * ws[k];
+    for (int64_t k0 = beg; k0 < end; k0 += sub) {
+      const int len = (int)(end - k0 < sub ? end - k0 : sub);
+      __syncthreads();
+      for (int k = threadIdx.x; k < len; k += LB_THREADS) {
+        const double wv = double(w[k0 + k]);
+        ws[k] = wv;
+        ww += wv * wv;
       }
-      acc = warp_sum(acc);
-      if (lane == 0) partial[(size_t)i * nchunks + blockIdx.x] = acc;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int i = warp + q * NW;
+        if (i < m) acc[q] += dot_chunk<TV>(V + i * ldv + k0, ws, len, lane, pairs);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int i = warp + q * NW;
+    if (i < m) {  // warp-uniform
+      const double v = warp_sum(acc[q]);
+      if (lane == 0) partial[(size_t)i * nb + blockIdx.x] = v;
+    }
+  }
+  if (with_ww) {
+    ww = warp_sum(ww);
+    if (lane == 0) red[warp] = ww;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < NW; ++q) t += red[q];
+      partial[(size_t)m * nb + blockIdx.x] = t;
     }
   }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
   __syncthreads();
-  if (ticket != (unsigned)(gridDim.x - 1)) return;
+  if (ticket != (unsigned)(nb - 1)) return;
   __threadfence();
-  for (int i = warp; i < mt; i += LB_THREADS / 32) {
+  const int mt = m + (with_ww ? 1 : 0);
+  for (int i = warp; i < mt; i += NW) {
     double v0 = 0.0, v1 = 0.0;
     int c = lane;
-    for (; c + 32 < nchunks; c += 64) {
-      v0 += __ldcg(partial + (size_t)i * nchunks + c);
-      v1 += __ldcg(partial + (size_t)i * nchunks + c + 32);
+    for (; c + 32 < nb; c += 64) {
+      v0 += __ldcg(partial + (size_t)i * nb + c);
+      v1 += __ldcg(partial + (size_t)i * nb + c + 32);
     }
-    for (; c < nchunks; c += 32) v0 += __ldcg(partial + (size_t)i * nchunks + c);
+    for (; c < nb; c += 32) v0 += __ldcg(partial + (size_t)i * nb + c);
     const double v = warp_sum(v0 + v1);
     if (lane == 0) out[i] = v;
   }
@@ -1077,19 +1195,20 @@ __global__ void __launch_bounds__(LB_THREADS) multidot_lb_kernel(const TV* __res
 // re-orthogonalisation or finalise the column; pass 2: add the second coefficients and finalise)
 template <typename TV>
 __global__ void __launch_bounds__(LB_THREADS) update_lb_kernel(const TV* __restrict__ V, int64_t ldv, int j,
-                                                                TV* __restrict__ w, int64_t N,
-                                                                double* __restrict__ partial, int nchunks,
-                                                                GmresDev* G, int pass) {
+                                                                TV* __restrict__ w, int64_t N, int64_t per,
+                                                                double* __restrict__ partial, GmresDev* G,
+                                                                int pass) {
   if (kry_skip(&G->done, pass == 2 ? &G->reorth : nullptr)) return;
   const int m = j + 1;
+  const int nb = gridDim.x;
   __shared__ double hs[KRY_MAXV];
   __shared__ double red[LB_THREADS / 32];
   __shared__ unsigned int ticket;
   const double* h = pass == 1 ? G->h1 : G->h2;
   if (threadIdx.x < m) hs[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
-  const int64_t k0 = (int64_t)blockIdx.x * KRY_CHUNK;
-  const int len = (int)((N - k0) < KRY_CHUNK ? (N - k0) : KRY_CHUNK);
+  const int64_t k0 = (int64_t)blockIdx.x * per;  // the block's range [k0, k0 + len)
+  const int len = (int)((N - k0) < per ? (N - k0) : per);
   double nrm = 0.0;
   if constexpr (sizeof(TV) == 4) {
     __shared__ float hh[KRY_MAXV], hl[KRY_MAXV];
@@ -1148,17 +1267,17 @@ __global__ void __launch_bounds__(LB_THREADS) update_lb_kernel(const TV* __restr
   __syncthreads();
   if (threadIdx.x == 0) ticket = atomicAdd(&G->counter, 1u);
   __syncthreads();
-  if (ticket != (unsigned)(gridDim.x - 1)) return;
+  if (ticket != (unsigned)(nb - 1)) return;
   __threadfence();
   const int lane = threadIdx.x & 31;
   if (threadIdx.x < 32) {
     double v0 = 0.0, v1 = 0.0;
     int c = lane;
-    for (; c + 32 < nchunks; c += 64) {
+    for (; c + 32 < nb; c += 64) {
       v0 += __ldcg(partial + c);
       v1 += __ldcg(partial + c + 32);
     }
-    for (; c < nchunks; c += 32) v0 += __ldcg(partial + c);
+    for (; c < nb; c += 32) v0 += __ldcg(partial + c);
     double v = warp_sum(v0 + v1);
     if (lane == 0) {
       G->counter = 0u;
@@ -1179,6 +1298,30 @@ __global__ void __launch_bounds__(LB_THREADS) update_lb_kernel(const TV* __restr
       }
     }
   }
+}
+
+// the multi-dot of w with m basis vectors (+ w.w) over one wave of blocks
+template <typename TV>
+static void launch_multidot(const TV* V, int64_t ldv, int m, const TV* w, int64_t N, int with_ww, double* partial,
+                            unsigned int* counter, double* out, const int* done, const int* need, cudaStream_t s) {
+  const KryShape sh = kry_shape(N, 64, kry_wave(multidot_lb_kernel<TV>, sizeof(TV) == 8 ? 0 : 1));
+  multidot_lb_kernel<TV><<<sh.grid, LB_THREADS, 0, s>>>(V, ldv, m, w, N, sh.per * 64, with_ww, partial, counter, out,
+                                                         done, need);
+}
+
+// w -= V h (pass 1 or 2) over one wave of blocks, ranges in multiples of 64 entries
+template <typename TV>
+static void launch_update(const TV* V, int64_t N, int j, TV* w, double* partial, GmresDev* G, int pass,
+                          cudaStream_t s) {
+  const KryShape sh = kry_shape(N, 64, kry_wave(update_lb_kernel<TV>, sizeof(TV) == 8 ? 2 : 3));
+  update_lb_kernel<TV><<<sh.grid, LB_THREADS, 0, s>>>(V, N, j, w, N, sh.per * 64, partial, G, pass);
+}
+
+// the occupancy queries of the pass kernels, run outside any stream capture (gmres_cycle)
+template <typename TV>
+static void kry_warm() {
+  kry_wave(multidot_lb_kernel<TV>, sizeof(TV) == 8 ? 0 : 1);
+  kry_wave(update_lb_kernel<TV>, sizeof(TV) == 8 ? 2 : 3);
 }
 
 // y = x * (*s); called in place (y == x), so x and y are not restrict-qualified
@@ -1206,10 +1349,8 @@ __global__ void extrapolate_kernel(double* __restrict__ x, double* __restrict__ 
 template <typename TV>
 static void norm2_dev(sap_ctx* c, const TV* v, int slot, cudaStream_t s) {
   const int64_t N = c->N;
-  const int nchunks = (int)((N + KRY_CHUNK - 1) / KRY_CHUNK);
   GmresDev* G = reinterpret_cast<GmresDev*>(c->gdev);
-  multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, s>>>(nullptr, N, 0, v, N, 1, c->small, nchunks, &G->counter,
-                                                         &G->misc[slot], nullptr, nullptr);
+  launch_multidot<TV>(nullptr, N, 0, v, N, 1, c->small, &G->counter, &G->misc[slot], nullptr, nullptr, s);
   ++g_launches;
 }
 
@@ -1228,7 +1369,6 @@ template <typename TV, bool TRANS>
 static cudaError_t enqueue_arnoldi(sap_ctx* c, const OpParams<TV>& PV, TV* V, double half, int j0, int cnt,
                                    cudaStream_t cs) {
   const int64_t N = c->N;
-  const int nchunks = (int)((N + KRY_CHUNK - 1) / KRY_CHUNK);
   double* partial = c->small;
   GmresDev* G = reinterpret_cast<GmresDev*>(c->gdev);
   GmresDev* Gh = reinterpret_cast<GmresDev*>(c->gdev_host);
@@ -1241,12 +1381,10 @@ static cudaError_t enqueue_arnoldi(sap_ctx* c, const OpParams<TV>& PV, TV* V, do
     if constexpr (TRANS) e1 = launch_applyT<TV>(PV, V + (size_t)j * N, e, cs);
     else e1 = launch_apply<TV>(PV, V + (size_t)j * N, e, cs);
     if (e1 != cudaSuccess) return e1;
-    multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j + 1, w, N, 1, partial, nchunks,
-                                                            &G->counter, G->h1, &G->done, nullptr);
-    update_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j, w, N, partial, nchunks, G, 1);
-    multidot_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j + 1, w, N, 0, partial, nchunks,
-                                                            &G->counter, G->h2, &G->done, &G->reorth);
-    update_lb_kernel<TV><<<nchunks, LB_THREADS, 0, cs>>>(V, N, j, w, N, partial, nchunks, G, 2);
+    launch_multidot<TV>(V, N, j + 1, w, N, 1, partial, &G->counter, G->h1, &G->done, nullptr, cs);
+    launch_update<TV>(V, N, j, w, partial, G, 1, cs);
+    launch_multidot<TV>(V, N, j + 1, w, N, 0, partial, &G->counter, G->h2, &G->done, &G->reorth, cs);
+    launch_update<TV>(V, N, j, w, partial, G, 2, cs);
     scale_dev_kernel<TV><<<1024, KRY_THREADS, 0, cs>>>(w, w, &G->inv_norm, N, &G->done);
     g_launches += 5;
   }
@@ -1301,13 +1439,18 @@ static cudaGraphExec_t arnoldi_graph(sap_ctx* c, const OpParams<TV>& PV, TV* V, 
 // *jd = the cycle's iterations.
 template <typename TV, bool TRANS>
 static cudaError_t gmres_cycle(sap_ctx* c, const OpParams<TV>& PV, TV* V, double alpha, double beta, double target,
-                               int mlen, double* x, cudaStream_t s, int* jd) {
+                               int mlen, double* x, cudaStream_t s, int* jd, int cyc) {
   const int64_t N = c->N;
   GmresDev* G = reinterpret_cast<GmresDev*>(c->gdev);
   GmresDev* Gh = reinterpret_cast<GmresDev*>(c->gdev_host);
-  const int group = 6;  // iterations enqueued between host checks
+  // iterations enqueued between host checks: the first group as long as the last converged cycle
+  // (iterations after convergence still launch and return at once), then groups of `group`
+  const int group = 6, later = 3;
+  int dummy = 0;
+  int& hint = cyc >= 0 && cyc < 4 ? c->gm_hint[TRANS ? 1 : 0][cyc] : dummy;
   cudaError_t err = cudaSuccess;
   *jd = 0;
+  kry_warm<TV>();  // the occupancy queries run here, not inside a graph capture
   Gh->g[0] = beta;
   Gh->beta = beta;
   Gh->inv_norm = 1.0 / beta;
@@ -1324,8 +1467,9 @@ static cudaError_t gmres_cycle(sap_ctx* c, const OpParams<TV>& PV, TV* V, double
     return err;
   scale_dev_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(V, V, &G->inv_norm, N, nullptr);
   ++g_launches;
-  for (int j0 = 0; j0 < mlen; j0 += group) {
-    const int cnt = std::min(group, mlen - j0);
+  for (int j0 = 0; j0 < mlen;) {
+    const int want = j0 == 0 ? (hint > 0 ? hint : group) : (hint > 0 ? later : group);
+    const int cnt = std::min(want, mlen - j0);
     cudaGraphExec_t ex = arnoldi_graph<TV, TRANS>(c, PV, V, alpha, j0, cnt);
     if (ex) {
       err = cudaGraphLaunch(ex, s);
@@ -1335,9 +1479,12 @@ static cudaError_t gmres_cycle(sap_ctx* c, const OpParams<TV>& PV, TV* V, double
     }
     if (err != cudaSuccess) return err;
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
+    j0 += cnt;
     if (Gh->done) break;
   }
   const int jdone = Gh->jdone;
+  // a cycle that converged before its length sets the next first group
+  if (jdone > 0 && jdone < mlen) hint = std::min(jdone, KRY_MAXV - 1);
   cudaMemcpyAsync(Gh->H, G->H, sizeof(double) * KRY_MAXV * (KRY_MAXV + 1), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(Gh->g, G->g, sizeof(double) * (KRY_MAXV + 1), cudaMemcpyDeviceToHost, s);
   if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
@@ -1350,7 +1497,8 @@ static cudaError_t gmres_cycle(sap_ctx* c, const OpParams<TV>& PV, TV* V, double
   for (int i2 = 0; i2 < jdone; ++i2) Gh->h2[i2] = y[i2];
   if ((err = cudaMemcpyAsync(G->h2, Gh->h2, sizeof(double) * jdone, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return err;
-  combine_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, G->h2, x, N);
+  if constexpr (sizeof(TV) == 4) combine_df_kernel<<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, G->h2, x, N);
+  else combine_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, G->h2, x, N);
   ++g_launches;
   *jd = jdone;
   return cudaGetLastError();
@@ -1431,10 +1579,10 @@ static sap_status cn_steps_t(sap_ctx* c, double* state, double dt, double theta,
       continue;
     }
     if (!std::isfinite(bnorm)) rel = bnorm;  // reported as not converged below
-    while (!(rel <= tol) && its < maxit && std::isfinite(rel)) {
+    for (int cyc = 0; !(rel <= tol) && its < maxit && std::isfinite(rel); ++cyc) {
       const double target = f64 ? 0.5 * beta * (tol / rel) : beta * std::max(0.5 * tol / rel, 1e-6);
       int jd = 0;
-      CK((gmres_cycle<TV, false>(c, PV, V, alpha, beta, target, std::min(m, maxit - its), state, s, &jd)));
+      CK((gmres_cycle<TV, false>(c, PV, V, alpha, beta, target, std::min(m, maxit - its), state, s, &jd, cyc)));
       its += jd;
       // true residual r = b - A zeta and its Jacobi-scaled copy (start of a further cycle)
       {
@@ -2434,7 +2582,7 @@ sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, doubl
     if (bnorm == 0.0) {
       CK(cudaMemsetAsync(mu, 0, sizeof(double) * N, s));
     } else {
-      for (;;) {
+      for (int cyc = 0;; ++cyc) {
         {  // r = b - A^T mu and its Jacobi-scaled copy in V_0
           Epi<double> e{};
           e.out = tmp; e.bvec = b; e.wb = 1.0; e.ax = -1.0; e.bl = -half; e.outj = V; e.cj = half;
@@ -2448,7 +2596,7 @@ sap_status adjoint_cn_step(sap_ctx* c, const double* zp, const double* zn, doubl
         if (rel <= tol || its >= maxit || !std::isfinite(rel)) break;
         int jd = 0;
         CK((gmres_cycle<double, true>(c, P, V, half, beta, 0.5 * beta * (tol / rel), std::min(m, maxit - its), mu, s,
-                                      &jd)));
+                                      &jd, cyc)));
         its += jd;
         if (jd == 0) break;
       }

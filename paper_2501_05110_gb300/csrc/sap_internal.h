@@ -219,6 +219,10 @@ struct sap_ctx {
   const double* cn_prev_ptr = nullptr;
   double cn_prev_dt = 0.0, cn_prev_theta = 0.5;
   bool cn_prev_valid = false;
+  // Arnoldi iterations of the last converged GMRES cycle with the same position in its solve (first,
+  // second, ... cycle; forward and transposed operator): the size of the first group of iterations
+  // enqueued for the next such cycle (0: fixed groups)
+  int gm_hint[2][4] = {};
   std::vector<double> bank_nnz;                // nnz per bank matrix (cost model)
   double pslot_cell_frac = 1.0;                // spatial cells with a tabulated |beta^p| point (cost model)
   double sf_zero_frac32[sap::SF_NCOMP] = {};        // spatial cells where a field component is 0 in FP32 (cost model)
