@@ -40,16 +40,16 @@ UNIT = "DoF-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e-3  # SMs x DFMA/clk/SM x 2 flop x max GHz = 1.2586 TFLOP/s (FP64)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3  # SMs x FFMA/clk/SM x 2 flop x max GHz = 80.5 TFLOP/s (FP32)
 HBM_FALLBACK_GBS = 6800.0
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture, valid only for the
-# kernel source it was taken on (first 16 hex of sha256 of csrc/apply_rows.cu); see profiles/
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one apply launch, keyed by (workload, precision,
-# sha256 prefix of the kernel source at capture): the shock at full size; the 48^3 box from a 32^3
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one apply launch), valid only for the sources it was
+# taken on: keyed by (workload, precision, apply_sha of the kernel source and the epilogue header at
+# capture); see profiles/.  The shock at full size; the 48^3 box from a 32^3
 # capture scaled by the cell ratio 3.375 (traffic grows with the cells; the rule on capture sizes keeps
 # the 48^3 case out of ncu)
-APPLY_TRAFFIC = {("shock", "fp64", "db4fdc5e07bd34b9"): 26137856.0,
-                 ("shock", "fp32", "db4fdc5e07bd34b9"): 13666560.0,
-                 ("box3d", "fp32", "a7df1f11032ab442"): 225672704.0 * 3.375,
-                 ("box3d", "fp64", "a7df1f11032ab442"): 492894208.0 * 3.375}
+APPLY_TRAFFIC = {("shock", "fp64", "7fc8fc6b12e2d515"): 26139392.0,
+                 ("shock", "fp32", "7fc8fc6b12e2d515"): 13666560.0,
+                 ("box3d", "fp32", "780e84dad4872f24"): 225314560.0 * 3.375,
+                 ("box3d", "fp64", "780e84dad4872f24"): 492046848.0 * 3.375}
 
 
 def parse():
@@ -129,10 +129,14 @@ def probe_alu(local):
 
 
 def apply_sha(source="apply_rows.cu"):
-    """First 16 hex digits of the sha256 of the kernel source an ncu traffic figure was taken from."""
+    """First 16 hex digits of the sha256 of the kernel source an ncu traffic figure was taken from,
+    followed by the shared epilogue header it includes."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2501_05110_gb300", "csrc", source), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in (source, "kernels_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2501_05110_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 # ------------------------------------------------------------------------------------------------

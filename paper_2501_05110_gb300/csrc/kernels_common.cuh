@@ -52,6 +52,7 @@ struct Epi {
   T* outj;              // optional: out2 (or out when out2 is null) / (1 + cj * diag(R - div beta))
   T axpost;             // added after the Jacobi scaling: out += axpost * x
   const int* skip;      // when non-null and *skip != 0 the launch does nothing
+  const double* xs;     // when non-null, out (only) is multiplied by *xs: the apply of the vector *xs * x
   // ERK stage (k = s - Lx):  acc += bdt k ; ynext = y0 + adt k ; final: state = acc + bdt k
   double* acc;
   const double* y0;
@@ -131,6 +132,7 @@ __device__ __forceinline__ void epi_write(const Epi<T>& E, size_t dof, T f, T ac
   }
   if (E.jacobi) o *= jacobi_scale(E.cj, rdiag);
   if (E.axpost != T(0)) o += E.axpost * f;
+  if (E.xs) o *= T(*E.xs);
   if (E.out) E.out[dof] = o;
 }
 

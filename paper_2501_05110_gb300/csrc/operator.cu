@@ -550,6 +550,7 @@ __device__ __forceinline__ void applyT_body(const OpParams<T>& P, const T* __res
   }
   if (E.jacobi) o *= jacobi_scale(E.cj, rdiag);
   if (E.axpost != T(0)) o += E.axpost * F[t];
+  if (E.xs) o *= T(*E.xs);
   if (E.out) E.out[dof] = o;
 }
 
@@ -834,6 +835,7 @@ struct GmresDev {
   double H[KRY_MAXV * (KRY_MAXV + 1)];  // H[i * KRY_MAXV + j]
   double g[KRY_MAXV + 1], cs[KRY_MAXV], sn[KRY_MAXV];
   double h1[KRY_MAXV + 1], h2[KRY_MAXV + 1];
+  double vs[KRY_MAXV + 1];  // the basis is stored unnormalised: v_i = vs[i] * V_i
   double nrm, inv_norm, target, beta;
   double misc[8];
   int done, reorth, jdone, m;
@@ -861,6 +863,7 @@ __device__ void gmres_finalize_column(GmresDev* G, int j) {
   G->g[j + 1] = -G->sn[j] * G->g[j];
   G->g[j] = G->cs[j] * G->g[j];
   G->inv_norm = hn > 0 ? 1.0 / hn : 0.0;
+  G->vs[j + 1] = G->inv_norm;  // V_{j+1} holds the orthogonalised w, of norm hn
   G->jdone = j + 1;
   if (fabs(G->g[j + 1]) <= G->target || hn == 0.0 || j + 1 >= G->m) G->done = 1;
 }
@@ -1098,7 +1101,8 @@ __global__ void __launch_bounds__(LB_THREADS) multidot_lb_kernel(const TV* __res
                                                                  const TV* __restrict__ w, int64_t N, int64_t per,
                                                                  int with_ww, double* __restrict__ partial,
                                                                  unsigned int* counter, double* out,
-                                                                 const int* done, const int* need) {
+                                                                 const double* vs, const int* done,
+                                                                 const int* need) {
   if (kry_skip(done, need)) return;
   constexpr int NW = LB_THREADS / 32;
   constexpr int NQ = (KRY_MAXV + NW - 1) / NW;  // basis vectors per warp
@@ -1186,7 +1190,7 @@ __global__ void __launch_bounds__(LB_THREADS) multidot_lb_kernel(const TV* __res
     }
     for (; c < nb; c += 32) v0 += __ldcg(partial + (size_t)i * nb + c);
     const double v = warp_sum(v0 + v1);
-    if (lane == 0) out[i] = v;
+    if (lane == 0) out[i] = vs && i < m ? vs[i] * v : v;
   }
   if (threadIdx.x == 0) *counter = 0u;
 }
@@ -1205,7 +1209,7 @@ __global__ void __launch_bounds__(LB_THREADS) update_lb_kernel(const TV* __restr
   __shared__ double red[LB_THREADS / 32];
   __shared__ unsigned int ticket;
   const double* h = pass == 1 ? G->h1 : G->h2;
-  if (threadIdx.x < m) hs[threadIdx.x] = h[threadIdx.x];
+  if (threadIdx.x < m) hs[threadIdx.x] = h[threadIdx.x] * G->vs[threadIdx.x];  // w -= sum h_i v_i
   __syncthreads();
   const int64_t k0 = (int64_t)blockIdx.x * per;  // the block's range [k0, k0 + len)
   const int len = (int)((N - k0) < per ? (N - k0) : per);
@@ -1303,10 +1307,11 @@ __global__ void __launch_bounds__(LB_THREADS) update_lb_kernel(const TV* __restr
 // the multi-dot of w with m basis vectors (+ w.w) over one wave of blocks
 template <typename TV>
 static void launch_multidot(const TV* V, int64_t ldv, int m, const TV* w, int64_t N, int with_ww, double* partial,
-                            unsigned int* counter, double* out, const int* done, const int* need, cudaStream_t s) {
+                            unsigned int* counter, double* out, const double* vs, const int* done, const int* need,
+                            cudaStream_t s) {
   const KryShape sh = kry_shape(N, 64, kry_wave(multidot_lb_kernel<TV>, sizeof(TV) == 8 ? 0 : 1));
   multidot_lb_kernel<TV><<<sh.grid, LB_THREADS, 0, s>>>(V, ldv, m, w, N, sh.per * 64, with_ww, partial, counter, out,
-                                                         done, need);
+                                                         vs, done, need);
 }
 
 // w -= V h (pass 1 or 2) over one wave of blocks, ranges in multiples of 64 entries
@@ -1324,14 +1329,19 @@ static void kry_warm() {
   kry_wave(update_lb_kernel<TV>, sizeof(TV) == 8 ? 2 : 3);
 }
 
-// y = x * (*s); called in place (y == x), so x and y are not restrict-qualified
-template <typename TV>
-__global__ void scale_dev_kernel(const TV* x, TV* y, const double* s, int64_t N,
-                                 const int* done) {
-  if (done && *done) return;
-  const double a = *s;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-    y[k] = TV(a * double(x[k]));
+// y = R^-1 g by back substitution over the jdone columns of the rotated Hessenberg matrix, then the
+// combination coefficients y_i vs_i of the stored (unnormalised) basis vectors, into h2 (one thread:
+// at most KRY_MAXV unknowns)
+__global__ void gmres_solve_kernel(GmresDev* G) {
+  if (threadIdx.x != 0) return;
+  const int jd = G->jdone;
+  double* y = G->h2;
+  for (int i = jd - 1; i >= 0; --i) {
+    double v = G->g[i];
+    for (int k = i + 1; k < jd; ++k) v -= G->H[i * KRY_MAXV + k] * y[k];
+    y[i] = v / G->H[i * KRY_MAXV + i];
+  }
+  for (int i = 0; i < jd; ++i) y[i] *= G->vs[i];  // x += sum y_i v_i = sum (y_i vs_i) V_i
 }
 
 size_t gmres_control_bytes() { return sizeof(GmresDev); }
@@ -1350,7 +1360,7 @@ template <typename TV>
 static void norm2_dev(sap_ctx* c, const TV* v, int slot, cudaStream_t s) {
   const int64_t N = c->N;
   GmresDev* G = reinterpret_cast<GmresDev*>(c->gdev);
-  launch_multidot<TV>(nullptr, N, 0, v, N, 1, c->small, &G->counter, &G->misc[slot], nullptr, nullptr, s);
+  launch_multidot<TV>(nullptr, N, 0, v, N, 1, c->small, &G->counter, &G->misc[slot], nullptr, nullptr, nullptr, s);
   ++g_launches;
 }
 
@@ -1377,16 +1387,16 @@ static cudaError_t enqueue_arnoldi(sap_ctx* c, const OpParams<TV>& PV, TV* V, do
     Epi<TV> e{};
     e.out = w; e.ax = TV(1); e.bl = TV(half); e.jacobi = 1; e.cj = TV(half); e.skip = &G->done;
     e.axpost = TV(-1);
+    e.xs = &G->vs[j];  // the apply of v_j = vs[j] V_j
     cudaError_t e1;
     if constexpr (TRANS) e1 = launch_applyT<TV>(PV, V + (size_t)j * N, e, cs);
     else e1 = launch_apply<TV>(PV, V + (size_t)j * N, e, cs);
     if (e1 != cudaSuccess) return e1;
-    launch_multidot<TV>(V, N, j + 1, w, N, 1, partial, &G->counter, G->h1, &G->done, nullptr, cs);
+    launch_multidot<TV>(V, N, j + 1, w, N, 1, partial, &G->counter, G->h1, G->vs, &G->done, nullptr, cs);
     launch_update<TV>(V, N, j, w, partial, G, 1, cs);
-    launch_multidot<TV>(V, N, j + 1, w, N, 0, partial, &G->counter, G->h2, &G->done, &G->reorth, cs);
+    launch_multidot<TV>(V, N, j + 1, w, N, 0, partial, &G->counter, G->h2, G->vs, &G->done, &G->reorth, cs);
     launch_update<TV>(V, N, j, w, partial, G, 2, cs);
-    scale_dev_kernel<TV><<<1024, KRY_THREADS, 0, cs>>>(w, w, &G->inv_norm, N, &G->done);
-    g_launches += 5;
+    g_launches += 4;
   }
   cudaMemcpyAsync(&Gh->done, &G->done, sizeof(int) * 4, cudaMemcpyDeviceToHost, cs);
   return cudaGetLastError();
@@ -1454,6 +1464,7 @@ static cudaError_t gmres_cycle(sap_ctx* c, const OpParams<TV>& PV, TV* V, double
   Gh->g[0] = beta;
   Gh->beta = beta;
   Gh->inv_norm = 1.0 / beta;
+  Gh->vs[0] = 1.0 / beta;  // V_0 = P^-1 r stays as it is: v_0 = V_0 / beta
   Gh->target = target;
   Gh->done = 0;
   Gh->reorth = 0;
@@ -1465,15 +1476,15 @@ static cudaError_t gmres_cycle(sap_ctx* c, const OpParams<TV>& PV, TV* V, double
     return err;
   if ((err = cudaMemcpyAsync(&G->done, &Gh->done, sizeof(int) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return err;
-  scale_dev_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(V, V, &G->inv_norm, N, nullptr);
-  ++g_launches;
+  if ((err = cudaMemcpyAsync(&G->vs[0], &Gh->vs[0], sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return err;
   for (int j0 = 0; j0 < mlen;) {
     const int want = j0 == 0 ? (hint > 0 ? hint : group) : (hint > 0 ? later : group);
     const int cnt = std::min(want, mlen - j0);
     cudaGraphExec_t ex = arnoldi_graph<TV, TRANS>(c, PV, V, alpha, j0, cnt);
     if (ex) {
       err = cudaGraphLaunch(ex, s);
-      g_launches += 6 * cnt;
+      g_launches += 5 * cnt;
     } else {
       err = enqueue_arnoldi<TV, TRANS>(c, PV, V, alpha, j0, cnt, s);
     }
@@ -1485,18 +1496,9 @@ static cudaError_t gmres_cycle(sap_ctx* c, const OpParams<TV>& PV, TV* V, double
   const int jdone = Gh->jdone;
   // a cycle that converged before its length sets the next first group
   if (jdone > 0 && jdone < mlen) hint = std::min(jdone, KRY_MAXV - 1);
-  cudaMemcpyAsync(Gh->H, G->H, sizeof(double) * KRY_MAXV * (KRY_MAXV + 1), cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(Gh->g, G->g, sizeof(double) * (KRY_MAXV + 1), cudaMemcpyDeviceToHost, s);
-  if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
-  double y[KRY_MAXV];
-  for (int i2 = jdone - 1; i2 >= 0; --i2) {
-    double v = Gh->g[i2];
-    for (int k2 = i2 + 1; k2 < jdone; ++k2) v -= Gh->H[i2 * KRY_MAXV + k2] * y[k2];
-    y[i2] = v / Gh->H[i2 * KRY_MAXV + i2];
-  }
-  for (int i2 = 0; i2 < jdone; ++i2) Gh->h2[i2] = y[i2];
-  if ((err = cudaMemcpyAsync(G->h2, Gh->h2, sizeof(double) * jdone, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return err;
+  // y = R^-1 g on the device (no copy of H to the host and back), then x += V y
+  gmres_solve_kernel<<<1, 32, 0, s>>>(G);
+  ++g_launches;
   if constexpr (sizeof(TV) == 4) combine_df_kernel<<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, G->h2, x, N);
   else combine_kernel<TV><<<1024, KRY_THREADS, 0, s>>>(V, N, jdone, G->h2, x, N);
   ++g_launches;
