@@ -918,6 +918,45 @@ __device__ __forceinline__ double dot_chunk_df(const float* __restrict__ a, cons
   return ((double(s0) + double(c0)) + (double(s1) + double(c1))) + ((double(s2) + double(c2)) + (double(s3) + double(c3)));
 }
 
+// V_i . w over one chunk by one warp, FP32 vectors with a and ws 16-byte aligned: four 16-byte loads
+// per lane in flight (sixteen entries), the same four compensated sums as dot_chunk_df
+__device__ __forceinline__ double dot_chunk_df4(const float* __restrict__ a, const float* ws, int len, int lane) {
+  float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f, s2 = 0.0f, c2 = 0.0f, s3 = 0.0f, c3 = 0.0f;
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* w4 = reinterpret_cast<const float4*>(ws);
+  const int nq = len >> 2;
+  int q = lane;
+  for (; q + 96 < nq; q += 128) {
+    const float4 x0 = __ldg(a4 + q), x1 = __ldg(a4 + q + 32), x2 = __ldg(a4 + q + 64), x3 = __ldg(a4 + q + 96);
+    const float4 y0 = w4[q], y1 = w4[q + 32], y2 = w4[q + 64], y3 = w4[q + 96];
+    df_fma(s0, c0, x0.x, y0.x);
+    df_fma(s1, c1, x0.y, y0.y);
+    df_fma(s2, c2, x0.z, y0.z);
+    df_fma(s3, c3, x0.w, y0.w);
+    df_fma(s0, c0, x1.x, y1.x);
+    df_fma(s1, c1, x1.y, y1.y);
+    df_fma(s2, c2, x1.z, y1.z);
+    df_fma(s3, c3, x1.w, y1.w);
+    df_fma(s0, c0, x2.x, y2.x);
+    df_fma(s1, c1, x2.y, y2.y);
+    df_fma(s2, c2, x2.z, y2.z);
+    df_fma(s3, c3, x2.w, y2.w);
+    df_fma(s0, c0, x3.x, y3.x);
+    df_fma(s1, c1, x3.y, y3.y);
+    df_fma(s2, c2, x3.z, y3.z);
+    df_fma(s3, c3, x3.w, y3.w);
+  }
+  for (; q < nq; q += 32) {
+    const float4 x = __ldg(a4 + q), y = w4[q];
+    df_fma(s0, c0, x.x, y.x);
+    df_fma(s1, c1, x.y, y.y);
+    df_fma(s2, c2, x.z, y.z);
+    df_fma(s3, c3, x.w, y.w);
+  }
+  for (int k = 4 * nq + lane; k < len; k += 32) df_fma(s0, c0, __ldg(a + k), ws[k]);
+  return ((double(s0) + double(c0)) + (double(s1) + double(c1))) + ((double(s2) + double(c2)) + (double(s3) + double(c3)));
+}
+
 // w . w over one chunk by one warp, double-float sums
 __device__ __forceinline__ double dot_self_df(const float* ws, int len, int lane) {
   float s = 0.0f, c = 0.0f;
@@ -1089,9 +1128,10 @@ static int kry_wave(K kernel, int slot) {
 }
 
 // dots of w with V_0..V_{m-1} (+ w.w): block b takes the range [b per, (b+1) per) (per a multiple of 64,
-// so V_i + k0 stays 16-byte aligned when ldv is even), staged through shared memory in equal
-// sub-chunks of at most KRY_CHUNK entries.  One basis vector per warp, streamed with four paired loads
-// per lane in flight, its partial sum kept per lane across the sub-chunks; w.w is summed by every
+// so V_i + k0 stays 16-byte aligned when ldv is even for FP64, a multiple of 4 for FP32), staged
+// through shared memory in equal sub-chunks of at most KRY_CHUNK entries.  One basis vector per warp,
+// streamed with four 16-byte loads per lane in flight, its partial sum kept per lane across the
+// sub-chunks; w.w is summed by every
 // thread while it stages w.  The last block sums the blocks' partials in block order.  out[i] for
 // i < m is the dot with V_i, out[m] (with_ww) is w.w.  (Measured on 2^20 entries against a variant
 // that keeps all basis vectors' sums per lane over 16-byte units: as fast up to 8 vectors, faster
@@ -1115,12 +1155,13 @@ __global__ void __launch_bounds__(LB_THREADS) multidot_lb_kernel(const TV* __res
   const int64_t sub = ((per + nsub - 1) / nsub + 63) / 64 * 64;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool pairs = ((ldv & 1) == 0);
+  const bool quads = ((ldv & 3) == 0);  // FP32: V_i + k0 16-byte aligned (k0 is a multiple of 64)
   double acc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
   double ww = 0.0;
   if constexpr (sizeof(TV) == 4) {
-    __shared__ float wsf[KRY_CHUNK];
+    __shared__ __align__(16) float wsf[KRY_CHUNK];
     float ss = 0.0f, sc = 0.0f;
     for (int64_t k0 = beg; k0 < end; k0 += sub) {
       const int len = (int)(end - k0 < sub ? end - k0 : sub);
@@ -1134,7 +1175,9 @@ __global__ void __launch_bounds__(LB_THREADS) multidot_lb_kernel(const TV* __res
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
         const int i = warp + q * NW;
-        if (i < m) acc[q] += dot_chunk_df(V + i * ldv + k0, wsf, len, lane, pairs);
+        if (i < m)
+          acc[q] += quads ? dot_chunk_df4(V + i * ldv + k0, wsf, len, lane)
+                          : dot_chunk_df(V + i * ldv + k0, wsf, len, lane, pairs);
       }
     }
     ww = double(ss) + double(sc);
