@@ -789,7 +789,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// The Krylov kernels work on chunks of KRY_CHUNK entries, one thread block per chunk.
+// The batched Krylov kernels work on chunks of KRY_CHUNK entries, one thread block per chunk; the
+// single-problem passes take one wave of blocks and stage their ranges in sub-chunks of at most
+// KRY_CHUNK entries.  The partial-sum scratch holds one slot per chunk.
 constexpr int KRY_CHUNK = 2048;
 
 // x (FP64) += sum_i y[i] V_i
